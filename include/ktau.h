@@ -1,0 +1,200 @@
+/*
+ * ktau.h -- C ABI of the GB300 all-pairs Kendall tau-b library (libktau.so).
+ *
+ * Method: Liu, Pan, Green, Aluru, "Parallelized Kendall's Tau Coefficient Computation via
+ * SIMD Vectorized Sorting On Many-Integrated-Core Processors" (arXiv 1704.03767).
+ *   - tau-b definition: Sec. 1, Eq. 3 and Table 1 (n_0, n_1, n_2, n_3).
+ *   - per-variable rank transform done once: Sec. 3 (opening paragraph).
+ *   - Knight counting with exact tie handling: Sec. 3.2, Steps 1-5 and Algorithm 2.
+ *   - sign form of the concordance count (naive kernel): Sec. 3.1, Algorithm 1.
+ *   - job-id <-> (y, x) bijection and tiling of the upper triangle: Sec. 4.1-4.2, Eq. 4-14.
+ *   - result sub-ranges processed pass by pass: Sec. 4.3.1.
+ *   - query-based co-expression search (motivation for the query form): Sec. 1.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a ktau_status; nothing throws across the ABI. On failure
+ *     ktau_last_error() returns a thread-local, human-readable message for the calling thread.
+ *   - "device pointer" means memory of the current CUDA device, allocated by the caller
+ *     (cudaMalloc, a torch tensor's data_ptr(), ...). The library never frees caller memory.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *     enqueued on it asynchronously unless a function says it synchronises.
+ *   - A matrix of m variables by n samples is row-major: variable i occupies
+ *     values[i*ld .. i*ld + n), with ld >= n (elements, not bytes).
+ *   - Pairs are the strict upper triangle of the m x m job matrix: pair (i, j) with i < j has the
+ *     packed index p = i*(2m-i-1)/2 + (j-i-1), i.e. rows are numbered left-to-right,
+ *     top-to-bottom as in the paper's Eq. 4-5 applied to the (m-1) x (m-1) triangle that
+ *     excludes the diagonal. u = variable i, v = variable j. All outputs are symmetric in (u, v).
+ *   - Counts per pair: S = n_c - n_d and n_3 (joint ties). The per-variable tie counts
+ *     n_1 (of u) and n_2 (of v) are T[i] and T[j] from ktau_tie_counts().
+ *   - tau-b = (double)S / sqrt((double)(n_0-T_u) * (double)(n_0-T_v)) in IEEE FP64
+ *     (round-to-nearest sqrt and divide); NaN when either factor is 0 (a constant variable).
+ *     The FP32 output is the FP64 value rounded to nearest-even.
+ *   - Limits: 2 <= n <= KTAU_MAX_N, 2 <= m <= KTAU_MAX_M. Values may be +-Inf; -0.0 equals +0.0;
+ *     a NaN anywhere fails the call with KTAU_ENAN.
+ */
+#ifndef KTAU_H
+#define KTAU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KTAU_ABI_VERSION 1
+#define KTAU_MAX_N 16384      /* samples per variable (ranks are stored as uint16) */
+#define KTAU_MAX_M 4194304    /* variables per matrix */
+
+typedef enum {
+  KTAU_OK = 0,
+  KTAU_EINVAL = 1,     /* bad argument: NULL where required, sizes out of range, mismatch */
+  KTAU_ENAN = 2,       /* a NaN value was found in the input */
+  KTAU_ETOOLARGE = 3,  /* n > KTAU_MAX_N, m > KTAU_MAX_M, or a count does not fit count_bits */
+  KTAU_ENOMEM = 4,     /* a device allocation made by the library failed */
+  KTAU_ECUDA = 5,      /* a CUDA runtime call failed; ktau_last_error() has the CUDA message */
+  KTAU_ETIMEOUT = 6,   /* a bounded device-side wait gave up (reported through a status word) */
+  KTAU_EBUSY = 7       /* the object is in use by a captured graph or another call */
+} ktau_status;
+
+typedef enum { KTAU_F32 = 0, KTAU_I32 = 1 } ktau_dtype;
+
+/* Which pairwise kernel computes the counts. */
+typedef enum {
+  KTAU_PATH_AUTO = 0,      /* pick by shape and measured timings (autotuner table) */
+  KTAU_PATH_MERGE = 1,     /* Knight merge-sort swap counting, Sec. 3.2 Steps 1-5 */
+  KTAU_PATH_SIGNGEMM = 2   /* exact sign-matrix contraction on tensor cores, Sec. 3.1 Alg. 1 */
+} ktau_path;
+
+/* Tuning knobs; any field left 0 means "library default / autotuned". */
+typedef struct {
+  int32_t path;         /* ktau_path */
+  int32_t tile_q;       /* variables per side of a square tile of the job matrix (Sec. 4.2 q) */
+  int32_t mapping;      /* merge path: 1 = one warp per pair, 2 = one CTA per pair */
+  int32_t schedule;     /* 1 = static stride over tile ids (Sec. 4.3.2), 2 = dynamic counter */
+  int32_t ctas_per_sm;  /* persistent grid = ctas_per_sm * SM count */
+  int32_t reserved[3];
+} ktau_options;
+
+/* Opaque, library-owned, device-resident ranked matrix (Sec. 3: each variable ranked once):
+ * stable sort permutation, dense ranks, per-variable tie counts, and (lazily) the sign
+ * expansion used by the tensor-core path. */
+typedef struct ktau_ranked ktau_ranked;
+
+/* Thread-local message describing the last failure of this thread (never NULL). */
+const char* ktau_last_error(void);
+/* Static name of a status code. */
+const char* ktau_status_string(ktau_status s);
+/* KTAU_ABI_VERSION of the loaded library. */
+int32_t ktau_abi_version(void);
+
+/*
+ * ktau_rank_prepare -- rank transform of every variable (Sec. 3, opening paragraph; the scans
+ * of Steps 2 and 4 for n_1 and n_2 are hoisted here because they depend on one variable only).
+ *   values : caller-owned device pointer, m x n row-major with row stride ld (elements),
+ *            dtype dt (KTAU_F32 or KTAU_I32). Read only; may be freed once the call returns.
+ *   out    : receives a new handle owned by the caller; release with ktau_ranked_free().
+ * Per variable u the handle holds the stable argsort pi_u (ties keep sample order), the dense
+ * rank r_u (equal values share a rank, -0.0 == +0.0), and T_u = sum over tie groups t(t-1)/2.
+ * Synchronises `stream` once (to read the NaN flag). On any error no handle is returned.
+ * Errors: EINVAL (NULL, m < 2, n < 2, ld < n, bad dtype), ETOOLARGE, ENAN, ENOMEM, ECUDA.
+ */
+ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int64_t n, int64_t ld,
+                              void* stream, ktau_ranked** out);
+
+/* Releases a handle (NULL is accepted). Synchronises the device before freeing. */
+ktau_status ktau_ranked_free(ktau_ranked* R);
+
+/* Shape of a handle (either output pointer may be NULL). Host only, no synchronisation. */
+ktau_status ktau_ranked_shape(const ktau_ranked* R, int64_t* m, int64_t* n);
+
+/* Copies T_u (n_1 / n_2 of Table 1) for every variable into the caller's device buffer
+ * T_dev[m] (int64). Asynchronous on `stream`. */
+ktau_status ktau_tie_counts(const ktau_ranked* R, int64_t* T_dev, void* stream);
+
+/* Copies the permutation pi (perm[m*n]) and dense ranks r (rank[m*n]) into caller device
+ * buffers, packed m x n (uint16). Either pointer may be NULL. Asynchronous on `stream`. */
+ktau_status ktau_ranked_export(const ktau_ranked* R, uint16_t* perm, uint16_t* rank, void* stream);
+
+/*
+ * ktau_allpairs -- exact tau-b for every pair with packed index in [p_begin, p_end)
+ * (Sec. 4.1-4.3: the upper triangle walked through the job-id bijection, tile by tile, in
+ * result sub-ranges so the output of one pass fits the caller's buffers).
+ *   [p_begin, p_end) : subrange of [0, m(m-1)/2); empty ranges are accepted and do nothing.
+ *   tau64, tau32, S, n3 : caller-owned device buffers of p_end - p_begin elements, element k
+ *            for pair p_begin + k. Any of them may be NULL (that output is not stored).
+ *            S and n3 are int32 when count_bits == 32, int64 when count_bits == 64.
+ *   count_bits : 32 or 64. 32 requires n_0 = n(n-1)/2 < 2^31, else ETOOLARGE.
+ *   opt    : NULL or options (path, tile, mapping, schedule); NULL = autotuned.
+ * Asynchronous on `stream`; the handle must stay alive until the work completes.
+ * The first tensor-core call on a handle allocates and fills its sign expansion (library
+ * memory, m * n_0 bytes rounded up) and is therefore not graph-capturable.
+ * Errors: EINVAL (NULL handle, range outside the triangle, bad count_bits/options), ETOOLARGE,
+ * ENOMEM, ECUDA.
+ */
+ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end, double* tau64,
+                          float* tau32, void* S, void* n3, int32_t count_bits,
+                          const ktau_options* opt, void* stream);
+
+/*
+ * Batched form: many independent matrices of uneven m and n processed by one persistent
+ * launch per kernel family (generalises the pass/tile scheduling of Sec. 4.2-4.3 to a list of
+ * datasets). A plan owns all scratch; ktau_batch_run allocates nothing and never synchronises,
+ * so it can be captured into a CUDA graph (ktau_batch_graph_launch does that itself).
+ */
+typedef struct {
+  const void* values;  /* device, m x n row-major, row stride ld, dtype */
+  int32_t dtype;       /* ktau_dtype */
+  int32_t count_bits;  /* 32 or 64, as in ktau_allpairs */
+  int64_t m, n, ld;
+  double* tau64;       /* m(m-1)/2 outputs each, any may be NULL */
+  float* tau32;
+  void* S;
+  void* n3;
+} ktau_batch_desc;
+
+typedef struct ktau_batch ktau_batch;
+
+/* Validates the descriptors (host-side only; the contents of `values` are read at run time),
+ * chooses a path per dataset (opt->path, or the autotuner table when AUTO), allocates device
+ * scratch and descriptor tables. The descriptors are copied; the pointed-to buffers must stay
+ * valid for the plan's lifetime. Errors: EINVAL, ETOOLARGE, ENOMEM, ECUDA. */
+ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t count, const ktau_options* opt,
+                              ktau_batch** out);
+/* Enqueues rank transform + all pairs of every dataset on `stream` (no allocation, no sync). */
+ktau_status ktau_batch_run(ktau_batch* B, void* stream);
+/* Same work through a CUDA graph captured on first use (on `stream`) and replayed after. */
+ktau_status ktau_batch_graph_launch(ktau_batch* B, void* stream);
+/* Synchronises `stream` and reports a NaN found in any dataset since the last check (ENAN). */
+ktau_status ktau_batch_check(ktau_batch* B, void* stream);
+/* Number of datasets routed to each path (either pointer may be NULL). */
+ktau_status ktau_batch_paths(const ktau_batch* B, int32_t* n_merge, int32_t* n_signgemm);
+/* Total pairs over all datasets. */
+ktau_status ktau_batch_pairs(const ktau_batch* B, uint64_t* pairs);
+ktau_status ktau_batch_free(ktau_batch* B);
+
+/*
+ * ktau_query -- query-based search (Sec. 1): exact tau-b of every query profile against every
+ * database variable, plus the k database rows with the largest |tau-b| per query.
+ *   db      : ranked database (m_db x n). queries: ranked queries (b x n, same n, else EINVAL).
+ *   tau     : device FP64 [b][m_db] or NULL.  S, n3: device [b][m_db] of count_bits, or NULL.
+ *   k       : 0 <= k <= min(m_db, 1024). topk_idx (int32 [b][k]) and topk_tau (FP64 [b][k]) are
+ *             required when k > 0. Order: |tau| descending by exact rational comparison of
+ *             S^2/(D_u D_v); equal values by smaller row index; NaN (constant rows) last.
+ *   opt     : as for ktau_allpairs (path choice). The database's sign expansion, when the
+ *             tensor-core path is chosen, is built on first use and kept in the handle.
+ * Asynchronous on `stream`. Errors: EINVAL, ETOOLARGE, ENOMEM, ECUDA.
+ */
+ktau_status ktau_query(const ktau_ranked* db, const ktau_ranked* queries, double* tau, void* S,
+                       void* n3, int32_t count_bits, int32_t k, int32_t* topk_idx, double* topk_tau,
+                       const ktau_options* opt, void* stream);
+
+/* Device memory (bytes) that ktau_query needs beyond its outputs for b queries against db;
+ * used by servers to admit work by free memory. */
+ktau_status ktau_query_scratch_bytes(const ktau_ranked* db, int64_t b, int32_t k, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KTAU_H */

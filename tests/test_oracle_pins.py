@@ -1,0 +1,178 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+* hand-worked counts (tests/golden/hand_worked.txt, counted pair by pair from Sec. 1 / Table 1)
+* scipy.stats.kendalltau (tau-b), an independent library implementation of Eq. 3
+* identities: tau(u,u) = 1 and tau(u, reverse u) = -1 without ties; symmetry (Sec. 1: the
+  computation is commutable); tau-a = tau-b without ties (Sec. 1, after Eq. 3)
+* brute force: the O(n^2) definition and the O(n log n) Knight counter (Sec. 3.2) agree on
+  every pair of vectors over small alphabets (exhaustive)
+* the Step 5 identity n_c - n_d = n_0 - n_1 - n_2 + n_3 - 2 n_d on definition-level counts
+* rank transform against numpy's stable argsort and np.unique
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_worked.txt")
+
+
+def _golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        u, v, c, t = [p.strip() for p in line.split("|")]
+        rows.append(
+            (
+                np.array([float(x) for x in u.split()]),
+                np.array([float(x) for x in v.split()]),
+                [int(x) for x in c.split()],
+                float(t),
+            )
+        )
+    return rows
+
+
+@pytest.mark.parametrize("method", ["definition", "knight"])
+def test_hand_worked(oracle_mod, method):
+    rows = _golden_rows()
+    assert len(rows) >= 8
+    for u, v, (nc, nd, n1, n2, n3, S), tau in rows:
+        c = oracle_mod.pair_counts(u, v, method)
+        assert (c["nc"], c["nd"], c["n1"], c["n2"], c["n3"], c["S"]) == (nc, nd, n1, n2, n3, S), (
+            u, v, c)
+        t = oracle_mod.tau_b(c["S"], c["n1"], c["n2"], len(u))
+        if math.isnan(tau):
+            assert math.isnan(t)
+        else:
+            assert abs(t - tau) <= 1e-15 * max(1.0, abs(tau)), (t, tau)
+
+
+def test_scipy_tau_b(oracle_mod):
+    stats = pytest.importorskip("scipy.stats")
+    g = np.random.default_rng(11)
+    for trial in range(300):
+        n = int(g.integers(2, 60))
+        levels = int(g.integers(2, 12)) if trial % 2 else 1000
+        u = g.integers(0, levels, n).astype(float)
+        v = g.integers(0, levels, n).astype(float)
+        if trial % 5 == 0:
+            v = u + g.integers(-1, 2, n)
+        c = oracle_mod.pair_counts(u, v, "knight")
+        t = oracle_mod.tau_b(c["S"], c["n1"], c["n2"], n)
+        ref = stats.kendalltau(u, v).statistic
+        if math.isnan(ref):
+            assert math.isnan(t)
+        else:
+            assert abs(t - ref) <= 1e-12 * max(1.0, abs(ref)), (u, v, t, ref)
+
+
+def test_identities(oracle_mod):
+    g = np.random.default_rng(5)
+    for n in (2, 3, 17, 128, 257):
+        u = g.permutation(n).astype(float) + 0.5
+        for method in ("definition", "knight"):
+            c = oracle_mod.pair_counts(u, u, method)
+            assert c["S"] == n * (n - 1) // 2 and c["nd"] == 0
+            assert oracle_mod.tau_b(c["S"], c["n1"], c["n2"], n) == 1.0
+            # reversing the order of the values (v = -u) gives the exact anti-order
+            c = oracle_mod.pair_counts(u, -u, method)
+            assert c["S"] == -(n * (n - 1) // 2) and c["nc"] == 0
+            assert oracle_mod.tau_b(c["S"], c["n1"], c["n2"], n) == -1.0
+        us = np.sort(u)
+        for method in ("definition", "knight"):
+            c = oracle_mod.pair_counts(us, us[::-1].copy(), method)
+            assert c["S"] == -(n * (n - 1) // 2) and c["nc"] == 0
+            assert oracle_mod.tau_b(c["S"], c["n1"], c["n2"], n) == -1.0
+
+
+def test_symmetry_and_tau_a(oracle_mod):
+    g = np.random.default_rng(7)
+    for trial in range(200):
+        n = int(g.integers(2, 80))
+        u = g.integers(0, 6 if trial % 2 else 10**6, n).astype(float)
+        v = g.integers(0, 6 if trial % 3 else 10**6, n).astype(float)
+        a = oracle_mod.pair_counts(u, v, "knight")
+        b = oracle_mod.pair_counts(v, u, "knight")
+        assert (a["S"], a["n3"], a["n1"], a["n2"]) == (b["S"], b["n3"], b["n2"], b["n1"])
+        ta = oracle_mod.tau_b(a["S"], a["n1"], a["n2"], n)
+        tb = oracle_mod.tau_b(b["S"], b["n1"], b["n2"], n)
+        assert (math.isnan(ta) and math.isnan(tb)) or ta == tb
+        if a["n1"] == 0 and a["n2"] == 0:
+            n0 = n * (n - 1) // 2
+            assert abs(ta - a["S"] / n0) <= 1e-15
+            assert a["nc"] + a["nd"] == n0
+
+
+def test_brute_force_exhaustive(oracle_mod):
+    """Definition and Knight agree on every (u, v) over a 3-letter alphabet, n = 1..5."""
+    for n in range(1, 6):
+        vecs = [np.array(t, float) for t in itertools.product(range(3), repeat=n)]
+        for u in vecs:
+            for v in vecs[:: max(1, len(vecs) // 40)]:
+                a = oracle_mod.pair_counts(u, v, "definition")
+                b = oracle_mod.pair_counts(u, v, "knight")
+                assert a == b, (u, v, a, b)
+
+
+def test_brute_force_random(oracle_mod):
+    g = np.random.default_rng(3)
+    for trial in range(300):
+        n = int(g.integers(2, 300))
+        lv = [2, 3, 8, 64, 10**9][trial % 5]
+        u = g.integers(0, lv, n).astype(float)
+        v = g.integers(0, [2, 5, 64, 10**9][trial % 4], n).astype(float)
+        a = oracle_mod.pair_counts(u, v, "definition")
+        b = oracle_mod.pair_counts(u, v, "knight")
+        assert a == b
+        n0 = n * (n - 1) // 2
+        # Step 5 (Sec. 3.2) on definition-level counts
+        assert a["nc"] - a["nd"] == n0 - a["n1"] - a["n2"] + a["n3"] - 2 * a["nd"]
+
+
+def test_rank_transform(oracle_mod):
+    g = np.random.default_rng(9)
+    for trial in range(100):
+        n = int(g.integers(1, 500))
+        x = g.integers(0, [3, 50, 10**9][trial % 3], n).astype(float)
+        if trial % 7 == 0:
+            x[g.integers(0, n)] = -0.0
+            x[g.integers(0, n)] = 0.0
+        perm, rk, T = oracle_mod.rank(x)
+        assert np.array_equal(perm, np.argsort(x, kind="stable"))
+        uniq, inv, cnt = np.unique(x, return_inverse=True, return_counts=True)
+        assert np.array_equal(rk, inv)
+        assert T == int((cnt * (cnt - 1) // 2).sum())
+
+
+def test_allpairs_matches_pairs(oracle_mod):
+    g = np.random.default_rng(1)
+    m, n = 21, 33
+    X = g.integers(0, 7, (m, n)).astype(float)
+    ref = []
+    for i in range(m):
+        for j in range(i + 1, m):
+            ref.append(oracle_mod.pair_counts(X[i], X[j], "definition"))
+    P = m * (m - 1) // 2
+    for method, q, threads in (("knight", 8, 1), ("knight", 3, 4), ("definition", 5, 3)):
+        out = oracle_mod.allpairs(X, method=method, q=q, threads=threads)
+        assert [int(s) for s in out["S"]] == [r["S"] for r in ref]
+        assert [int(s) for s in out["n3"]] == [r["n3"] for r in ref]
+    # sub-ranges (Sec. 4.3.1 passes) concatenate to the full result
+    full = oracle_mod.allpairs(X)
+    cuts = [0, 1, 50, 51, 199, P]
+    parts = [oracle_mod.allpairs(X, p_begin=a, p_end=b)["S"] for a, b in zip(cuts, cuts[1:])]
+    assert np.array_equal(np.concatenate(parts), full["S"])
+
+
+def test_topk_order(oracle_mod):
+    # exact ordering by |tau| with index tie-break, NaN last
+    S = [3, -3, 0, 5, 3, -5]
+    Dv = [10, 10, 10, 0, 9, 25]
+    # |tau|^2 * Du = S^2/Dv: 0.9, 0.9, 0, nan, 1.0, 1.0
+    assert oracle_mod.topk_order(S, 7, Dv, 6) == [4, 5, 0, 1, 2, 3]
+    assert oracle_mod.topk_order(S, 0, Dv, 3) == [0, 1, 2]
