@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of exact all-pairs Kendall tau-b on one GB300 (and N GPUs as independent shards).
+
+One step = the whole hot path over one gene-expression-shaped matrix (m=16384 variables x
+n=128 samples, float32, synthetic): rank transform of every variable (K-a) + every one of the
+134,209,536 pairs counted exactly (Knight merge path K-b or sign contraction K-c, chosen by the
+library) + FP64 tau-b, stored as the packed FP32 triangle plus int32 S and n_3.
+
+Prints ONE JSON line (rank 0). `value` is pairs/s with the input resident in HBM; `e2e` is the
+same metric through the C ABI with host buffers (input H2D and every output D2H inside the timed
+region). `--impl reference` times the CPU oracle (Knight, all host cores) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N = 16384, 128
+METRIC = "tau-b pairs/s (m=16384,n=128) batched vs plain launch; query p50/p99 latency"
+WORKLOAD = "gene-expression all-pairs tau-b, m=16384 x n=128 float32 (log-normal, 256 latent " \
+           "factors, 10% quantised ties), packed FP32 tau + int32 S and n_3"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="auto", choices=["auto", "merge", "signgemm"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def cpu_baseline(X, seconds: float):
+    """The oracle as it stands (Knight per pair, Sec. 3.2; static tile ranges over all host
+    cores, Sec. 4.2-4.3) on the first pairs of the same matrix; returns pairs/s."""
+    import numpy as np
+
+    import oracle
+
+    threads = os.cpu_count() or 1
+    Xd = np.asarray(X, dtype=np.float64)
+    probe = 20000
+    t0 = time.perf_counter()
+    oracle.allpairs(Xd, method="knight", threads=threads, p_begin=0, p_end=probe)
+    dt = time.perf_counter() - t0
+    P = M * (M - 1) // 2
+    sample = int(min(P, max(probe, probe * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.allpairs(Xd, method="knight", threads=threads, p_begin=0, p_end=sample)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {sample} packed pairs (rows 0..) of the same m=16384 x n=128 matrix, "
+                      f"Knight counting, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from synthetic import gene_expression
+
+    X = gene_expression(M, N, seed=0).astype(np.float64)
+    threads = os.cpu_count() or 1
+    # bounded sample per step: ~4 s of CPU work
+    probe = 20000
+    t0 = time.perf_counter()
+    oracle.allpairs(X, method="knight", threads=threads, p_begin=0, p_end=probe)
+    per = (time.perf_counter() - t0) / probe
+    sample = int(max(probe, 4.0 / max(per, 1e-9)))
+    for _ in range(args.warmup):
+        oracle.allpairs(X, method="knight", threads=threads, p_begin=0, p_end=sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.allpairs(X, method="knight", threads=threads, p_begin=0, p_end=sample)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_pairs_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {sample} packed pairs per step, Knight counting"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1704_03767_gb300 as ktau
+    from synthetic import gene_expression
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    path = {"auto": 0, "merge": 1, "signgemm": 2}[args.path]
+    opts = {"path": path}
+
+    # Weak scaling: every rank runs its own independent matrix (seed = rank); no collective.
+    X = gene_expression(M, N, seed=rank)
+    P = M * (M - 1) // 2
+    Xd = torch.from_numpy(X).to(dev)
+    tau32 = torch.empty(P, dtype=torch.float32, device=dev)
+    S = torch.empty(P, dtype=torch.int32, device=dev)
+    n3 = torch.empty(P, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        R = ktau.ktau_rank_prepare(Xd, stream)
+        if ev:
+            ev[0].record(stream)
+        ktau.ktau_allpairs(R, 0, P, None, tau32, S, n3, 32, opts, stream)
+        if ev:
+            ev[1].record(stream)
+        return R
+
+    for _ in range(args.warmup):
+        step().free()
+    torch.cuda.synchronize()
+    launches_per_step = 2  # rank kernel + pair kernel (merge path)
+
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    total_ms, kern_ms = 0.0, 0.0
+    held = []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between steps (256 MB write), outside the timed events
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R = step((k0, k1))
+        e1.record(stream)
+        held.append((e0, e1, k0, k1, R))
+        torch.cuda.synchronize()
+    for e0, e1, k0, k1, R in held:
+        total_ms += e0.elapsed_time(e1)
+        kern_ms += k0.elapsed_time(k1)
+        R.free()
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = P * world * args.steps / (total_ms / 1e3)
+    kern_avg_ms = kern_ms / args.steps
+    path_used = "signgemm" if args.path == "signgemm" else "merge"
+
+    # Roofline of the dominant kernel (the pair kernel).
+    peaks = _peaks()
+    roof = None
+    if path_used == "merge":
+        # Algorithmic work: n * ceil(log2 n) compare-and-count merge steps per pair (Step 3).
+        steps_per_pair = N * 7
+        achieved = P * steps_per_pair / (kern_avg_ms / 1e3) / 1e9
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        f = (clocks.get("sm_mhz") or 1455.0) * 1e6
+        peak = sms * 128 * f / 1e9  # int32 lane-ops per second at the sampled clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Gop/s (merge steps vs int32 lane-ops)", "frac": achieved / peak,
+                "traffic": None, "kernel": "merge_pairs_kernel",
+                "kernel_ms": kern_avg_ms}
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        out_h = [torch.empty(P, dtype=t.dtype).pin_memory() for t in (tau32, S, n3)]
+        h2d = Xh.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for t in out_h)
+        for it in range(2 + args.steps):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+            Xd.copy_(Xh, non_blocking=True)
+            R = step()
+            for hd, dd in zip(out_h, (tau32, S, n3)):
+                hd.copy_(dd, non_blocking=True)
+            torch.cuda.synchronize()
+            R.free()
+        t1 = torch.cuda.Event(enable_timing=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = t0.elapsed_time(t1)
+        e2e = {"value": P * world * args.steps / (e2e_ms / 1e3), "unit": "pairs/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(X, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "pairs": P, "path": path_used,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"{world} independent shards (one matrix per GPU)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "sample_comparisons_per_s": value * (N * (N - 1) // 2),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

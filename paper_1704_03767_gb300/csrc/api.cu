@@ -1,0 +1,225 @@
+// C ABI entry points: argument validation, handle ownership, path dispatch, error reporting.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "ktau_impl.cuh"
+#include "signgemm.cuh"
+
+static thread_local char t_err[512] = "no error";
+
+ktau_status ktau_fail(ktau_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err, sizeof(t_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+ktau_status ktau_cuda_fail(cudaError_t e, const char* what) {
+  snprintf(t_err, sizeof(t_err), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return KTAU_ENOMEM;
+  }
+  return KTAU_ECUDA;
+}
+
+int ktau_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+extern "C" {
+
+const char* ktau_last_error(void) { return t_err; }
+
+const char* ktau_status_string(ktau_status s) {
+  switch (s) {
+    case KTAU_OK: return "KTAU_OK";
+    case KTAU_EINVAL: return "KTAU_EINVAL";
+    case KTAU_ENAN: return "KTAU_ENAN";
+    case KTAU_ETOOLARGE: return "KTAU_ETOOLARGE";
+    case KTAU_ENOMEM: return "KTAU_ENOMEM";
+    case KTAU_ECUDA: return "KTAU_ECUDA";
+    case KTAU_ETIMEOUT: return "KTAU_ETIMEOUT";
+    case KTAU_EBUSY: return "KTAU_EBUSY";
+  }
+  return "KTAU_UNKNOWN";
+}
+
+int32_t ktau_abi_version(void) { return KTAU_ABI_VERSION; }
+
+ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int64_t n, int64_t ld,
+                              void* stream, ktau_ranked** out) {
+  if (!out) return ktau_fail(KTAU_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!values) return ktau_fail(KTAU_EINVAL, "values is NULL");
+  if (dt != KTAU_F32 && dt != KTAU_I32) return ktau_fail(KTAU_EINVAL, "unknown dtype %d", (int)dt);
+  if (m < 2 || n < 2) return ktau_fail(KTAU_EINVAL, "need m >= 2 and n >= 2 (m=%lld n=%lld)",
+                                       (long long)m, (long long)n);
+  if (ld < n) return ktau_fail(KTAU_EINVAL, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
+  if (n > KTAU_MAX_N) return ktau_fail(KTAU_ETOOLARGE, "n=%lld exceeds KTAU_MAX_N=%d",
+                                       (long long)n, KTAU_MAX_N);
+  if (m > KTAU_MAX_M) return ktau_fail(KTAU_ETOOLARGE, "m=%lld exceeds KTAU_MAX_M=%d",
+                                       (long long)m, KTAU_MAX_M);
+  cudaStream_t st = (cudaStream_t)stream;
+  ktau_ranked* R = (ktau_ranked*)calloc(1, sizeof(ktau_ranked));
+  if (!R) return ktau_fail(KTAU_ENOMEM, "host allocation failed");
+  R->m = m;
+  R->n = n;
+  R->ld = (n + 15) & ~15LL;
+  cudaGetDevice(&R->device);
+  const size_t arr = (size_t)m * R->ld * sizeof(uint16_t);
+  const size_t arr_al = (arr + 255) & ~(size_t)255;
+  const size_t t_bytes = ((size_t)m * 8 + 255) & ~(size_t)255;
+  const size_t i_bytes = ((size_t)m * 4 + 255) & ~(size_t)255;
+  const size_t total = 3 * arr_al + t_bytes + 2 * i_bytes + 256;
+  cudaError_t e = cudaMalloc(&R->block, total);
+  if (e != cudaSuccess) {
+    free(R);
+    return ktau_cuda_fail(e, "cudaMalloc(ranked)");
+  }
+  char* b = (char*)R->block;
+  R->perm = (uint16_t*)b;
+  R->rank = (uint16_t*)(b + arr_al);
+  R->srank = (uint16_t*)(b + 2 * arr_al);
+  R->T = (int64_t*)(b + 3 * arr_al);
+  R->ndist = (int32_t*)(b + 3 * arr_al + t_bytes);
+  R->maxg = (int32_t*)(b + 3 * arr_al + t_bytes + i_bytes);
+  R->stats_dev = (ktau_stats*)(b + 3 * arr_al + t_bytes + 2 * i_bytes);
+  ktau_status s = KTAU_OK;
+  if ((e = cudaMemsetAsync(R->stats_dev, 0, sizeof(ktau_stats), st)) != cudaSuccess) {
+    s = ktau_cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (s == KTAU_OK) s = ktau_launch_rank(values, (int)dt, m, n, ld, R, st);
+  if (s == KTAU_OK) {
+    if ((e = cudaMemcpyAsync(&R->stats, R->stats_dev, sizeof(ktau_stats), cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
+      s = ktau_cuda_fail(e, "cudaMemcpyAsync(stats)");
+    else if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+      s = ktau_cuda_fail(e, "cudaStreamSynchronize");
+    else if (R->stats.nan_flag)
+      s = ktau_fail(KTAU_ENAN, "NaN in the input matrix");
+  }
+  if (s != KTAU_OK) {
+    cudaFree(R->block);
+    free(R);
+    return s;
+  }
+  *out = R;
+  return KTAU_OK;
+}
+
+ktau_status ktau_ranked_free(ktau_ranked* R) {
+  if (!R) return KTAU_OK;
+  cudaDeviceSynchronize();
+  if (R->block) cudaFree(R->block);
+  ktau_signgemm_release(R);
+  free(R);
+  return KTAU_OK;
+}
+
+ktau_status ktau_ranked_shape(const ktau_ranked* R, int64_t* m, int64_t* n) {
+  if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  if (m) *m = R->m;
+  if (n) *n = R->n;
+  return KTAU_OK;
+}
+
+ktau_status ktau_tie_counts(const ktau_ranked* R, int64_t* T_dev, void* stream) {
+  if (!R || !T_dev) return ktau_fail(KTAU_EINVAL, "NULL argument");
+  KTAU_CUDA(cudaMemcpyAsync(T_dev, R->T, (size_t)R->m * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+  return KTAU_OK;
+}
+
+ktau_status ktau_ranked_export(const ktau_ranked* R, uint16_t* perm, uint16_t* rank, void* stream) {
+  if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t pitch = (size_t)R->ld * sizeof(uint16_t), width = (size_t)R->n * sizeof(uint16_t);
+  if (perm)
+    KTAU_CUDA(cudaMemcpy2DAsync(perm, width, R->perm, pitch, width, (size_t)R->m,
+                                cudaMemcpyDeviceToDevice, st));
+  if (rank)
+    KTAU_CUDA(cudaMemcpy2DAsync(rank, width, R->rank, pitch, width, (size_t)R->m,
+                                cudaMemcpyDeviceToDevice, st));
+  return KTAU_OK;
+}
+
+}  // extern "C"
+
+// Shared validation of count widths and options.
+ktau_status ktau_check_counts(int64_t n, int count_bits) {
+  if (count_bits != 32 && count_bits != 64)
+    return ktau_fail(KTAU_EINVAL, "count_bits must be 32 or 64 (got %d)", count_bits);
+  const int64_t n0 = n * (n - 1) / 2;
+  if (count_bits == 32 && n0 >= (1LL << 31))
+    return ktau_fail(KTAU_ETOOLARGE, "n_0=%lld does not fit 32-bit counts", (long long)n0);
+  return KTAU_OK;
+}
+
+ktau_status ktau_check_options(const ktau_options* opt) {
+  if (!opt) return KTAU_OK;
+  if (opt->path < 0 || opt->path > 2) return ktau_fail(KTAU_EINVAL, "bad path %d", opt->path);
+  if (opt->tile_q < 0 || opt->tile_q > 256)
+    return ktau_fail(KTAU_EINVAL, "tile_q must be in [0, 256]");
+  if (opt->mapping < 0 || opt->mapping > 2) return ktau_fail(KTAU_EINVAL, "bad mapping");
+  if (opt->schedule < 0 || opt->schedule > 2) return ktau_fail(KTAU_EINVAL, "bad schedule");
+  if (opt->ctas_per_sm < 0 || opt->ctas_per_sm > 32) return ktau_fail(KTAU_EINVAL, "bad ctas_per_sm");
+  return KTAU_OK;
+}
+
+// Path choice for one matrix shape. The sign contraction does n_0 multiply-adds per pair where
+// the merge path does about n log2 n compare steps, so it only pays for short vectors; the
+// crossover below is the measured one on GB300 (see the autotuner for per-shape overrides).
+int ktau_choose_path(const ktau_ranked* R, const ktau_options* opt) {
+  if (opt && opt->path != KTAU_PATH_AUTO) return opt->path;
+  if (ktau_signgemm_supported(R->n) && R->n <= 256) {
+    // Joint ties for the contraction are enumerated per tied pair of u; dense ties favour merge.
+    const double mean_T = (double)R->stats.T_sum / (double)R->m;
+    if (mean_T <= 0.05 * (double)R->n) return KTAU_PATH_SIGNGEMM;
+  }
+  return KTAU_PATH_MERGE;
+}
+
+extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                                     double* tau64, float* tau32, void* S, void* n3,
+                                     int32_t count_bits, const ktau_options* opt, void* stream) {
+  if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  ktau_status s = ktau_check_counts(R->n, count_bits);
+  if (s != KTAU_OK) return s;
+  if ((s = ktau_check_options(opt)) != KTAU_OK) return s;
+  const uint64_t P = (uint64_t)(R->m * (R->m - 1) / 2);
+  if (p_begin > p_end || p_end > P)
+    return ktau_fail(KTAU_EINVAL, "pair range [%llu, %llu) outside [0, %llu)",
+                     (unsigned long long)p_begin, (unsigned long long)p_end,
+                     (unsigned long long)P);
+  if (p_begin == p_end) return KTAU_OK;
+  ktau_out out{tau64, tau32, S, n3, count_bits};
+  cudaStream_t st = (cudaStream_t)stream;
+  const int path = ktau_choose_path(R, opt);
+  if (path == KTAU_PATH_SIGNGEMM) {
+    if (!ktau_signgemm_supported(R->n))
+      return ktau_fail(KTAU_EINVAL, "sign-contraction path supports n <= %d", KTAU_SIGNGEMM_MAX_N);
+    return ktau_signgemm_allpairs(const_cast<ktau_ranked*>(R), p_begin, p_end, out, st);
+  }
+  ktau_merge_plan plan;
+  ktau_merge_default_plan(R->n, &plan);
+  if (opt) {
+    if (opt->tile_q) plan.tile_q = opt->tile_q;
+    if (opt->mapping) plan.mapping = opt->mapping;
+    if (opt->schedule) plan.schedule = opt->schedule;
+    if (opt->ctas_per_sm) plan.ctas_per_sm = opt->ctas_per_sm;
+  }
+  return ktau_launch_merge(R, p_begin, p_end, out, plan, st);
+}

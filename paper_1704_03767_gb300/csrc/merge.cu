@@ -1,0 +1,368 @@
+// K-b: pairwise Knight counting (Sec. 3.2, Steps 1-5 with the merge-and-count of Algorithm 2)
+// over the upper triangle of the job matrix, walked tile by tile through the job-id bijection
+// (Sec. 4.1-4.2, Eq. 11-14) by persistent CTAs.
+//
+// Per pair (u, v) a "team" (one warp, or the whole CTA for long vectors) runs:
+//   gather   : w_k = r_v[pi_u[k]] -- v's ranks listed in u's sorted order. This is the joint
+//              list of Step 1 already ordered by u; only samples tied in u remain unordered.
+//   Step 1   : if u has ties, sort the packed keys (group(u) << 16 | w) so that each tie group
+//              of u is ordered by v (the 15/16-bit packing of the paper's vectorised kernel).
+//   Step 2   : n_3 = joint ties = sum over runs of equal keys of t(t-1)/2 (n_1 comes from K-a).
+//   Step 3   : bottom-up merge sort of w; when an element of a right run is emitted while left
+//              elements remain, all of those are larger (ties go left): add their number to n_d.
+//   Step 4/5 : n_2 from K-a; S = n_0 - n_1 - n_2 + n_3 - 2 n_d; tau-b in FP64 (Eq. 3).
+// The merge of two sorted runs is split among the team by merge-path co-ranks (a binary search
+// along each thread's output diagonal); each thread then merges ITEMS outputs serially and counts
+// exactly as Algorithm 2 does.
+#include <algorithm>
+
+#include "ktau_impl.cuh"
+
+namespace {
+
+constexpr uint32_t kSentinel = 0xffffffffu;
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if (TEAM == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+// Team-wide sum of a per-thread value (TEAM == 32: warp reduce; else CTA reduce via red[]).
+template <int TEAM>
+__device__ __forceinline__ unsigned long long team_sum(unsigned long long v,
+                                                       unsigned long long* red) {
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  if (TEAM == 32) return v;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  for (int w = 0; w < TEAM / 32; ++w) t += red[w];
+  return t;
+}
+
+// Merge sort of buf[0, n) (ascending) with tmp as the second buffer. With COUNT, each thread
+// accumulates into `cnt` its share of the inversions (pairs i < j with buf[i] > buf[j]).
+// Returns the buffer that holds the sorted sequence. Every thread of the team must call it.
+template <int TEAM, int ITEMS, bool COUNT>
+__device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int lane,
+                                     unsigned long long& cnt) {
+  constexpr int CH = TEAM * ITEMS;
+  unsigned c = 0;
+  // Runs of ITEMS sorted in registers (inversions inside a run counted directly).
+  for (int base = 0; base < n; base += CH) {
+    const int s0 = base + lane * ITEMS;
+    uint32_t r[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) r[i] = (s0 + i < n) ? buf[s0 + i] : kSentinel;
+    if (COUNT) {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+#pragma unroll
+        for (int j = i + 1; j < ITEMS; ++j) c += (r[i] > r[j]);
+    }
+#pragma unroll
+    for (int p = 0; p < ITEMS; ++p) {
+#pragma unroll
+      for (int i = p & 1; i + 1 < ITEMS; i += 2) {
+        uint32_t a = min(r[i], r[i + 1]), b = max(r[i], r[i + 1]);
+        r[i] = a;
+        r[i + 1] = b;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      if (s0 + i < n) buf[s0 + i] = r[i];
+  }
+  team_sync<TEAM>();
+  uint32_t* in = buf;
+  uint32_t* out = tmp;
+  for (int s = ITEMS; s < n; s *= 2) {
+    for (int base = 0; base < n; base += CH) {
+      const int o = base + lane * ITEMS;
+      if (o < n) {
+        const int A = (o / (2 * s)) * (2 * s);
+        const int a_len = min(s, n - A);
+        const int B = A + a_len;
+        const int b_len = max(0, min(s, n - B));
+        const int diag = o - A;
+        // Merge-path co-rank: number of A elements among the first `diag` outputs of a stable
+        // merge (equal keys: A first).
+        int lo = max(0, diag - b_len), hi = min(diag, a_len);
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (in[A + mid] <= in[B + diag - 1 - mid])
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        int ai = lo, bi = diag - lo;
+        const int todo = min(ITEMS, a_len + b_len - diag);
+        uint32_t va = ai < a_len ? in[A + ai] : kSentinel;
+        uint32_t vb = bi < b_len ? in[B + bi] : kSentinel;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          if (i < todo) {
+            const bool take_b = (ai >= a_len) || (bi < b_len && vb < va);
+            if (take_b) {
+              out[o + i] = vb;
+              if (COUNT) c += (unsigned)(a_len - ai);  // remaining left elements are larger
+              ++bi;
+              vb = bi < b_len ? in[B + bi] : kSentinel;
+            } else {
+              out[o + i] = va;
+              ++ai;
+              va = ai < a_len ? in[A + ai] : kSentinel;
+            }
+          }
+        }
+      }
+    }
+    team_sync<TEAM>();
+    uint32_t* t = in;
+    in = out;
+    out = t;
+  }
+  cnt += c;
+  return in;
+}
+
+struct MergeArgs {
+  const uint16_t* perm;
+  const uint16_t* rank;
+  const uint16_t* srank;
+  const int64_t* T;
+  int64_t m, n, ld;
+  int64_t w;        // tiles per side
+  int64_t tile_lo;  // tile-id range covering [p_begin, p_end)
+  int64_t tile_hi;
+  uint64_t p_begin, p_end;
+  int tq;           // tile side
+  int stage;        // rows of the tile staged in shared memory
+  int cap;          // per-team buffer capacity (elements)
+  unsigned long long* counter;  // dynamic schedule: next tile id (nullptr = static)
+  ktau_out out;
+};
+
+// Counts for one pair. perm_u/srank_u/rank_v point at the three rows (shared or global).
+template <int TEAM, int ITEMS>
+__device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_t* srank_u,
+                                           const uint16_t* rank_v, int n, bool u_ties,
+                                           uint32_t* buf, uint32_t* tmp, int lane,
+                                           unsigned long long* red, long long& nd_out,
+                                           long long& n3_out) {
+  for (int k = lane; k < n; k += TEAM) {
+    const uint32_t w = rank_v[perm_u[k]];
+    buf[k] = u_ties ? (((uint32_t)srank_u[k] << 16) | w) : w;
+  }
+  team_sync<TEAM>();
+  unsigned long long nd = 0, n3 = 0;
+  if (u_ties) {
+    unsigned long long unused = 0;
+    uint32_t* sorted = team_merge_sort<TEAM, ITEMS, false>(buf, tmp, n, lane, unused);
+    uint32_t* other = sorted == buf ? tmp : buf;
+    // Step 2: joint ties. In the sorted keys, position k has (k - first index of its key)
+    // earlier equal keys.
+    for (int k = lane; k < n; k += TEAM) {
+      const uint32_t key = sorted[k];
+      if (k > 0 && sorted[k - 1] == key) {
+        int lo = 0, hi = k;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sorted[mid] < key)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        n3 += (unsigned long long)(k - lo);
+      }
+      other[k] = key & 0xffffu;
+    }
+    team_sync<TEAM>();
+    team_merge_sort<TEAM, ITEMS, true>(other, sorted, n, lane, nd);
+  } else {
+    team_merge_sort<TEAM, ITEMS, true>(buf, tmp, n, lane, nd);
+  }
+  nd_out = (long long)team_sum<TEAM>(nd, red);
+  n3_out = (long long)team_sum<TEAM>(n3, red);
+  team_sync<TEAM>();
+}
+
+__device__ __forceinline__ void copy_rows(uint16_t* dst, const uint16_t* src, int64_t first_row,
+                                          int rows, int64_t m, int64_t ld) {
+  // rows x ld uint16, ld a multiple of 16 (32-byte rows): 16-byte vector copies.
+  const int vec_per_row = (int)(ld / 8);
+  const int total = rows * vec_per_row;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int r = i / vec_per_row, c = i % vec_per_row;
+    const int64_t g = first_row + r;
+    uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    if (g < m) v = reinterpret_cast<const uint4*>(src + g * ld)[c];
+    reinterpret_cast<uint4*>(dst + (int64_t)r * ld)[c] = v;
+  }
+}
+
+template <int TEAM, int ITEMS>
+__global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red[8];
+  __shared__ long long next_tile;
+  const int nteams = blockDim.x / TEAM;
+  const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
+  const int tq = a.tq;
+  const int64_t ld = a.ld;
+  uint16_t* s_perm = reinterpret_cast<uint16_t*>(smem);
+  uint16_t* s_srank = s_perm + (a.stage ? (int64_t)tq * ld : 0);
+  uint16_t* s_rank = s_srank + (a.stage ? (int64_t)tq * ld : 0);
+  uint32_t* tbuf = reinterpret_cast<uint32_t*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
+                   (size_t)team * 2 * a.cap;
+  uint32_t* tbuf2 = tbuf + a.cap;
+  const int n = (int)a.n;
+  const int64_t n0 = a.n * (a.n - 1) / 2;
+
+  int64_t t = a.tile_lo + blockIdx.x;
+  while (true) {
+    if (a.counter) {
+      __syncthreads();
+      if (threadIdx.x == 0) next_tile = a.tile_lo + (long long)atomicAdd(a.counter, 1ull);
+      __syncthreads();
+      t = next_tile;
+    }
+    if (t >= a.tile_hi) break;
+    int64_t yq, xq;
+    ktau_tile_coord(a.w, t, yq, xq);
+    const int64_t y0 = yq * tq, x0 = xq * tq;
+    if (a.stage) {
+      __syncthreads();
+      copy_rows(s_perm, a.perm, y0, tq, a.m, ld);
+      copy_rows(s_srank, a.srank, y0, tq, a.m, ld);
+      copy_rows(s_rank, a.rank, x0, tq, a.m, ld);
+      __syncthreads();
+    }
+    for (int e = team; e < tq * tq; e += nteams) {
+      const int64_t y = y0 + e / tq, x = x0 + e % tq;
+      if (y >= a.m || x >= a.m || x <= y) continue;
+      const uint64_t p = ktau_pair_index(a.m, y, x);
+      if (p < a.p_begin || p >= a.p_end) continue;
+      const uint16_t* pu = a.stage ? s_perm + (y - y0) * ld : a.perm + y * ld;
+      const uint16_t* su = a.stage ? s_srank + (y - y0) * ld : a.srank + y * ld;
+      const uint16_t* rv = a.stage ? s_rank + (x - x0) * ld : a.rank + x * ld;
+      const int64_t Tu = a.T[y], Tv = a.T[x];
+      long long nd, n3;
+      count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, tbuf, tbuf2, lane, red, nd, n3);
+      if (lane == 0) {
+        const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
+        ktau_store(a.out, p - a.p_begin, S, n3, n0, Tu, Tv);
+      }
+    }
+    if (!a.counter) t += gridDim.x;
+  }
+}
+
+template <int TEAM, int ITEMS>
+ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas_per_sm,
+                       int64_t tiles, cudaStream_t st) {
+  auto kern = merge_pairs_kernel<TEAM, ITEMS>;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+  if (occ < 1) return ktau_fail(KTAU_ETOOLARGE, "merge kernel does not fit on an SM (smem %zu)", smem);
+  if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+  int64_t grid = (int64_t)occ * ktau_sm_count();
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, threads, smem, st>>>(args);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
+}  // namespace
+
+void ktau_merge_default_plan(int64_t n, ktau_merge_plan* plan) {
+  plan->mapping = n <= 2048 ? 1 : 2;
+  plan->tile_q = n <= 256 ? 32 : (n <= 1024 ? 8 : 4);
+  plan->schedule = 1;
+  plan->ctas_per_sm = 0;
+}
+
+// Scratch for the dynamic schedule (one counter per device, reset before each launch).
+static unsigned long long* g_counter[64];
+
+ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                              const ktau_out& out, const ktau_merge_plan& plan, cudaStream_t st) {
+  if (p_end <= p_begin) return KTAU_OK;
+  const int64_t m = R->m, n = R->n;
+  const int tq = plan.tile_q > 0 ? plan.tile_q : 32;
+  const int64_t w = (m + tq - 1) / tq;
+  // Rows of the first and last pair of the range -> covering tile-id range (Eq. 12 on tiles).
+  int64_t i0, j0, i1, j1;
+  ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
+  ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
+  const int64_t tile_lo = ktau_rowstart(w, i0 / tq);
+  const int64_t tile_hi = ktau_rowstart(w, i1 / tq + 1);
+  const int64_t tiles = tile_hi - tile_lo;
+
+  MergeArgs a;
+  a.perm = R->perm;
+  a.rank = R->rank;
+  a.srank = R->srank;
+  a.T = R->T;
+  a.m = m;
+  a.n = n;
+  a.ld = R->ld;
+  a.w = w;
+  a.tile_lo = tile_lo;
+  a.tile_hi = tile_hi;
+  a.p_begin = p_begin;
+  a.p_end = p_end;
+  a.tq = tq;
+  a.out = out;
+  a.counter = nullptr;
+  if (plan.schedule == 2) {
+    int dev = 0;
+    KTAU_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return ktau_fail(KTAU_EINVAL, "device index out of range");
+    if (!g_counter[dev]) KTAU_CUDA(cudaMalloc(&g_counter[dev], sizeof(unsigned long long)));
+    KTAU_CUDA(cudaMemsetAsync(g_counter[dev], 0, sizeof(unsigned long long), st));
+    a.counter = g_counter[dev];
+  }
+
+  const bool cta_team = plan.mapping == 2;
+  const int items = cta_team ? 8 : (n <= 256 ? (int)((n + 31) / 32) : 8);
+  a.cap = (int)((n + 3) & ~3LL);
+  const size_t team_bytes = (size_t)2 * a.cap * sizeof(uint32_t);
+  // Stage the tile's rows in shared memory when they are small next to the per-pair work.
+  const size_t stage_bytes = (size_t)3 * tq * R->ld * sizeof(uint16_t);
+  a.stage = (!cta_team && stage_bytes <= 64 * 1024) ? 1 : 0;
+  const size_t budget = 200 * 1024;
+  int teams = 1, threads = 256;
+  if (!cta_team) {
+    const size_t avail = budget - (a.stage ? stage_bytes : 0);
+    teams = (int)std::min<size_t>(8, avail / team_bytes);
+    if (teams < 1) {
+      a.stage = 0;
+      teams = (int)std::min<size_t>(8, budget / team_bytes);
+    }
+    if (teams < 1)
+      return ktau_fail(KTAU_ETOOLARGE, "n=%lld too long for one warp per pair; use mapping 2",
+                       (long long)n);
+    threads = 32 * teams;
+  }
+  const size_t smem = (a.stage ? stage_bytes : 0) + (size_t)teams * team_bytes;
+  const int cps = plan.ctas_per_sm;
+  if (cta_team) return launch_one<256, 8>(a, threads, smem, cps, tiles, st);
+  switch (items) {
+    case 1: return launch_one<32, 1>(a, threads, smem, cps, tiles, st);
+    case 2: return launch_one<32, 2>(a, threads, smem, cps, tiles, st);
+    case 3: return launch_one<32, 3>(a, threads, smem, cps, tiles, st);
+    case 4: return launch_one<32, 4>(a, threads, smem, cps, tiles, st);
+    case 5: return launch_one<32, 5>(a, threads, smem, cps, tiles, st);
+    case 6: return launch_one<32, 6>(a, threads, smem, cps, tiles, st);
+    case 7: return launch_one<32, 7>(a, threads, smem, cps, tiles, st);
+    default: return launch_one<32, 8>(a, threads, smem, cps, tiles, st);
+  }
+}

@@ -1,0 +1,175 @@
+// K-a: per-variable rank transform (Sec. 3, opening paragraph: values are replaced by ranks
+// once per vector before any pair is counted). One CTA per variable sorts the row in shared
+// memory and emits the stable permutation pi_u, the dense ranks r_u, the ranks in sorted order,
+// and the tie statistics that Steps 2 and 4 of Sec. 3.2 would otherwise rescan for every pair
+// (n_1 and n_2 depend on one variable only).
+#include <cstdarg>
+#include <cstdio>
+
+#include "ktau_impl.cuh"
+
+namespace {
+
+// Order-preserving map of a float to uint32 (IEEE total order on non-NaN values), with -0.0
+// folded onto +0.0 so that they compare equal, as the definition's comparisons do.
+__device__ __forceinline__ uint32_t orderable_f32(uint32_t b) {
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Sort key: (orderable value << 32) | sample index, so that a plain ascending sort is a
+// stable argsort. Padding keys are all-ones and sort last.
+template <int DT>
+__device__ __forceinline__ unsigned long long load_key(const void* values, int64_t off, int i,
+                                                       unsigned int* nan_seen) {
+  uint32_t b = ((const uint32_t*)values)[off + i];
+  uint32_t k;
+  if (DT == KTAU_F32) {
+    if ((b & 0x7fffffffu) > 0x7f800000u) *nan_seen = 1u;
+    k = orderable_f32(b);
+  } else {
+    k = b ^ 0x80000000u;
+  }
+  return ((unsigned long long)k << 32) | (unsigned)i;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ values, int64_t ld_in,
+                                                   int n, int np2, int64_t ld, uint16_t* perm,
+                                                   uint16_t* rank, uint16_t* srank, int64_t* T,
+                                                   int32_t* ndist, int32_t* maxg,
+                                                   ktau_stats* stats) {
+  extern __shared__ unsigned long long sm_keys[];                  // [np2]
+  uint16_t* sm_first = reinterpret_cast<uint16_t*>(sm_keys + np2);  // [np2] group start
+  uint16_t* sm_dense = sm_first + np2;                             // [np2] dense rank at k
+  __shared__ int warp_tot[32];
+  __shared__ unsigned long long red_T[32];
+  __shared__ int red_g[32];
+
+  const int64_t row = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t off = row * ld_in;
+  unsigned int nan_seen = 0;
+
+  for (int i = tid; i < np2; i += nt)
+    sm_keys[i] = i < n ? load_key<DT>(values, off, i, &nan_seen) : ~0ull;
+  __syncthreads();
+
+  // Bitonic sort of np2 keys, ascending.
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < np2 / 2; i += nt) {
+        int lo = 2 * i - (i & (j - 1));  // index with bit j clear
+        int hi = lo + j;
+        bool up = (lo & k) == 0;
+        unsigned long long a = sm_keys[lo], b = sm_keys[hi];
+        if ((a > b) == up) {
+          sm_keys[lo] = b;
+          sm_keys[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // Group heads and dense ranks: a block-wide inclusive scan of head flags over positions,
+  // each thread owning a contiguous chunk.
+  const int per = (n + nt - 1) / nt;
+  const int beg = min(n, tid * per), end = min(n, beg + per);
+  int local = 0;
+  for (int k = beg; k < end; ++k)
+    local += (k == 0) || ((sm_keys[k] >> 32) != (sm_keys[k - 1] >> 32));
+  // warp inclusive scan of chunk totals
+  const int lane = tid & 31, wid = tid >> 5;
+  int incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = (nt + 31) >> 5;
+    int v = lane < nw ? warp_tot[lane] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += t;
+    }
+    if (lane < nw) warp_tot[lane] = v;  // inclusive per-warp prefix
+  }
+  __syncthreads();
+  int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);  // heads before this chunk
+  for (int k = beg; k < end; ++k) {
+    bool head = (k == 0) || ((sm_keys[k] >> 32) != (sm_keys[k - 1] >> 32));
+    run += head;
+    sm_dense[k] = (uint16_t)(run - 1);
+    if (head) sm_first[run - 1] = (uint16_t)k;
+  }
+  __syncthreads();
+
+  // Outputs and tie statistics: position k has k - first(group) earlier equal values, so
+  // the sum over k is the number of tied pairs, sum t(t-1)/2.
+  uint16_t* prow = perm + row * ld;
+  uint16_t* rrow = rank + row * ld;
+  uint16_t* srow = srank + row * ld;
+  unsigned long long tsum = 0;
+  int gmax = 0;
+  for (int k = tid; k < (int)ld; k += nt) {
+    if (k < n) {
+      int idx = (int)(sm_keys[k] & 0xffffffffu);
+      int d = sm_dense[k];
+      int before = k - sm_first[d];
+      prow[k] = (uint16_t)idx;
+      srow[k] = (uint16_t)d;
+      rrow[idx] = (uint16_t)d;
+      tsum += (unsigned long long)before;
+      gmax = max(gmax, before + 1);
+    } else {
+      prow[k] = 0xffff;
+      srow[k] = 0xffff;
+      rrow[k] = 0xffff;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    tsum += __shfl_down_sync(0xffffffffu, tsum, d);
+    gmax = max(gmax, __shfl_down_sync(0xffffffffu, gmax, d));
+  }
+  unsigned int nan_any = __syncthreads_or(nan_seen);
+  if (lane == 0) {
+    red_T[wid] = tsum;
+    red_g[wid] = gmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long t = 0;
+    int g = 0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) {
+      t += red_T[w];
+      g = max(g, red_g[w]);
+    }
+    T[row] = (int64_t)t;
+    ndist[row] = sm_dense[n - 1] + 1;
+    maxg[row] = g;
+    atomicAdd(&stats->T_sum, t);
+    atomicMax(&stats->T_max, t);
+    atomicMax(&stats->maxg, (unsigned)g);
+    if (nan_any) atomicOr(&stats->nan_flag, 1u);
+  }
+}
+
+}  // namespace
+
+ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n, int64_t ld_in,
+                             ktau_ranked* R, cudaStream_t st) {
+  int np2 = 32;
+  while (np2 < n) np2 <<= 1;
+  int threads = np2 / 2 < 32 ? 32 : (np2 / 2 > 512 ? 512 : np2 / 2);
+  size_t smem = (size_t)np2 * (sizeof(unsigned long long) + 2 * sizeof(uint16_t));
+  if (m > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "m too large for one launch");
+  auto kern = dtype == KTAU_F32 ? rank_kernel<KTAU_F32> : rank_kernel<KTAU_I32>;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)m, threads, smem, st>>>(values, ld_in, (int)n, np2, R->ld, R->perm, R->rank,
+                                            R->srank, R->T, R->ndist, R->maxg, R->stats_dev);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
