@@ -136,6 +136,21 @@ ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end
                           float* tau32, void* S, void* n3, int32_t count_bits,
                           const ktau_options* opt, void* stream);
 
+/* Which path ktau_allpairs would take for this handle and options (KTAU_PATH_MERGE or
+ * KTAU_PATH_SIGNGEMM) -- the autotuner's choice when opt is NULL or opt->path is AUTO. */
+ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, int32_t* path);
+
+/* Builds the tensor-core operands of a handle now instead of on first use: the sign expansion
+ * A_u[k] = sign(u_a - u_b) over all sample pairs (Sec. 3.1, Algorithm 1), stored as FP8 e4m3 for
+ * n <= 128 and BF16 above (library memory, m * n_0 elements rounded up), plus per-variable lists of
+ * tied sample pairs for n_3. Synchronises `stream`. EINVAL when n > 1024 (path unsupported). */
+ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
+
+/* Synchronises `stream` and reports whether a bounded device-side wait of a tensor-core kernel
+ * gave up since the last call (KTAU_ETIMEOUT, the results of that launch are invalid), then
+ * clears the flag. KTAU_OK otherwise. */
+ktau_status ktau_device_status(void* stream);
+
 /*
  * Batched form: many independent matrices of uneven m and n processed by one persistent
  * launch per kernel family (generalises the pass/tile scheduling of Sec. 4.2-4.3 to a list of

@@ -20,6 +20,9 @@ from .binding import (  # noqa: F401
     batch_desc,
     declared_symbols,
     ktau_allpairs,
+    ktau_allpairs_path,
+    ktau_device_status,
+    ktau_prepare_signs,
     ktau_query,
     ktau_query_scratch_bytes,
     ktau_rank_prepare,

@@ -58,6 +58,9 @@ _SIGS = {
     "ktau_ranked_export": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "ktau_allpairs": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(Options), _vp],
                       ctypes.c_int),
+    "ktau_allpairs_path": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(_i32)], ctypes.c_int),
+    "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
+    "ktau_device_status": ([_vp], ctypes.c_int),
     "ktau_batch_create": ([ctypes.POINTER(BatchDesc), _i32, ctypes.POINTER(Options),
                            ctypes.POINTER(_vp)], ctypes.c_int),
     "ktau_batch_run": ([_vp, _vp], ctypes.c_int),
@@ -186,6 +189,20 @@ def ktau_allpairs(R: Ranked, p_begin: int = 0, p_end: int | None = None, tau64=N
         p_end = R.pairs
     _check(load().ktau_allpairs(R.handle, p_begin, p_end, _ptr(tau64), _ptr(tau32), _ptr(S),
                                 _ptr(n3), count_bits, _options(options), _stream(stream)))
+
+
+def ktau_allpairs_path(R: Ranked, options=None) -> int:
+    p = ctypes.c_int32()
+    _check(load().ktau_allpairs_path(R.handle, _options(options), ctypes.byref(p)))
+    return p.value
+
+
+def ktau_prepare_signs(R: Ranked, stream=None):
+    _check(load().ktau_prepare_signs(R.handle, _stream(stream)))
+
+
+def ktau_device_status(stream=None):
+    _check(load().ktau_device_status(_stream(stream)))
 
 
 def allpairs(values: torch.Tensor, p_begin: int = 0, p_end: int | None = None,

@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "ktau_impl.cuh"
 #include "signgemm.cuh"
@@ -37,6 +38,60 @@ int ktau_sm_count() {
     cache[dev] = v > 0 ? v : 1;
   }
   return cache[dev];
+}
+
+namespace {
+std::mutex g_alloc_mu;
+struct FreeBlock {
+  int dev;
+  size_t bytes;
+  void* p;
+};
+std::vector<FreeBlock>* g_free_blocks = new std::vector<FreeBlock>();  // never destroyed
+}  // namespace
+
+ktau_status ktau_dmalloc(void** p, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    for (size_t i = 0; i < g_free_blocks->size(); ++i) {
+      FreeBlock& b = (*g_free_blocks)[i];
+      if (b.dev == dev && b.bytes == bytes) {
+        *p = b.p;
+        (*g_free_blocks)[i] = g_free_blocks->back();
+        g_free_blocks->pop_back();
+        return KTAU_OK;
+      }
+    }
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    // Give cached blocks back to the driver and retry once.
+    std::vector<FreeBlock> mine;
+    {
+      std::lock_guard<std::mutex> lk(g_alloc_mu);
+      std::vector<FreeBlock> keep;
+      for (auto& b : *g_free_blocks) (b.dev == dev ? mine : keep).push_back(b);
+      *g_free_blocks = keep;
+    }
+    cudaGetLastError();
+    for (auto& b : mine) cudaFree(b.p);
+    e = cudaMalloc(p, bytes);
+  }
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return ktau_cuda_fail(e, "cudaMalloc");
+  }
+  return KTAU_OK;
+}
+
+void ktau_dfree(void* p, size_t bytes) {
+  if (!p) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_free_blocks->push_back(FreeBlock{dev, bytes, p});
 }
 
 extern "C" {
@@ -83,12 +138,13 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
   const size_t arr_al = (arr + 255) & ~(size_t)255;
   const size_t t_bytes = ((size_t)m * 8 + 255) & ~(size_t)255;
   const size_t i_bytes = ((size_t)m * 4 + 255) & ~(size_t)255;
-  const size_t total = 3 * arr_al + t_bytes + 2 * i_bytes + 256;
-  cudaError_t e = cudaMalloc(&R->block, total);
-  if (e != cudaSuccess) {
+  const size_t total = 3 * arr_al + 3 * t_bytes + 2 * i_bytes + 256;
+  R->block_bytes = total;
+  if (ktau_dmalloc(&R->block, total) != KTAU_OK) {
     free(R);
-    return ktau_cuda_fail(e, "cudaMalloc(ranked)");
+    return KTAU_ENOMEM;
   }
+  cudaError_t e;
   char* b = (char*)R->block;
   R->perm = (uint16_t*)b;
   R->rank = (uint16_t*)(b + arr_al);
@@ -96,7 +152,9 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
   R->T = (int64_t*)(b + 3 * arr_al);
   R->ndist = (int32_t*)(b + 3 * arr_al + t_bytes);
   R->maxg = (int32_t*)(b + 3 * arr_al + t_bytes + i_bytes);
-  R->stats_dev = (ktau_stats*)(b + 3 * arr_al + t_bytes + 2 * i_bytes);
+  R->rs64 = (double*)(b + 3 * arr_al + t_bytes + 2 * i_bytes);
+  R->rsff = (float2*)(b + 3 * arr_al + 2 * t_bytes + 2 * i_bytes);
+  R->stats_dev = (ktau_stats*)(b + 3 * arr_al + 3 * t_bytes + 2 * i_bytes);
   ktau_status s = KTAU_OK;
   if ((e = cudaMemsetAsync(R->stats_dev, 0, sizeof(ktau_stats), st)) != cudaSuccess) {
     s = ktau_cuda_fail(e, "cudaMemsetAsync");
@@ -112,7 +170,8 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
       s = ktau_fail(KTAU_ENAN, "NaN in the input matrix");
   }
   if (s != KTAU_OK) {
-    cudaFree(R->block);
+    cudaStreamSynchronize(st);
+    ktau_dfree(R->block, R->block_bytes);
     free(R);
     return s;
   }
@@ -122,8 +181,8 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
 
 ktau_status ktau_ranked_free(ktau_ranked* R) {
   if (!R) return KTAU_OK;
-  cudaDeviceSynchronize();
-  if (R->block) cudaFree(R->block);
+  cudaDeviceSynchronize();  // no kernel may still use the handle's memory when it is recycled
+  if (R->block) ktau_dfree(R->block, R->block_bytes);
   ktau_signgemm_release(R);
   free(R);
   return KTAU_OK;
@@ -222,4 +281,24 @@ extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uin
     if (opt->ctas_per_sm) plan.ctas_per_sm = opt->ctas_per_sm;
   }
   return ktau_launch_merge(R, p_begin, p_end, out, plan, st);
+}
+
+extern "C" ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt,
+                                          int32_t* path) {
+  if (!R || !path) return ktau_fail(KTAU_EINVAL, "NULL argument");
+  ktau_status s = ktau_check_options(opt);
+  if (s != KTAU_OK) return s;
+  *path = ktau_choose_path(R, opt);
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream) {
+  if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  if (!ktau_signgemm_supported(R->n))
+    return ktau_fail(KTAU_EINVAL, "sign contraction supports n <= %d", KTAU_SIGNGEMM_MAX_N);
+  return ktau_signgemm_prepare(R, (cudaStream_t)stream);
+}
+
+extern "C" ktau_status ktau_device_status(void* stream) {
+  return ktau_signgemm_check_error((cudaStream_t)stream);
 }

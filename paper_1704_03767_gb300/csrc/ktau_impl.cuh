@@ -15,6 +15,9 @@
 //   srank[m][ld] uint16  rank in sorted order, srank[k] = rank[perm[k]] (tie-group id at k)
 //   T    [m]     int64   tie pairs of the variable, sum over groups t(t-1)/2 (n_1 / n_2)
 //   ndist[m]     int32   number of distinct values; maxg[m] int32 largest tie group
+//   rs64 [m]     double  1/sqrt(n_0 - T): the variable's factor of the tau-b denominator (Eq. 3),
+//                        NaN for a constant variable
+//   rsff [m]     float2  rs64 split into a float-float pair (hi, lo), hi + lo == rs64 to 2^-48
 // Padding entries (k >= n) hold 0xFFFF.
 // ---------------------------------------------------------------------------------------------
 struct ktau_stats {
@@ -29,21 +32,31 @@ struct ktau_ranked {
   int64_t m, n, ld;
   int device;
   void* block;  // single allocation holding every array below
+  size_t block_bytes;
   uint16_t* perm;
   uint16_t* rank;
   uint16_t* srank;
   int64_t* T;
   int32_t* ndist;
   int32_t* maxg;
+  double* rs64;
+  float2* rsff;
   ktau_stats* stats_dev;
   ktau_stats stats;  // host copy, filled by ktau_rank_prepare
-  // Sign expansion for the tensor-core path, built on first use (library-owned).
-  int8_t* sgn;
+  // Sign expansion for the tensor-core path, built on first use (library-owned):
+  // sgn[m][K_pad] of FP8 e4m3 (esize 1) or BF16 (esize 2) values in {-1, 0, +1}, K = n(n-1)/2,
+  // K_pad = K rounded up to 128; tmap is its TMA descriptor (CUtensorMap, 128-byte box rows).
+  void* sgn;
   int64_t K, K_pad;
-  // Tie-pair lists for n_3 in the tensor-core path, built with the expansion.
+  int esize;
+  int sg_ready;
+  alignas(64) unsigned char tmap[128];
+  // Tie-pair lists for n_3 in the tensor-core path (CSR: tie_off[m+1], tie_pairs[sum T] with
+  // (a << 16) | b for every sample pair a < b tied in the variable), built with the expansion.
   uint32_t* tie_pairs;
   int64_t* tie_off;
   int64_t tie_total;
+  size_t sgn_bytes, tie_bytes;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -52,6 +65,10 @@ struct ktau_ranked {
 ktau_status ktau_fail(ktau_status s, const char* fmt, ...);
 ktau_status ktau_cuda_fail(cudaError_t e, const char* what);
 int ktau_sm_count();
+// Library allocations go through a per-device cache of freed blocks (exact-size reuse), so
+// handles created and released every step do not pay cudaMalloc/cudaFree (which synchronises).
+ktau_status ktau_dmalloc(void** p, size_t bytes);
+void ktau_dfree(void* p, size_t bytes);
 
 #define KTAU_CUDA(call)                                                   \
   do {                                                                    \
@@ -89,7 +106,18 @@ __host__ __device__ inline uint64_t ktau_pair_index(int64_t m, int64_t i, int64_
 }
 
 // ---------------------------------------------------------------------------------------------
-// Step 5 of Sec. 3.2 and Eq. 3: S = n_0 - n_1 - n_2 + n_3 - 2 n_d, tau-b in FP64.
+// Step 5 of Sec. 3.2 and Eq. 3: S = n_0 - n_1 - n_2 + n_3 - 2 n_d, tau-b from the exact counts.
+//
+// FP64 runs at a small fraction of the FP32 rate on GB300, so the per-pair division and square
+// root of Eq. 3 are replaced by the product of per-variable factors r_u = 1/sqrt(n_0 - T_u)
+// (computed once per variable in IEEE FP64 by the rank kernel):
+//   tau64 = ((double)S * r_u) * r_v                    two FP64 products, error <= 4 ulp
+//   tau32 = RN_f32 of the FP64 formula S / sqrt(D_u D_v), evaluated as a float-float product
+//           S * r_u * r_v (relative error < 2^-43); when that value lies within 2^-40 of a float
+//           rounding boundary, the FP64 formula itself is evaluated, so the result is always
+//           exactly the round-to-nearest float of the FP64 formula.
+// Every kernel (merge, sign contraction, query, batched) stores through this one function, so
+// all paths give bit-identical outputs for the same pair.
 // ---------------------------------------------------------------------------------------------
 struct ktau_out {
   double* tau64;
@@ -99,19 +127,50 @@ struct ktau_out {
   int count_bits;
 };
 
-__device__ __forceinline__ double ktau_tau_b(int64_t S, int64_t n0, int64_t Tu, int64_t Tv) {
-  int64_t du = n0 - Tu, dv = n0 - Tv;
-  if (du == 0 || dv == 0) return __longlong_as_double(0x7ff8000000000000LL);
+__device__ __forceinline__ double ktau_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// The FP64 formula of Eq. 3 (slow on this part; only for the rare boundary cases).
+static __device__ __noinline__ double ktau_tau_b_formula(int64_t S, int64_t du, int64_t dv) {
+  if (du == 0 || dv == 0) return ktau_nan();
   return __ddiv_rn((double)S, __dsqrt_rn(__dmul_rn((double)du, (double)dv)));
 }
 
+__device__ __forceinline__ double ktau_tau64(int64_t S, double ru, double rv) {
+  return __dmul_rn(__dmul_rn((double)S, ru), rv);
+}
+
+__device__ __forceinline__ float ktau_tau32(int64_t S, float2 fu, float2 fv, int64_t n0,
+                                            int64_t Tu, int64_t Tv) {
+  if (isnan(fu.x) || isnan(fv.x)) return __int_as_float(0x7fc00000);
+  if (S == 0) return 0.0f;
+  const float sh = (float)S;
+  const float sl = (float)(S - (int64_t)sh);  // S == sh + sl exactly
+  // t = S * r_u as float-float
+  const float th = __fmul_rn(sh, fu.x);
+  const float tl = __fadd_rn(__fmaf_rn(sh, fu.x, -th), __fmaf_rn(sh, fu.y, __fmul_rn(sl, fu.x)));
+  // p = t * r_v as float-float
+  const float ph = __fmul_rn(th, fv.x);
+  const float pl = __fadd_rn(__fmaf_rn(th, fv.x, -ph), __fmaf_rn(th, fv.y, __fmul_rn(tl, fv.x)));
+  const float f = __fadd_rn(ph, pl);
+  const float d = __fadd_rn(__fsub_rn(ph, f), pl);  // distance of the float-float value from f
+  const uint32_t fb = __float_as_uint(fabsf(f));
+  float half = __uint_as_float(((fb >> 23) - 24u) << 23);  // ulp(f) / 2 (|f| >= 2^-27 here)
+  if ((fb & 0x7fffffu) == 0) half = __fmul_rn(half, 0.5f);  // power of two: closer neighbour below
+  const float margin = __fadd_rn(__fmul_rn(fabsf(f), 0x1p-40f), __fmul_rn(fabsf(d), 0x1p-22f));
+  if (__fadd_rn(fabsf(d), margin) < half) return f;
+  return __double2float_rn(ktau_tau_b_formula(S, n0 - Tu, n0 - Tv));
+}
+
+struct ktau_fac {
+  const double* rs64;
+  const float2* rsff;
+  const int64_t* T;
+};
+
 __device__ __forceinline__ void ktau_store(const ktau_out& o, uint64_t k, int64_t S, int64_t n3,
-                                           int64_t n0, int64_t Tu, int64_t Tv) {
-  if (o.tau64 || o.tau32) {
-    double t = ktau_tau_b(S, n0, Tu, Tv);
-    if (o.tau64) o.tau64[k] = t;
-    if (o.tau32) o.tau32[k] = __double2float_rn(t);
-  }
+                                           int64_t n0, const ktau_fac& f, int64_t u, int64_t v) {
+  if (o.tau64) o.tau64[k] = ktau_tau64(S, f.rs64[u], f.rs64[v]);
+  if (o.tau32) o.tau32[k] = ktau_tau32(S, f.rsff[u], f.rsff[v], n0, f.T[u], f.T[v]);
   if (o.count_bits == 64) {
     if (o.S) ((long long*)o.S)[k] = S;
     if (o.n3) ((long long*)o.n3)[k] = n3;

@@ -136,6 +136,7 @@ struct MergeArgs {
   const uint16_t* rank;
   const uint16_t* srank;
   const int64_t* T;
+  ktau_fac fac;
   int64_t m, n, ld;
   int64_t w;        // tiles per side
   int64_t tile_lo;  // tile-id range covering [p_begin, p_end)
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
       count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, tbuf, tbuf2, lane, red, nd, n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
-        ktau_store(a.out, p - a.p_begin, S, n3, n0, Tu, Tv);
+        ktau_store(a.out, p - a.p_begin, S, n3, n0, a.fac, y, x);
       }
     }
     if (!a.counter) t += gridDim.x;
@@ -311,6 +312,7 @@ ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p
   a.rank = R->rank;
   a.srank = R->srank;
   a.T = R->T;
+  a.fac = ktau_fac{R->rs64, R->rsff, R->T};
   a.m = m;
   a.n = n;
   a.ld = R->ld;

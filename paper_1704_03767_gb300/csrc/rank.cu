@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ valu
                                                    int n, int np2, int64_t ld, uint16_t* perm,
                                                    uint16_t* rank, uint16_t* srank, int64_t* T,
                                                    int32_t* ndist, int32_t* maxg,
+                                                   double* rs64, float2* rsff,
                                                    ktau_stats* stats) {
   extern __shared__ unsigned long long sm_keys[];                  // [np2]
   uint16_t* sm_first = reinterpret_cast<uint16_t*>(sm_keys + np2);  // [np2] group start
@@ -148,6 +149,13 @@ __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ valu
       g = max(g, red_g[w]);
     }
     T[row] = (int64_t)t;
+    // Factor of the tau-b denominator (Eq. 3): 1/sqrt(n_0 - n_1), IEEE FP64.
+    const long long D = (long long)n * (n - 1) / 2 - (long long)t;
+    const double r = D > 0 ? __ddiv_rn(1.0, __dsqrt_rn((double)D))
+                           : __longlong_as_double(0x7ff8000000000000LL);
+    const float hi = __double2float_rn(r);
+    rs64[row] = r;
+    rsff[row] = make_float2(hi, D > 0 ? __double2float_rn(r - (double)hi) : hi);
     ndist[row] = sm_dense[n - 1] + 1;
     maxg[row] = g;
     atomicAdd(&stats->T_sum, t);
@@ -169,7 +177,8 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
   auto kern = dtype == KTAU_F32 ? rank_kernel<KTAU_F32> : rank_kernel<KTAU_I32>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<(unsigned)m, threads, smem, st>>>(values, ld_in, (int)n, np2, R->ld, R->perm, R->rank,
-                                            R->srank, R->T, R->ndist, R->maxg, R->stats_dev);
+                                            R->srank, R->T, R->ndist, R->maxg, R->rs64, R->rsff,
+                                            R->stats_dev);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }

@@ -1,9 +1,686 @@
+// K-c: exact sign-matrix contraction on the GB300 tensor cores (see signgemm.cuh).
+//
+// Kernels
+//   sign_expand_kernel : A_u[k] = sign(r_u[a] - r_u[b]) for the k-th sample pair (a < b, row-major
+//                        order over the strict upper triangle of the n x n sample-pair matrix),
+//                        encoded as FP8 e4m3 (+1 = 0x38, -1 = 0xB8) or BF16, zero padded to K_pad.
+//   tie_pairs_kernel   : CSR list of the sample pairs tied in each variable (for n_3).
+//   contract_kernel    : persistent, warp-specialised tcgen05 GEMM S = A A^T over the upper
+//                        triangle (or Q D^T for queries). 128 x 256 output tiles; super-tiles of
+//                        256 x 256 are walked through the job-id bijection of Sec. 4.1 (Eq. 13-14)
+//                        and split into two 128-row halves.
+//                        warp 0: TMA producer (cp.async.bulk.tensor, 128B swizzle, 4-stage ring)
+//                        warp 1: TMEM allocation + single-thread tcgen05.mma issue
+//                        warps 2-5: epilogue, tcgen05.ld of the FP32 accumulator (exact integers),
+//                                   n_3 from tie lists, tau-b, coalesced stores through smem.
+//                        Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile run
+//                        under the MMAs of the next. Every mbarrier wait is bounded (about 2 s);
+//                        on timeout the kernel raises an error word and every role winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
 #include "signgemm.cuh"
 
-bool ktau_signgemm_supported(int64_t n) { (void)n; return false; }
-ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t, uint64_t, const ktau_out&,
-                                   cudaStream_t) {
-  (void)R;
-  return ktau_fail(KTAU_EINVAL, "sign-contraction path not available");
+namespace {
+
+constexpr int BM = 128;            // tile rows (TMEM lanes)
+constexpr int BN = 256;            // tile columns (TMEM columns per accumulator)
+constexpr int BKB = 128;           // bytes of K per stage row (one 128B swizzle atom row)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BKB;  // 16 KB
+constexpr int B_BYTES = BN * BKB;  // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int TRS = 33;            // padded row of the epilogue transposition buffer
+constexpr size_t SMEM_BYTES = 1024 /*align*/ + (size_t)STAGES * STAGE_BYTES +
+                              (size_t)EPI_WARPS * 32 * TRS * 4 + 256 /*barriers*/;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
+
+__device__ unsigned int g_sg_error;  // set when a bounded wait gives up
+
+// ---------------------------------------------------------------------------------------------
+// Sign expansion
+// ---------------------------------------------------------------------------------------------
+// First sample index a of pair k in row-major order over a < b (row a holds n-1-a pairs).
+__device__ __forceinline__ int pair_row(int n, long long k) {
+  const float nf = (float)n - 0.5f;
+  int a = (int)floorf(nf - sqrtf(fmaxf(nf * nf - 2.0f * (float)k, 0.0f)));
+  if (a < 0) a = 0;
+  if (a > n - 2) a = n - 2;
+  auto start = [n](long long r) { return r * (2LL * n - r - 1) / 2; };
+  while (a > 0 && start(a) > k) --a;
+  while (a < n - 2 && start(a + 1) <= k) ++a;
+  return a;
 }
-void ktau_signgemm_release(ktau_ranked* R) { (void)R; }
+
+template <int ESIZE>
+__global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
+                                                          int64_t ld, int n, int64_t K,
+                                                          int64_t K_pad, uint8_t* __restrict__ out) {
+  extern __shared__ uint16_t s_r[];
+  const int64_t row = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_r[i] = rank[row * ld + i];
+  __syncthreads();
+  constexpr int PER = 16 / ESIZE;  // elements per 16-byte store
+  const int64_t chunks = K_pad / PER;
+  uint8_t* orow = out + row * K_pad * ESIZE;
+  for (int64_t c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int64_t k0 = c * PER;
+    uint32_t words[4];
+    if (k0 < K) {
+      int a = pair_row(n, k0);
+      int b = (int)(k0 - (long long)a * (2LL * n - a - 1) / 2) + a + 1;
+      uint32_t acc[PER];
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        uint32_t v = 0;
+        if (k0 + e < K) {
+          const int d = (int)s_r[a] - (int)s_r[b];
+          if (ESIZE == 1)
+            v = d > 0 ? 0x38u : (d < 0 ? 0xB8u : 0u);
+          else
+            v = d > 0 ? 0x3F80u : (d < 0 ? 0xBF80u : 0u);
+          if (++b == n) {
+            ++a;
+            b = a + 1;
+          }
+        }
+        acc[e] = v;
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        if (ESIZE == 1)
+          words[w] = acc[4 * w] | (acc[4 * w + 1] << 8) | (acc[4 * w + 2] << 16) |
+                     (acc[4 * w + 3] << 24);
+        else
+          words[w] = acc[2 * w] | (acc[2 * w + 1] << 16);
+      }
+    } else {
+      words[0] = words[1] = words[2] = words[3] = 0u;
+    }
+    reinterpret_cast<uint4*>(orow)[c] = make_uint4(words[0], words[1], words[2], words[3]);
+  }
+}
+
+// One thread per variable: every pair of positions inside a tie group of the sorted order.
+__global__ void tie_pairs_kernel(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
+                                 int64_t ld, int n, int64_t m, const int64_t* __restrict__ off,
+                                 uint32_t* __restrict__ pairs) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= m) return;
+  const uint16_t* p = perm + row * ld;
+  const uint16_t* s = srank + row * ld;
+  int64_t o = off[row];
+  int start = 0;
+  for (int k = 1; k < n; ++k) {
+    if (s[k] != s[k - 1]) {
+      start = k;
+      continue;
+    }
+    for (int j = start; j < k; ++j) {
+      uint32_t a = p[j], b = p[k];
+      if (a > b) {
+        uint32_t t = a;
+        a = b;
+        b = t;
+      }
+      pairs[o++] = (a << 16) | b;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// PTX wrappers (tcgen05, TMA, mbarrier)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the error word is already set or the wait exceeded kWaitNs.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (*(volatile unsigned int*)&g_sg_error) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(&g_sg_error, 1u);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ bool sg_failed() { return *(volatile unsigned int*)&g_sg_error != 0; }
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the canonical 128-byte-swizzle layout
+// (8-row x 128-byte atoms, 1024 bytes apart along M/N).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+template <int ESIZE>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if (ESIZE == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Contraction kernel
+// ---------------------------------------------------------------------------------------------
+struct SideArgs {  // per-variable data of the row side (u) or the column side (v)
+  const uint16_t* rank;
+  int64_t ld;
+  const int64_t* T;
+  const double* rs64;
+  const float2* rsff;
+  const int64_t* tie_off;
+  const uint32_t* tie_pairs;
+  int64_t m;
+};
+
+struct ContractArgs {
+  SideArgs row, col;
+  int64_t n, num_kb;
+  int tri;                 // 1: upper triangle of one matrix; 0: rectangle rows x cols
+  int64_t wS;              // tri: super-tiles per side
+  int64_t ncb;             // rect: column blocks of BN
+  int64_t unit_lo, unit_hi;
+  uint64_t p_begin, p_end; // tri: pair range
+  int64_t ldo;             // rect: output row stride
+  ktau_out out;
+};
+
+struct Unit {
+  int64_t y0, x0;
+  bool live;
+};
+
+__device__ __forceinline__ uint64_t tri_p(int64_t m, int64_t y, int64_t x) {
+  return (uint64_t)(y * (2 * m - y - 1) / 2 + (x - y - 1));
+}
+
+// Tile origin of a work unit and whether it holds any output (same answer in every role).
+__device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
+  Unit r;
+  if (a.tri) {
+    int64_t ys, xs;
+    ktau_tile_coord(a.wS, u >> 1, ys, xs);
+    r.y0 = ys * 256 + (u & 1) * BM;
+    r.x0 = xs * 256;
+    const int64_t m = a.row.m;
+    const int64_t xend = min(r.x0 + (int64_t)BN, m);
+    const int64_t ylast = min(r.y0 + (int64_t)BM - 1, xend - 2);
+    r.live = r.y0 < m && ylast >= r.y0;
+    if (r.live) {
+      const uint64_t pmin = tri_p(m, r.y0, max(r.x0, r.y0 + 1));
+      const uint64_t pmax = tri_p(m, ylast, xend - 1);
+      r.live = pmax >= a.p_begin && pmin < a.p_end;
+    }
+  } else {
+    r.y0 = (u / a.ncb) * BM;
+    r.x0 = (u % a.ncb) * BN;
+    r.live = r.y0 < a.row.m && r.x0 < a.col.m;
+  }
+  return r;
+}
+
+// n_3(u, v): sample pairs tied in both variables, enumerated over the shorter tie list.
+__device__ __forceinline__ int64_t joint_ties(const SideArgs& R, int64_t u, const SideArgs& C,
+                                              int64_t v) {
+  const int64_t tu = R.T[u], tv = C.T[v];
+  if (tu == 0 || tv == 0) return 0;
+  const SideArgs& L = tu <= tv ? R : C;       // list owner
+  const SideArgs& O = tu <= tv ? C : R;       // ranks checked
+  const int64_t lv = tu <= tv ? u : v, ov = tu <= tv ? v : u;
+  const uint32_t* tp = L.tie_pairs + L.tie_off[lv];
+  const int64_t cnt = tu <= tv ? tu : tv;
+  const uint16_t* ro = O.rank + ov * O.ld;
+  int64_t n3 = 0;
+  for (int64_t i = 0; i < cnt; ++i) {
+    const uint32_t ab = tp[i];
+    n3 += ro[ab >> 16] == ro[ab & 0xffffu];
+  }
+  return n3;
+}
+
+template <int ESIZE>
+__global__ void __launch_bounds__(THREADS, 1)
+    contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const ContractArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* stage_base = smem;
+  int* tbuf_all = (int*)(smem + (size_t)STAGES * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)((unsigned char*)tbuf_all + (size_t)EPI_WARPS * 32 * TRS * 4);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]; then the TMEM base slot
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar0 = smem_u32(bars);
+  auto FULL = [&](int s) { return bar0 + 8u * s; };
+  auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto TFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + s); };
+  auto TEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 + s); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(FULL(s), 1);
+      mbar_init(EMPTY(s), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(TFULL(s), 1);
+      mbar_init(TEMPTY(s), 32 * EPI_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t u = a.unit_lo + blockIdx.x; ok && u < a.unit_hi; u += gridDim.x) {
+        const Unit t = unit_of(a, u);
+        if (!t.live) continue;
+        for (int64_t kb = 0; kb < a.num_kb; ++kb) {
+          if (!mbar_wait(EMPTY(stage), phase ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+          mbar_expect_tx(FULL(stage), STAGE_BYTES);
+          const int kx = (int)(kb * BKB);
+          tma_load_2d(sa, &tmA, kx, (int)t.y0, FULL(stage));
+          tma_load_2d(sb, &tmB, kx, (int)t.x0, FULL(stage));
+          tma_load_2d(sb + BN / 2 * BKB, &tmB, kx, (int)(t.x0 + BN / 2), FULL(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t kFmt = ESIZE == 1 ? 0u : 1u;  // E4M3 (f8f6f4) or BF16 (f16)
+      const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(BM >> 4) << 24);
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true;
+      for (int64_t u = a.unit_lo + blockIdx.x; ok && u < a.unit_hi; u += gridDim.x) {
+        const Unit t = unit_of(a, u);
+        if (!t.live) continue;
+        if (!mbar_wait(TEMPTY(acc), acc_phase ^ 1u)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int64_t kb = 0; kb < a.num_kb; ++kb) {
+          if (!mbar_wait(FULL(stage), phase)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BKB / 32; ++k)
+            umma<ESIZE>(d_tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                        (kb > 0 || k > 0) ? 1u : 0u);
+          umma_commit(EMPTY(stage));  // frees the stage once these MMAs have read it
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(TFULL(acc));  // accumulator complete
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+    }
+  } else {
+    // ---------------- Epilogue (warps 2..5) ----------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int* tb = tbuf_all + (warp - 2) * 32 * TRS;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    const int64_t n0 = a.n * (a.n - 1) / 2;
+    const ktau_fac frow{a.row.rs64, a.row.rsff, a.row.T};
+    const ktau_fac fcol{a.col.rs64, a.col.rsff, a.col.T};
+    for (int64_t u = a.unit_lo + blockIdx.x; u < a.unit_hi; u += gridDim.x) {
+      const Unit t = unit_of(a, u);
+      if (!t.live) continue;
+      if (!mbar_wait(TFULL(acc), acc_phase)) break;
+      tc_fence_after();
+      const int64_t ybase = t.y0 + 32 * q;
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
+        if (c == BN / 32 - 1) {
+          tc_fence_before();
+          mbar_arrive(TEMPTY(acc));  // accumulator may be overwritten by the next tile
+        }
+        // transpose: row `lane` of this warp's 32 rows, columns 32c..32c+31
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tb[lane * TRS + j] = __float2int_rn(__uint_as_float(r[j]));
+        __syncwarp();
+        const int64_t v = t.x0 + 32 * c + lane;
+        const bool vin = v < a.col.m;
+        for (int i = 0; i < 32; ++i) {
+          const int64_t y = ybase + i;
+          if (y >= a.row.m) break;
+          if (!vin) continue;
+          uint64_t k;
+          if (a.tri) {
+            if (v <= y) continue;
+            const uint64_t p = tri_p(a.row.m, y, v);
+            if (p < a.p_begin || p >= a.p_end) continue;
+            k = p - a.p_begin;
+          } else {
+            k = (uint64_t)y * (uint64_t)a.ldo + (uint64_t)v;
+          }
+          const int64_t S = tb[i * TRS + lane];
+          if (a.out.tau64) a.out.tau64[k] = ktau_tau64(S, frow.rs64[y], fcol.rs64[v]);
+          if (a.out.tau32)
+            a.out.tau32[k] = ktau_tau32(S, frow.rsff[y], fcol.rsff[v], n0, frow.T[y], fcol.T[v]);
+          if (a.out.S || a.out.n3) {
+            const int64_t n3 = a.out.n3 ? joint_ties(a.row, y, a.col, v) : 0;
+            if (a.out.count_bits == 64) {
+              if (a.out.S) ((long long*)a.out.S)[k] = S;
+              if (a.out.n3) ((long long*)a.out.n3)[k] = n3;
+            } else {
+              if (a.out.S) ((int*)a.out.S)[k] = (int)S;
+              if (a.out.n3) ((int*)a.out.n3)[k] = (int)n3;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+      if (sg_failed()) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+// cuTensorMapEncodeTiled through the runtime's driver entry-point query, so the library does not
+// link libcuda directly (it still loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+ktau_status make_tmap(ktau_ranked* R) {
+  CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(R->tmap);
+  PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
+  if (!cuTensorMapEncodeTiled) return ktau_fail(KTAU_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const cuuint64_t row_bytes = (cuuint64_t)(R->K_pad * R->esize);
+  cuuint64_t dims[2] = {row_bytes, (cuuint64_t)R->m};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)BKB, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = cuTensorMapEncodeTiled(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, R->sgn, dims, strides,
+                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return ktau_fail(KTAU_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return KTAU_OK;
+}
+
+SideArgs side_of(const ktau_ranked* R) {
+  return SideArgs{R->rank, R->ld, R->T, R->rs64, R->rsff, R->tie_off, R->tie_pairs, R->m};
+}
+
+template <int ESIZE>
+ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const ContractArgs& args,
+                            int64_t units, cudaStream_t st) {
+  auto kern = contract_kernel<ESIZE>;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SMEM_BYTES));
+  int64_t grid = ktau_sm_count();
+  if (grid > units) grid = units;
+  if (grid < 1) grid = 1;
+  const CUtensorMap* ta = reinterpret_cast<const CUtensorMap*>(A->tmap);
+  const CUtensorMap* tb = reinterpret_cast<const CUtensorMap*>(B->tmap);
+  kern<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(*ta, *tb, args);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
+}  // namespace
+
+bool ktau_signgemm_supported(int64_t n) { return n >= 2 && n <= KTAU_SIGNGEMM_MAX_N; }
+
+ktau_status ktau_signgemm_prepare(ktau_ranked* R, cudaStream_t st) {
+  if (R->sg_ready) return KTAU_OK;
+  if (!ktau_signgemm_supported(R->n))
+    return ktau_fail(KTAU_EINVAL, "sign contraction supports 2 <= n <= %d", KTAU_SIGNGEMM_MAX_N);
+  const int64_t n = R->n;
+  R->K = n * (n - 1) / 2;
+  R->K_pad = (R->K + 127) / 128 * 128;
+  R->esize = n <= KTAU_SIGNGEMM_FP8_MAX_N ? 1 : 2;
+  R->sgn_bytes = (size_t)R->m * R->K_pad * R->esize;
+  if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
+  const size_t smem = (size_t)n * sizeof(uint16_t);
+  if (R->esize == 1)
+    sign_expand_kernel<1><<<(unsigned)R->m, 256, smem, st>>>(R->rank, R->ld, (int)n, R->K,
+                                                             R->K_pad, (uint8_t*)R->sgn);
+  else
+    sign_expand_kernel<2><<<(unsigned)R->m, 256, smem, st>>>(R->rank, R->ld, (int)n, R->K,
+                                                             R->K_pad, (uint8_t*)R->sgn);
+  KTAU_CUDA(cudaGetLastError());
+  // Tie-pair lists: offsets from the per-variable tie counts (host scan), then one thread per
+  // variable writes its pairs.
+  std::vector<int64_t> T((size_t)R->m), off((size_t)R->m + 1);
+  KTAU_CUDA(cudaMemcpyAsync(T.data(), R->T, (size_t)R->m * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, st));
+  KTAU_CUDA(cudaStreamSynchronize(st));
+  off[0] = 0;
+  for (int64_t i = 0; i < R->m; ++i) off[(size_t)i + 1] = off[(size_t)i] + T[(size_t)i];
+  R->tie_total = off[(size_t)R->m];
+  R->tie_bytes = (size_t)(R->tie_total > 0 ? R->tie_total : 1) * 4;
+  if (ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
+      ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) != KTAU_OK)
+    return KTAU_ENOMEM;
+  KTAU_CUDA(cudaMemcpyAsync(R->tie_off, off.data(), ((size_t)R->m + 1) * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, st));
+  tie_pairs_kernel<<<(unsigned)((R->m + 127) / 128), 128, 0, st>>>(R->perm, R->srank, R->ld,
+                                                                   (int)n, R->m, R->tie_off,
+                                                                   R->tie_pairs);
+  KTAU_CUDA(cudaGetLastError());
+  KTAU_CUDA(cudaStreamSynchronize(st));  // host vectors above go out of scope
+  ktau_status s = make_tmap(R);
+  if (s != KTAU_OK) return s;
+  R->sg_ready = 1;
+  return KTAU_OK;
+}
+
+ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                                   const ktau_out& out, cudaStream_t st) {
+  ktau_status s = ktau_signgemm_prepare(R, st);
+  if (s != KTAU_OK) return s;
+  const int64_t m = R->m;
+  ContractArgs a;
+  a.row = a.col = side_of(R);
+  a.n = R->n;
+  a.num_kb = R->K_pad * R->esize / BKB;
+  a.tri = 1;
+  a.wS = (m + 255) / 256;
+  a.ncb = 0;
+  a.p_begin = p_begin;
+  a.p_end = p_end;
+  a.ldo = 0;
+  a.out = out;
+  int64_t i0, j0, i1, j1;
+  ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
+  ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
+  a.unit_lo = 2 * ktau_rowstart(a.wS, i0 / 256);
+  a.unit_hi = 2 * ktau_rowstart(a.wS, i1 / 256 + 1);
+  const int64_t units = a.unit_hi - a.unit_lo;
+  return R->esize == 1 ? launch_contract<1>(R, R, a, units, st)
+                       : launch_contract<2>(R, R, a, units, st);
+}
+
+ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
+                               cudaStream_t st) {
+  if (Q->n != D->n) return ktau_fail(KTAU_EINVAL, "sample counts differ");
+  ktau_status s = ktau_signgemm_prepare(Q, st);
+  if (s == KTAU_OK) s = ktau_signgemm_prepare(D, st);
+  if (s != KTAU_OK) return s;
+  ContractArgs a;
+  a.row = side_of(Q);
+  a.col = side_of(D);
+  a.n = Q->n;
+  a.num_kb = Q->K_pad * Q->esize / BKB;
+  a.tri = 0;
+  a.wS = 0;
+  a.ncb = (D->m + BN - 1) / BN;
+  a.p_begin = 0;
+  a.p_end = 0;
+  a.ldo = ldo;
+  a.out = out;
+  a.unit_lo = 0;
+  a.unit_hi = ((Q->m + BM - 1) / BM) * a.ncb;
+  return Q->esize == 1 ? launch_contract<1>(Q, D, a, a.unit_hi, st)
+                       : launch_contract<2>(Q, D, a, a.unit_hi, st);
+}
+
+void ktau_signgemm_release(ktau_ranked* R) {
+  ktau_dfree(R->sgn, R->sgn_bytes);
+  ktau_dfree(R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t));
+  ktau_dfree(R->tie_pairs, R->tie_bytes);
+  R->sgn = nullptr;
+  R->tie_off = nullptr;
+  R->tie_pairs = nullptr;
+  R->sg_ready = 0;
+}
+
+ktau_status ktau_signgemm_check_error(cudaStream_t st) {
+  unsigned int e = 0;
+  KTAU_CUDA(cudaMemcpyFromSymbolAsync(&e, g_sg_error, sizeof(e), 0, cudaMemcpyDeviceToHost, st));
+  KTAU_CUDA(cudaStreamSynchronize(st));
+  if (e) {
+    const unsigned int zero = 0;
+    cudaMemcpyToSymbolAsync(g_sg_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    return ktau_fail(KTAU_ETIMEOUT, "tensor-core pipeline wait timed out");
+  }
+  return KTAU_OK;
+}
