@@ -76,34 +76,7 @@ void ktau_dfree(void* p, size_t bytes);
     if (e_ != cudaSuccess) return ktau_cuda_fail(e_, #call);              \
   } while (0)
 
-// ---------------------------------------------------------------------------------------------
-// Job-id <-> coordinate bijection (Sec. 4.1, Eq. 4-10), applied to a w x w matrix of tiles
-// (Sec. 4.2, Eq. 11-14) with the diagonal included.
-// ---------------------------------------------------------------------------------------------
-__host__ __device__ inline int64_t ktau_rowstart(int64_t w, int64_t y) {  // Eq. 5 / Eq. 12
-  return y * (2 * w - y + 1) / 2;
-}
-
-// Eq. 13-14: y = ceil(w - 1/2 - sqrt(w^2 + w + 1/4 - 2(J+1))), x = J + y - F(y). The FP64
-// square root can land the ceiling one row off when z is (nearly) an integer, so the result is
-// checked against F(y) <= J < F(y+1) (Eq. 6) and moved by one row if needed.
-__host__ __device__ inline void ktau_tile_coord(int64_t w, int64_t J, int64_t& y, int64_t& x) {
-  double wd = (double)w;
-  double z = wd - 0.5 - sqrt(wd * wd + wd + 0.25 - 2.0 * ((double)J + 1.0));
-  int64_t yy = (int64_t)ceil(z);
-  if (yy < 0) yy = 0;
-  if (yy > w - 1) yy = w - 1;
-  while (yy > 0 && ktau_rowstart(w, yy) > J) --yy;
-  while (yy < w - 1 && ktau_rowstart(w, yy + 1) <= J) ++yy;
-  y = yy;
-  x = J + yy - ktau_rowstart(w, yy);
-}
-
-// Packed index of pair (i, j), i < j, in the strict upper triangle of an m x m job matrix
-// (Eq. 4 applied to the (m-1)-triangle: p = J_{m-1}(i, j-1)).
-__host__ __device__ inline uint64_t ktau_pair_index(int64_t m, int64_t i, int64_t j) {
-  return (uint64_t)(i * (2 * m - i - 1) / 2 + (j - i - 1));
-}
+#include "bijection.cuh"
 
 // ---------------------------------------------------------------------------------------------
 // Step 5 of Sec. 3.2 and Eq. 3: S = n_0 - n_1 - n_2 + n_3 - 2 n_d, tau-b from the exact counts.
@@ -143,8 +116,10 @@ __device__ __forceinline__ float ktau_tau32(int64_t S, float2 fu, float2 fv, int
                                             int64_t Tu, int64_t Tv) {
   if (isnan(fu.x) || isnan(fv.x)) return __int_as_float(0x7fc00000);
   if (S == 0) return 0.0f;
-  const float sh = (float)S;
-  const float sl = (float)(S - (int64_t)sh);  // S == sh + sl exactly
+  // S as an exact float-float pair (S fits int32 because |S| <= n_0 < 2^27).
+  const int Si = (int)S;
+  const float sh = __int2float_rn(Si);
+  const float sl = __int2float_rn(Si - __float2int_rn(sh));
   // t = S * r_u as float-float
   const float th = __fmul_rn(sh, fu.x);
   const float tl = __fadd_rn(__fmaf_rn(sh, fu.x, -th), __fmaf_rn(sh, fu.y, __fmul_rn(sl, fu.x)));

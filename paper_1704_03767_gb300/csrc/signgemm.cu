@@ -35,7 +35,8 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;  // 16 KB
 constexpr int B_BYTES = BN * BKB;  // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter, each half of the columns
+constexpr int GROUP = 8;           // super-tiles per side of a traversal group (L2 locality)
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int TRS = 33;            // padded row of the epilogue transposition buffer
 constexpr size_t SMEM_BYTES = 1024 /*align*/ + (size_t)STAGES * STAGE_BYTES +
@@ -183,12 +184,18 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 __device__ __forceinline__ bool sg_failed() { return *(volatile unsigned int*)&g_sg_error != 0; }
 
+// Operand tiles are re-read by many CTAs: keep them in L2 ahead of the streamed outputs.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
-                                            uint32_t bar) {
+                                            uint32_t bar, uint64_t pol) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar), "l"(pol)
       : "memory");
 }
 
@@ -262,6 +269,7 @@ struct ContractArgs {
   int64_t n, num_kb;
   int tri;                 // 1: upper triangle of one matrix; 0: rectangle rows x cols
   int64_t wS;              // tri: super-tiles per side
+  int64_t wG;              // tri: traversal groups per side
   int64_t ncb;             // rect: column blocks of BN
   int64_t unit_lo, unit_hi;
   uint64_t p_begin, p_end; // tri: pair range
@@ -282,10 +290,21 @@ __device__ __forceinline__ uint64_t tri_p(int64_t m, int64_t y, int64_t x) {
 __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
   Unit r;
   if (a.tri) {
-    int64_t ys, xs;
-    ktau_tile_coord(a.wS, u >> 1, ys, xs);
+    // Slot u -> (group of GROUP x GROUP super-tiles, walked by the bijection on the group matrix;
+    // row-major inside the group) -> 256 x 256 super-tile -> 128-row half. Consecutive slots,
+    // which run at the same time on neighbouring CTAs, stay inside one group and share operand
+    // blocks in L2. Slots below the diagonal or past the edge are dead.
+    const int64_t s2 = u >> 1;
+    const int64_t gid = s2 / (GROUP * GROUP), loc = s2 % (GROUP * GROUP);
+    int64_t gy, gx;
+    ktau_tile_coord(a.wG, gid, gy, gx);
+    const int64_t ys = gy * GROUP + loc / GROUP, xs = gx * GROUP + loc % GROUP;
     r.y0 = ys * 256 + (u & 1) * BM;
     r.x0 = xs * 256;
+    if (ys >= a.wS || xs >= a.wS || ys > xs) {
+      r.live = false;
+      return r;
+    }
     const int64_t m = a.row.m;
     const int64_t xend = min(r.x0 + (int64_t)BN, m);
     const int64_t ylast = min(r.y0 + (int64_t)BM - 1, xend - 2);
@@ -303,23 +322,94 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
   return r;
 }
 
-// n_3(u, v): sample pairs tied in both variables, enumerated over the shorter tie list.
-__device__ __forceinline__ int64_t joint_ties(const SideArgs& R, int64_t u, const SideArgs& C,
-                                              int64_t v) {
-  const int64_t tu = R.T[u], tv = C.T[v];
-  if (tu == 0 || tv == 0) return 0;
-  const SideArgs& L = tu <= tv ? R : C;       // list owner
-  const SideArgs& O = tu <= tv ? C : R;       // ranks checked
-  const int64_t lv = tu <= tv ? u : v, ov = tu <= tv ? v : u;
-  const uint32_t* tp = L.tie_pairs + L.tie_off[lv];
-  const int64_t cnt = tu <= tv ? tu : tv;
-  const uint16_t* ro = O.rank + ov * O.ld;
-  int64_t n3 = 0;
-  for (int64_t i = 0; i < cnt; ++i) {
-    const uint32_t ab = tp[i];
-    n3 += ro[ab >> 16] == ro[ab & 0xffffu];
+// n_3(u, v) = number of sample pairs tied in u that are also tied in v (Table 1). Tiles of
+// JT x JT variable pairs; the column variables' ranks are staged transposed in shared memory
+// (rT[a][j]) so that, for each tied pair (a, b) of a row variable, the 32 lanes of a warp check 32
+// column variables with conflict-free loads. Writes every n_3 of the range (zeros included).
+constexpr int JT = 64;
+constexpr int JTP = JT + 1;  // padded row (uint16) of the transposed rank block
+constexpr int JCAP = 4096;  // tie pairs of one tile's rows staged in shared memory
+
+__global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const SideArgs C,
+                                                         int64_t n, int tri, int64_t w,
+                                                         int64_t ncb, int64_t tile_lo,
+                                                         int64_t tile_hi, uint64_t p_begin,
+                                                         uint64_t p_end, int64_t ldo, void* n3out,
+                                                         int count_bits) {
+  extern __shared__ uint32_t jsm[];
+  uint32_t* s_pairs = jsm;                                     // [JCAP]
+  int* s_off = (int*)(jsm + JCAP);                             // [JT + 1], relative offsets
+  uint16_t* rT = (uint16_t*)(jsm + JCAP + JT + 8);             // [n][JTP]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
+    int64_t y0, x0;
+    if (tri) {
+      int64_t yq, xq;
+      ktau_tile_coord(w, t, yq, xq);
+      y0 = yq * JT;
+      x0 = xq * JT;
+    } else {
+      y0 = (t / ncb) * JT;
+      x0 = (t % ncb) * JT;
+    }
+    const int rows = (int)min((int64_t)JT, R.m - y0);
+    const int64_t base_off = R.tie_off[y0];
+    const int64_t seg = R.tie_off[y0 + rows] - base_off;
+    const bool staged = seg <= JCAP;
+    __syncthreads();
+    // Stage the JT column variables' rank rows transposed, 8 ranks (16 bytes) per load, the
+    // row variables' tie-list offsets, and (when it fits) their tie pairs.
+    const int vec = (int)(C.ld >> 3);
+    for (int e = threadIdx.x; e < JT * vec; e += blockDim.x) {
+      const int j = e / vec, c8 = e - j * vec;
+      const int64_t v = x0 + j;
+      uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+      if (v < C.m) w4 = __ldg(reinterpret_cast<const uint4*>(C.rank + v * C.ld) + c8);
+      const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int aa = c8 * 8 + h;
+        if (aa < n) rT[aa * JTP + j] = (uint16_t)(wd[h >> 1] >> (16 * (h & 1)));
+      }
+    }
+    for (int i = threadIdx.x; i <= rows; i += blockDim.x)
+      s_off[i] = (int)(R.tie_off[y0 + i] - base_off);
+    if (staged)
+      for (int64_t i = threadIdx.x; i < seg; i += blockDim.x) s_pairs[i] = R.tie_pairs[base_off + i];
+    __syncthreads();
+    const uint32_t* plist = staged ? s_pairs : R.tie_pairs + base_off;
+    for (int i = warp; i < rows; i += blockDim.x / 32) {
+      const int64_t y = y0 + i;
+      const int e0 = s_off[i], e1 = s_off[i + 1];
+      int c0 = 0, c1 = 0;
+      for (int e = e0; e < e1; ++e) {
+        const uint32_t ab = plist[e];
+        const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
+        c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
+        c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+      }
+      const int64_t rowbase = tri ? y * (2 * R.m - y - 1) / 2 - y - 1 : y * ldo;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t v = x0 + lane + 32 * h;
+        if (v >= C.m) continue;
+        uint64_t k;
+        if (tri) {
+          if (v <= y) continue;
+          const uint64_t p = (uint64_t)(rowbase + v);
+          if (p < p_begin || p >= p_end) continue;
+          k = p - p_begin;
+        } else {
+          k = (uint64_t)(rowbase + v);
+        }
+        const int val = h ? c1 : c0;
+        if (count_bits == 64)
+          __stcs((long long*)n3out + k, (long long)val);
+        else
+          __stcs((int*)n3out + k, val);
+      }
+    }
   }
-  return n3;
 }
 
 template <int ESIZE>
@@ -370,6 +460,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      const uint64_t pol = l2_evict_last_policy();
       for (int64_t u = a.unit_lo + blockIdx.x; ok && u < a.unit_hi; u += gridDim.x) {
         const Unit t = unit_of(a, u);
         if (!t.live) continue;
@@ -382,9 +473,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sb = sa + A_BYTES;
           mbar_expect_tx(FULL(stage), STAGE_BYTES);
           const int kx = (int)(kb * BKB);
-          tma_load_2d(sa, &tmA, kx, (int)t.y0, FULL(stage));
-          tma_load_2d(sb, &tmB, kx, (int)t.x0, FULL(stage));
-          tma_load_2d(sb + BN / 2 * BKB, &tmB, kx, (int)(t.x0 + BN / 2), FULL(stage));
+          tma_load_2d(sa, &tmA, kx, (int)t.y0, FULL(stage), pol);
+          tma_load_2d(sb, &tmB, kx, (int)t.x0, FULL(stage), pol);
+          tma_load_2d(sb + BN / 2 * BKB, &tmB, kx, (int)(t.x0 + BN / 2), FULL(stage), pol);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -438,22 +529,33 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ---------------- Epilogue (warps 2..5) ----------------
     const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int half_sel = (warp - 2) >> 2;  // which half of the 256 columns
     int* tb = tbuf_all + (warp - 2) * 32 * TRS;
     int acc = 0;
     uint32_t acc_phase = 0;
     const int64_t n0 = a.n * (a.n - 1) / 2;
-    const ktau_fac frow{a.row.rs64, a.row.rsff, a.row.T};
-    const ktau_fac fcol{a.col.rs64, a.col.rsff, a.col.T};
+    const int64_t mrow = a.row.m, mcol = a.col.m;
+    const bool want64 = a.out.tau64 != nullptr, want32 = a.out.tau32 != nullptr;
+    const bool wantS = a.out.S != nullptr, s64 = a.out.count_bits == 64;
     for (int64_t u = a.unit_lo + blockIdx.x; u < a.unit_hi; u += gridDim.x) {
       const Unit t = unit_of(a, u);
       if (!t.live) continue;
       if (!mbar_wait(TFULL(acc), acc_phase)) break;
       tc_fence_after();
       const int64_t ybase = t.y0 + 32 * q;
-      for (int c = 0; c < BN / 32; ++c) {
+      // Per-row data of this warp's 32 rows, one row per lane (broadcast by shuffle below).
+      const int64_t my_y = ybase + lane;
+      const bool my_row_ok = my_y < mrow;
+      const double my_r64 = my_row_ok ? __ldg(a.row.rs64 + my_y) : 0.0;
+      const float2 my_rff = my_row_ok ? __ldg(a.row.rsff + my_y) : make_float2(0.f, 0.f);
+      const long long my_T = my_row_ok ? __ldg((const long long*)a.row.T + my_y) : 0;
+      const long long my_base =
+          a.tri ? (long long)(my_y * (2 * mrow - my_y - 1) / 2 - my_y - 1) : (long long)my_y * a.ldo;
+      const int rows_here = (int)min((int64_t)32, mrow - ybase);
+      for (int c = half_sel * (BN / 64); c < (half_sel + 1) * (BN / 64); ++c) {
         uint32_t r[32];
         tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
-        if (c == BN / 32 - 1) {
+        if (c == (half_sel + 1) * (BN / 64) - 1) {
           tc_fence_before();
           mbar_arrive(TEMPTY(acc));  // accumulator may be overwritten by the next tile
         }
@@ -462,33 +564,36 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int j = 0; j < 32; ++j) tb[lane * TRS + j] = __float2int_rn(__uint_as_float(r[j]));
         __syncwarp();
         const int64_t v = t.x0 + 32 * c + lane;
-        const bool vin = v < a.col.m;
+        const bool vin = v < mcol;
+        const double c_r64 = vin ? __ldg(a.col.rs64 + v) : 0.0;
+        const float2 c_rff = vin ? __ldg(a.col.rsff + v) : make_float2(0.f, 0.f);
+        const long long c_T = vin ? __ldg((const long long*)a.col.T + v) : 0;
+#pragma unroll 4
         for (int i = 0; i < 32; ++i) {
+          const double r64 = __shfl_sync(0xffffffffu, my_r64, i);
+          const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
+          const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
+          const long long Tu = __shfl_sync(0xffffffffu, my_T, i);
+          const long long base = __shfl_sync(0xffffffffu, my_base, i);
           const int64_t y = ybase + i;
-          if (y >= a.row.m) break;
-          if (!vin) continue;
+          if (i >= rows_here || !vin) continue;
           uint64_t k;
           if (a.tri) {
             if (v <= y) continue;
-            const uint64_t p = tri_p(a.row.m, y, v);
+            const uint64_t p = (uint64_t)(base + v);
             if (p < a.p_begin || p >= a.p_end) continue;
             k = p - a.p_begin;
           } else {
-            k = (uint64_t)y * (uint64_t)a.ldo + (uint64_t)v;
+            k = (uint64_t)(base + v);
           }
-          const int64_t S = tb[i * TRS + lane];
-          if (a.out.tau64) a.out.tau64[k] = ktau_tau64(S, frow.rs64[y], fcol.rs64[v]);
-          if (a.out.tau32)
-            a.out.tau32[k] = ktau_tau32(S, frow.rsff[y], fcol.rsff[v], n0, frow.T[y], fcol.T[v]);
-          if (a.out.S || a.out.n3) {
-            const int64_t n3 = a.out.n3 ? joint_ties(a.row, y, a.col, v) : 0;
-            if (a.out.count_bits == 64) {
-              if (a.out.S) ((long long*)a.out.S)[k] = S;
-              if (a.out.n3) ((long long*)a.out.n3)[k] = n3;
-            } else {
-              if (a.out.S) ((int*)a.out.S)[k] = (int)S;
-              if (a.out.n3) ((int*)a.out.n3)[k] = (int)n3;
-            }
+          const int S = tb[i * TRS + lane];
+          if (want64) __stcs(a.out.tau64 + k, ktau_tau64(S, r64, c_r64));
+          if (want32) __stcs(a.out.tau32 + k, ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, Tu, c_T));
+          if (wantS) {
+            if (s64)
+              __stcs((long long*)a.out.S + k, (long long)S);
+            else
+              __stcs((int*)a.out.S + k, S);
           }
         }
         __syncwarp();
@@ -547,6 +652,37 @@ ktau_status make_tmap(ktau_ranked* R) {
 
 SideArgs side_of(const ktau_ranked* R) {
   return SideArgs{R->rank, R->ld, R->T, R->rs64, R->rsff, R->tie_off, R->tie_pairs, R->m};
+}
+
+ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tri, uint64_t p_begin,
+                              uint64_t p_end, int64_t ldo, void* n3, int count_bits,
+                              cudaStream_t st) {
+  const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)B->n * JTP * sizeof(uint16_t);
+  KTAU_CUDA(cudaFuncSetAttribute(joint_ties_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  int64_t w = 0, ncb = 0, lo = 0, hi = 0;
+  if (tri) {
+    const int64_t m = A->m;
+    w = (m + JT - 1) / JT;
+    int64_t i0, j0, i1, j1;
+    ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
+    ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
+    lo = ktau_rowstart(w, i0 / JT);
+    hi = ktau_rowstart(w, i1 / JT + 1);
+  } else {
+    ncb = (B->m + JT - 1) / JT;
+    hi = ((A->m + JT - 1) / JT) * ncb;
+  }
+  int occ = 0;
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, joint_ties_kernel, 256, smem));
+  int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
+  if (grid > hi - lo) grid = hi - lo;
+  if (grid < 1) grid = 1;
+  joint_ties_kernel<<<(unsigned)grid, 256, smem, st>>>(side_of(A), side_of(B), A->n, tri, w, ncb,
+                                                       lo, hi, p_begin, p_end, ldo, n3,
+                                                       count_bits);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
 }
 
 template <int ESIZE>
@@ -632,11 +768,15 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   int64_t i0, j0, i1, j1;
   ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
   ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
-  a.unit_lo = 2 * ktau_rowstart(a.wS, i0 / 256);
-  a.unit_hi = 2 * ktau_rowstart(a.wS, i1 / 256 + 1);
+  a.wG = (a.wS + GROUP - 1) / GROUP;
+  a.unit_lo = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i0 / 256 / GROUP);
+  a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / 256 / GROUP + 1);
   const int64_t units = a.unit_hi - a.unit_lo;
-  return R->esize == 1 ? launch_contract<1>(R, R, a, units, st)
-                       : launch_contract<2>(R, R, a, units, st);
+  a.out.n3 = nullptr;
+  s = R->esize == 1 ? launch_contract<1>(R, R, a, units, st) : launch_contract<2>(R, R, a, units, st);
+  if (s == KTAU_OK && out.n3)
+    s = launch_joint_ties(R, R, 1, p_begin, p_end, 0, out.n3, out.count_bits, st);
+  return s;
 }
 
 ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
@@ -652,6 +792,7 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.num_kb = Q->K_pad * Q->esize / BKB;
   a.tri = 0;
   a.wS = 0;
+  a.wG = 0;
   a.ncb = (D->m + BN - 1) / BN;
   a.p_begin = 0;
   a.p_end = 0;
@@ -659,8 +800,11 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.out = out;
   a.unit_lo = 0;
   a.unit_hi = ((Q->m + BM - 1) / BM) * a.ncb;
-  return Q->esize == 1 ? launch_contract<1>(Q, D, a, a.unit_hi, st)
-                       : launch_contract<2>(Q, D, a, a.unit_hi, st);
+  a.out.n3 = nullptr;
+  s = Q->esize == 1 ? launch_contract<1>(Q, D, a, a.unit_hi, st)
+                    : launch_contract<2>(Q, D, a, a.unit_hi, st);
+  if (s == KTAU_OK && out.n3) s = launch_joint_ties(Q, D, 0, 0, 0, ldo, out.n3, out.count_bits, st);
+  return s;
 }
 
 void ktau_signgemm_release(ktau_ranked* R) {
