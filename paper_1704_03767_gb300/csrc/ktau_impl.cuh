@@ -136,6 +136,27 @@ __device__ __forceinline__ float ktau_tau32(int64_t S, float2 fu, float2 fv, int
   return __double2float_rn(ktau_tau_b_formula(S, n0 - Tu, n0 - Tv));
 }
 
+// Fast part of ktau_tau32 (the float-float product and the boundary test) for a non-NaN
+// variable pair; returns false when the slow FP64 formula is needed.
+__device__ __forceinline__ bool ktau_tau32_fast(int S, float2 fu, float2 fv, float& out) {
+  const float sh = __int2float_rn(S);
+  const float sl = __int2float_rn(S - __float2int_rn(sh));
+  const float th = __fmul_rn(sh, fu.x);
+  const float tl = __fadd_rn(__fmaf_rn(sh, fu.x, -th), __fmaf_rn(sh, fu.y, __fmul_rn(sl, fu.x)));
+  const float ph = __fmul_rn(th, fv.x);
+  const float pl = __fadd_rn(__fmaf_rn(th, fv.x, -ph), __fmaf_rn(th, fv.y, __fmul_rn(tl, fv.x)));
+  const float f = __fadd_rn(ph, pl);
+  const float d = __fadd_rn(__fsub_rn(ph, f), pl);
+  const uint32_t fb = __float_as_uint(fabsf(f));
+  float half = __uint_as_float(((fb >> 23) - 24u) << 23);
+  if ((fb & 0x7fffffu) == 0) half = __fmul_rn(half, 0.5f);
+  const float margin = __fadd_rn(__fmul_rn(fabsf(f), 0x1p-40f), __fmul_rn(fabsf(d), 0x1p-22f));
+  out = S == 0 ? 0.0f : f;
+  // NaN factors (constant variables) take the slow path, which returns NaN.
+  if (isnan(fu.x) || isnan(fv.x)) return false;
+  return S == 0 || __fadd_rn(fabsf(d), margin) < half;
+}
+
 struct ktau_fac {
   const double* rs64;
   const float2* rsff;

@@ -326,9 +326,10 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
 // JT x JT variable pairs; the column variables' ranks are staged transposed in shared memory
 // (rT[a][j]) so that, for each tied pair (a, b) of a row variable, the 32 lanes of a warp check 32
 // column variables with conflict-free loads. Writes every n_3 of the range (zeros included).
-constexpr int JT = 64;
-constexpr int JTP = JT + 1;  // padded row (uint16) of the transposed rank block
-constexpr int JCAP = 4096;  // tie pairs of one tile's rows staged in shared memory
+constexpr int JT = 256;      // tile side (rows and columns) walked through the bijection
+constexpr int JC = 64;       // columns staged at a time
+constexpr int JTP = JC + 1;  // padded row (uint16) of the transposed rank block
+constexpr int JCAP = 8192;   // tie pairs of one tile's rows staged in shared memory
 
 __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const SideArgs C,
                                                          int64_t n, int tri, int64_t w,
@@ -341,6 +342,7 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
   int* s_off = (int*)(jsm + JCAP);                             // [JT + 1], relative offsets
   uint16_t* rT = (uint16_t*)(jsm + JCAP + JT + 8);             // [n][JTP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
     int64_t y0, x0;
     if (tri) {
@@ -357,56 +359,62 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
     const int64_t seg = R.tie_off[y0 + rows] - base_off;
     const bool staged = seg <= JCAP;
     __syncthreads();
-    // Stage the JT column variables' rank rows transposed, 8 ranks (16 bytes) per load, the
-    // row variables' tie-list offsets, and (when it fits) their tie pairs.
-    const int vec = (int)(C.ld >> 3);
-    for (int e = threadIdx.x; e < JT * vec; e += blockDim.x) {
-      const int j = e / vec, c8 = e - j * vec;
-      const int64_t v = x0 + j;
-      uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
-      if (v < C.m) w4 = __ldg(reinterpret_cast<const uint4*>(C.rank + v * C.ld) + c8);
-      const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-      for (int h = 0; h < 8; ++h) {
-        const int aa = c8 * 8 + h;
-        if (aa < n) rT[aa * JTP + j] = (uint16_t)(wd[h >> 1] >> (16 * (h & 1)));
-      }
-    }
     for (int i = threadIdx.x; i <= rows; i += blockDim.x)
       s_off[i] = (int)(R.tie_off[y0 + i] - base_off);
     if (staged)
       for (int64_t i = threadIdx.x; i < seg; i += blockDim.x) s_pairs[i] = R.tie_pairs[base_off + i];
-    __syncthreads();
     const uint32_t* plist = staged ? s_pairs : R.tie_pairs + base_off;
-    for (int i = warp; i < rows; i += blockDim.x / 32) {
-      const int64_t y = y0 + i;
-      const int e0 = s_off[i], e1 = s_off[i + 1];
-      int c0 = 0, c1 = 0;
-      for (int e = e0; e < e1; ++e) {
-        const uint32_t ab = plist[e];
-        const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
-        c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
-        c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
-      }
-      const int64_t rowbase = tri ? y * (2 * R.m - y - 1) / 2 - y - 1 : y * ldo;
+    for (int cs = 0; cs < JT / JC; ++cs) {
+      const int64_t xs = x0 + cs * JC;
+      if (xs >= C.m) break;
+      if (tri && xs + JC - 1 <= y0) continue;  // sub-block entirely on or below the diagonal
+      __syncthreads();
+      // Stage the JC column variables' rank rows transposed, 8 ranks (16 bytes) per load.
+      const int vec = (int)(C.ld >> 3);
+      for (int e = threadIdx.x; e < JC * vec; e += blockDim.x) {
+        const int j = e / vec, c8 = e - j * vec;
+        const int64_t v = xs + j;
+        uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+        if (v < C.m) w4 = __ldg(reinterpret_cast<const uint4*>(C.rank + v * C.ld) + c8);
+        const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t v = x0 + lane + 32 * h;
-        if (v >= C.m) continue;
-        uint64_t k;
-        if (tri) {
-          if (v <= y) continue;
-          const uint64_t p = (uint64_t)(rowbase + v);
-          if (p < p_begin || p >= p_end) continue;
-          k = p - p_begin;
-        } else {
-          k = (uint64_t)(rowbase + v);
+        for (int h = 0; h < 8; ++h) {
+          const int aa = c8 * 8 + h;
+          if (aa < n) rT[aa * JTP + j] = (uint16_t)(wd[h >> 1] >> (16 * (h & 1)));
         }
-        const int val = h ? c1 : c0;
-        if (count_bits == 64)
-          __stcs((long long*)n3out + k, (long long)val);
-        else
-          __stcs((int*)n3out + k, val);
+      }
+      __syncthreads();
+      const int rows_here = tri ? (int)min((int64_t)rows, xs + JC - 1 - y0) : rows;
+      for (int i = warp; i < rows_here; i += nwarps) {
+        const int64_t y = y0 + i;
+        const int e0 = s_off[i], e1 = s_off[i + 1];
+        int c0 = 0, c1 = 0;
+        for (int e = e0; e < e1; ++e) {
+          const uint32_t ab = plist[e];
+          const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
+          c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
+          c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+        }
+        const int64_t rowbase = tri ? y * (2 * R.m - y - 1) / 2 - y - 1 : y * ldo;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t v = xs + lane + 32 * h;
+          if (v >= C.m) continue;
+          uint64_t k;
+          if (tri) {
+            if (v <= y) continue;
+            const uint64_t p = (uint64_t)(rowbase + v);
+            if (p < p_begin || p >= p_end) continue;
+            k = p - p_begin;
+          } else {
+            k = (uint64_t)(rowbase + v);
+          }
+          const int val = h ? c1 : c0;
+          if (count_bits == 64)
+            __stcs((long long*)n3out + k, (long long)val);
+          else
+            __stcs((int*)n3out + k, val);
+        }
       }
     }
   }
@@ -546,12 +554,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       // Per-row data of this warp's 32 rows, one row per lane (broadcast by shuffle below).
       const int64_t my_y = ybase + lane;
       const bool my_row_ok = my_y < mrow;
-      const double my_r64 = my_row_ok ? __ldg(a.row.rs64 + my_y) : 0.0;
       const float2 my_rff = my_row_ok ? __ldg(a.row.rsff + my_y) : make_float2(0.f, 0.f);
-      const long long my_T = my_row_ok ? __ldg((const long long*)a.row.T + my_y) : 0;
       const long long my_base =
           a.tri ? (long long)(my_y * (2 * mrow - my_y - 1) / 2 - my_y - 1) : (long long)my_y * a.ldo;
       const int rows_here = (int)min((int64_t)32, mrow - ybase);
+      // Whole 32 x 32 blocks strictly above the diagonal, inside the matrix and inside the pair
+      // range need no per-element checks.
+      bool range_all = true;
+      if (a.tri) {
+        const int64_t ylast = ybase + rows_here - 1;
+        range_all = (uint64_t)(ybase * (2 * mrow - ybase - 1) / 2) >= a.p_begin &&
+                    (uint64_t)(ylast * (2 * mrow - ylast - 1) / 2 + (mrow - ylast - 1)) <= a.p_end;
+      }
       for (int c = half_sel * (BN / 64); c < (half_sel + 1) * (BN / 64); ++c) {
         uint32_t r[32];
         tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
@@ -563,37 +577,60 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) tb[lane * TRS + j] = __float2int_rn(__uint_as_float(r[j]));
         __syncwarp();
-        const int64_t v = t.x0 + 32 * c + lane;
+        const int64_t xc = t.x0 + 32 * c;
+        const int64_t v = xc + lane;
         const bool vin = v < mcol;
-        const double c_r64 = vin ? __ldg(a.col.rs64 + v) : 0.0;
         const float2 c_rff = vin ? __ldg(a.col.rsff + v) : make_float2(0.f, 0.f);
-        const long long c_T = vin ? __ldg((const long long*)a.col.T + v) : 0;
+        const bool fast = range_all && rows_here == 32 && xc + 32 <= mcol &&
+                          (!a.tri || xc > ybase + 31);
+        if (fast && want32 && !want64) {
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          const double r64 = __shfl_sync(0xffffffffu, my_r64, i);
-          const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
-          const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
-          const long long Tu = __shfl_sync(0xffffffffu, my_T, i);
-          const long long base = __shfl_sync(0xffffffffu, my_base, i);
-          const int64_t y = ybase + i;
-          if (i >= rows_here || !vin) continue;
-          uint64_t k;
-          if (a.tri) {
-            if (v <= y) continue;
-            const uint64_t p = (uint64_t)(base + v);
-            if (p < a.p_begin || p >= a.p_end) continue;
-            k = p - a.p_begin;
-          } else {
-            k = (uint64_t)(base + v);
+          for (int i = 0; i < 32; ++i) {
+            const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
+            const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
+            const long long base = __shfl_sync(0xffffffffu, my_base, i);
+            const uint64_t k = (uint64_t)(base + v) - a.p_begin;
+            const int S = tb[i * TRS + lane];
+            float tv;
+            if (!ktau_tau32_fast(S, make_float2(rhi, rlo), c_rff, tv)) {
+              const int64_t y = ybase + i;
+              tv = ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, a.row.T[y], a.col.T[v]);
+            }
+            __stcs(a.out.tau32 + k, tv);
+            if (wantS) {
+              if (s64)
+                __stcs((long long*)a.out.S + k, (long long)S);
+              else
+                __stcs((int*)a.out.S + k, S);
+            }
           }
-          const int S = tb[i * TRS + lane];
-          if (want64) __stcs(a.out.tau64 + k, ktau_tau64(S, r64, c_r64));
-          if (want32) __stcs(a.out.tau32 + k, ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, Tu, c_T));
-          if (wantS) {
-            if (s64)
-              __stcs((long long*)a.out.S + k, (long long)S);
-            else
-              __stcs((int*)a.out.S + k, S);
+        } else {
+          for (int i = 0; i < 32; ++i) {
+            const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
+            const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
+            const long long base = __shfl_sync(0xffffffffu, my_base, i);
+            const int64_t y = ybase + i;
+            if (i >= rows_here || !vin) continue;
+            uint64_t k;
+            if (a.tri) {
+              if (v <= y) continue;
+              const uint64_t p = (uint64_t)(base + v);
+              if (p < a.p_begin || p >= a.p_end) continue;
+              k = p - a.p_begin;
+            } else {
+              k = (uint64_t)(base + v);
+            }
+            const int S = tb[i * TRS + lane];
+            if (want64) __stcs(a.out.tau64 + k, ktau_tau64(S, a.row.rs64[y], a.col.rs64[v]));
+            if (want32)
+              __stcs(a.out.tau32 + k,
+                     ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, a.row.T[y], a.col.T[v]));
+            if (wantS) {
+              if (s64)
+                __stcs((long long*)a.out.S + k, (long long)S);
+              else
+                __stcs((int*)a.out.S + k, S);
+            }
           }
         }
         __syncwarp();
@@ -658,6 +695,7 @@ ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tr
                               uint64_t p_end, int64_t ldo, void* n3, int count_bits,
                               cudaStream_t st) {
   const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)B->n * JTP * sizeof(uint16_t);
+  if (smem > 227 * 1024) return ktau_fail(KTAU_ETOOLARGE, "joint-ties staging too large");
   KTAU_CUDA(cudaFuncSetAttribute(joint_ties_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   int64_t w = 0, ncb = 0, lo = 0, hi = 0;
