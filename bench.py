@@ -233,6 +233,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     total_ms, kern_ms = 0.0, 0.0
+    ktau.ktau_trace_collect()
+    ktau.ktau_trace_enable(True)  # per-kernel CUDA events on the launching stream
     for _ in range(args.steps):
         flush.zero_()  # L2 flush between steps (256 MB write), outside the timed events
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -245,7 +247,15 @@ def run_ours(args):
         kern_ms += k0.elapsed_time(k1)
         R.free()
     clocks = sampler.stop()
+    ktau.ktau_trace_enable(False)
+    trace = ktau.ktau_trace_collect()
     ktau.ktau_device_status(stream)
+    per_kernel = {}
+    for name, ms in trace:
+        c, t = per_kernel.get(name, (0, 0.0))
+        per_kernel[name] = (c + 1, t + ms)
+    kernels = {k: {"launches": c, "avg_ms": t / c, "share": t / max(1e-9, sum(
+        x[1] for x in per_kernel.values()))} for k, (c, t) in per_kernel.items()}
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -261,6 +271,7 @@ def run_ours(args):
     if path_used == "merge":
         # Algorithmic work: n * ceil(log2 n) compare-and-count merge steps per pair (Step 3).
         steps_per_pair = N * 7
+        kern_avg_ms = kernels["merge_pairs_kernel"]["avg_ms"]
         achieved = P * steps_per_pair / (kern_avg_ms / 1e3) / 1e9
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         f = (clocks.get("sm_mhz") or 1455.0) * 1e6
@@ -273,6 +284,7 @@ def run_ours(args):
         # Algorithmic work of the contraction: n_0 multiply-adds (2 flops) per pair, FP8 e4m3
         # operands; peak = measured dense BF16 rate x 2 (FP8/BF16 nominal ratio).
         flops = 2.0 * P * (N * (N - 1) // 2)
+        kern_avg_ms = kernels["contract_kernel"]["avg_ms"]
         achieved = flops / (kern_avg_ms / 1e3) / 1e12
         bf16 = (peaks or {}).get("bf16_tflops", 1921.4)
         peak = 2.0 * bf16
@@ -319,7 +331,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "m": M, "n": N, "pairs": P, "path": path_used,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{world} independent shards (one matrix per GPU)"},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": len(trace),
+        "kernels": kernels,
         "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "sample_comparisons_per_s": value * (N * (N - 1) // 2),
     }

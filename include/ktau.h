@@ -142,14 +142,25 @@ ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, in
 
 /* Builds the tensor-core operands of a handle now instead of on first use: the sign expansion
  * A_u[k] = sign(u_a - u_b) over all sample pairs (Sec. 3.1, Algorithm 1), stored as FP8 e4m3 for
- * n <= 128 and BF16 above (library memory, m * n_0 elements rounded up), plus per-variable lists of
- * tied sample pairs for n_3. Synchronises `stream`. EINVAL when n > 1024 (path unsupported). */
+ * n <= 128 and BF16 above (library memory, m * n_0 elements rounded up). Asynchronous on `stream`
+ * (allocates on first use). EINVAL when n > 1024 (path unsupported). */
 ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
 
 /* Synchronises `stream` and reports whether a bounded device-side wait of a tensor-core kernel
  * gave up since the last call (KTAU_ETIMEOUT, the results of that launch are invalid), then
  * clears the flag. KTAU_OK otherwise. */
 ktau_status ktau_device_status(void* stream);
+
+/* Kernel trace: when enabled, every kernel the library launches is bracketed by CUDA events on
+ * its stream (no extra synchronisation). ktau_trace_collect waits for the recorded launches,
+ * copies up to `cap` records (kernel name, milliseconds, in launch order) and clears the list.
+ * Tracing must be off while a stream is being captured into a CUDA graph. */
+typedef struct {
+  char name[48];
+  float ms;
+} ktau_trace_record;
+ktau_status ktau_trace_enable(int32_t on);
+ktau_status ktau_trace_collect(ktau_trace_record* out, int32_t cap, int32_t* count);
 
 /*
  * Batched form: many independent matrices of uneven m and n processed by one persistent

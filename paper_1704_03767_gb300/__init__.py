@@ -28,5 +28,7 @@ from .binding import (  # noqa: F401
     ktau_rank_prepare,
     ktau_ranked_export,
     ktau_tie_counts,
+    ktau_trace_collect,
+    ktau_trace_enable,
     load,
 )

@@ -37,6 +37,10 @@ class Options(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
+class TraceRecord(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("ms", ctypes.c_float)]
+
+
 class BatchDesc(ctypes.Structure):
     _fields_ = [("values", ctypes.c_void_p), ("dtype", ctypes.c_int32),
                 ("count_bits", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
@@ -61,6 +65,9 @@ _SIGS = {
     "ktau_allpairs_path": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(_i32)], ctypes.c_int),
     "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
     "ktau_device_status": ([_vp], ctypes.c_int),
+    "ktau_trace_enable": ([_i32], ctypes.c_int),
+    "ktau_trace_collect": ([ctypes.POINTER(TraceRecord), _i32, ctypes.POINTER(_i32)],
+                           ctypes.c_int),
     "ktau_batch_create": ([ctypes.POINTER(BatchDesc), _i32, ctypes.POINTER(Options),
                            ctypes.POINTER(_vp)], ctypes.c_int),
     "ktau_batch_run": ([_vp, _vp], ctypes.c_int),
@@ -203,6 +210,18 @@ def ktau_prepare_signs(R: Ranked, stream=None):
 
 def ktau_device_status(stream=None):
     _check(load().ktau_device_status(_stream(stream)))
+
+
+def ktau_trace_enable(on: bool = True):
+    _check(load().ktau_trace_enable(1 if on else 0))
+
+
+def ktau_trace_collect(cap: int = 65536):
+    """List of (kernel name, milliseconds) for the launches recorded since the last collect."""
+    arr = (TraceRecord * cap)()
+    n = ctypes.c_int32()
+    _check(load().ktau_trace_collect(arr, cap, ctypes.byref(n)))
+    return [(arr[i].name.decode(), float(arr[i].ms)) for i in range(n.value)]
 
 
 def allpairs(values: torch.Tensor, p_begin: int = 0, p_end: int | None = None,

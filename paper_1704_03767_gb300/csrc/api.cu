@@ -302,3 +302,65 @@ extern "C" ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream) {
 extern "C" ktau_status ktau_device_status(void* stream) {
   return ktau_signgemm_check_error((cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------------------------
+// Kernel trace
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct TraceRec {
+  char name[48];
+  cudaEvent_t e0, e1;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRec>* g_trace = new std::vector<TraceRec>();
+}  // namespace
+
+ktau_trace_scope::ktau_trace_scope(const char* name, cudaStream_t s) : slot(-1), st(s) {
+  if (!g_trace_on) return;
+  TraceRec r;
+  snprintf(r.name, sizeof(r.name), "%s", name);
+  if (cudaEventCreate(&r.e0) != cudaSuccess) return;
+  if (cudaEventCreate(&r.e1) != cudaSuccess) {
+    cudaEventDestroy(r.e0);
+    return;
+  }
+  cudaEventRecord(r.e0, s);
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  slot = (int)g_trace->size();
+  g_trace->push_back(r);
+}
+
+ktau_trace_scope::~ktau_trace_scope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (slot < (int)g_trace->size()) cudaEventRecord((*g_trace)[slot].e1, st);
+}
+
+extern "C" ktau_status ktau_trace_enable(int32_t on) {
+  g_trace_on = on != 0;
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_trace_collect(ktau_trace_record* out, int32_t cap, int32_t* count) {
+  std::vector<TraceRec> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    recs.swap(*g_trace);
+  }
+  int32_t n = 0;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.e1);
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    if (out && n < cap) {
+      memcpy(out[n].name, r.name, sizeof(r.name));
+      out[n].ms = ms;
+    }
+    ++n;
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  if (count) *count = n < cap ? n : cap;
+  return KTAU_OK;
+}

@@ -51,12 +51,13 @@ struct ktau_ranked {
   int esize;
   int sg_ready;
   alignas(64) unsigned char tmap[128];
-  // Tie-pair lists for n_3 in the tensor-core path (CSR: tie_off[m+1], tie_pairs[sum T] with
-  // (a << 16) | b for every sample pair a < b tied in the variable), built with the expansion.
-  uint32_t* tie_pairs;
+  size_t sgn_bytes;
+  // Lists of tied sample pairs for n_3 (tie_off[m+1] = prefix of T, tie_pairs[(a << 16) | b]);
+  // a variable is listed when its list ends within tie_cap entries.
   int64_t* tie_off;
-  int64_t tie_total;
-  size_t sgn_bytes, tie_bytes;
+  uint32_t* tie_pairs;
+  int64_t tie_cap;
+  size_t tie_bytes;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -69,6 +70,15 @@ int ktau_sm_count();
 // handles created and released every step do not pay cudaMalloc/cudaFree (which synchronises).
 ktau_status ktau_dmalloc(void** p, size_t bytes);
 void ktau_dfree(void* p, size_t bytes);
+
+// Kernel trace (ktau_trace_enable): events around each launch when enabled.
+struct ktau_trace_scope {
+  int slot;
+  cudaStream_t st;
+  ktau_trace_scope(const char* name, cudaStream_t s);
+  ~ktau_trace_scope();
+};
+#define KTAU_TRACE(name, stream) ktau_trace_scope ktau_trace_scope_##__LINE__(name, stream)
 
 #define KTAU_CUDA(call)                                                   \
   do {                                                                    \

@@ -276,6 +276,7 @@ ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas
   int64_t grid = (int64_t)occ * ktau_sm_count();
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
+  KTAU_TRACE("merge_pairs_kernel", st);
   kern<<<(unsigned)grid, threads, smem, st>>>(args);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;

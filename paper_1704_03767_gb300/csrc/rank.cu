@@ -176,6 +176,7 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
   if (m > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "m too large for one launch");
   auto kern = dtype == KTAU_F32 ? rank_kernel<KTAU_F32> : rank_kernel<KTAU_I32>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KTAU_TRACE("rank_kernel", st);
   kern<<<(unsigned)m, threads, smem, st>>>(values, ld_in, (int)n, np2, R->ld, R->perm, R->rank,
                                             R->srank, R->T, R->ndist, R->maxg, R->rs64, R->rsff,
                                             R->stats_dev);

@@ -4,7 +4,6 @@
 //   sign_expand_kernel : A_u[k] = sign(r_u[a] - r_u[b]) for the k-th sample pair (a < b, row-major
 //                        order over the strict upper triangle of the n x n sample-pair matrix),
 //                        encoded as FP8 e4m3 (+1 = 0x38, -1 = 0xB8) or BF16, zero padded to K_pad.
-//   tie_pairs_kernel   : CSR list of the sample pairs tied in each variable (for n_3).
 //   contract_kernel    : persistent, warp-specialised tcgen05 GEMM S = A A^T over the upper
 //                        triangle (or Q D^T for queries). 128 x 256 output tiles; super-tiles of
 //                        256 x 256 are walked through the job-id bijection of Sec. 4.1 (Eq. 13-14)
@@ -12,7 +11,8 @@
 //                        warp 0: TMA producer (cp.async.bulk.tensor, 128B swizzle, 4-stage ring)
 //                        warp 1: TMEM allocation + single-thread tcgen05.mma issue
 //                        warps 2-5: epilogue, tcgen05.ld of the FP32 accumulator (exact integers),
-//                                   n_3 from tie lists, tau-b, coalesced stores through smem.
+//                                   tau-b, coalesced stores through smem.
+//   joint_ties_kernel  : n_3 for every pair from the variables' tie groups (see below).
 //                        Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile run
 //                        under the MMAs of the next. Every mbarrier wait is bounded (about 2 s);
 //                        on timeout the kernel raises an error word and every role winds down.
@@ -106,33 +106,6 @@ __global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __rest
       words[0] = words[1] = words[2] = words[3] = 0u;
     }
     reinterpret_cast<uint4*>(orow)[c] = make_uint4(words[0], words[1], words[2], words[3]);
-  }
-}
-
-// One thread per variable: every pair of positions inside a tie group of the sorted order.
-__global__ void tie_pairs_kernel(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
-                                 int64_t ld, int n, int64_t m, const int64_t* __restrict__ off,
-                                 uint32_t* __restrict__ pairs) {
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= m) return;
-  const uint16_t* p = perm + row * ld;
-  const uint16_t* s = srank + row * ld;
-  int64_t o = off[row];
-  int start = 0;
-  for (int k = 1; k < n; ++k) {
-    if (s[k] != s[k - 1]) {
-      start = k;
-      continue;
-    }
-    for (int j = start; j < k; ++j) {
-      uint32_t a = p[j], b = p[k];
-      if (a > b) {
-        uint32_t t = a;
-        a = b;
-        b = t;
-      }
-      pairs[o++] = (a << 16) | b;
-    }
   }
 }
 
@@ -255,12 +228,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // ---------------------------------------------------------------------------------------------
 struct SideArgs {  // per-variable data of the row side (u) or the column side (v)
   const uint16_t* rank;
+  const uint16_t* perm;
+  const uint16_t* srank;
   int64_t ld;
   const int64_t* T;
   const double* rs64;
   const float2* rsff;
-  const int64_t* tie_off;
-  const uint32_t* tie_pairs;
+  const int64_t* tie_off;     // [m + 1] prefix of T
+  const uint32_t* tie_pairs;  // listed tied pairs, (a << 16) | b
+  int64_t tie_cap;            // a variable is listed iff tie_off[v] + T[v] <= tie_cap
   int64_t m;
 };
 
@@ -322,15 +298,99 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
   return r;
 }
 
-// n_3(u, v) = number of sample pairs tied in u that are also tied in v (Table 1). Tiles of
-// JT x JT variable pairs; the column variables' ranks are staged transposed in shared memory
-// (rT[a][j]) so that, for each tied pair (a, b) of a row variable, the 32 lanes of a warp check 32
-// column variables with conflict-free loads. Writes every n_3 of the range (zeros included).
 constexpr int JT = 256;      // tile side (rows and columns) walked through the bijection
 constexpr int JC = 64;       // columns staged at a time
 constexpr int JTP = JC + 1;  // padded row (uint16) of the transposed rank block
-constexpr int JCAP = 8192;   // tie pairs of one tile's rows staged in shared memory
+constexpr int JCAP = 8192;   // tied sample pairs of one tile's rows listed in shared memory
 
+// Tied sample pairs of variable y (sorted order: tie groups are runs of equal srank), written
+// to out[0 .. T_y) by one warp. Position k of a group starting at g0 pairs with g0 .. k-1.
+__device__ void warp_list_ties(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
+                               int n, uint32_t* out, int lane) {
+  int run = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    int cnt = 0, g0 = 0;
+    if (k > 0 && k < n && srank[k] == srank[k - 1]) {
+      const uint16_t key = srank[k];
+      int lo = 0, hi = k;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (srank[mid] < key)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      g0 = lo;
+      cnt = k - g0;
+    }
+    int incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int off = run + incl - cnt;
+    if (cnt) {
+      const uint32_t b = perm[k];
+      for (int j = 0; j < cnt; ++j) {
+        uint32_t a = perm[g0 + j], bb = b;
+        if (a > bb) {
+          const uint32_t t = a;
+          a = bb;
+          bb = t;
+        }
+        out[off + j] = (a << 16) | bb;
+      }
+    }
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// Exclusive prefix of the tie counts T over m variables (one CTA): off[i] = sum_{r<i} T[r].
+// A variable's list is stored only when it ends within `cap` entries; the others are walked
+// from their tie groups directly by the joint-ties kernel (same test on both sides).
+__global__ void __launch_bounds__(1024) ties_scan_kernel(const int64_t* __restrict__ T, int64_t m,
+                                                         int64_t* __restrict__ off) {
+  __shared__ long long wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t per = (m + blockDim.x - 1) / blockDim.x;
+  const int64_t b = min(m, tid * per), e = min(m, b + per);
+  long long local = 0;
+  for (int64_t i = b; i < e; ++i) local += T[i];
+  long long incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  long long before = 0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  long long run = before + incl - local;
+  for (int64_t i = b; i < e; ++i) {
+    off[i] = run;
+    run += T[i];
+  }
+  if (e == m && b < e) off[m] = run;
+  if (m == 0 && tid == 0) off[0] = 0;
+}
+
+__global__ void ties_list_kernel(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
+                                 const int64_t* __restrict__ T, const int64_t* __restrict__ off,
+                                 int64_t ld, int n, int64_t m, int64_t cap,
+                                 uint32_t* __restrict__ pairs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (row >= m) return;
+  if (T[row] == 0 || off[row] + T[row] > cap) return;
+  warp_list_ties(perm + row * ld, srank + row * ld, n, pairs + off[row], lane);
+}
+
+// n_3(u, v) = number of sample pairs tied in u that are also tied in v (Table 1). Square JT x JT
+// tiles of the job matrix (bijection, Eq. 13-14); the tied pairs of the tile's row variables are
+// listed in shared memory, and the column variables' ranks are staged transposed (rT[a][j]) 64
+// at a time so that, for each tied pair (a, b), the 32 lanes of a warp check 32 column variables
+// with conflict-free loads. Writes every n_3 of the range (zeros included).
 __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const SideArgs C,
                                                          int64_t n, int tri, int64_t w,
                                                          int64_t ncb, int64_t tile_lo,
@@ -339,7 +399,7 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
                                                          int count_bits) {
   extern __shared__ uint32_t jsm[];
   uint32_t* s_pairs = jsm;                                     // [JCAP]
-  int* s_off = (int*)(jsm + JCAP);                             // [JT + 1], relative offsets
+  int* s_off = (int*)(jsm + JCAP);                             // [JT + 1], tile-relative offsets
   uint16_t* rT = (uint16_t*)(jsm + JCAP + JT + 8);             // [n][JTP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
@@ -355,15 +415,15 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
       x0 = (t % ncb) * JT;
     }
     const int rows = (int)min((int64_t)JT, R.m - y0);
+    __syncthreads();
+    // The tile rows' lists are one contiguous segment of the global list (when all are listed).
     const int64_t base_off = R.tie_off[y0];
     const int64_t seg = R.tie_off[y0 + rows] - base_off;
-    const bool staged = seg <= JCAP;
-    __syncthreads();
+    const bool listed = R.tie_off[y0 + rows] <= R.tie_cap && seg <= JCAP;
     for (int i = threadIdx.x; i <= rows; i += blockDim.x)
-      s_off[i] = (int)(R.tie_off[y0 + i] - base_off);
-    if (staged)
+      s_off[i] = (int)min(R.tie_off[y0 + i] - base_off, (int64_t)JCAP);
+    if (listed)
       for (int64_t i = threadIdx.x; i < seg; i += blockDim.x) s_pairs[i] = R.tie_pairs[base_off + i];
-    const uint32_t* plist = staged ? s_pairs : R.tie_pairs + base_off;
     for (int cs = 0; cs < JT / JC; ++cs) {
       const int64_t xs = x0 + cs * JC;
       if (xs >= C.m) break;
@@ -387,13 +447,39 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
       const int rows_here = tri ? (int)min((int64_t)rows, xs + JC - 1 - y0) : rows;
       for (int i = warp; i < rows_here; i += nwarps) {
         const int64_t y = y0 + i;
-        const int e0 = s_off[i], e1 = s_off[i + 1];
         int c0 = 0, c1 = 0;
-        for (int e = e0; e < e1; ++e) {
-          const uint32_t ab = plist[e];
-          const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
-          c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
-          c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+        if (listed) {
+          for (int e = s_off[i]; e < s_off[i + 1]; ++e) {
+            const uint32_t ab = s_pairs[e];
+            const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
+            c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
+            c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+          }
+        } else if (R.T[y] > 0 && R.tie_off[y] + R.T[y] <= R.tie_cap) {
+          const uint32_t* tp = R.tie_pairs + R.tie_off[y];
+          for (long long e = 0; e < R.T[y]; ++e) {
+            const uint32_t ab = tp[e];
+            const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
+            c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
+            c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+          }
+        } else if (R.T[y] > 0) {
+          // Not listed (capacity): walk the tie groups of y in its sorted order directly.
+          const uint16_t* pp = R.perm + y * R.ld;
+          const uint16_t* ss = R.srank + y * R.ld;
+          int g0 = 0;
+          for (int k = 1; k < n; ++k) {
+            if (ss[k] != ss[k - 1]) {
+              g0 = k;
+              continue;
+            }
+            const int b = pp[k];
+            for (int j = g0; j < k; ++j) {
+              const int a = pp[j];
+              c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
+              c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+            }
+          }
         }
         const int64_t rowbase = tri ? y * (2 * R.m - y - 1) / 2 - y - 1 : y * ldo;
 #pragma unroll
@@ -688,7 +774,8 @@ ktau_status make_tmap(ktau_ranked* R) {
 }
 
 SideArgs side_of(const ktau_ranked* R) {
-  return SideArgs{R->rank, R->ld, R->T, R->rs64, R->rsff, R->tie_off, R->tie_pairs, R->m};
+  return SideArgs{R->rank,    R->perm,      R->srank,   R->ld, R->T, R->rs64, R->rsff,
+                  R->tie_off, R->tie_pairs, R->tie_cap, R->m};
 }
 
 ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tri, uint64_t p_begin,
@@ -716,6 +803,7 @@ ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tr
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
   if (grid > hi - lo) grid = hi - lo;
   if (grid < 1) grid = 1;
+  KTAU_TRACE("joint_ties_kernel", st);
   joint_ties_kernel<<<(unsigned)grid, 256, smem, st>>>(side_of(A), side_of(B), A->n, tri, w, ncb,
                                                        lo, hi, p_begin, p_end, ldo, n3,
                                                        count_bits);
@@ -734,6 +822,7 @@ ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const Co
   if (grid < 1) grid = 1;
   const CUtensorMap* ta = reinterpret_cast<const CUtensorMap*>(A->tmap);
   const CUtensorMap* tb = reinterpret_cast<const CUtensorMap*>(B->tmap);
+  KTAU_TRACE("contract_kernel", st);
   kern<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(*ta, *tb, args);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
@@ -754,33 +843,33 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, cudaStream_t st) {
   R->sgn_bytes = (size_t)R->m * R->K_pad * R->esize;
   if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
   const size_t smem = (size_t)n * sizeof(uint16_t);
+  {
+  KTAU_TRACE("sign_expand_kernel", st);
   if (R->esize == 1)
     sign_expand_kernel<1><<<(unsigned)R->m, 256, smem, st>>>(R->rank, R->ld, (int)n, R->K,
                                                              R->K_pad, (uint8_t*)R->sgn);
   else
     sign_expand_kernel<2><<<(unsigned)R->m, 256, smem, st>>>(R->rank, R->ld, (int)n, R->K,
                                                              R->K_pad, (uint8_t*)R->sgn);
+  }
   KTAU_CUDA(cudaGetLastError());
-  // Tie-pair lists: offsets from the per-variable tie counts (host scan), then one thread per
-  // variable writes its pairs.
-  std::vector<int64_t> T((size_t)R->m), off((size_t)R->m + 1);
-  KTAU_CUDA(cudaMemcpyAsync(T.data(), R->T, (size_t)R->m * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, st));
-  KTAU_CUDA(cudaStreamSynchronize(st));
-  off[0] = 0;
-  for (int64_t i = 0; i < R->m; ++i) off[(size_t)i + 1] = off[(size_t)i] + T[(size_t)i];
-  R->tie_total = off[(size_t)R->m];
-  R->tie_bytes = (size_t)(R->tie_total > 0 ? R->tie_total : 1) * 4;
+  // Lists of tied sample pairs for n_3: exact capacity from the rank statistics.
+  R->tie_cap = (int64_t)R->stats.T_sum;
+  R->tie_bytes = (size_t)(R->tie_cap > 0 ? R->tie_cap : 1) * 4;
   if (ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
       ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) != KTAU_OK)
     return KTAU_ENOMEM;
-  KTAU_CUDA(cudaMemcpyAsync(R->tie_off, off.data(), ((size_t)R->m + 1) * sizeof(int64_t),
-                            cudaMemcpyHostToDevice, st));
-  tie_pairs_kernel<<<(unsigned)((R->m + 127) / 128), 128, 0, st>>>(R->perm, R->srank, R->ld,
-                                                                   (int)n, R->m, R->tie_off,
-                                                                   R->tie_pairs);
+  {
+    KTAU_TRACE("ties_scan_kernel", st);
+    ties_scan_kernel<<<1, 1024, 0, st>>>(R->T, R->m, R->tie_off);
+  }
   KTAU_CUDA(cudaGetLastError());
-  KTAU_CUDA(cudaStreamSynchronize(st));  // host vectors above go out of scope
+  {
+    KTAU_TRACE("ties_list_kernel", st);
+    ties_list_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, st>>>(
+        R->perm, R->srank, R->T, R->tie_off, R->ld, (int)n, R->m, R->tie_cap, R->tie_pairs);
+  }
+  KTAU_CUDA(cudaGetLastError());
   ktau_status s = make_tmap(R);
   if (s != KTAU_OK) return s;
   R->sg_ready = 1;
@@ -849,9 +938,9 @@ void ktau_signgemm_release(ktau_ranked* R) {
   ktau_dfree(R->sgn, R->sgn_bytes);
   ktau_dfree(R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t));
   ktau_dfree(R->tie_pairs, R->tie_bytes);
-  R->sgn = nullptr;
   R->tie_off = nullptr;
   R->tie_pairs = nullptr;
+  R->sgn = nullptr;
   R->sg_ready = 0;
 }
 
