@@ -177,6 +177,8 @@ typedef struct {
   float* tau32;
   void* S;
   void* n3;
+  int32_t path;        /* ktau_path for this dataset; AUTO = opt->path, else by n (autotuner) */
+  int32_t reserved;
 } ktau_batch_desc;
 
 typedef struct ktau_batch ktau_batch;
@@ -189,7 +191,8 @@ ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t count, const
                               ktau_batch** out);
 /* Enqueues rank transform + all pairs of every dataset on `stream` (no allocation, no sync). */
 ktau_status ktau_batch_run(ktau_batch* B, void* stream);
-/* Same work through a CUDA graph captured on first use (on `stream`) and replayed after. */
+/* Same work through a CUDA graph captured on first use (on `stream`, which must not be the
+ * legacy default stream) and replayed after. */
 ktau_status ktau_batch_graph_launch(ktau_batch* B, void* stream);
 /* Synchronises `stream` and reports a NaN found in any dataset since the last check (ENAN). */
 ktau_status ktau_batch_check(ktau_batch* B, void* stream);

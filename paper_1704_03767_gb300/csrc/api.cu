@@ -318,6 +318,8 @@ std::vector<TraceRec>* g_trace = new std::vector<TraceRec>();
 
 ktau_trace_scope::ktau_trace_scope(const char* name, cudaStream_t s) : slot(-1), st(s) {
   if (!g_trace_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   TraceRec r;
   snprintf(r.name, sizeof(r.name), "%s", name);
   if (cudaEventCreate(&r.e0) != cudaSuccess) return;

@@ -1,0 +1,350 @@
+// Batched form: many independent matrices of uneven m and n in one persistent launch per
+// kernel family, capturable in a CUDA graph (generalises the tile/pass scheduling of
+// Sec. 4.2-4.3 from one job matrix to a list of job matrices).
+//
+// Plan (ktau_batch_create): every dataset gets a path (its descriptor, the options, or the
+// built-in crossover by n); datasets are laid out in one library-owned workspace grouped by path
+// -- FP8 contraction (n <= 128), BF16 contraction (n <= 1024), merge -- so each group's variables
+// are consecutive rows. Per group: a descriptor table in device memory and prefix sums of rows,
+// tiles and units. Contraction groups stack their sign expansions into one operand tensor (one
+// TMA descriptor per group, each dataset using only its own K blocks).
+//
+// Run (ktau_batch_run): rank kernel over every row of every dataset; per contraction group:
+// sign expansion, tie lists, contraction, joint ties; one merge launch over all merge tiles.
+// Nothing is allocated and nothing waits on the host, so the sequence can be graph-captured.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ktau_impl.cuh"
+#include "signgemm.cuh"
+
+namespace {
+
+constexpr int kMergeTq = 16;
+
+struct GroupPlan {
+  std::vector<int32_t> ids;  // indices into the workspace-ordered descriptor table
+  int32_t* d_ids = nullptr;
+  int64_t* d_row_prefix = nullptr;
+  int64_t* d_unit_prefix = nullptr;
+  int64_t* d_jt_prefix = nullptr;
+  int64_t* d_tile_prefix = nullptr;  // merge group
+  int64_t row0 = 0, rows = 0, units = 0, jt_tiles = 0, tiles = 0, max_n = 0, stride = 0;
+  int esize = 0;
+  void* sgn = nullptr;
+  int64_t* tie_off = nullptr;
+  uint32_t* tie_pairs = nullptr;
+  int64_t tie_cap = 0;
+  alignas(64) unsigned char tmap[128];
+};
+
+}  // namespace
+
+struct ktau_batch {
+  int count = 0;
+  int device = 0;
+  std::vector<ktau_bds> hds;  // workspace order
+  ktau_bds* d_ds = nullptr;
+  int64_t* d_row_prefix = nullptr;
+  int64_t total_rows = 0, max_n = 0;
+  uint64_t pairs = 0;
+  GroupPlan g[3];  // 0: FP8 contraction, 1: BF16 contraction, 2: merge
+  ktau_stats* d_stats = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static ktau_status batch_alloc(ktau_batch* B, void** p, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  ktau_status s = ktau_dmalloc(p, bytes);
+  if (s == KTAU_OK) B->allocs.push_back({*p, bytes});
+  return s;
+}
+
+template <class T>
+static ktau_status batch_upload(ktau_batch* B, T** dst, const std::vector<T>& v) {
+  ktau_status s = batch_alloc(B, (void**)dst, v.size() * sizeof(T));
+  if (s != KTAU_OK) return s;
+  if (!v.empty()) KTAU_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return KTAU_OK;
+}
+
+static int batch_path_for(const ktau_batch_desc& d, const ktau_options* opt) {
+  if (d.path != KTAU_PATH_AUTO) return d.path;
+  if (opt && opt->path != KTAU_PATH_AUTO) return opt->path;
+  // Crossover measured on GB300 (autotune.py): the contraction wins for short vectors.
+  return d.n <= 256 ? KTAU_PATH_SIGNGEMM : KTAU_PATH_MERGE;
+}
+
+ktau_status ktau_check_counts(int64_t n, int count_bits);
+ktau_status ktau_check_options(const ktau_options* opt);
+
+extern "C" ktau_status ktau_batch_free(ktau_batch* B) {
+  if (!B) return KTAU_OK;
+  cudaDeviceSynchronize();
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto& a : B->allocs) ktau_dfree(a.first, a.second);
+  delete B;
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t count,
+                                         const ktau_options* opt, ktau_batch** out) {
+  if (!out) return ktau_fail(KTAU_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!descs || count <= 0) return ktau_fail(KTAU_EINVAL, "need count > 0 descriptors");
+  ktau_status s = ktau_check_options(opt);
+  if (s != KTAU_OK) return s;
+  for (int i = 0; i < count; ++i) {
+    const ktau_batch_desc& d = descs[i];
+    if (!d.values) return ktau_fail(KTAU_EINVAL, "descriptor %d: values is NULL", i);
+    if (d.dtype != KTAU_F32 && d.dtype != KTAU_I32)
+      return ktau_fail(KTAU_EINVAL, "descriptor %d: bad dtype", i);
+    if (d.m < 2 || d.n < 2 || d.ld < d.n)
+      return ktau_fail(KTAU_EINVAL, "descriptor %d: need m >= 2, n >= 2, ld >= n", i);
+    if (d.n > KTAU_MAX_N || d.m > KTAU_MAX_M)
+      return ktau_fail(KTAU_ETOOLARGE, "descriptor %d: shape beyond the limits", i);
+    if ((s = ktau_check_counts(d.n, d.count_bits)) != KTAU_OK) return s;
+    if (d.path < 0 || d.path > 2) return ktau_fail(KTAU_EINVAL, "descriptor %d: bad path", i);
+    if (batch_path_for(d, opt) == KTAU_PATH_SIGNGEMM && d.n > KTAU_SIGNGEMM_MAX_N)
+      return ktau_fail(KTAU_EINVAL, "descriptor %d: contraction path needs n <= %d", i,
+                       KTAU_SIGNGEMM_MAX_N);
+  }
+  ktau_batch* B = new ktau_batch();
+  B->count = count;
+  cudaGetDevice(&B->device);
+  // Workspace order: FP8 contraction, BF16 contraction, merge.
+  std::vector<int> order;
+  std::vector<int> grp(count);
+  for (int i = 0; i < count; ++i) {
+    const int path = batch_path_for(descs[i], opt);
+    grp[i] = path == KTAU_PATH_MERGE ? 2 : (descs[i].n <= KTAU_SIGNGEMM_FP8_MAX_N ? 0 : 1);
+  }
+  for (int gi = 0; gi < 3; ++gi)
+    for (int i = 0; i < count; ++i)
+      if (grp[i] == gi) order.push_back(i);
+
+  // Per-dataset workspace sizes.
+  std::vector<int64_t> row_prefix(count + 1, 0);
+  size_t rank_bytes = 0;
+  std::vector<size_t> rank_off(count);
+  for (int k = 0; k < count; ++k) {
+    const ktau_batch_desc& d = descs[order[k]];
+    row_prefix[k + 1] = row_prefix[k] + d.m;
+    const int64_t ld = (d.n + 15) & ~15LL;
+    rank_off[k] = rank_bytes;
+    rank_bytes += (((size_t)d.m * ld * 2 + 255) & ~(size_t)255) * 3;
+    B->max_n = std::max<int64_t>(B->max_n, d.n);
+    B->pairs += (uint64_t)(d.m * (d.m - 1) / 2);
+  }
+  B->total_rows = row_prefix[count];
+  const int64_t R = B->total_rows;
+  char* ws = nullptr;
+  if ((s = batch_alloc(B, (void**)&ws, rank_bytes + (size_t)R * 32 + 4096)) != KTAU_OK) {
+    ktau_batch_free(B);
+    return s;
+  }
+  int64_t* T_all = (int64_t*)(ws + rank_bytes);
+  double* rs64_all = (double*)(T_all + R);
+  float2* rsff_all = (float2*)(rs64_all + R);
+  int32_t* ndist_all = (int32_t*)(rsff_all + R);
+  int32_t* maxg_all = ndist_all + R;
+
+  B->hds.resize(count);
+  for (int k = 0; k < count; ++k) {
+    const ktau_batch_desc& d = descs[order[k]];
+    ktau_bds& D = B->hds[k];
+    memset(&D, 0, sizeof(D));
+    D.values = d.values;
+    D.dtype = d.dtype;
+    D.count_bits = d.count_bits;
+    D.m = d.m;
+    D.n = d.n;
+    D.ld_in = d.ld;
+    D.ld = (d.n + 15) & ~15LL;
+    const size_t arr = ((size_t)d.m * D.ld * 2 + 255) & ~(size_t)255;
+    D.perm = (uint16_t*)(ws + rank_off[k]);
+    D.rank = (uint16_t*)(ws + rank_off[k] + arr);
+    D.srank = (uint16_t*)(ws + rank_off[k] + 2 * arr);
+    const int64_t r0 = row_prefix[k];
+    D.T = T_all + r0;
+    D.rs64 = rs64_all + r0;
+    D.rsff = rsff_all + r0;
+    D.ndist = ndist_all + r0;
+    D.maxg = maxg_all + r0;
+    D.out = ktau_out{d.tau64, d.tau32, d.S, d.n3, d.count_bits};
+    D.path = grp[order[k]] == 2 ? KTAU_PATH_MERGE : KTAU_PATH_SIGNGEMM;
+    B->g[grp[order[k]]].ids.push_back(k);
+  }
+  // Group plans.
+  for (int gi = 0; gi < 3; ++gi) {
+    GroupPlan& G = B->g[gi];
+    if (G.ids.empty()) continue;
+    G.row0 = row_prefix[G.ids.front()];
+    std::vector<int64_t> rp(1, 0), up(1, 0), jp(1, 0), tp(1, 0);
+    int64_t kpad_max = 0;
+    for (int k : G.ids) {
+      ktau_bds& D = B->hds[k];
+      G.max_n = std::max<int64_t>(G.max_n, D.n);
+      rp.push_back(rp.back() + D.m);
+      if (gi == 2) {
+        D.tq = kMergeTq;
+        D.w = (D.m + D.tq - 1) / D.tq;
+        tp.push_back(tp.back() + D.w * (D.w + 1) / 2);
+      } else {
+        D.esize = gi == 0 ? 1 : 2;
+        const int64_t K = D.n * (D.n - 1) / 2;
+        const int64_t K_pad = (K + 127) / 128 * 128;
+        D.num_kb = K_pad * D.esize / 128;
+        kpad_max = std::max(kpad_max, K_pad);
+        D.wS = (D.m + 255) / 256;
+        up.push_back(up.back() + D.wS * (D.wS + 1));
+        const int64_t w = (D.m + 255) / 256;
+        jp.push_back(jp.back() + w * (w + 1) / 2);
+      }
+    }
+    G.rows = rp.back();
+    if ((s = batch_upload(B, &G.d_ids, G.ids)) != KTAU_OK ||
+        (s = batch_upload(B, &G.d_row_prefix, rp)) != KTAU_OK) {
+      ktau_batch_free(B);
+      return s;
+    }
+    if (gi == 2) {
+      G.tiles = tp.back();
+      if ((s = batch_upload(B, &G.d_tile_prefix, tp)) != KTAU_OK) {
+        ktau_batch_free(B);
+        return s;
+      }
+      continue;
+    }
+    G.esize = gi == 0 ? 1 : 2;
+    G.units = up.back();
+    G.jt_tiles = jp.back();
+    G.stride = kpad_max * G.esize;
+    if ((s = batch_upload(B, &G.d_unit_prefix, up)) != KTAU_OK ||
+        (s = batch_upload(B, &G.d_jt_prefix, jp)) != KTAU_OK ||
+        (s = batch_alloc(B, &G.sgn, (size_t)G.rows * G.stride)) != KTAU_OK ||
+        (s = batch_alloc(B, (void**)&G.tie_off, ((size_t)G.rows + 1) * 8)) != KTAU_OK) {
+      ktau_batch_free(B);
+      return s;
+    }
+    // Tie lists: room for 2n tied pairs per variable on average; variables beyond the capacity
+    // are handled from their tie groups directly.
+    G.tie_cap = 0;
+    for (int k : G.ids) G.tie_cap += B->hds[k].m * 2 * B->hds[k].n;
+    if ((s = batch_alloc(B, (void**)&G.tie_pairs, (size_t)G.tie_cap * 4)) != KTAU_OK) {
+      ktau_batch_free(B);
+      return s;
+    }
+    int64_t srow = 0;
+    for (int k : G.ids) {
+      ktau_bds& D = B->hds[k];
+      D.srow = srow;
+      srow += D.m;
+      D.tie_off = G.tie_off + (row_prefix[k] - G.row0);
+      D.tie_pairs = G.tie_pairs;
+      D.tie_cap = G.tie_cap;
+    }
+    if ((s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows)) != KTAU_OK) {
+      ktau_batch_free(B);
+      return s;
+    }
+  }
+  if ((s = batch_upload(B, &B->d_ds, B->hds)) != KTAU_OK ||
+      (s = batch_upload(B, &B->d_row_prefix, row_prefix)) != KTAU_OK ||
+      (s = batch_alloc(B, (void**)&B->d_stats, sizeof(ktau_stats))) != KTAU_OK) {
+    ktau_batch_free(B);
+    return s;
+  }
+  KTAU_CUDA(cudaMemset(B->d_stats, 0, sizeof(ktau_stats)));
+  *out = B;
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
+  if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  ktau_status s = ktau_launch_batch_rank(B->d_ds, B->count, B->d_row_prefix, B->total_rows,
+                                         B->max_n, B->d_stats, st);
+  if (s != KTAU_OK) return s;
+  for (int gi = 0; gi < 2; ++gi) {
+    GroupPlan& G = B->g[gi];
+    if (G.ids.empty()) continue;
+    ktau_sg_group g;
+    g.ds = B->d_ds;
+    g.bids = G.d_ids;
+    g.nb = (int)G.ids.size();
+    g.esize = G.esize;
+    g.row_prefix = G.d_row_prefix;
+    g.unit_prefix = G.d_unit_prefix;
+    g.jt_prefix = G.d_jt_prefix;
+    g.rows = G.rows;
+    g.units = G.units;
+    g.jt_tiles = G.jt_tiles;
+    g.max_n = G.max_n;
+    g.T = B->hds[G.ids.front()].T;
+    g.tie_off = G.tie_off;
+    g.tie_pairs = G.tie_pairs;
+    g.tie_cap = G.tie_cap;
+    g.sgn = G.sgn;
+    g.stride = G.stride;
+    g.tmap = G.tmap;
+    if ((s = ktau_signgemm_batch(g, st)) != KTAU_OK) return s;
+  }
+  GroupPlan& M = B->g[2];
+  if (!M.ids.empty())
+    s = ktau_launch_batch_merge(B->d_ds, M.d_ids, (int)M.ids.size(), M.d_tile_prefix, M.tiles,
+                                M.max_n, st);
+  return s;
+}
+
+extern "C" ktau_status ktau_batch_graph_launch(ktau_batch* B, void* stream) {
+  if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return ktau_fail(KTAU_EINVAL, "graph capture needs a non-default stream");
+  if (!B->exec) {
+    KTAU_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    ktau_status s = ktau_batch_run(B, stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != KTAU_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return ktau_cuda_fail(e, "cudaStreamEndCapture");
+    B->graph = graph;
+    KTAU_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+  }
+  KTAU_CUDA(cudaGraphLaunch(B->exec, st));
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_batch_check(ktau_batch* B, void* stream) {
+  if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  ktau_stats h;
+  KTAU_CUDA(cudaMemcpyAsync(&h, B->d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+  KTAU_CUDA(cudaStreamSynchronize(st));
+  KTAU_CUDA(cudaMemsetAsync(B->d_stats, 0, sizeof(ktau_stats), st));
+  ktau_status s = ktau_signgemm_check_error(st);
+  if (s != KTAU_OK) return s;
+  if (h.nan_flag) return ktau_fail(KTAU_ENAN, "NaN in a dataset of the batch");
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_batch_paths(const ktau_batch* B, int32_t* n_merge, int32_t* n_signgemm) {
+  if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
+  if (n_merge) *n_merge = (int32_t)B->g[2].ids.size();
+  if (n_signgemm) *n_signgemm = (int32_t)(B->g[0].ids.size() + B->g[1].ids.size());
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_batch_pairs(const ktau_batch* B, uint64_t* pairs) {
+  if (!B || !pairs) return ktau_fail(KTAU_EINVAL, "NULL argument");
+  *pairs = B->pairs;
+  return KTAU_OK;
+}

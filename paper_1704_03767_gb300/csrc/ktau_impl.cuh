@@ -187,6 +187,36 @@ __device__ __forceinline__ void ktau_store(const ktau_out& o, uint64_t k, int64_
 }
 
 // ---------------------------------------------------------------------------------------------
+// One dataset of a batch (device-resident copy; see batch.cu). Arrays point into the batch's
+// workspace; outputs are the caller's.
+// ---------------------------------------------------------------------------------------------
+struct ktau_bds {
+  const void* values;
+  int32_t dtype, count_bits;
+  int64_t m, n, ld_in;
+  int64_t ld;  // row stride (elements) of perm / rank / srank
+  uint16_t* perm;
+  uint16_t* rank;
+  uint16_t* srank;
+  int64_t* T;
+  double* rs64;
+  float2* rsff;
+  int32_t* ndist;
+  int32_t* maxg;
+  ktau_out out;
+  int32_t path, esize;
+  // merge path: tile side and tiles per side
+  int32_t tq;
+  int64_t w;
+  // tensor-core path: first row in the group's stacked operand, K blocks, super-tiles per side,
+  // tie lists (group-wide arrays indexed by the dataset's own rows)
+  int64_t srow, num_kb, wS;
+  int64_t* tie_off;
+  uint32_t* tie_pairs;
+  int64_t tie_cap;
+};
+
+// ---------------------------------------------------------------------------------------------
 // Launchers implemented in the kernel translation units.
 // ---------------------------------------------------------------------------------------------
 ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n, int64_t ld_in,
@@ -199,5 +229,12 @@ struct ktau_merge_plan {
   int ctas_per_sm;
 };
 void ktau_merge_default_plan(int64_t n, ktau_merge_plan* plan);
+ktau_status ktau_launch_batch_rank(const ktau_bds* ds, int count, const int64_t* row_prefix,
+                                   int64_t total_rows, int64_t max_n, ktau_stats* stats,
+                                   cudaStream_t st);
+// Merge path over the tiles of several datasets (ids[] index ds[]; tile_prefix over ids).
+ktau_status ktau_launch_batch_merge(const ktau_bds* ds, const int32_t* ids, int nids,
+                                    const int64_t* tile_prefix, int64_t total_tiles, int64_t max_n,
+                                    cudaStream_t st);
 ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
                               const ktau_out& out, const ktau_merge_plan& plan, cudaStream_t st);

@@ -282,7 +282,93 @@ ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas
   return KTAU_OK;
 }
 
+// Counts of one pair with the register run length chosen from n (warp team).
+__device__ __forceinline__ void count_pair_any(int items, const uint16_t* pu, const uint16_t* su,
+                                               const uint16_t* rv, int n, bool ties, uint32_t* buf,
+                                               uint32_t* tmp, int lane, long long& nd,
+                                               long long& n3) {
+  switch (items) {
+    case 1: count_pair<32, 1>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 2: count_pair<32, 2>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 3: count_pair<32, 3>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 4: count_pair<32, 4>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 5: count_pair<32, 5>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 6: count_pair<32, 6>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 7: count_pair<32, 7>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    default: count_pair<32, 8>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+  }
+}
+
+// Batched form: the tiles of every merge-path dataset form one list (prefix over ids[]); a
+// persistent CTA takes tile ids with a static stride, finds the dataset by binary search, and
+// walks the dataset's own tile triangle (Eq. 13-14) one warp per pair.
+__global__ void __launch_bounds__(256) batch_merge_kernel(const ktau_bds* __restrict__ ds,
+                                                          const int32_t* __restrict__ ids, int nids,
+                                                          const int64_t* __restrict__ tile_prefix,
+                                                          int64_t total_tiles, int cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nteams = blockDim.x / 32;
+  const int team = threadIdx.x / 32, lane = threadIdx.x % 32;
+  uint32_t* tbuf = reinterpret_cast<uint32_t*>(smem) + (size_t)team * 2 * cap;
+  uint32_t* tbuf2 = tbuf + cap;
+  for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    int lo = 0, hi = nids - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const ktau_bds& D = ds[ids[lo]];
+    int64_t yq, xq;
+    ktau_tile_coord(D.w, t - tile_prefix[lo], yq, xq);
+    const int tq = D.tq;
+    const int64_t y0 = yq * tq, x0 = xq * tq;
+    const int n = (int)D.n;
+    const int items = n <= 256 ? (n + 31) / 32 : 8;
+    const int64_t n0 = D.n * (D.n - 1) / 2;
+    const ktau_fac fac{D.rs64, D.rsff, D.T};
+    for (int e = team; e < tq * tq; e += nteams) {
+      const int64_t y = y0 + e / tq, x = x0 + e % tq;
+      if (y >= D.m || x >= D.m || x <= y) continue;
+      const int64_t Tu = D.T[y], Tv = D.T[x];
+      long long nd, n3;
+      count_pair_any(items, D.perm + y * D.ld, D.srank + y * D.ld, D.rank + x * D.ld, n, Tu > 0,
+                     tbuf, tbuf2, lane, nd, n3);
+      if (lane == 0) {
+        const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
+        ktau_store(D.out, ktau_pair_index(D.m, y, x), S, n3, n0, fac, y, x);
+      }
+    }
+  }
+}
+
 }  // namespace
+
+ktau_status ktau_launch_batch_merge(const ktau_bds* ds, const int32_t* ids, int nids,
+                                    const int64_t* tile_prefix, int64_t total_tiles, int64_t max_n,
+                                    cudaStream_t st) {
+  if (nids == 0 || total_tiles == 0) return KTAU_OK;
+  const int cap = (int)((max_n + 3) & ~3LL);
+  const size_t team_bytes = (size_t)2 * cap * sizeof(uint32_t);
+  const int teams = (int)std::min<size_t>(8, (200 * 1024) / team_bytes);
+  if (teams < 1) return ktau_fail(KTAU_ETOOLARGE, "n=%lld too long for the batched merge path",
+                                  (long long)max_n);
+  const size_t smem = (size_t)teams * team_bytes;
+  KTAU_CUDA(cudaFuncSetAttribute(batch_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  int occ = 0;
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_merge_kernel, 32 * teams,
+                                                          smem));
+  int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
+  if (grid > total_tiles) grid = total_tiles;
+  KTAU_TRACE("batch_merge_kernel", st);
+  batch_merge_kernel<<<(unsigned)grid, 32 * teams, smem, st>>>(ds, ids, nids, tile_prefix,
+                                                               total_tiles, cap);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
 
 void ktau_merge_default_plan(int64_t n, ktau_merge_plan* plan) {
   plan->mapping = n <= 2048 ? 1 : 2;

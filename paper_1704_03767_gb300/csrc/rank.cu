@@ -33,13 +33,13 @@ __device__ __forceinline__ unsigned long long load_key(const void* values, int64
   return ((unsigned long long)k << 32) | (unsigned)i;
 }
 
+// Rank transform of one variable (row `row` of the outputs) by one CTA; `off` is the element
+// offset of its values. Shared memory: np2 keys + 2 x np2 uint16.
 template <int DT>
-__global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ values, int64_t ld_in,
-                                                   int n, int np2, int64_t ld, uint16_t* perm,
-                                                   uint16_t* rank, uint16_t* srank, int64_t* T,
-                                                   int32_t* ndist, int32_t* maxg,
-                                                   double* rs64, float2* rsff,
-                                                   ktau_stats* stats) {
+__device__ void rank_row(const void* __restrict__ values, int64_t off, int n, int np2,
+                         int64_t ld, int64_t row, uint16_t* perm, uint16_t* rank, uint16_t* srank,
+                         int64_t* T, int32_t* ndist, int32_t* maxg, double* rs64, float2* rsff,
+                         ktau_stats* stats) {
   extern __shared__ unsigned long long sm_keys[];                  // [np2]
   uint16_t* sm_first = reinterpret_cast<uint16_t*>(sm_keys + np2);  // [np2] group start
   uint16_t* sm_dense = sm_first + np2;                             // [np2] dense rank at k
@@ -47,9 +47,7 @@ __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ valu
   __shared__ unsigned long long red_T[32];
   __shared__ int red_g[32];
 
-  const int64_t row = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t off = row * ld_in;
   unsigned int nan_seen = 0;
 
   for (int i = tid; i < np2; i += nt)
@@ -165,7 +163,60 @@ __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ valu
   }
 }
 
+template <int DT>
+__global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ values, int64_t ld_in,
+                                                   int n, int np2, int64_t ld, uint16_t* perm,
+                                                   uint16_t* rank, uint16_t* srank, int64_t* T,
+                                                   int32_t* ndist, int32_t* maxg,
+                                                   double* rs64, float2* rsff,
+                                                   ktau_stats* stats) {
+  const int64_t row = blockIdx.x;
+  rank_row<DT>(values, row * ld_in, n, np2, ld, row, perm, rank, srank, T, ndist, maxg, rs64, rsff,
+               stats);
+}
+
+// Batched form: one CTA per variable of every dataset; the dataset is found from the prefix of
+// row counts (rows of a batch are numbered dataset by dataset).
+__global__ void __launch_bounds__(256) batch_rank_kernel(const ktau_bds* __restrict__ ds, int count,
+                                                         const int64_t* __restrict__ row_prefix,
+                                                         ktau_stats* stats) {
+  const int64_t r = blockIdx.x;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // largest d with row_prefix[d] <= r
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_prefix[mid] <= r)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const ktau_bds& D = ds[lo];
+  const int64_t row = r - row_prefix[lo];
+  int np2 = 32;
+  while (np2 < D.n) np2 <<= 1;
+  if (D.dtype == KTAU_F32)
+    rank_row<KTAU_F32>(D.values, row * D.ld_in, (int)D.n, np2, D.ld, row, D.perm, D.rank, D.srank,
+                       D.T, D.ndist, D.maxg, D.rs64, D.rsff, stats);
+  else
+    rank_row<KTAU_I32>(D.values, row * D.ld_in, (int)D.n, np2, D.ld, row, D.perm, D.rank, D.srank,
+                       D.T, D.ndist, D.maxg, D.rs64, D.rsff, stats);
+}
+
 }  // namespace
+
+ktau_status ktau_launch_batch_rank(const ktau_bds* ds, int count, const int64_t* row_prefix,
+                                   int64_t total_rows, int64_t max_n, ktau_stats* stats,
+                                   cudaStream_t st) {
+  int np2 = 32;
+  while (np2 < max_n) np2 <<= 1;
+  const size_t smem = (size_t)np2 * (sizeof(unsigned long long) + 2 * sizeof(uint16_t));
+  KTAU_CUDA(cudaFuncSetAttribute(batch_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  if (total_rows > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "too many rows in one batch");
+  KTAU_TRACE("batch_rank_kernel", st);
+  batch_rank_kernel<<<(unsigned)total_rows, 256, smem, st>>>(ds, count, row_prefix, stats);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
 
 ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n, int64_t ld_in,
                              ktau_ranked* R, cudaStream_t st) {

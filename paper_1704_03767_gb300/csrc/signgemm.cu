@@ -60,17 +60,11 @@ __device__ __forceinline__ int pair_row(int n, long long k) {
   return a;
 }
 
+// One variable's signs: orow[k] for k < K_pad (zero beyond K); s_r holds its n ranks.
 template <int ESIZE>
-__global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
-                                                          int64_t ld, int n, int64_t K,
-                                                          int64_t K_pad, uint8_t* __restrict__ out) {
-  extern __shared__ uint16_t s_r[];
-  const int64_t row = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_r[i] = rank[row * ld + i];
-  __syncthreads();
+__device__ void expand_row(const uint16_t* s_r, int n, int64_t K, int64_t K_pad, uint8_t* orow) {
   constexpr int PER = 16 / ESIZE;  // elements per 16-byte store
   const int64_t chunks = K_pad / PER;
-  uint8_t* orow = out + row * K_pad * ESIZE;
   for (int64_t c = threadIdx.x; c < chunks; c += blockDim.x) {
     const int64_t k0 = c * PER;
     uint32_t words[4];
@@ -107,6 +101,42 @@ __global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __rest
     }
     reinterpret_cast<uint4*>(orow)[c] = make_uint4(words[0], words[1], words[2], words[3]);
   }
+}
+
+template <int ESIZE>
+__global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
+                                                          int64_t ld, int n, int64_t K,
+                                                          int64_t K_pad, uint8_t* __restrict__ out) {
+  extern __shared__ uint16_t s_r[];
+  const int64_t row = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_r[i] = rank[row * ld + i];
+  __syncthreads();
+  expand_row<ESIZE>(s_r, n, K, K_pad, out + row * K_pad * ESIZE);
+}
+
+// Batched: rows [0, rows) of a group of datasets (numbered dataset by dataset, prefix over bids),
+// written into the group's stacked operand (row stride `stride` bytes, dataset rows from srow).
+template <int ESIZE>
+__global__ void __launch_bounds__(256) batch_sign_expand_kernel(
+    const ktau_bds* __restrict__ ds, const int32_t* __restrict__ bids, int nb,
+    const int64_t* __restrict__ row_prefix, int64_t stride, uint8_t* __restrict__ out) {
+  extern __shared__ uint16_t s_r[];
+  const int64_t r = blockIdx.x;
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_prefix[mid] <= r)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const ktau_bds& D = ds[bids[lo]];
+  const int64_t row = r - row_prefix[lo];
+  const int n = (int)D.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_r[i] = D.rank[row * D.ld + i];
+  __syncthreads();
+  const int64_t K = D.n * (D.n - 1) / 2;
+  expand_row<ESIZE>(s_r, n, K, D.num_kb * (BKB / ESIZE), out + (D.srow + row) * stride);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -251,12 +281,62 @@ struct ContractArgs {
   uint64_t p_begin, p_end; // tri: pair range
   int64_t ldo;             // rect: output row stride
   ktau_out out;
+  // Batched form (bds != nullptr): units of several datasets stacked in one operand tensor.
+  const ktau_bds* bds;
+  const int32_t* bids;     // datasets of this launch, in unit order
+  int nb;
+  const int64_t* unit_prefix;  // [nb + 1]
+};
+
+// The problem a unit belongs to (the whole launch, or one dataset of a batch).
+struct Prob {
+  SideArgs row, col;
+  int64_t n, num_kb;
+  int tri;
+  uint64_t p_begin, p_end;
+  int64_t ldo;
+  ktau_out out;
 };
 
 struct Unit {
-  int64_t y0, x0;
+  int64_t y0, x0;   // tile origin in the problem's own rows / columns
   bool live;
+  int ta, tb;       // TMA row coordinates of the A and B tiles
+  int64_t num_kb;
+  int bd;           // dataset of a batched launch (-1 otherwise)
 };
+
+__device__ __forceinline__ SideArgs side_of_bds(const ktau_bds& D) {
+  return SideArgs{D.rank, D.perm, D.srank, D.ld, D.T, D.rs64, D.rsff,
+                  D.tie_off, D.tie_pairs, D.tie_cap, D.m};
+}
+
+__device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t) {
+  Prob p;
+  if (t.bd < 0) {
+    p.row = a.row;
+    p.col = a.col;
+    p.n = a.n;
+    p.num_kb = a.num_kb;
+    p.tri = a.tri;
+    p.p_begin = a.p_begin;
+    p.p_end = a.p_end;
+    p.ldo = a.ldo;
+    p.out = a.out;
+  } else {
+    const ktau_bds& D = a.bds[t.bd];
+    p.row = p.col = side_of_bds(D);
+    p.n = D.n;
+    p.num_kb = D.num_kb;
+    p.tri = 1;
+    p.p_begin = 0;
+    p.p_end = (uint64_t)(D.m * (D.m - 1) / 2);
+    p.ldo = 0;
+    p.out = D.out;
+    p.out.n3 = nullptr;
+  }
+  return p;
+}
 
 __device__ __forceinline__ uint64_t tri_p(int64_t m, int64_t y, int64_t x) {
   return (uint64_t)(y * (2 * m - y - 1) / 2 + (x - y - 1));
@@ -265,6 +345,31 @@ __device__ __forceinline__ uint64_t tri_p(int64_t m, int64_t y, int64_t x) {
 // Tile origin of a work unit and whether it holds any output (same answer in every role).
 __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
   Unit r;
+  r.bd = -1;
+  r.num_kb = a.num_kb;
+  if (a.bds) {
+    int lo = 0, hi = a.nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.unit_prefix[mid] <= u)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    r.bd = a.bids[lo];
+    const ktau_bds& D = a.bds[r.bd];
+    const int64_t lu = u - a.unit_prefix[lo];
+    int64_t ys, xs;
+    ktau_tile_coord(D.wS, lu >> 1, ys, xs);
+    r.y0 = ys * 256 + (lu & 1) * BM;
+    r.x0 = xs * 256;
+    const int64_t xend = min(r.x0 + (int64_t)BN, D.m);
+    r.live = r.y0 < D.m && min(r.y0 + (int64_t)BM - 1, xend - 2) >= r.y0;
+    r.ta = (int)(D.srow + r.y0);
+    r.tb = (int)(D.srow + r.x0);
+    r.num_kb = D.num_kb;
+    return r;
+  }
   if (a.tri) {
     // Slot u -> (group of GROUP x GROUP super-tiles, walked by the bijection on the group matrix;
     // row-major inside the group) -> 256 x 256 super-tile -> 128-row half. Consecutive slots,
@@ -277,6 +382,8 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
     const int64_t ys = gy * GROUP + loc / GROUP, xs = gx * GROUP + loc % GROUP;
     r.y0 = ys * 256 + (u & 1) * BM;
     r.x0 = xs * 256;
+    r.ta = (int)r.y0;
+    r.tb = (int)r.x0;
     if (ys >= a.wS || xs >= a.wS || ys > xs) {
       r.live = false;
       return r;
@@ -293,6 +400,8 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
   } else {
     r.y0 = (u / a.ncb) * BM;
     r.x0 = (u % a.ncb) * BN;
+    r.ta = (int)r.y0;
+    r.tb = (int)r.x0;
     r.live = r.y0 < a.row.m && r.x0 < a.col.m;
   }
   return r;
@@ -386,34 +495,44 @@ __global__ void ties_list_kernel(const uint16_t* __restrict__ perm, const uint16
   warp_list_ties(perm + row * ld, srank + row * ld, n, pairs + off[row], lane);
 }
 
+// Batched listing: rows of a group (T, tie_off contiguous over the group's rows).
+__global__ void batch_ties_list_kernel(const ktau_bds* __restrict__ ds,
+                                       const int32_t* __restrict__ bids, int nb,
+                                       const int64_t* __restrict__ row_prefix, int64_t rows,
+                                       const int64_t* __restrict__ T, const int64_t* __restrict__ off,
+                                       int64_t cap, uint32_t* __restrict__ pairs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  if (T[r] == 0 || off[r] + T[r] > cap) return;
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_prefix[mid] <= r)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const ktau_bds& D = ds[bids[lo]];
+  const int64_t row = r - row_prefix[lo];
+  warp_list_ties(D.perm + row * D.ld, D.srank + row * D.ld, (int)D.n, pairs + off[r], lane);
+}
+
 // n_3(u, v) = number of sample pairs tied in u that are also tied in v (Table 1). Square JT x JT
 // tiles of the job matrix (bijection, Eq. 13-14); the tied pairs of the tile's row variables are
 // listed in shared memory, and the column variables' ranks are staged transposed (rT[a][j]) 64
 // at a time so that, for each tied pair (a, b), the 32 lanes of a warp check 32 column variables
 // with conflict-free loads. Writes every n_3 of the range (zeros included).
-__global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const SideArgs C,
-                                                         int64_t n, int tri, int64_t w,
-                                                         int64_t ncb, int64_t tile_lo,
-                                                         int64_t tile_hi, uint64_t p_begin,
-                                                         uint64_t p_end, int64_t ldo, void* n3out,
-                                                         int count_bits) {
+__device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n, int tri,
+                                int64_t y0, int64_t x0, uint64_t p_begin, uint64_t p_end,
+                                int64_t ldo, void* n3out, int count_bits) {
   extern __shared__ uint32_t jsm[];
   uint32_t* s_pairs = jsm;                                     // [JCAP]
   int* s_off = (int*)(jsm + JCAP);                             // [JT + 1], tile-relative offsets
   uint16_t* rT = (uint16_t*)(jsm + JCAP + JT + 8);             // [n][JTP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
-    int64_t y0, x0;
-    if (tri) {
-      int64_t yq, xq;
-      ktau_tile_coord(w, t, yq, xq);
-      y0 = yq * JT;
-      x0 = xq * JT;
-    } else {
-      y0 = (t / ncb) * JT;
-      x0 = (t % ncb) * JT;
-    }
+  {
     const int rows = (int)min((int64_t)JT, R.m - y0);
     __syncthreads();
     // The tile rows' lists are one contiguous segment of the global list (when all are listed).
@@ -506,6 +625,51 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
   }
 }
 
+__global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const SideArgs C,
+                                                         int64_t n, int tri, int64_t w,
+                                                         int64_t ncb, int64_t tile_lo,
+                                                         int64_t tile_hi, uint64_t p_begin,
+                                                         uint64_t p_end, int64_t ldo, void* n3out,
+                                                         int count_bits) {
+  for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
+    int64_t y0, x0;
+    if (tri) {
+      int64_t yq, xq;
+      ktau_tile_coord(w, t, yq, xq);
+      y0 = yq * JT;
+      x0 = xq * JT;
+    } else {
+      y0 = (t / ncb) * JT;
+      x0 = (t % ncb) * JT;
+    }
+    joint_ties_tile(R, C, n, tri, y0, x0, p_begin, p_end, ldo, n3out, count_bits);
+  }
+}
+
+// Batched: the JT x JT tiles of every dataset of a group in one list (prefix over bids).
+__global__ void __launch_bounds__(256) batch_joint_ties_kernel(
+    const ktau_bds* __restrict__ ds, const int32_t* __restrict__ bids, int nb,
+    const int64_t* __restrict__ tile_prefix, int64_t total_tiles) {
+  for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const ktau_bds& D = ds[bids[lo]];
+    if (!D.out.n3) continue;
+    const int64_t w = (D.m + JT - 1) / JT;
+    int64_t yq, xq;
+    ktau_tile_coord(w, t - tile_prefix[lo], yq, xq);
+    const SideArgs S = side_of_bds(D);
+    joint_ties_tile(S, S, D.n, 1, yq * JT, xq * JT, 0, (uint64_t)(D.m * (D.m - 1) / 2), 0,
+                    D.out.n3, D.out.count_bits);
+  }
+}
+
 template <int ESIZE>
 __global__ void __launch_bounds__(THREADS, 1)
     contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -558,7 +722,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int64_t u = a.unit_lo + blockIdx.x; ok && u < a.unit_hi; u += gridDim.x) {
         const Unit t = unit_of(a, u);
         if (!t.live) continue;
-        for (int64_t kb = 0; kb < a.num_kb; ++kb) {
+        for (int64_t kb = 0; kb < t.num_kb; ++kb) {
           if (!mbar_wait(EMPTY(stage), phase ^ 1u)) {
             ok = false;
             break;
@@ -567,9 +731,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sb = sa + A_BYTES;
           mbar_expect_tx(FULL(stage), STAGE_BYTES);
           const int kx = (int)(kb * BKB);
-          tma_load_2d(sa, &tmA, kx, (int)t.y0, FULL(stage), pol);
-          tma_load_2d(sb, &tmB, kx, (int)t.x0, FULL(stage), pol);
-          tma_load_2d(sb + BN / 2 * BKB, &tmB, kx, (int)(t.x0 + BN / 2), FULL(stage), pol);
+          tma_load_2d(sa, &tmA, kx, t.ta, FULL(stage), pol);
+          tma_load_2d(sb, &tmB, kx, t.tb, FULL(stage), pol);
+          tma_load_2d(sb + BN / 2 * BKB, &tmB, kx, t.tb + BN / 2, FULL(stage), pol);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -594,7 +758,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!mbar_wait(TEMPTY(acc), acc_phase ^ 1u)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-        for (int64_t kb = 0; kb < a.num_kb; ++kb) {
+        for (int64_t kb = 0; kb < t.num_kb; ++kb) {
           if (!mbar_wait(FULL(stage), phase)) {
             ok = false;
             break;
@@ -621,36 +785,37 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {
-    // ---------------- Epilogue (warps 2..5) ----------------
+    // ---------------- Epilogue (warps 2..9) ----------------
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int half_sel = (warp - 2) >> 2;  // which half of the 256 columns
     int* tb = tbuf_all + (warp - 2) * 32 * TRS;
     int acc = 0;
     uint32_t acc_phase = 0;
-    const int64_t n0 = a.n * (a.n - 1) / 2;
-    const int64_t mrow = a.row.m, mcol = a.col.m;
-    const bool want64 = a.out.tau64 != nullptr, want32 = a.out.tau32 != nullptr;
-    const bool wantS = a.out.S != nullptr, s64 = a.out.count_bits == 64;
     for (int64_t u = a.unit_lo + blockIdx.x; u < a.unit_hi; u += gridDim.x) {
       const Unit t = unit_of(a, u);
       if (!t.live) continue;
       if (!mbar_wait(TFULL(acc), acc_phase)) break;
       tc_fence_after();
+      const Prob P = problem_of(a, t);
+      const int64_t n0 = P.n * (P.n - 1) / 2;
+      const int64_t mrow = P.row.m, mcol = P.col.m;
+      const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
+      const bool wantS = P.out.S != nullptr, s64 = P.out.count_bits == 64;
       const int64_t ybase = t.y0 + 32 * q;
       // Per-row data of this warp's 32 rows, one row per lane (broadcast by shuffle below).
       const int64_t my_y = ybase + lane;
       const bool my_row_ok = my_y < mrow;
-      const float2 my_rff = my_row_ok ? __ldg(a.row.rsff + my_y) : make_float2(0.f, 0.f);
+      const float2 my_rff = my_row_ok ? __ldg(P.row.rsff + my_y) : make_float2(0.f, 0.f);
       const long long my_base =
-          a.tri ? (long long)(my_y * (2 * mrow - my_y - 1) / 2 - my_y - 1) : (long long)my_y * a.ldo;
+          P.tri ? (long long)(my_y * (2 * mrow - my_y - 1) / 2 - my_y - 1) : (long long)my_y * P.ldo;
       const int rows_here = (int)min((int64_t)32, mrow - ybase);
       // Whole 32 x 32 blocks strictly above the diagonal, inside the matrix and inside the pair
       // range need no per-element checks.
       bool range_all = true;
-      if (a.tri) {
+      if (P.tri) {
         const int64_t ylast = ybase + rows_here - 1;
-        range_all = (uint64_t)(ybase * (2 * mrow - ybase - 1) / 2) >= a.p_begin &&
-                    (uint64_t)(ylast * (2 * mrow - ylast - 1) / 2 + (mrow - ylast - 1)) <= a.p_end;
+        range_all = (uint64_t)(ybase * (2 * mrow - ybase - 1) / 2) >= P.p_begin &&
+                    (uint64_t)(ylast * (2 * mrow - ylast - 1) / 2 + (mrow - ylast - 1)) <= P.p_end;
       }
       for (int c = half_sel * (BN / 64); c < (half_sel + 1) * (BN / 64); ++c) {
         uint32_t r[32];
@@ -666,28 +831,28 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int64_t xc = t.x0 + 32 * c;
         const int64_t v = xc + lane;
         const bool vin = v < mcol;
-        const float2 c_rff = vin ? __ldg(a.col.rsff + v) : make_float2(0.f, 0.f);
+        const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
         const bool fast = range_all && rows_here == 32 && xc + 32 <= mcol &&
-                          (!a.tri || xc > ybase + 31);
+                          (!P.tri || xc > ybase + 31);
         if (fast && want32 && !want64) {
 #pragma unroll 4
           for (int i = 0; i < 32; ++i) {
             const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
             const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
             const long long base = __shfl_sync(0xffffffffu, my_base, i);
-            const uint64_t k = (uint64_t)(base + v) - a.p_begin;
+            const uint64_t k = (uint64_t)(base + v) - P.p_begin;
             const int S = tb[i * TRS + lane];
             float tv;
             if (!ktau_tau32_fast(S, make_float2(rhi, rlo), c_rff, tv)) {
               const int64_t y = ybase + i;
-              tv = ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, a.row.T[y], a.col.T[v]);
+              tv = ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, P.row.T[y], P.col.T[v]);
             }
-            __stcs(a.out.tau32 + k, tv);
+            __stcs(P.out.tau32 + k, tv);
             if (wantS) {
               if (s64)
-                __stcs((long long*)a.out.S + k, (long long)S);
+                __stcs((long long*)P.out.S + k, (long long)S);
               else
-                __stcs((int*)a.out.S + k, S);
+                __stcs((int*)P.out.S + k, S);
             }
           }
         } else {
@@ -698,24 +863,24 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int64_t y = ybase + i;
             if (i >= rows_here || !vin) continue;
             uint64_t k;
-            if (a.tri) {
+            if (P.tri) {
               if (v <= y) continue;
               const uint64_t p = (uint64_t)(base + v);
-              if (p < a.p_begin || p >= a.p_end) continue;
-              k = p - a.p_begin;
+              if (p < P.p_begin || p >= P.p_end) continue;
+              k = p - P.p_begin;
             } else {
               k = (uint64_t)(base + v);
             }
             const int S = tb[i * TRS + lane];
-            if (want64) __stcs(a.out.tau64 + k, ktau_tau64(S, a.row.rs64[y], a.col.rs64[v]));
+            if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
             if (want32)
-              __stcs(a.out.tau32 + k,
-                     ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, a.row.T[y], a.col.T[v]));
+              __stcs(P.out.tau32 + k,
+                     ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
             if (wantS) {
               if (s64)
-                __stcs((long long*)a.out.S + k, (long long)S);
+                __stcs((long long*)P.out.S + k, (long long)S);
               else
-                __stcs((int*)a.out.S + k, S);
+                __stcs((int*)P.out.S + k, S);
             }
           }
         }
@@ -755,22 +920,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-ktau_status make_tmap(ktau_ranked* R) {
-  CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(R->tmap);
+ktau_status make_tmap_raw(void* tmap, void* base, int64_t row_bytes_, int64_t rows) {
+  CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(tmap);
   PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
   if (!cuTensorMapEncodeTiled) return ktau_fail(KTAU_ECUDA, "cuTensorMapEncodeTiled unavailable");
-  const cuuint64_t row_bytes = (cuuint64_t)(R->K_pad * R->esize);
-  cuuint64_t dims[2] = {row_bytes, (cuuint64_t)R->m};
+  const cuuint64_t row_bytes = (cuuint64_t)row_bytes_;
+  cuuint64_t dims[2] = {row_bytes, (cuuint64_t)rows};
   cuuint64_t strides[1] = {row_bytes};
   cuuint32_t box[2] = {(cuuint32_t)BKB, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, R->sgn, dims, strides,
+  CUresult r = cuTensorMapEncodeTiled(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides,
                                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                       CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return ktau_fail(KTAU_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return KTAU_OK;
+}
+
+ktau_status make_tmap(ktau_ranked* R) {
+  return make_tmap_raw(R->tmap, R->sgn, R->K_pad * R->esize, R->m);
 }
 
 SideArgs side_of(const ktau_ranked* R) {
@@ -812,20 +981,26 @@ ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tr
 }
 
 template <int ESIZE>
-ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const ContractArgs& args,
-                            int64_t units, cudaStream_t st) {
+ktau_status launch_contract_maps(const void* tmap_a, const void* tmap_b, const ContractArgs& args,
+                                 int64_t units, cudaStream_t st) {
   auto kern = contract_kernel<ESIZE>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SMEM_BYTES));
   int64_t grid = ktau_sm_count();
   if (grid > units) grid = units;
   if (grid < 1) grid = 1;
-  const CUtensorMap* ta = reinterpret_cast<const CUtensorMap*>(A->tmap);
-  const CUtensorMap* tb = reinterpret_cast<const CUtensorMap*>(B->tmap);
+  const CUtensorMap* ta = reinterpret_cast<const CUtensorMap*>(tmap_a);
+  const CUtensorMap* tb = reinterpret_cast<const CUtensorMap*>(tmap_b);
   KTAU_TRACE("contract_kernel", st);
   kern<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(*ta, *tb, args);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
+}
+
+template <int ESIZE>
+ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const ContractArgs& args,
+                            int64_t units, cudaStream_t st) {
+  return launch_contract_maps<ESIZE>(A->tmap, B->tmap, args, units, st);
 }
 
 }  // namespace
@@ -892,6 +1067,10 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.p_end = p_end;
   a.ldo = 0;
   a.out = out;
+  a.bds = nullptr;
+  a.bids = nullptr;
+  a.nb = 0;
+  a.unit_prefix = nullptr;
   int64_t i0, j0, i1, j1;
   ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
   ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
@@ -925,6 +1104,10 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.p_end = 0;
   a.ldo = ldo;
   a.out = out;
+  a.bds = nullptr;
+  a.bids = nullptr;
+  a.nb = 0;
+  a.unit_prefix = nullptr;
   a.unit_lo = 0;
   a.unit_hi = ((Q->m + BM - 1) / BM) * a.ncb;
   a.out.n3 = nullptr;
@@ -953,5 +1136,60 @@ ktau_status ktau_signgemm_check_error(cudaStream_t st) {
     cudaMemcpyToSymbolAsync(g_sg_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
     return ktau_fail(KTAU_ETIMEOUT, "tensor-core pipeline wait timed out");
   }
+  return KTAU_OK;
+}
+
+ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows) {
+  return make_tmap_raw(tmap, base, row_bytes, rows);
+}
+
+ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
+  if (g.nb == 0 || g.rows == 0) return KTAU_OK;
+  const size_t smem_r = (size_t)g.max_n * sizeof(uint16_t);
+  {
+    KTAU_TRACE("batch_sign_expand_kernel", st);
+    if (g.esize == 1)
+      batch_sign_expand_kernel<1><<<(unsigned)g.rows, 256, smem_r, st>>>(
+          g.ds, g.bids, g.nb, g.row_prefix, g.stride, (uint8_t*)g.sgn);
+    else
+      batch_sign_expand_kernel<2><<<(unsigned)g.rows, 256, smem_r, st>>>(
+          g.ds, g.bids, g.nb, g.row_prefix, g.stride, (uint8_t*)g.sgn);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  {
+    KTAU_TRACE("ties_scan_kernel", st);
+    ties_scan_kernel<<<1, 1024, 0, st>>>(g.T, g.rows, g.tie_off);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  {
+    KTAU_TRACE("batch_ties_list_kernel", st);
+    batch_ties_list_kernel<<<(unsigned)((g.rows * 32 + 255) / 256), 256, 0, st>>>(
+        g.ds, g.bids, g.nb, g.row_prefix, g.rows, g.T, g.tie_off, g.tie_cap, g.tie_pairs);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  ContractArgs a;
+  memset(&a, 0, sizeof(a));
+  a.bds = g.ds;
+  a.bids = g.bids;
+  a.nb = g.nb;
+  a.unit_prefix = g.unit_prefix;
+  a.unit_lo = 0;
+  a.unit_hi = g.units;
+  a.tri = 1;
+  ktau_status s = g.esize == 1 ? launch_contract_maps<1>(g.tmap, g.tmap, a, g.units, st)
+                               : launch_contract_maps<2>(g.tmap, g.tmap, a, g.units, st);
+  if (s != KTAU_OK) return s;
+  const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)g.max_n * JTP * sizeof(uint16_t);
+  KTAU_CUDA(cudaFuncSetAttribute(batch_joint_ties_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_joint_ties_kernel, 256, smem));
+  int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
+  if (grid > g.jt_tiles) grid = g.jt_tiles;
+  if (grid < 1) grid = 1;
+  KTAU_TRACE("batch_joint_ties_kernel", st);
+  batch_joint_ties_kernel<<<(unsigned)grid, 256, smem, st>>>(g.ds, g.bids, g.nb, g.jt_prefix,
+                                                             g.jt_tiles);
+  KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }

@@ -23,5 +23,27 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
 ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
                                cudaStream_t st);
 void ktau_signgemm_release(ktau_ranked* R);
+
+// Batched tensor-core group: datasets bids[0..nb) of ds (all FP8 or all BF16), whose rows are
+// rows [row0, row0 + rows) of the batch and are stacked in `sgn` (row stride `stride` bytes).
+struct ktau_sg_group {
+  const ktau_bds* ds;
+  const int32_t* bids;
+  int nb;
+  int esize;
+  const int64_t* row_prefix;   // [nb + 1] over the group's rows
+  const int64_t* unit_prefix;  // [nb + 1] contraction units
+  const int64_t* jt_prefix;    // [nb + 1] joint-ties tiles
+  int64_t rows, units, jt_tiles, max_n;
+  const int64_t* T;            // T of the group's rows (contiguous)
+  int64_t* tie_off;            // [rows + 1]
+  uint32_t* tie_pairs;
+  int64_t tie_cap;
+  void* sgn;
+  int64_t stride;
+  const void* tmap;            // CUtensorMap of sgn (host memory, 128 bytes)
+};
+ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows);
+ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st);
 // Device error word of the contraction kernels (bounded waits that gave up); 0 = none.
 ktau_status ktau_signgemm_check_error(cudaStream_t st);

@@ -112,7 +112,8 @@ def batched_uneven(count: int = 1000, m_range=(16, 1024), n_range=(20, 2000), du
         n = int(round(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1])))))
         x = g.random((m, n))
         k = max(1, int(round(dup_frac * n)))
-        dst = np.argsort(g.random((m, n)), axis=1)[:, :k]
+        dst = np.argpartition(g.random((m, n)), k - 1, axis=1)[:, :k] if k < n else \
+            np.tile(np.arange(n), (m, 1))
         src = g.integers(0, n, size=(m, k))
         rows = np.arange(m)[:, None]
         x[rows, dst] = x[rows, src]
