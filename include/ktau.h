@@ -146,9 +146,10 @@ ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, in
  * (allocates on first use). EINVAL when n > 1024 (path unsupported). */
 ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
 
-/* Synchronises `stream` and reports whether a bounded device-side wait of a tensor-core kernel
- * gave up since the last call (KTAU_ETIMEOUT, the results of that launch are invalid), then
- * clears the flag. KTAU_OK otherwise. */
+/* Synchronises `stream` and reports device-side status words raised since the last call, then
+ * clears them: KTAU_ETIMEOUT when a bounded wait of a tensor-core kernel gave up (that launch's
+ * results are invalid), KTAU_ETOOLARGE when a top-k selection met more than 2048 rows tied at
+ * its boundary without exact keys (n > 300; that query's top-k order is not exact). */
 ktau_status ktau_device_status(void* stream);
 
 /* Kernel trace: when enabled, every kernel the library launches is bracketed by CUDA events on

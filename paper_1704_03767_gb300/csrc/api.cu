@@ -299,8 +299,12 @@ extern "C" ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream) {
   return ktau_signgemm_prepare(R, (cudaStream_t)stream);
 }
 
+ktau_status ktau_query_check_status(cudaStream_t st);
+
 extern "C" ktau_status ktau_device_status(void* stream) {
-  return ktau_signgemm_check_error((cudaStream_t)stream);
+  ktau_status s = ktau_signgemm_check_error((cudaStream_t)stream);
+  if (s != KTAU_OK) return s;
+  return ktau_query_check_status((cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -238,3 +238,7 @@ ktau_status ktau_launch_batch_merge(const ktau_bds* ds, const int32_t* ids, int 
                                     cudaStream_t st);
 ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
                               const ktau_out& out, const ktau_merge_plan& plan, cudaStream_t st);
+// Every row of Q against every row of D (outputs [Q.m][ldo]).
+ktau_status ktau_launch_merge_rect(const ktau_ranked* Q, const ktau_ranked* D, int64_t ldo,
+                                   const ktau_out& out, const ktau_merge_plan& plan,
+                                   cudaStream_t st);

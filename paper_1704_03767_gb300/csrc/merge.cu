@@ -132,12 +132,20 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
 }
 
 struct MergeArgs {
+  // row side (u): permutation, sorted ranks, tie counts, factors; column side (v): ranks.
   const uint16_t* perm;
-  const uint16_t* rank;
   const uint16_t* srank;
   const int64_t* T;
   ktau_fac fac;
-  int64_t m, n, ld;
+  const uint16_t* rank;  // column side
+  const int64_t* Tc;
+  ktau_fac facc;
+  int64_t m;             // row variables
+  int64_t mc;            // column variables
+  int64_t n, ld;
+  int rect;              // 0: upper triangle of one matrix, 1: every row x every column
+  int64_t ncb;           // rect: column tiles
+  int64_t ldo;           // rect: output row stride
   int64_t w;        // tiles per side
   int64_t tile_lo;  // tile-id range covering [p_begin, p_end)
   int64_t tile_hi;
@@ -235,29 +243,50 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
     }
     if (t >= a.tile_hi) break;
     int64_t yq, xq;
-    ktau_tile_coord(a.w, t, yq, xq);
+    if (a.rect) {
+      yq = t / a.ncb;
+      xq = t % a.ncb;
+    } else {
+      ktau_tile_coord(a.w, t, yq, xq);
+    }
     const int64_t y0 = yq * tq, x0 = xq * tq;
     if (a.stage) {
       __syncthreads();
       copy_rows(s_perm, a.perm, y0, tq, a.m, ld);
       copy_rows(s_srank, a.srank, y0, tq, a.m, ld);
-      copy_rows(s_rank, a.rank, x0, tq, a.m, ld);
+      copy_rows(s_rank, a.rank, x0, tq, a.mc, ld);
       __syncthreads();
     }
     for (int e = team; e < tq * tq; e += nteams) {
       const int64_t y = y0 + e / tq, x = x0 + e % tq;
-      if (y >= a.m || x >= a.m || x <= y) continue;
-      const uint64_t p = ktau_pair_index(a.m, y, x);
-      if (p < a.p_begin || p >= a.p_end) continue;
+      if (y >= a.m || x >= a.mc) continue;
+      uint64_t k;
+      if (a.rect) {
+        k = (uint64_t)y * (uint64_t)a.ldo + (uint64_t)x;
+      } else {
+        if (x <= y) continue;
+        const uint64_t p = ktau_pair_index(a.m, y, x);
+        if (p < a.p_begin || p >= a.p_end) continue;
+        k = p - a.p_begin;
+      }
       const uint16_t* pu = a.stage ? s_perm + (y - y0) * ld : a.perm + y * ld;
       const uint16_t* su = a.stage ? s_srank + (y - y0) * ld : a.srank + y * ld;
       const uint16_t* rv = a.stage ? s_rank + (x - x0) * ld : a.rank + x * ld;
-      const int64_t Tu = a.T[y], Tv = a.T[x];
+      const int64_t Tu = a.T[y], Tv = a.Tc[x];
       long long nd, n3;
       count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, tbuf, tbuf2, lane, red, nd, n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
-        ktau_store(a.out, p - a.p_begin, S, n3, n0, a.fac, y, x);
+        if (a.out.tau64) a.out.tau64[k] = ktau_tau64(S, a.fac.rs64[y], a.facc.rs64[x]);
+        if (a.out.tau32)
+          a.out.tau32[k] = ktau_tau32(S, a.fac.rsff[y], a.facc.rsff[x], n0, Tu, Tv);
+        if (a.out.count_bits == 64) {
+          if (a.out.S) ((long long*)a.out.S)[k] = S;
+          if (a.out.n3) ((long long*)a.out.n3)[k] = n3;
+        } else {
+          if (a.out.S) ((int*)a.out.S)[k] = (int)S;
+          if (a.out.n3) ((int*)a.out.n3)[k] = (int)n3;
+        }
       }
     }
     if (!a.counter) t += gridDim.x;
@@ -380,27 +409,40 @@ void ktau_merge_default_plan(int64_t n, ktau_merge_plan* plan) {
 // Scratch for the dynamic schedule (one counter per device, reset before each launch).
 static unsigned long long* g_counter[64];
 
-ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
-                              const ktau_out& out, const ktau_merge_plan& plan, cudaStream_t st) {
-  if (p_end <= p_begin) return KTAU_OK;
+static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C, int rect,
+                                     uint64_t p_begin, uint64_t p_end, int64_t ldo,
+                                     const ktau_out& out, const ktau_merge_plan& plan,
+                                     cudaStream_t st) {
   const int64_t m = R->m, n = R->n;
   const int tq = plan.tile_q > 0 ? plan.tile_q : 32;
   const int64_t w = (m + tq - 1) / tq;
-  // Rows of the first and last pair of the range -> covering tile-id range (Eq. 12 on tiles).
-  int64_t i0, j0, i1, j1;
-  ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
-  ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
-  const int64_t tile_lo = ktau_rowstart(w, i0 / tq);
-  const int64_t tile_hi = ktau_rowstart(w, i1 / tq + 1);
+  int64_t tile_lo = 0, tile_hi = 0, ncb = 0;
+  if (rect) {
+    ncb = (C->m + tq - 1) / tq;
+    tile_hi = w * ncb;
+  } else {
+    // Rows of the first and last pair of the range -> covering tile-id range (Eq. 12 on tiles).
+    int64_t i0, j0, i1, j1;
+    ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
+    ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
+    tile_lo = ktau_rowstart(w, i0 / tq);
+    tile_hi = ktau_rowstart(w, i1 / tq + 1);
+  }
   const int64_t tiles = tile_hi - tile_lo;
 
   MergeArgs a;
   a.perm = R->perm;
-  a.rank = R->rank;
   a.srank = R->srank;
   a.T = R->T;
   a.fac = ktau_fac{R->rs64, R->rsff, R->T};
+  a.rank = C->rank;
+  a.Tc = C->T;
+  a.facc = ktau_fac{C->rs64, C->rsff, C->T};
   a.m = m;
+  a.mc = C->m;
+  a.rect = rect;
+  a.ncb = ncb;
+  a.ldo = ldo;
   a.n = n;
   a.ld = R->ld;
   a.w = w;
@@ -454,4 +496,16 @@ ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p
     case 7: return launch_one<32, 7>(a, threads, smem, cps, tiles, st);
     default: return launch_one<32, 8>(a, threads, smem, cps, tiles, st);
   }
+}
+
+ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                              const ktau_out& out, const ktau_merge_plan& plan, cudaStream_t st) {
+  if (p_end <= p_begin) return KTAU_OK;
+  return launch_merge_impl(R, R, 0, p_begin, p_end, 0, out, plan, st);
+}
+
+ktau_status ktau_launch_merge_rect(const ktau_ranked* Q, const ktau_ranked* D, int64_t ldo,
+                                   const ktau_out& out, const ktau_merge_plan& plan,
+                                   cudaStream_t st) {
+  return launch_merge_impl(Q, D, 1, 0, 0, ldo, out, plan, st);
 }

@@ -1,0 +1,332 @@
+// Query form (Sec. 1: query-based co-expression search): exact tau-b of every query profile
+// against every database variable, plus the k database rows with the largest |tau-b| per query.
+//
+// Counts come from the rectangular sign contraction (n <= 1024) or the rectangular merge path;
+// the top-k kernel then orders each query's row exactly:
+//   |tau| = |S| / sqrt(D_u D_v) with D_u fixed per query, so the order is that of S^2 / D_v.
+//   key(v) = floor(S^2 2^f / D_v) + 1 (0 for NaN, i.e. D_v = 0) is monotone in that rational;
+//   f is the largest shift that keeps S^2 2^f below 2^62. When 2^f > n_0^2, distinct rationals
+//   (which differ by at least 1 / (D_v D_v') >= 1 / n_0^2) get distinct keys, so equal keys are
+//   exact ties (broken by the smaller row index); otherwise equal keys at the selection boundary
+//   are ordered by exact 128-bit cross-multiplication S_a^2 D_b vs S_b^2 D_a.
+//   A radix select over the 64-bit keys (8 passes of 8 bits, one CTA per query) finds the k-th
+//   largest key, the selected rows are collected in shared memory and sorted (bitonic) with the
+//   exact comparator, and tau is formed by the shared epilogue (bit-identical to the pair output).
+#include <algorithm>
+
+#include "ktau_impl.cuh"
+#include "signgemm.cuh"
+
+namespace {
+
+constexpr int TK_THREADS = 512;
+constexpr int TK_MAXK = 1024;
+constexpr int TK_EQCAP = 2048;  // boundary ties collected for the exact comparator
+
+struct TopkArgs {
+  const void* S;  // [b][ldS], int32 or int64
+  int s64;
+  int64_t ldS;
+  int64_t m_db, n0;
+  const int64_t* Tdb;
+  const int64_t* Tq;
+  const double* rs_db;
+  const double* rs_q;
+  int k;
+  int shift;      // f
+  int injective;  // 2^f > n0^2
+  int32_t* idx_out;
+  double* tau_out;
+  unsigned int* status;  // set to 1 when the boundary group exceeded TK_EQCAP
+};
+
+__device__ __forceinline__ long long load_S(const TopkArgs& a, int64_t q, int64_t j) {
+  return a.s64 ? ((const long long*)a.S)[q * a.ldS + j] : (long long)((const int*)a.S)[q * a.ldS + j];
+}
+
+__device__ __forceinline__ unsigned long long topk_key(const TopkArgs& a, long long S, int64_t Dv,
+                                                       bool qnan) {
+  if (qnan || Dv == 0) return 0ull;
+  const unsigned long long s2 = (unsigned long long)(S < 0 ? -S : S);
+  return ((s2 * s2) << a.shift) / (unsigned long long)Dv + 1ull;
+}
+
+// a before b in the final order? (exact |tau| descending, NaN last, then smaller index)
+struct Cand {
+  int S;  // |S| <= n_0 < 2^27
+  int D;  // D_v, 0 = NaN
+  int j;
+};
+__device__ __forceinline__ bool cand_before(const Cand& x, const Cand& y) {
+  if ((x.D == 0) != (y.D == 0)) return y.D == 0;
+  if (x.D != 0) {
+    const unsigned long long sx = (unsigned long long)(x.S < 0 ? -x.S : x.S);
+    const unsigned long long sy = (unsigned long long)(y.S < 0 ? -y.S : y.S);
+    const unsigned long long ax = sx * sx, ay = sy * sy;  // < 2^54
+    // compare ax * y.D vs ay * x.D in 128 bits
+    const unsigned long long lx = ax * (unsigned long long)y.D, hx = __umul64hi(ax, (unsigned long long)y.D);
+    const unsigned long long ly = ay * (unsigned long long)x.D, hy = __umul64hi(ay, (unsigned long long)x.D);
+    if (hx != hy) return hx > hy;
+    if (lx != ly) return lx > ly;
+  }
+  return x.j < y.j;
+}
+
+__global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a) {
+  __shared__ unsigned int hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_remaining, s_cnt, s_eqcnt, s_wsum[TK_THREADS / 32];
+  __shared__ Cand sel[TK_MAXK];
+  __shared__ Cand eq[TK_EQCAP];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool qnan = a.Tq[q] == a.n0;  // constant query variable: every tau is NaN
+  if (tid == 0) {
+    s_prefix = 0ull;
+    s_remaining = a.k;
+    s_cnt = 0;
+    s_eqcnt = 0;
+  }
+  __syncthreads();
+  // Radix select of the k-th largest key, most significant digit first.
+  for (int pass = 7; pass >= 0; --pass) {
+    for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const unsigned long long prefix = s_prefix;
+    const unsigned long long hmask = pass == 7 ? 0ull : (~0ull << (8 * (pass + 1)));
+    for (int64_t j = tid; j < a.m_db; j += blockDim.x) {
+      const unsigned long long key = topk_key(a, load_S(a, q, j), a.n0 - a.Tdb[j], qnan);
+      if ((key & hmask) == prefix) atomicAdd(&hist[(key >> (8 * pass)) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int rem = s_remaining;
+      int d = 255;
+      for (; d > 0; --d) {
+        if ((int)hist[d] >= rem) break;
+        rem -= (int)hist[d];
+      }
+      s_remaining = rem;
+      s_prefix = prefix | ((unsigned long long)d << (8 * pass));
+    }
+    __syncthreads();
+  }
+  const unsigned long long t = s_prefix;
+  const int need_eq = s_remaining;  // how many rows with key == t are selected
+  // Rows with key > t are all selected; rows with key == t: the lowest indices when keys are
+  // exact, otherwise all of them go through the exact comparator.
+  int eq_before = 0;
+  for (int64_t base = 0; base < a.m_db; base += blockDim.x) {
+    const int64_t j = base + tid;
+    long long S = 0, Dv = 0;
+    unsigned long long key = 0;
+    if (j < a.m_db) {
+      S = load_S(a, q, j);
+      Dv = a.n0 - a.Tdb[j];
+      key = topk_key(a, S, Dv, qnan);
+    }
+    const bool gt = j < a.m_db && key > t;
+    const bool eqf = j < a.m_db && key == t;
+    if (gt) {
+      const int pos = atomicAdd(&s_cnt, 1);
+      sel[pos] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
+    }
+    // ordered rank among equal keys (block-wide exclusive scan in index order)
+    int incl = eqf ? 1 : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    int before = eq_before;
+    for (int w = 0; w < warp; ++w) before += s_wsum[w];
+    const int rank_eq = before + incl - (eqf ? 1 : 0);
+    if (eqf) {
+      if (a.injective) {
+        if (rank_eq < need_eq) sel[a.k - need_eq + rank_eq] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
+      } else if (rank_eq < TK_EQCAP) {
+        eq[rank_eq] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
+      }
+    }
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wsum[w];
+    eq_before += tot;
+    __syncthreads();
+  }
+  if (!a.injective) {
+    // exact order of the boundary group, keep the first need_eq
+    const int g = min(eq_before, TK_EQCAP);
+    if (eq_before > TK_EQCAP && tid == 0) atomicExch(a.status, 1u);
+    int p2 = 1;
+    while (p2 < g) p2 <<= 1;
+    for (int i = g + tid; i < p2 && i < TK_EQCAP; i += blockDim.x) eq[i] = Cand{0, 0, 0x7fffffff};
+    __syncthreads();
+    for (int kk = 2; kk <= p2; kk <<= 1)
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = tid; i < p2; i += blockDim.x) {
+          const int l = i ^ jj;
+          if (l > i) {
+            const bool up = (i & kk) == 0;
+            const bool sw = up ? cand_before(eq[l], eq[i]) : cand_before(eq[i], eq[l]);
+            if (sw) {
+              const Cand tmp = eq[i];
+              eq[i] = eq[l];
+              eq[l] = tmp;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int i = tid; i < need_eq; i += blockDim.x) sel[a.k - need_eq + i] = eq[i];
+  }
+  __syncthreads();
+  // Final exact order of the k selected rows.
+  int p2 = 1;
+  while (p2 < a.k) p2 <<= 1;
+  for (int i = a.k + tid; i < p2; i += blockDim.x) sel[i] = Cand{0, 0, 0x7fffffff};
+  __syncthreads();
+  for (int kk = 2; kk <= p2; kk <<= 1)
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = tid; i < p2; i += blockDim.x) {
+        const int l = i ^ jj;
+        if (l > i) {
+          const bool up = (i & kk) == 0;
+          const bool sw = up ? cand_before(sel[l], sel[i]) : cand_before(sel[i], sel[l]);
+          if (sw) {
+            const Cand tmp = sel[i];
+            sel[i] = sel[l];
+            sel[l] = tmp;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = tid; i < a.k; i += blockDim.x) {
+    const Cand c = sel[i];
+    a.idx_out[q * a.k + i] = c.j;
+    a.tau_out[q * a.k + i] = ktau_tau64(c.S, a.rs_q[q], a.rs_db[c.j]);
+  }
+}
+
+__device__ unsigned int g_topk_status;
+
+}  // namespace
+
+ktau_status ktau_check_counts(int64_t n, int count_bits);
+ktau_status ktau_check_options(const ktau_options* opt);
+int ktau_choose_path(const ktau_ranked* R, const ktau_options* opt);
+
+static size_t scratch_S_bytes(const ktau_ranked* db, int64_t b) {
+  return ((size_t)b * db->m * sizeof(int) + 255) & ~(size_t)255;
+}
+
+extern "C" ktau_status ktau_query_scratch_bytes(const ktau_ranked* db, int64_t b, int32_t k,
+                                                size_t* bytes) {
+  if (!db || !bytes || b < 0) return ktau_fail(KTAU_EINVAL, "bad argument");
+  *bytes = k > 0 ? scratch_S_bytes(db, b) : 0;
+  if (ktau_signgemm_supported(db->n)) *bytes += (size_t)b * ((db->n * (db->n - 1) / 2 + 127) / 128 * 128) * 2;
+  return KTAU_OK;
+}
+
+// Shared by ktau_query and its caller-scratch variant: counts for every (query, row) into `out`
+// (S may be the scratch buffer), then the top-k when k > 0.
+ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, const ktau_out& out,
+                           int32_t k, int32_t* topk_idx, double* topk_tau, const ktau_options* opt,
+                           cudaStream_t st) {
+  ktau_ranked* Q = const_cast<ktau_ranked*>(queries);
+  ktau_ranked* D = const_cast<ktau_ranked*>(db);
+  const int path = ktau_choose_path(db, opt);
+  ktau_status s;
+  if (path == KTAU_PATH_SIGNGEMM && ktau_signgemm_supported(db->n)) {
+    s = ktau_signgemm_rect(Q, D, out, db->m, st);
+  } else {
+    ktau_merge_plan plan;
+    ktau_merge_default_plan(db->n, &plan);
+    plan.mapping = 1;
+    if (db->n > 2048) plan.mapping = 1;
+    if (opt && opt->tile_q) plan.tile_q = opt->tile_q;
+    s = ktau_launch_merge_rect(Q, D, db->m, out, plan, st);
+  }
+  if (s != KTAU_OK || k == 0) return s;
+  TopkArgs a;
+  a.S = out.S;
+  a.s64 = out.count_bits == 64;
+  a.ldS = db->m;
+  a.m_db = db->m;
+  a.n0 = db->n * (db->n - 1) / 2;
+  a.Tdb = db->T;
+  a.Tq = queries->T;
+  a.rs_db = db->rs64;
+  a.rs_q = queries->rs64;
+  a.k = k;
+  int bits = 0;
+  const unsigned long long s2max = (unsigned long long)a.n0 * (unsigned long long)a.n0;
+  while (bits < 64 && (s2max >> bits)) ++bits;
+  a.shift = std::max(0, 62 - bits);
+  a.injective = a.shift >= bits ? 1 : 0;  // 2^f >= 2^bits > n0^2
+  a.idx_out = topk_idx;
+  a.tau_out = topk_tau;
+  unsigned int* st_ptr = nullptr;
+  KTAU_CUDA(cudaGetSymbolAddress((void**)&st_ptr, g_topk_status));
+  a.status = st_ptr;
+  KTAU_TRACE("topk_kernel", st);
+  topk_kernel<<<(unsigned)queries->m, TK_THREADS, 0, st>>>(a);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
+ktau_status ktau_query_validate(const ktau_ranked* db, const ktau_ranked* queries, int32_t count_bits,
+                                int32_t k, int32_t* topk_idx, double* topk_tau,
+                                const ktau_options* opt) {
+  if (!db || !queries) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  if (db->n != queries->n)
+    return ktau_fail(KTAU_EINVAL, "queries have n=%lld samples, database n=%lld",
+                     (long long)queries->n, (long long)db->n);
+  ktau_status s = ktau_check_counts(db->n, count_bits);
+  if (s != KTAU_OK) return s;
+  if ((s = ktau_check_options(opt)) != KTAU_OK) return s;
+  if (k < 0 || k > TK_MAXK || k > db->m)
+    return ktau_fail(KTAU_EINVAL, "k must be in [0, min(m_db, %d)]", TK_MAXK);
+  if (k > 0 && (!topk_idx || !topk_tau)) return ktau_fail(KTAU_EINVAL, "top-k outputs are NULL");
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_query(const ktau_ranked* db, const ktau_ranked* queries, double* tau,
+                                  void* S, void* n3, int32_t count_bits, int32_t k,
+                                  int32_t* topk_idx, double* topk_tau, const ktau_options* opt,
+                                  void* stream) {
+  ktau_status s = ktau_query_validate(db, queries, count_bits, k, topk_idx, topk_tau, opt);
+  if (s != KTAU_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  ktau_out out{tau, nullptr, S, n3, count_bits};
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  if (k > 0 && !S) {
+    // The top-k needs S: library scratch (cached), released to the cache when the work is done.
+    scratch_bytes = scratch_S_bytes(db, queries->m);
+    if ((s = ktau_dmalloc(&scratch, scratch_bytes)) != KTAU_OK) return s;
+    out.S = scratch;
+    out.count_bits = 32;
+  }
+  s = ktau_query_run(db, queries, out, k, topk_idx, topk_tau, opt, st);
+  if (scratch) {
+    cudaStreamSynchronize(st);
+    ktau_dfree(scratch, scratch_bytes);
+  }
+  return s;
+}
+
+// Reports (and clears) a top-k boundary group that exceeded the exact-comparator capacity.
+ktau_status ktau_query_check_status(cudaStream_t st) {
+  unsigned int e = 0;
+  KTAU_CUDA(cudaMemcpyFromSymbolAsync(&e, g_topk_status, sizeof(e), 0, cudaMemcpyDeviceToHost, st));
+  KTAU_CUDA(cudaStreamSynchronize(st));
+  if (e) {
+    const unsigned int zero = 0;
+    cudaMemcpyToSymbolAsync(g_topk_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    return ktau_fail(KTAU_ETOOLARGE, "top-k: more than %d rows tied at the selection boundary",
+                     TK_EQCAP);
+  }
+  return KTAU_OK;
+}
