@@ -136,6 +136,30 @@ ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end
                           float* tau32, void* S, void* n3, int32_t count_bits,
                           const ktau_options* opt, void* stream);
 
+/*
+ * ktau_allpairs_noalloc -- ktau_allpairs (merge path) for one matrix straight from its values,
+ * allocating nothing. The paper has no counterpart: this entry point is for callers that may not
+ * allocate device memory when they need the result, such as code running while its stream is
+ * captured into a CUDA graph, plug-ins confined to a memory budget owned by a host framework's
+ * allocator, or latency-critical loops where cudaMalloc/cudaFree (which can synchronise the
+ * device) are not allowed.
+ *   values, dt, m, n, ld : as ktau_rank_prepare. [p_begin, p_end), tau64, tau32, S, n3,
+ *            count_bits : as ktau_allpairs. All caller-owned; the library allocates nothing.
+ * Working memory is a fixed array of KTAU_NOALLOC_SCRATCH_BYTES compiled into the library (every
+ * GPU that loads the library holds it until the process exits). It must hold the ranked matrix,
+ * 3*m*ld16*2 + 32*m bytes (ld16 = n rounded up to 16, arrays padded to 256 bytes) plus 256; larger
+ * inputs fail with KTAU_ETOOLARGE (m <= 16384 at n = 128 fits). The first call on a device looks
+ * up the array's device address, so make that first call before any stream capture. Every call
+ * uses the same array: calls whose GPU work overlaps (other streams, other threads) race and must
+ * be serialised by the caller. Synchronises `stream` once to read the NaN flag (KTAU_ENAN).
+ * Errors: EINVAL, ETOOLARGE, ENAN, ECUDA.
+ */
+#define KTAU_NOALLOC_SCRATCH_BYTES (16u << 20)
+ktau_status ktau_allpairs_noalloc(const void* values, ktau_dtype dt, int64_t m, int64_t n,
+                                  int64_t ld, uint64_t p_begin, uint64_t p_end, double* tau64,
+                                  float* tau32, void* S, void* n3, int32_t count_bits,
+                                  void* stream);
+
 /* Which path ktau_allpairs would take for this handle and options (KTAU_PATH_MERGE or
  * KTAU_PATH_SIGNGEMM) -- the autotuner's choice when opt is NULL or opt->path is AUTO. */
 ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, int32_t* path);

@@ -63,6 +63,8 @@ _SIGS = {
     "ktau_ranked_export": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "ktau_allpairs": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(Options), _vp],
                       ctypes.c_int),
+    "ktau_allpairs_noalloc": ([_vp, ctypes.c_int, _i64, _i64, _i64, _u64, _u64, _vp, _vp, _vp,
+                               _vp, _i32, _vp], ctypes.c_int),
     "ktau_allpairs_path": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(_i32)], ctypes.c_int),
     "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
     "ktau_device_status": ([_vp], ctypes.c_int),
@@ -197,6 +199,21 @@ def ktau_allpairs(R: Ranked, p_begin: int = 0, p_end: int | None = None, tau64=N
         p_end = R.pairs
     _check(load().ktau_allpairs(R.handle, p_begin, p_end, _ptr(tau64), _ptr(tau32), _ptr(S),
                                 _ptr(n3), count_bits, _options(options), _stream(stream)))
+
+
+def ktau_allpairs_noalloc(values: torch.Tensor, p_begin: int = 0, p_end: int | None = None,
+                          tau64=None, tau32=None, S=None, n3=None, count_bits: int = 32,
+                          stream=None):
+    """ktau_allpairs for one matrix from its values, using only the library's fixed scratch."""
+    if values.dim() != 2 or not values.is_cuda or values.stride(1) != 1:
+        raise ValueError("values must be a 2-D CUDA tensor with unit column stride")
+    dt = KTAU_F32 if values.dtype == torch.float32 else KTAU_I32
+    m, n = values.shape
+    if p_end is None:
+        p_end = m * (m - 1) // 2
+    _check(load().ktau_allpairs_noalloc(values.data_ptr(), dt, m, n, values.stride(0), p_begin,
+                                        p_end, _ptr(tau64), _ptr(tau32), _ptr(S), _ptr(n3),
+                                        count_bits, _stream(stream)))
 
 
 def ktau_allpairs_path(R: Ranked, options=None) -> int:
