@@ -29,7 +29,7 @@
  *   - tau-b = (double)S / sqrt((double)(n_0-T_u) * (double)(n_0-T_v)) in IEEE FP64
  *     (round-to-nearest sqrt and divide); NaN when either factor is 0 (a constant variable).
  *     The FP32 output is the FP64 value rounded to nearest-even.
- *   - Limits: 2 <= n <= KTAU_MAX_N, 2 <= m <= KTAU_MAX_M. Values may be +-Inf; -0.0 equals +0.0;
+ *   - Limits: 2 <= n <= KTAU_MAX_N, 1 <= m <= KTAU_MAX_M (a single variable has no pairs). Values may be +-Inf; -0.0 equals +0.0;
  *     a NaN anywhere fails the call with KTAU_ENAN.
  */
 #ifndef KTAU_H
@@ -97,13 +97,16 @@ int32_t ktau_abi_version(void);
  * Per variable u the handle holds the stable argsort pi_u (ties keep sample order), the dense
  * rank r_u (equal values share a rank, -0.0 == +0.0), and T_u = sum over tie groups t(t-1)/2.
  * Synchronises `stream` once (to read the NaN flag). On any error no handle is returned.
- * Errors: EINVAL (NULL, m < 2, n < 2, ld < n, bad dtype), ETOOLARGE, ENAN, ENOMEM, ECUDA.
+ * Errors: EINVAL (NULL, m < 1, n < 2, ld < n, bad dtype), ETOOLARGE, ENAN, ENOMEM, ECUDA.
  */
 ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int64_t n, int64_t ld,
                               void* stream, ktau_ranked** out);
 
 /* Releases a handle (NULL is accepted). Synchronises the device before freeing. */
 ktau_status ktau_ranked_free(ktau_ranked* R);
+/* Releases a handle whose every use was enqueued on `stream`: synchronises that stream only
+ * (other streams keep running), then returns its memory to the library's cache. */
+ktau_status ktau_ranked_free_on(ktau_ranked* R, void* stream);
 
 /* Shape of a handle (either output pointer may be NULL). Host only, no synchronisation. */
 ktau_status ktau_ranked_shape(const ktau_ranked* R, int64_t* m, int64_t* n);

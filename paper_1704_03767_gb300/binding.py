@@ -58,6 +58,7 @@ _SIGS = {
     "ktau_rank_prepare": ([_vp, ctypes.c_int, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)],
                           ctypes.c_int),
     "ktau_ranked_free": ([_vp], ctypes.c_int),
+    "ktau_ranked_free_on": ([_vp, _vp], ctypes.c_int),
     "ktau_ranked_shape": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "ktau_tie_counts": ([_vp, _vp, _vp], ctypes.c_int),
     "ktau_ranked_export": ([_vp, _vp, _vp, _vp], ctypes.c_int),
@@ -150,6 +151,12 @@ class Ranked:
     def free(self):
         if self.handle:
             load().ktau_ranked_free(self.handle)
+            self.handle = None
+
+    def free_on(self, stream):
+        """Release after synchronising only `stream` (all uses of the handle were on it)."""
+        if self.handle:
+            _check(load().ktau_ranked_free_on(self.handle, _stream(stream)))
             self.handle = None
 
     def __del__(self):

@@ -120,7 +120,7 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
   *out = nullptr;
   if (!values) return ktau_fail(KTAU_EINVAL, "values is NULL");
   if (dt != KTAU_F32 && dt != KTAU_I32) return ktau_fail(KTAU_EINVAL, "unknown dtype %d", (int)dt);
-  if (m < 2 || n < 2) return ktau_fail(KTAU_EINVAL, "need m >= 2 and n >= 2 (m=%lld n=%lld)",
+  if (m < 1 || n < 2) return ktau_fail(KTAU_EINVAL, "need m >= 1 and n >= 2 (m=%lld n=%lld)",
                                        (long long)m, (long long)n);
   if (ld < n) return ktau_fail(KTAU_EINVAL, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
   if (n > KTAU_MAX_N) return ktau_fail(KTAU_ETOOLARGE, "n=%lld exceeds KTAU_MAX_N=%d",
@@ -182,6 +182,15 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
 ktau_status ktau_ranked_free(ktau_ranked* R) {
   if (!R) return KTAU_OK;
   cudaDeviceSynchronize();  // no kernel may still use the handle's memory when it is recycled
+  if (R->block) ktau_dfree(R->block, R->block_bytes);
+  ktau_signgemm_release(R);
+  free(R);
+  return KTAU_OK;
+}
+
+ktau_status ktau_ranked_free_on(ktau_ranked* R, void* stream) {
+  if (!R) return KTAU_OK;
+  KTAU_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   if (R->block) ktau_dfree(R->block, R->block_bytes);
   ktau_signgemm_release(R);
   free(R);

@@ -1,0 +1,226 @@
+"""Continuous-batching query server over a database kept resident in HBM (query-based
+co-expression search, Sec. 1 of the paper).
+
+The database is ranked once and its tensor-core operands are built once; they stay on the GPU.
+Clients submit batches of query profiles (b x n) at any time. A dispatcher admits pending
+batches in arrival order whenever a stream slot is free and the batch's device memory fits the
+budget still unreserved; each slot is a thread with its own CUDA stream that runs
+
+    host->device copy of the profiles, ktau_rank_prepare, ktau_query (exact tau-b against every
+    database row + exact top-k by |tau|), device->host copy of the top-k
+
+so batches that arrive while others are on the GPU overlap with them. The result of a batch
+does not depend on what else is in flight: every kernel writes only that batch's buffers and the
+counts are exact integers formed into tau by one fixed epilogue.
+
+All computation is in libktau.so; this module is host-side scheduling only.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import binding as kb
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    queries: np.ndarray           # [b, n] float32 (host)
+    arrival: float                # time.perf_counter() at submission (or the scheduled time)
+    admitted: float = 0.0
+    finished: float = 0.0
+    topk_idx: np.ndarray | None = None
+    topk_tau: np.ndarray | None = None
+    tau: torch.Tensor | None = None   # [b, m_db] FP64 on the device when keep_tau
+    error: str | None = None
+    reserved: int = 0
+    slot: int = -1
+    done: threading.Event = dataclasses.field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Admission:
+    """Admission by device memory: a batch enters when its estimated footprint fits the budget
+    that in-flight batches have not reserved, and a stream slot is free. Batches are admitted in
+    arrival order (no overtaking)."""
+
+    def __init__(self, budget_bytes: int, slots: int):
+        self.budget = int(budget_bytes)
+        self.reserved = 0
+        self.free_slots = list(range(slots))
+
+    def try_admit(self, need: int):
+        if not self.free_slots:
+            return None
+        if need > self.budget:
+            raise ValueError(f"batch needs {need} bytes, more than the whole budget {self.budget}")
+        if self.reserved + need > self.budget:
+            return None
+        self.reserved += need
+        return self.free_slots.pop(0)
+
+    def release(self, slot: int, need: int):
+        self.reserved -= need
+        self.free_slots.append(slot)
+        self.free_slots.sort()
+
+
+class QueryServer:
+    def __init__(self, db: np.ndarray | torch.Tensor, k: int = 100, slots: int = 4,
+                 mem_budget: int | None = None, keep_tau: bool = False, options=None,
+                 device: int = 0):
+        self.dev = torch.device("cuda", device)
+        torch.cuda.set_device(self.dev)
+        dbt = torch.as_tensor(db).to(self.dev, dtype=torch.float32).contiguous()
+        self.db = kb.ktau_rank_prepare(dbt)
+        self.m_db, self.n = dbt.shape
+        self.k = min(k, self.m_db)
+        self.options = options
+        self.keep_tau = keep_tau
+        if self.n <= 1024:
+            kb.ktau_prepare_signs(self.db)  # resident tensor-core operands of the database
+        torch.cuda.synchronize(self.dev)
+        del dbt
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            mem_budget = int(free * 0.6)
+        self.admission = Admission(mem_budget, slots)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.cv = threading.Condition()
+        self.pending = collections.deque()
+        self.slot_q = [collections.deque() for _ in range(slots)]
+        self.running = True
+        self.next_id = 0
+        self.timeline = []  # (rid, slot, admitted, finished)
+        self.threads = [threading.Thread(target=self._dispatch, daemon=True)]
+        self.threads += [threading.Thread(target=self._slot, args=(i,), daemon=True)
+                         for i in range(slots)]
+        for t in self.threads:
+            t.start()
+
+    # -- memory estimate of one batch (outputs + query ranks + library scratch)
+    def footprint(self, b: int) -> int:
+        ld = (self.n + 15) // 16 * 16
+        ranked = b * ld * 6 + b * 64 + 4096
+        outs = b * self.m_db * 4 + b * self.k * 12
+        if self.keep_tau:
+            outs += b * self.m_db * 8
+        return ranked + outs + kb.ktau_query_scratch_bytes(self.db, b, self.k)
+
+    def submit(self, queries, arrival: float | None = None) -> Request:
+        q = np.ascontiguousarray(np.asarray(queries, dtype=np.float32))
+        if q.ndim != 2 or q.shape[1] != self.n:
+            raise ValueError(f"queries must be [b, {self.n}]")
+        with self.cv:
+            r = Request(self.next_id, q, time.perf_counter() if arrival is None else arrival)
+            self.next_id += 1
+            self.pending.append(r)
+            self.cv.notify_all()
+        return r
+
+    def _dispatch(self):
+        while True:
+            with self.cv:
+                while self.running and not self.pending:
+                    self.cv.wait()
+                if not self.running and not self.pending:
+                    return
+                r = self.pending[0]
+                need = self.footprint(r.queries.shape[0])
+                try:
+                    slot = self.admission.try_admit(need)
+                except ValueError as e:
+                    self.pending.popleft()
+                    r.error = str(e)
+                    r.finished = time.perf_counter()
+                    r.done.set()
+                    continue
+                if slot is None:
+                    self.cv.wait()
+                    continue
+                self.pending.popleft()
+                r.reserved, r.slot, r.admitted = need, slot, time.perf_counter()
+                self.slot_q[slot].append(r)
+                self.cv.notify_all()
+
+    def _slot(self, i: int):
+        torch.cuda.set_device(self.dev)
+        st = self.streams[i]
+        while True:
+            with self.cv:
+                while self.running and not self.slot_q[i]:
+                    self.cv.wait()
+                if not self.slot_q[i]:
+                    return
+                r = self.slot_q[i].popleft()
+            try:
+                self._run(r, st)
+            except Exception as e:  # reported on the request; the server keeps running
+                r.error = repr(e)
+            r.finished = time.perf_counter()
+            with self.cv:
+                self.admission.release(r.slot, r.reserved)
+                self.timeline.append((r.rid, r.slot, r.admitted, r.finished))
+                self.cv.notify_all()
+            r.done.set()
+
+    def _run(self, r: Request, st: torch.cuda.Stream):
+        b = r.queries.shape[0]
+        with torch.cuda.stream(st):
+            qd = torch.from_numpy(r.queries).pin_memory().to(self.dev, non_blocking=True)
+            R = kb.ktau_rank_prepare(qd, st)
+            S = torch.empty((b, self.m_db), dtype=torch.int32, device=self.dev)
+            tau = torch.empty((b, self.m_db), dtype=torch.float64, device=self.dev) \
+                if self.keep_tau else None
+            idx = torch.empty((b, self.k), dtype=torch.int32, device=self.dev)
+            tk = torch.empty((b, self.k), dtype=torch.float64, device=self.dev)
+            kb.ktau_query(self.db, R, tau, S, None, 32, self.k, idx, tk, self.options, st)
+            idx_h = idx.to("cpu", non_blocking=True)
+            tk_h = tk.to("cpu", non_blocking=True)
+            R.free_on(st)  # waits for this slot's stream only
+        r.topk_idx = idx_h.numpy()
+        r.topk_tau = tk_h.numpy()
+        r.tau = tau
+
+    def stop(self):
+        with self.cv:
+            self.running = False
+            self.cv.notify_all()
+        for t in self.threads:
+            t.join(timeout=30)
+        self.db.free()
+
+
+def percentile(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return float("nan")
+    i = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def run_open_loop(server: QueryServer, batches, rate_per_s: float, arrivals=None):
+    """Submits `batches` as a Poisson stream of the given rate (arrival times from
+    synthetic.poisson_arrivals when not given) and waits for all. Returns the requests."""
+    from synthetic import poisson_arrivals
+
+    arr = poisson_arrivals(len(batches), rate_per_s) if arrivals is None else arrivals
+    t0 = time.perf_counter()
+    reqs = []
+    for a, q in zip(arr, batches):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
+        reqs.append(server.submit(q, arrival=t0 + a))
+    for r in reqs:
+        r.done.wait()
+    return reqs

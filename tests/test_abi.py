@@ -55,8 +55,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.ktau_rank_prepare(None, 0, 10, 10, 10, None, ctypes.byref(h)) == 1
     # bad dtype
     assert lib.ktau_rank_prepare(fake, 7, 10, 10, 10, None, ctypes.byref(h)) == 1
-    # m < 2, n < 2, ld < n
-    assert lib.ktau_rank_prepare(fake, 0, 1, 10, 10, None, ctypes.byref(h)) == 1
+    # m < 1, n < 2, ld < n
+    assert lib.ktau_rank_prepare(fake, 0, 0, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare(fake, 0, 10, 1, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare(fake, 0, 10, 10, 9, None, ctypes.byref(h)) == 1
     # n beyond the 16-bit rank storage
