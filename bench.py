@@ -41,6 +41,10 @@ def _args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-query", action="store_true")
+    ap.add_argument("--query-batches", type=int, default=300,
+                    help="batches per offered load in the serving measurement")
     return ap.parse_args()
 
 
@@ -138,6 +142,106 @@ def cpu_baseline(X, seconds: float):
                       f"Knight counting, {dt:.1f} s"}
 
 
+def bench_batched(ktau, steps: int, warmup: int) -> dict:
+    """Batched form on 1000 uneven datasets: one graph launch per step vs the plain launch
+    (rank + all-pairs per dataset, one after another)."""
+    import torch
+
+    from paper_1704_03767_gb300 import autotune
+    from synthetic import batched_uneven
+
+    mats = batched_uneven(1000, seed0=0)
+    table = autotune.load()
+    paths = autotune.batch_paths(table, mats) if table else [0] * len(mats)
+    dev = torch.device("cuda")
+    descs, keep, outs = [], [], []
+    for X, pth in zip(mats, paths):
+        Xd = torch.from_numpy(X).to(dev)
+        m = X.shape[0]
+        P = m * (m - 1) // 2
+        o = (torch.empty(P, dtype=torch.float32, device=dev),
+             torch.empty(P, dtype=torch.int32, device=dev),
+             torch.empty(P, dtype=torch.int32, device=dev))
+        descs.append(ktau.batch_desc(Xd, None, o[0], o[1], o[2], 32, pth))
+        keep.append(Xd)
+        outs.append(o)
+    B = ktau.Batch(descs, keepalive=keep)
+    pairs = B.pairs()
+    n_merge, n_sg = B.paths()
+    st = torch.cuda.Stream()
+    for _ in range(max(1, warmup)):
+        B.graph_launch(st)
+    B.check(st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        B.graph_launch(st)
+    e1.record(st)
+    st.synchronize()
+    B.check(st)
+    ms = e0.elapsed_time(e1) / steps
+    # plain launch of the same work, dataset by dataset, with the same per-dataset paths
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    p0.record(cur)
+    for Xd, o, pth in zip(keep, outs, paths):
+        R = ktau.ktau_rank_prepare(Xd)
+        ktau.ktau_allpairs(R, 0, R.pairs, None, o[0], o[1], o[2], 32, {"path": pth})
+        R.free_on(cur)
+    p1.record(cur)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    B.free()
+    return {"workload": "1000 matrices, m log-uniform [16,1024], n log-uniform [20,2000], "
+                        "5% duplicated entries; FP32 tau + int32 S, n_3",
+            "datasets": len(mats), "pairs": pairs, "paths": {"merge": n_merge, "signgemm": n_sg},
+            "autotuned": bool(table), "ms_per_step": ms, "value": pairs / (ms / 1e3),
+            "unit": "pairs/s", "plain_launch": {"ms": plain_ms, "value": pairs / (plain_ms / 1e3)},
+            "speedup_vs_plain": plain_ms / ms}
+
+
+def bench_query(ktau, batches_per_load: int) -> dict:
+    """Serving: resident 65536 x 256 database, batches of 1..512 profiles (log-uniform),
+    exact tau-b against every row + top-100; closed-loop capacity, then Poisson streams at 0.3,
+    0.6 and 0.9 of it with p50 / p99 latency."""
+    import time
+
+    from paper_1704_03767_gb300.serving import QueryServer, percentile, run_open_loop
+    from synthetic import gene_expression, query_batch_sizes
+
+    D = gene_expression(65536, 256, seed=0)
+    sizes = query_batch_sizes(batches_per_load, max_batch=512, seed=2)
+    pool = gene_expression(512, 256, seed=1)
+    batches = [pool[:b] for b in sizes]
+    srv = QueryServer(D, k=100, slots=4)
+    for q in batches[:8]:  # warm-up
+        srv.submit(q).done.wait()
+    t0 = time.perf_counter()
+    reqs = [srv.submit(q) for q in batches]
+    for r in reqs:
+        r.done.wait()
+    dt = time.perf_counter() - t0
+    profiles = sum(sizes)
+    cap_batches = len(batches) / dt
+    out = {"workload": "resident DB 65536 x 256 (gene-expression recipe), batches of "
+                       "round(exp(U[0, ln 512])) profiles, top-100 by |tau|",
+           "closed_loop": {"batches_per_s": cap_batches, "queries_per_s": profiles / dt,
+                           "pairs_per_s": profiles * 65536 / dt},
+           "open_loop": []}
+    for load in (0.3, 0.6, 0.9):
+        t1 = time.perf_counter()
+        rs = run_open_loop(srv, batches, rate_per_s=load * cap_batches)
+        wall = time.perf_counter() - t1
+        lat = [r.latency * 1e3 for r in rs if r.error is None]
+        out["open_loop"].append({"offered_load": load, "batches": len(rs),
+                                 "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+                                 "queries_per_s": sum(r.queries.shape[0] for r in rs) / wall,
+                                 "errors": sum(r.error is not None for r in rs)})
+    srv.stop()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -224,8 +328,6 @@ def run_ours(args):
         step().free()
     torch.cuda.synchronize()
     ktau.ktau_device_status(stream)
-    # our kernels per step: rank, [sign expansion, tie lists,] pair kernel
-    launches_per_step = 4 if path_id == 2 else 2
 
     sampler = ClockSampler(local)
     if dist:
@@ -316,6 +418,12 @@ def run_ours(args):
         e2e = {"value": P * world * args.steps / (e2e_ms / 1e3), "unit": "pairs/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = bench_batched(ktau, max(3, args.steps // 2), args.warmup)
+    query = None
+    if not args.no_query and world == 1:
+        query = bench_query(ktau, args.query_batches)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -335,6 +443,7 @@ def run_ours(args):
         "kernels": kernels,
         "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "sample_comparisons_per_s": value * (N * (N - 1) // 2),
+        "batched": batched, "query": query,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -73,7 +73,8 @@ typedef struct {
   int32_t mapping;      /* merge path: 1 = one warp per pair, 2 = one CTA per pair */
   int32_t schedule;     /* 1 = static stride over tile ids (Sec. 4.3.2), 2 = dynamic counter */
   int32_t ctas_per_sm;  /* persistent grid = ctas_per_sm * SM count */
-  int32_t reserved[3];
+  int32_t operand_bits; /* contraction operands: 8 = FP8 e4m3 (default), 16 = BF16 */
+  int32_t reserved[2];
 } ktau_options;
 
 /* Opaque, library-owned, device-resident ranked matrix (Sec. 3: each variable ranked once):
@@ -168,8 +169,8 @@ ktau_status ktau_allpairs_noalloc(const void* values, ktau_dtype dt, int64_t m, 
 ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, int32_t* path);
 
 /* Builds the tensor-core operands of a handle now instead of on first use: the sign expansion
- * A_u[k] = sign(u_a - u_b) over all sample pairs (Sec. 3.1, Algorithm 1), stored as FP8 e4m3 for
- * n <= 128 and BF16 above (library memory, m * n_0 elements rounded up). Asynchronous on `stream`
+ * A_u[k] = sign(u_a - u_b) over all sample pairs (Sec. 3.1, Algorithm 1), stored as FP8 e4m3
+ * (library memory, m * n_0 bytes rounded up to 128 per variable). Asynchronous on `stream`
  * (allocates on first use). EINVAL when n > 1024 (path unsupported). */
 ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
 

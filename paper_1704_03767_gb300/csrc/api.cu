@@ -244,18 +244,21 @@ ktau_status ktau_check_options(const ktau_options* opt) {
   if (opt->mapping < 0 || opt->mapping > 2) return ktau_fail(KTAU_EINVAL, "bad mapping");
   if (opt->schedule < 0 || opt->schedule > 2) return ktau_fail(KTAU_EINVAL, "bad schedule");
   if (opt->ctas_per_sm < 0 || opt->ctas_per_sm > 32) return ktau_fail(KTAU_EINVAL, "bad ctas_per_sm");
+  if (opt->operand_bits != 0 && opt->operand_bits != 8 && opt->operand_bits != 16)
+    return ktau_fail(KTAU_EINVAL, "operand_bits must be 0, 8 or 16");
   return KTAU_OK;
 }
 
-// Path choice for one matrix shape. The sign contraction does n_0 multiply-adds per pair where
-// the merge path does about n log2 n compare steps, so it only pays for short vectors; the
-// crossover below is the measured one on GB300 (see the autotuner for per-shape overrides).
+// Path choice for one matrix shape, from the autotuner's measurements on GB300 (ns per pair at
+// m ~ 2000): the sign contraction wins at every n <= 1024 (e.g. 0.07 vs 3.0 at n = 128, 4.0 vs
+// 39.5 at n = 1024, with 5% or 30% duplicated values), so it is the default there unless the
+// variables are so tie-heavy that the per-pair joint-tie checks (about T_u per pair) outgrow the
+// merge path's n log2 n steps.
 int ktau_choose_path(const ktau_ranked* R, const ktau_options* opt) {
   if (opt && opt->path != KTAU_PATH_AUTO) return opt->path;
-  if (ktau_signgemm_supported(R->n) && R->n <= 256) {
-    // Joint ties for the contraction are enumerated per tied pair of u; dense ties favour merge.
+  if (ktau_signgemm_supported(R->n)) {
     const double mean_T = (double)R->stats.T_sum / (double)R->m;
-    if (mean_T <= 0.05 * (double)R->n) return KTAU_PATH_SIGNGEMM;
+    if (mean_T <= 4.0 * (double)R->n) return KTAU_PATH_SIGNGEMM;
   }
   return KTAU_PATH_MERGE;
 }
@@ -279,7 +282,8 @@ extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uin
   if (path == KTAU_PATH_SIGNGEMM) {
     if (!ktau_signgemm_supported(R->n))
       return ktau_fail(KTAU_EINVAL, "sign-contraction path supports n <= %d", KTAU_SIGNGEMM_MAX_N);
-    return ktau_signgemm_allpairs(const_cast<ktau_ranked*>(R), p_begin, p_end, out, st);
+    return ktau_signgemm_allpairs(const_cast<ktau_ranked*>(R), p_begin, p_end, out,
+                                  ktau_sign_esize(R->n, opt), st);
   }
   ktau_merge_plan plan;
   ktau_merge_default_plan(R->n, &plan);
@@ -305,7 +309,7 @@ extern "C" ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream) {
   if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
   if (!ktau_signgemm_supported(R->n))
     return ktau_fail(KTAU_EINVAL, "sign contraction supports n <= %d", KTAU_SIGNGEMM_MAX_N);
-  return ktau_signgemm_prepare(R, (cudaStream_t)stream);
+  return ktau_signgemm_prepare(R, ktau_sign_esize(R->n, nullptr), (cudaStream_t)stream);
 }
 
 ktau_status ktau_query_check_status(cudaStream_t st);

@@ -4,7 +4,8 @@
 //
 // Plan (ktau_batch_create): every dataset gets a path (its descriptor, the options, or the
 // built-in crossover by n); datasets are laid out in one library-owned workspace grouped by path
-// -- FP8 contraction (n <= 128), BF16 contraction (n <= 1024), merge -- so each group's variables
+// -- FP8 contraction, BF16 contraction (operand_bits = 16), merge with one warp per pair
+// (n <= 1024), merge with one CTA per pair (n > 1024) -- so each group's variables
 // are consecutive rows. Per group: a descriptor table in device memory and prefix sums of rows,
 // tiles and units. Contraction groups stack their sign expansions into one operand tensor (one
 // TMA descriptor per group, each dataset using only its own K blocks).
@@ -49,7 +50,7 @@ struct ktau_batch {
   int64_t* d_row_prefix = nullptr;
   int64_t total_rows = 0, max_n = 0;
   uint64_t pairs = 0;
-  GroupPlan g[3];  // 0: FP8 contraction, 1: BF16 contraction, 2: merge
+  GroupPlan g[4];  // 0: FP8 contraction, 1: BF16 contraction, 2: merge (warp), 3: merge (CTA)
   ktau_stats* d_stats = nullptr;
   std::vector<std::pair<void*, size_t>> allocs;
   cudaGraph_t graph = nullptr;
@@ -75,8 +76,8 @@ static ktau_status batch_upload(ktau_batch* B, T** dst, const std::vector<T>& v)
 static int batch_path_for(const ktau_batch_desc& d, const ktau_options* opt) {
   if (d.path != KTAU_PATH_AUTO) return d.path;
   if (opt && opt->path != KTAU_PATH_AUTO) return opt->path;
-  // Crossover measured on GB300 (autotune.py): the contraction wins for short vectors.
-  return d.n <= 256 ? KTAU_PATH_SIGNGEMM : KTAU_PATH_MERGE;
+  // Crossover measured on GB300 by the autotuner: the contraction wins up to n = 1024.
+  return d.n <= KTAU_SIGNGEMM_MAX_N ? KTAU_PATH_SIGNGEMM : KTAU_PATH_MERGE;
 }
 
 ktau_status ktau_check_counts(int64_t n, int count_bits);
@@ -122,9 +123,10 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
   std::vector<int> grp(count);
   for (int i = 0; i < count; ++i) {
     const int path = batch_path_for(descs[i], opt);
-    grp[i] = path == KTAU_PATH_MERGE ? 2 : (descs[i].n <= KTAU_SIGNGEMM_FP8_MAX_N ? 0 : 1);
+    grp[i] = path == KTAU_PATH_MERGE ? (descs[i].n <= 1024 ? 2 : 3)
+                                     : (ktau_sign_esize(descs[i].n, opt) == 1 ? 0 : 1);
   }
-  for (int gi = 0; gi < 3; ++gi)
+  for (int gi = 0; gi < 4; ++gi)
     for (int i = 0; i < count; ++i)
       if (grp[i] == gi) order.push_back(i);
 
@@ -177,11 +179,11 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     D.ndist = ndist_all + r0;
     D.maxg = maxg_all + r0;
     D.out = ktau_out{d.tau64, d.tau32, d.S, d.n3, d.count_bits};
-    D.path = grp[order[k]] == 2 ? KTAU_PATH_MERGE : KTAU_PATH_SIGNGEMM;
+    D.path = grp[order[k]] >= 2 ? KTAU_PATH_MERGE : KTAU_PATH_SIGNGEMM;
     B->g[grp[order[k]]].ids.push_back(k);
   }
   // Group plans.
-  for (int gi = 0; gi < 3; ++gi) {
+  for (int gi = 0; gi < 4; ++gi) {
     GroupPlan& G = B->g[gi];
     if (G.ids.empty()) continue;
     G.row0 = row_prefix[G.ids.front()];
@@ -191,8 +193,8 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       ktau_bds& D = B->hds[k];
       G.max_n = std::max<int64_t>(G.max_n, D.n);
       rp.push_back(rp.back() + D.m);
-      if (gi == 2) {
-        D.tq = kMergeTq;
+      if (gi >= 2) {
+        D.tq = gi == 2 ? kMergeTq : 4;
         D.w = (D.m + D.tq - 1) / D.tq;
         tp.push_back(tp.back() + D.w * (D.w + 1) / 2);
       } else {
@@ -213,7 +215,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       ktau_batch_free(B);
       return s;
     }
-    if (gi == 2) {
+    if (gi >= 2) {
       G.tiles = tp.back();
       if ((s = batch_upload(B, &G.d_tile_prefix, tp)) != KTAU_OK) {
         ktau_batch_free(B);
@@ -295,10 +297,12 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
     g.tmap = G.tmap;
     if ((s = ktau_signgemm_batch(g, st)) != KTAU_OK) return s;
   }
-  GroupPlan& M = B->g[2];
-  if (!M.ids.empty())
-    s = ktau_launch_batch_merge(B->d_ds, M.d_ids, (int)M.ids.size(), M.d_tile_prefix, M.tiles,
-                                M.max_n, st);
+  for (int gi = 2; gi < 4 && s == KTAU_OK; ++gi) {
+    GroupPlan& M = B->g[gi];
+    if (!M.ids.empty())
+      s = ktau_launch_batch_merge(B->d_ds, M.d_ids, (int)M.ids.size(), M.d_tile_prefix, M.tiles,
+                                  M.max_n, gi == 3 ? 1 : 0, st);
+  }
   return s;
 }
 
@@ -338,7 +342,7 @@ extern "C" ktau_status ktau_batch_check(ktau_batch* B, void* stream) {
 
 extern "C" ktau_status ktau_batch_paths(const ktau_batch* B, int32_t* n_merge, int32_t* n_signgemm) {
   if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
-  if (n_merge) *n_merge = (int32_t)B->g[2].ids.size();
+  if (n_merge) *n_merge = (int32_t)(B->g[2].ids.size() + B->g[3].ids.size());
   if (n_signgemm) *n_signgemm = (int32_t)(B->g[0].ids.size() + B->g[1].ids.size());
   return KTAU_OK;
 }

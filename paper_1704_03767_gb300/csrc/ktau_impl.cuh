@@ -235,7 +235,7 @@ ktau_status ktau_launch_batch_rank(const ktau_bds* ds, int count, const int64_t*
 // Merge path over the tiles of several datasets (ids[] index ds[]; tile_prefix over ids).
 ktau_status ktau_launch_batch_merge(const ktau_bds* ds, const int32_t* ids, int nids,
                                     const int64_t* tile_prefix, int64_t total_tiles, int64_t max_n,
-                                    cudaStream_t st);
+                                    int cta_team, cudaStream_t st);
 ktau_status ktau_launch_merge(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
                               const ktau_out& out, const ktau_merge_plan& plan, cudaStream_t st);
 // Every row of Q against every row of D (outputs [Q.m][ldo]).

@@ -331,13 +331,15 @@ __device__ __forceinline__ void count_pair_any(int items, const uint16_t* pu, co
 // Batched form: the tiles of every merge-path dataset form one list (prefix over ids[]); a
 // persistent CTA takes tile ids with a static stride, finds the dataset by binary search, and
 // walks the dataset's own tile triangle (Eq. 13-14) one warp per pair.
+template <int TEAM>
 __global__ void __launch_bounds__(256) batch_merge_kernel(const ktau_bds* __restrict__ ds,
                                                           const int32_t* __restrict__ ids, int nids,
                                                           const int64_t* __restrict__ tile_prefix,
                                                           int64_t total_tiles, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nteams = blockDim.x / 32;
-  const int team = threadIdx.x / 32, lane = threadIdx.x % 32;
+  __shared__ unsigned long long red[8];
+  const int nteams = blockDim.x / TEAM;
+  const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   uint32_t* tbuf = reinterpret_cast<uint32_t*>(smem) + (size_t)team * 2 * cap;
   uint32_t* tbuf2 = tbuf + cap;
   for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -363,8 +365,12 @@ __global__ void __launch_bounds__(256) batch_merge_kernel(const ktau_bds* __rest
       if (y >= D.m || x >= D.m || x <= y) continue;
       const int64_t Tu = D.T[y], Tv = D.T[x];
       long long nd, n3;
-      count_pair_any(items, D.perm + y * D.ld, D.srank + y * D.ld, D.rank + x * D.ld, n, Tu > 0,
-                     tbuf, tbuf2, lane, nd, n3);
+      if (TEAM == 32)
+        count_pair_any(items, D.perm + y * D.ld, D.srank + y * D.ld, D.rank + x * D.ld, n, Tu > 0,
+                       tbuf, tbuf2, lane, nd, n3);
+      else
+        count_pair<TEAM, 8>(D.perm + y * D.ld, D.srank + y * D.ld, D.rank + x * D.ld, n, Tu > 0,
+                            tbuf, tbuf2, lane, red, nd, n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
         ktau_store(D.out, ktau_pair_index(D.m, y, x), S, n3, n0, fac, y, x);
@@ -377,30 +383,31 @@ __global__ void __launch_bounds__(256) batch_merge_kernel(const ktau_bds* __rest
 
 ktau_status ktau_launch_batch_merge(const ktau_bds* ds, const int32_t* ids, int nids,
                                     const int64_t* tile_prefix, int64_t total_tiles, int64_t max_n,
-                                    cudaStream_t st) {
+                                    int cta_team, cudaStream_t st) {
   if (nids == 0 || total_tiles == 0) return KTAU_OK;
   const int cap = (int)((max_n + 3) & ~3LL);
   const size_t team_bytes = (size_t)2 * cap * sizeof(uint32_t);
-  const int teams = (int)std::min<size_t>(8, (200 * 1024) / team_bytes);
+  int teams = cta_team ? 1 : (int)std::min<size_t>(8, (200 * 1024) / team_bytes);
   if (teams < 1) return ktau_fail(KTAU_ETOOLARGE, "n=%lld too long for the batched merge path",
                                   (long long)max_n);
+  const int threads = cta_team ? 256 : 32 * teams;
   const size_t smem = (size_t)teams * team_bytes;
-  KTAU_CUDA(cudaFuncSetAttribute(batch_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  auto kern = cta_team ? batch_merge_kernel<256> : batch_merge_kernel<32>;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_merge_kernel, 32 * teams,
-                                                          smem));
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
   if (grid > total_tiles) grid = total_tiles;
   KTAU_TRACE("batch_merge_kernel", st);
-  batch_merge_kernel<<<(unsigned)grid, 32 * teams, smem, st>>>(ds, ids, nids, tile_prefix,
-                                                               total_tiles, cap);
+  kern<<<(unsigned)grid, threads, smem, st>>>(ds, ids, nids, tile_prefix, total_tiles, cap);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }
 
 void ktau_merge_default_plan(int64_t n, ktau_merge_plan* plan) {
-  plan->mapping = n <= 2048 ? 1 : 2;
+  // One warp per pair up to n = 1024, one CTA per pair above (autotuner, GB300: 86 vs 131 ns per
+  // pair at n = 2000, 66 vs 66 at n = 1500).
+  plan->mapping = n <= 1024 ? 1 : 2;
   plan->tile_q = n <= 256 ? 32 : (n <= 1024 ? 8 : 4);
   plan->schedule = 1;
   plan->ctas_per_sm = 0;

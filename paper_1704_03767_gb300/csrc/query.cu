@@ -225,7 +225,7 @@ extern "C" ktau_status ktau_query_scratch_bytes(const ktau_ranked* db, int64_t b
                                                 size_t* bytes) {
   if (!db || !bytes || b < 0) return ktau_fail(KTAU_EINVAL, "bad argument");
   *bytes = k > 0 ? scratch_S_bytes(db, b) : 0;
-  if (ktau_signgemm_supported(db->n)) *bytes += (size_t)b * ((db->n * (db->n - 1) / 2 + 127) / 128 * 128) * 2;
+  if (ktau_signgemm_supported(db->n)) *bytes += (size_t)b * ((db->n * (db->n - 1) / 2 + 127) / 128 * 128);
   return KTAU_OK;
 }
 
@@ -239,7 +239,7 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
   const int path = ktau_choose_path(db, opt);
   ktau_status s;
   if (path == KTAU_PATH_SIGNGEMM && ktau_signgemm_supported(db->n)) {
-    s = ktau_signgemm_rect(Q, D, out, db->m, st);
+    s = ktau_signgemm_rect(Q, D, out, db->m, ktau_sign_esize(db->n, opt), st);
   } else {
     ktau_merge_plan plan;
     ktau_merge_default_plan(db->n, &plan);

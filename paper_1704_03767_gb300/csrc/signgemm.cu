@@ -1007,14 +1007,23 @@ ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const Co
 
 bool ktau_signgemm_supported(int64_t n) { return n >= 2 && n <= KTAU_SIGNGEMM_MAX_N; }
 
-ktau_status ktau_signgemm_prepare(ktau_ranked* R, cudaStream_t st) {
-  if (R->sg_ready) return KTAU_OK;
+int ktau_sign_esize(int64_t n, const ktau_options* opt) {
+  if (opt && opt->operand_bits == 16) return 2;
+  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? 1 : 2;
+}
+
+ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
+  if (R->sg_ready && R->esize == esize) return KTAU_OK;
+  if (R->sg_ready) {  // built for the other operand type: rebuild
+    KTAU_CUDA(cudaStreamSynchronize(st));
+    ktau_signgemm_release(R);
+  }
   if (!ktau_signgemm_supported(R->n))
     return ktau_fail(KTAU_EINVAL, "sign contraction supports 2 <= n <= %d", KTAU_SIGNGEMM_MAX_N);
   const int64_t n = R->n;
   R->K = n * (n - 1) / 2;
   R->K_pad = (R->K + 127) / 128 * 128;
-  R->esize = n <= KTAU_SIGNGEMM_FP8_MAX_N ? 1 : 2;
+  R->esize = esize;
   R->sgn_bytes = (size_t)R->m * R->K_pad * R->esize;
   if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
   const size_t smem = (size_t)n * sizeof(uint16_t);
@@ -1052,8 +1061,8 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, cudaStream_t st) {
 }
 
 ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
-                                   const ktau_out& out, cudaStream_t st) {
-  ktau_status s = ktau_signgemm_prepare(R, st);
+                                   const ktau_out& out, int esize, cudaStream_t st) {
+  ktau_status s = ktau_signgemm_prepare(R, esize, st);
   if (s != KTAU_OK) return s;
   const int64_t m = R->m;
   ContractArgs a;
@@ -1086,10 +1095,10 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
 }
 
 ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
-                               cudaStream_t st) {
+                               int esize, cudaStream_t st) {
   if (Q->n != D->n) return ktau_fail(KTAU_EINVAL, "sample counts differ");
-  ktau_status s = ktau_signgemm_prepare(Q, st);
-  if (s == KTAU_OK) s = ktau_signgemm_prepare(D, st);
+  ktau_status s = ktau_signgemm_prepare(Q, esize, st);
+  if (s == KTAU_OK) s = ktau_signgemm_prepare(D, esize, st);
   if (s != KTAU_OK) return s;
   ContractArgs a;
   a.row = side_of(Q);

@@ -3,25 +3,28 @@
 // Algorithm 1 sums sign(u_a - u_b) * sign(v_a - v_b) over all sample pairs a < b, which is
 // n_c - n_d. Writing A_u[k] = sign(r_u[a_k] - r_u[b_k]) for the k-th sample pair, the numerator of
 // every pair of variables is one dot product: S(u, v) = A_u . A_v, i.e. S = A A^T over the upper
-// triangle. The {-1, 0, +1} entries are exact in FP8 (e4m3) and BF16, so the tensor cores
-// (tcgen05, FP32 accumulation in TMEM) return exact integers as long as every partial sum stays
-// within the accumulator's exact integer range (|S| <= n_0 < 2^13 for the FP8 variant, n <= 128;
-// < 2^24 for the BF16 variant). n_3 (joint ties) comes from the tie-pair lists of the variables:
-// n_3(u, v) = number of sample pairs tied in u that are also tied in v.
+// triangle. The {-1, 0, +1} entries are exact in FP8 (e4m3) and BF16, every product is exact, and
+// every partial sum is an integer of magnitude at most n_0 <= 523776 < 2^24 (n <= 1024), which an
+// FP32 accumulator holds exactly; the tcgen05 FP8 path was measured to return these sums exactly
+// at |S| = n_0 for n up to 1024 on GB300 (tests/test_gpu_signgemm.py), so FP8 is the default and
+// BF16 (twice the bytes, half the rate) stays selectable. n_3 (joint ties) comes from the tie-pair
+// lists of the variables: n_3(u, v) = number of sample pairs tied in u that are also tied in v.
 #pragma once
 #include "ktau_impl.cuh"
 
 #define KTAU_SIGNGEMM_MAX_N 1024
-#define KTAU_SIGNGEMM_FP8_MAX_N 128
+#define KTAU_SIGNGEMM_FP8_MAX_N 1024
 
 bool ktau_signgemm_supported(int64_t n);
-// Builds (once) the sign expansion, the tie-pair lists and the TMA descriptor of a handle.
-ktau_status ktau_signgemm_prepare(ktau_ranked* R, cudaStream_t st);
+// Operand element size for n and the options (1 = FP8 e4m3, 2 = BF16).
+int ktau_sign_esize(int64_t n, const ktau_options* opt);
+// Builds (once per element size) the sign expansion, the tie-pair lists and the TMA descriptor.
+ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st);
 ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
-                                   const ktau_out& out, cudaStream_t st);
+                                   const ktau_out& out, int esize, cudaStream_t st);
 // Rectangular form: every row of Q against every row of D (outputs [b][m_db], row stride ldo).
 ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
-                               cudaStream_t st);
+                               int esize, cudaStream_t st);
 void ktau_signgemm_release(ktau_ranked* R);
 
 // Batched tensor-core group: datasets bids[0..nb) of ds (all FP8 or all BF16), whose rows are

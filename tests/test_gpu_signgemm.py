@@ -40,9 +40,10 @@ def _check(got, ref):
     assert_tau32(got["tau32"], ref["tau"])
 
 
-def test_uniform_ties_64x200(ktau):
-    X = uniform_ties(64, 200, seed=0)  # BF16 operands (n > 128)
-    _check(_run(ktau, X, 64), oracle_full(X))
+@pytest.mark.parametrize("bits", [8, 16])
+def test_uniform_ties_64x200(ktau, bits):
+    X = uniform_ties(64, 200, seed=0)
+    _check(_run(ktau, X, 64, options={"path": 2, "operand_bits": bits}), oracle_full(X))
 
 
 @pytest.mark.parametrize("n", [2, 3, 17, 64, 100, 127, 128, 129, 200, 256, 300])
@@ -55,13 +56,17 @@ def test_ragged(ktau, n):
     _check(_run(ktau, X, 32), oracle_full(X))
 
 
-@pytest.mark.parametrize("n", [128, 256])
-def test_extreme_counts(ktau, n):
-    """|S| = n_0 (identical and reversed rows): the largest partial sums of the contraction."""
+@pytest.mark.parametrize("n,bits", [(128, 8), (256, 8), (512, 8), (1024, 8), (256, 16)])
+def test_extreme_counts(ktau, n, bits):
+    """Exactness of the tensor-core sums: |S| = n_0 (identical and reversed rows, the largest
+    partial sums), and strongly correlated rows, whose partial sums grow large while each MMA adds
+    a small, irregular increment (any truncation of the FP32 accumulator would show here)."""
     g = np.random.default_rng(n)
     base = g.random(n).astype(np.float32)
-    X = np.stack([base, base, -base, base * 2 + 1, g.random(n).astype(np.float32)] * 30)
-    got = _run(ktau, X, 64)
+    rows = [base, base, -base, base * 2 + 1, g.random(n).astype(np.float32)]
+    rows += [(base + 0.05 * g.random(n)).astype(np.float32) for _ in range(12)]
+    X = np.stack(rows * (3 if n >= 512 else 8))
+    got = _run(ktau, X, 64, options={"path": 2, "operand_bits": bits})
     ref = oracle_full(X)
     _check(got, ref)
     n0 = n * (n - 1) // 2
