@@ -8,7 +8,7 @@ per sample count n and tie density, the fastest exact path and merge-path mappin
     autotune.batch_paths(table, matrices)                # -> per-dataset path for ktau_batch
 
 Candidates per (n, tie density): the merge path with one warp per pair (tile side 32 or 8) and
-with one CTA per pair (n > 256), and the sign contraction (n <= 1024). Times come from the
+with one CTA per pair (n > 256), and the sign contraction (n <= 2048). Times come from the
 library's own kernel trace (CUDA events around each launch), best of a few repetitions.
 """
 from __future__ import annotations
@@ -75,7 +75,7 @@ def measure(n_grid=N_GRID, tie_grid=TIE_GRID, target_pairs=2_000_000, verbose=Tr
                      "merge_warp_q8": {"path": 1, "mapping": 1, "tile_q": 8}}
             if n > 256:
                 cands["merge_cta_q4"] = {"path": 1, "mapping": 2, "tile_q": 4}
-            if n <= 1024:
+            if n <= 2048:
                 cands["signgemm"] = {"path": 2}
             times = {}
             for name, o in cands.items():
@@ -123,8 +123,8 @@ def choose(table, n: int, tie_frac: float = 0.05) -> dict:
     cand = [e for e in ents if e["tie_frac"] == ties[0]]
     e = min(cand, key=lambda e: abs(np.log(e["n"]) - np.log(n)))
     opts = dict(e["options"])
-    if opts.get("path") == kb.KTAU_PATH_SIGNGEMM and n > 1024:
-        opts = {"path": kb.KTAU_PATH_MERGE}
+    if opts.get("path") == kb.KTAU_PATH_SIGNGEMM and n > 2048:
+        opts = {"path": kb.KTAU_PATH_MERGE, "mapping": 2}
     return opts
 
 

@@ -4,14 +4,12 @@
 //
 // Plan (ktau_batch_create): every dataset gets a path (its descriptor, the options, or the
 // built-in crossover by n); datasets are laid out in one library-owned workspace grouped by path
-// -- FP8 contraction, BF16 contraction (operand_bits = 16), merge with one warp per pair
-// (n <= 1024), merge with one CTA per pair (n > 1024) -- so each group's variables
-// are consecutive rows. Per group: a descriptor table in device memory and prefix sums of rows,
+// (see GroupKind) so each group's variables are consecutive rows. Per group: a descriptor table in device memory and prefix sums of rows,
 // tiles and units. Contraction groups stack their sign expansions into one operand tensor (one
 // TMA descriptor per group, each dataset using only its own K blocks).
 //
 // Run (ktau_batch_run): rank kernel over every row of every dataset; per contraction group:
-// sign expansion, tie lists, contraction, joint ties; one merge launch over all merge tiles.
+// sign expansion, tie lists, contraction, joint ties; one launch per merge group.
 // Nothing is allocated and nothing waits on the host, so the sequence can be graph-captured.
 #include <algorithm>
 #include <cstring>
@@ -24,7 +22,14 @@ namespace {
 
 constexpr int kMergeTq = 16;
 
+// Group kinds: contraction groups (one per operand element size and stride class, stride = K_pad
+// bytes rounded up to a power of two, so stacking wastes at most half of the operand memory),
+// merge with one warp per pair (n <= 1024), merge with one CTA per pair (n > 1024).
+enum GroupKind { kContract = 0, kMergeWarp = 1, kMergeCta = 2 };
+
 struct GroupPlan {
+  int kind = kContract;
+  int64_t key = 0;           // contraction: esize * 64 + log2(stride)
   std::vector<int32_t> ids;  // indices into the workspace-ordered descriptor table
   int32_t* d_ids = nullptr;
   int64_t* d_row_prefix = nullptr;
@@ -50,7 +55,7 @@ struct ktau_batch {
   int64_t* d_row_prefix = nullptr;
   int64_t total_rows = 0, max_n = 0;
   uint64_t pairs = 0;
-  GroupPlan g[4];  // 0: FP8 contraction, 1: BF16 contraction, 2: merge (warp), 3: merge (CTA)
+  std::vector<GroupPlan> g;  // in workspace order
   ktau_stats* d_stats = nullptr;
   std::vector<std::pair<void*, size_t>> allocs;
   cudaGraph_t graph = nullptr;
@@ -118,17 +123,37 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
   ktau_batch* B = new ktau_batch();
   B->count = count;
   cudaGetDevice(&B->device);
-  // Workspace order: FP8 contraction, BF16 contraction, merge.
+  // Group of every dataset; workspace order = group order (contraction groups by stride class,
+  // then the two merge groups).
+  std::vector<int64_t> gkey(count);
+  for (int i = 0; i < count; ++i) {
+    const ktau_batch_desc& d = descs[i];
+    if (batch_path_for(d, opt) == KTAU_PATH_MERGE) {
+      gkey[i] = (int64_t)1 << 40 | (d.n <= 1024 ? 0 : 1);
+    } else {
+      const int es = ktau_sign_esize(d.n, opt);
+      const int64_t bytes = (d.n * (d.n - 1) / 2 + 127) / 128 * 128 * es;
+      int lg = 7;
+      while (((int64_t)1 << lg) < bytes) ++lg;
+      gkey[i] = es * 64 + lg;
+    }
+  }
+  std::vector<int64_t> keys(gkey);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
   std::vector<int> order;
   std::vector<int> grp(count);
-  for (int i = 0; i < count; ++i) {
-    const int path = batch_path_for(descs[i], opt);
-    grp[i] = path == KTAU_PATH_MERGE ? (descs[i].n <= 1024 ? 2 : 3)
-                                     : (ktau_sign_esize(descs[i].n, opt) == 1 ? 0 : 1);
-  }
-  for (int gi = 0; gi < 4; ++gi)
+  B->g.resize(keys.size());
+  for (size_t gi = 0; gi < keys.size(); ++gi) {
+    GroupPlan& G = B->g[gi];
+    G.key = keys[gi];
+    G.kind = keys[gi] >> 40 ? (keys[gi] & 1 ? kMergeCta : kMergeWarp) : kContract;
     for (int i = 0; i < count; ++i)
-      if (grp[i] == gi) order.push_back(i);
+      if (gkey[i] == keys[gi]) {
+        grp[i] = (int)gi;
+        order.push_back(i);
+      }
+  }
 
   // Per-dataset workspace sizes.
   std::vector<int64_t> row_prefix(count + 1, 0);
@@ -179,11 +204,11 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     D.ndist = ndist_all + r0;
     D.maxg = maxg_all + r0;
     D.out = ktau_out{d.tau64, d.tau32, d.S, d.n3, d.count_bits};
-    D.path = grp[order[k]] >= 2 ? KTAU_PATH_MERGE : KTAU_PATH_SIGNGEMM;
+    D.path = B->g[grp[order[k]]].kind == kContract ? KTAU_PATH_SIGNGEMM : KTAU_PATH_MERGE;
     B->g[grp[order[k]]].ids.push_back(k);
   }
   // Group plans.
-  for (int gi = 0; gi < 4; ++gi) {
+  for (size_t gi = 0; gi < B->g.size(); ++gi) {
     GroupPlan& G = B->g[gi];
     if (G.ids.empty()) continue;
     G.row0 = row_prefix[G.ids.front()];
@@ -193,12 +218,12 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       ktau_bds& D = B->hds[k];
       G.max_n = std::max<int64_t>(G.max_n, D.n);
       rp.push_back(rp.back() + D.m);
-      if (gi >= 2) {
-        D.tq = gi == 2 ? kMergeTq : 4;
+      if (G.kind != kContract) {
+        D.tq = G.kind == kMergeWarp ? kMergeTq : 4;
         D.w = (D.m + D.tq - 1) / D.tq;
         tp.push_back(tp.back() + D.w * (D.w + 1) / 2);
       } else {
-        D.esize = gi == 0 ? 1 : 2;
+        D.esize = (int)(G.key / 64);
         const int64_t K = D.n * (D.n - 1) / 2;
         const int64_t K_pad = (K + 127) / 128 * 128;
         D.num_kb = K_pad * D.esize / 128;
@@ -215,7 +240,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       ktau_batch_free(B);
       return s;
     }
-    if (gi >= 2) {
+    if (G.kind != kContract) {
       G.tiles = tp.back();
       if ((s = batch_upload(B, &G.d_tile_prefix, tp)) != KTAU_OK) {
         ktau_batch_free(B);
@@ -223,7 +248,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       }
       continue;
     }
-    G.esize = gi == 0 ? 1 : 2;
+    G.esize = (int)(G.key / 64);
     G.units = up.back();
     G.jt_tiles = jp.back();
     G.stride = kpad_max * G.esize;
@@ -273,9 +298,13 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
   ktau_status s = ktau_launch_batch_rank(B->d_ds, B->count, B->d_row_prefix, B->total_rows,
                                          B->max_n, B->d_stats, st);
   if (s != KTAU_OK) return s;
-  for (int gi = 0; gi < 2; ++gi) {
-    GroupPlan& G = B->g[gi];
-    if (G.ids.empty()) continue;
+  for (GroupPlan& G : B->g) {
+    if (G.ids.empty() || s != KTAU_OK) continue;
+    if (G.kind != kContract) {
+      s = ktau_launch_batch_merge(B->d_ds, G.d_ids, (int)G.ids.size(), G.d_tile_prefix, G.tiles,
+                                  G.max_n, G.kind == kMergeCta ? 1 : 0, st);
+      continue;
+    }
     ktau_sg_group g;
     g.ds = B->d_ds;
     g.bids = G.d_ids;
@@ -295,13 +324,7 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
     g.sgn = G.sgn;
     g.stride = G.stride;
     g.tmap = G.tmap;
-    if ((s = ktau_signgemm_batch(g, st)) != KTAU_OK) return s;
-  }
-  for (int gi = 2; gi < 4 && s == KTAU_OK; ++gi) {
-    GroupPlan& M = B->g[gi];
-    if (!M.ids.empty())
-      s = ktau_launch_batch_merge(B->d_ds, M.d_ids, (int)M.ids.size(), M.d_tile_prefix, M.tiles,
-                                  M.max_n, gi == 3 ? 1 : 0, st);
+    s = ktau_signgemm_batch(g, st);
   }
   return s;
 }
@@ -342,8 +365,10 @@ extern "C" ktau_status ktau_batch_check(ktau_batch* B, void* stream) {
 
 extern "C" ktau_status ktau_batch_paths(const ktau_batch* B, int32_t* n_merge, int32_t* n_signgemm) {
   if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
-  if (n_merge) *n_merge = (int32_t)(B->g[2].ids.size() + B->g[3].ids.size());
-  if (n_signgemm) *n_signgemm = (int32_t)(B->g[0].ids.size() + B->g[1].ids.size());
+  int32_t nm = 0, ns = 0;
+  for (const GroupPlan& G : B->g) (G.kind == kContract ? ns : nm) += (int32_t)G.ids.size();
+  if (n_merge) *n_merge = nm;
+  if (n_signgemm) *n_signgemm = ns;
   return KTAU_OK;
 }
 

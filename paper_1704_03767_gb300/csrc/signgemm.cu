@@ -408,8 +408,6 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
 }
 
 constexpr int JT = 256;      // tile side (rows and columns) walked through the bijection
-constexpr int JC = 64;       // columns staged at a time
-constexpr int JTP = JC + 1;  // padded row (uint16) of the transposed rank block
 constexpr int JCAP = 8192;   // tied sample pairs of one tile's rows listed in shared memory
 
 // Tied sample pairs of variable y (sorted order: tie groups are runs of equal srank), written
@@ -523,13 +521,16 @@ __global__ void batch_ties_list_kernel(const ktau_bds* __restrict__ ds,
 // listed in shared memory, and the column variables' ranks are staged transposed (rT[a][j]) 64
 // at a time so that, for each tied pair (a, b), the 32 lanes of a warp check 32 column variables
 // with conflict-free loads. Writes every n_3 of the range (zeros included).
+template <int JCOLS>
 __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n, int tri,
                                 int64_t y0, int64_t x0, uint64_t p_begin, uint64_t p_end,
                                 int64_t ldo, void* n3out, int count_bits) {
   extern __shared__ uint32_t jsm[];
   uint32_t* s_pairs = jsm;                                     // [JCAP]
   int* s_off = (int*)(jsm + JCAP);                             // [JT + 1], tile-relative offsets
-  uint16_t* rT = (uint16_t*)(jsm + JCAP + JT + 8);             // [n][JTP]
+  constexpr int JTPC = JCOLS + 1;  // padded row (uint16) of the transposed rank block
+  constexpr int H = JCOLS / 32;     // columns per lane
+  uint16_t* rT = (uint16_t*)(jsm + JCAP + JT + 8);             // [n][JTPC]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   {
@@ -543,14 +544,14 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
       s_off[i] = (int)min(R.tie_off[y0 + i] - base_off, (int64_t)JCAP);
     if (listed)
       for (int64_t i = threadIdx.x; i < seg; i += blockDim.x) s_pairs[i] = R.tie_pairs[base_off + i];
-    for (int cs = 0; cs < JT / JC; ++cs) {
-      const int64_t xs = x0 + cs * JC;
+    for (int cs = 0; cs < JT / JCOLS; ++cs) {
+      const int64_t xs = x0 + cs * JCOLS;
       if (xs >= C.m) break;
-      if (tri && xs + JC - 1 <= y0) continue;  // sub-block entirely on or below the diagonal
+      if (tri && xs + JCOLS - 1 <= y0) continue;  // sub-block entirely on or below the diagonal
       __syncthreads();
-      // Stage the JC column variables' rank rows transposed, 8 ranks (16 bytes) per load.
+      // Stage the JCOLS column variables' rank rows transposed, 8 ranks (16 bytes) per load.
       const int vec = (int)(C.ld >> 3);
-      for (int e = threadIdx.x; e < JC * vec; e += blockDim.x) {
+      for (int e = threadIdx.x; e < JCOLS * vec; e += blockDim.x) {
         const int j = e / vec, c8 = e - j * vec;
         const int64_t v = xs + j;
         uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
@@ -559,11 +560,11 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
           const int aa = c8 * 8 + h;
-          if (aa < n) rT[aa * JTP + j] = (uint16_t)(wd[h >> 1] >> (16 * (h & 1)));
+          if (aa < n) rT[aa * JTPC + j] = (uint16_t)(wd[h >> 1] >> (16 * (h & 1)));
         }
       }
       __syncthreads();
-      const int rows_here = tri ? (int)min((int64_t)rows, xs + JC - 1 - y0) : rows;
+      const int rows_here = tri ? (int)min((int64_t)rows, xs + JCOLS - 1 - y0) : rows;
       for (int i = warp; i < rows_here; i += nwarps) {
         const int64_t y = y0 + i;
         int c0 = 0, c1 = 0;
@@ -571,16 +572,16 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
           for (int e = s_off[i]; e < s_off[i + 1]; ++e) {
             const uint32_t ab = s_pairs[e];
             const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
-            c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
-            c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+            c0 += rT[a * JTPC + lane] == rT[b * JTPC + lane];
+            if (H == 2) c1 += rT[a * JTPC + lane + 32] == rT[b * JTPC + lane + 32];
           }
         } else if (R.T[y] > 0 && R.tie_off[y] + R.T[y] <= R.tie_cap) {
           const uint32_t* tp = R.tie_pairs + R.tie_off[y];
           for (long long e = 0; e < R.T[y]; ++e) {
             const uint32_t ab = tp[e];
             const int a = (int)(ab >> 16), b = (int)(ab & 0xffffu);
-            c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
-            c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+            c0 += rT[a * JTPC + lane] == rT[b * JTPC + lane];
+            if (H == 2) c1 += rT[a * JTPC + lane + 32] == rT[b * JTPC + lane + 32];
           }
         } else if (R.T[y] > 0) {
           // Not listed (capacity): walk the tie groups of y in its sorted order directly.
@@ -595,14 +596,14 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
             const int b = pp[k];
             for (int j = g0; j < k; ++j) {
               const int a = pp[j];
-              c0 += rT[a * JTP + lane] == rT[b * JTP + lane];
-              c1 += rT[a * JTP + lane + 32] == rT[b * JTP + lane + 32];
+              c0 += rT[a * JTPC + lane] == rT[b * JTPC + lane];
+              if (H == 2) c1 += rT[a * JTPC + lane + 32] == rT[b * JTPC + lane + 32];
             }
           }
         }
         const int64_t rowbase = tri ? y * (2 * R.m - y - 1) / 2 - y - 1 : y * ldo;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < H; ++h) {
           const int64_t v = xs + lane + 32 * h;
           if (v >= C.m) continue;
           uint64_t k;
@@ -625,6 +626,7 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
   }
 }
 
+template <int JCOLS>
 __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const SideArgs C,
                                                          int64_t n, int tri, int64_t w,
                                                          int64_t ncb, int64_t tile_lo,
@@ -642,11 +644,12 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
       y0 = (t / ncb) * JT;
       x0 = (t % ncb) * JT;
     }
-    joint_ties_tile(R, C, n, tri, y0, x0, p_begin, p_end, ldo, n3out, count_bits);
+    joint_ties_tile<JCOLS>(R, C, n, tri, y0, x0, p_begin, p_end, ldo, n3out, count_bits);
   }
 }
 
 // Batched: the JT x JT tiles of every dataset of a group in one list (prefix over bids).
+template <int JCOLS>
 __global__ void __launch_bounds__(256) batch_joint_ties_kernel(
     const ktau_bds* __restrict__ ds, const int32_t* __restrict__ bids, int nb,
     const int64_t* __restrict__ tile_prefix, int64_t total_tiles) {
@@ -665,8 +668,8 @@ __global__ void __launch_bounds__(256) batch_joint_ties_kernel(
     int64_t yq, xq;
     ktau_tile_coord(w, t - tile_prefix[lo], yq, xq);
     const SideArgs S = side_of_bds(D);
-    joint_ties_tile(S, S, D.n, 1, yq * JT, xq * JT, 0, (uint64_t)(D.m * (D.m - 1) / 2), 0,
-                    D.out.n3, D.out.count_bits);
+    joint_ties_tile<JCOLS>(S, S, D.n, 1, yq * JT, xq * JT, 0, (uint64_t)(D.m * (D.m - 1) / 2), 0,
+                           D.out.n3, D.out.count_bits);
   }
 }
 
@@ -947,13 +950,14 @@ SideArgs side_of(const ktau_ranked* R) {
                   R->tie_off, R->tie_pairs, R->tie_cap, R->m};
 }
 
-ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tri, uint64_t p_begin,
-                              uint64_t p_end, int64_t ldo, void* n3, int count_bits,
-                              cudaStream_t st) {
-  const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)B->n * JTP * sizeof(uint16_t);
+template <int JCOLS>
+ktau_status launch_joint_ties_t(const ktau_ranked* A, const ktau_ranked* B, int tri,
+                                uint64_t p_begin, uint64_t p_end, int64_t ldo, void* n3,
+                                int count_bits, cudaStream_t st) {
+  const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)B->n * (JCOLS + 1) * sizeof(uint16_t);
   if (smem > 227 * 1024) return ktau_fail(KTAU_ETOOLARGE, "joint-ties staging too large");
-  KTAU_CUDA(cudaFuncSetAttribute(joint_ties_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  auto kern = joint_ties_kernel<JCOLS>;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int64_t w = 0, ncb = 0, lo = 0, hi = 0;
   if (tri) {
     const int64_t m = A->m;
@@ -968,16 +972,24 @@ ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tr
     hi = ((A->m + JT - 1) / JT) * ncb;
   }
   int occ = 0;
-  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, joint_ties_kernel, 256, smem));
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
   if (grid > hi - lo) grid = hi - lo;
   if (grid < 1) grid = 1;
   KTAU_TRACE("joint_ties_kernel", st);
-  joint_ties_kernel<<<(unsigned)grid, 256, smem, st>>>(side_of(A), side_of(B), A->n, tri, w, ncb,
-                                                       lo, hi, p_begin, p_end, ldo, n3,
-                                                       count_bits);
+  kern<<<(unsigned)grid, 256, smem, st>>>(side_of(A), side_of(B), A->n, tri, w, ncb, lo, hi,
+                                          p_begin, p_end, ldo, n3, count_bits);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
+}
+
+ktau_status launch_joint_ties(const ktau_ranked* A, const ktau_ranked* B, int tri, uint64_t p_begin,
+                              uint64_t p_end, int64_t ldo, void* n3, int count_bits,
+                              cudaStream_t st) {
+  // 64 column variables staged at a time; 32 for long vectors (shared memory).
+  return B->n <= 1024
+             ? launch_joint_ties_t<64>(A, B, tri, p_begin, p_end, ldo, n3, count_bits, st)
+             : launch_joint_ties_t<32>(A, B, tri, p_begin, p_end, ldo, n3, count_bits, st);
 }
 
 template <int ESIZE>
@@ -1188,17 +1200,17 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   ktau_status s = g.esize == 1 ? launch_contract_maps<1>(g.tmap, g.tmap, a, g.units, st)
                                : launch_contract_maps<2>(g.tmap, g.tmap, a, g.units, st);
   if (s != KTAU_OK) return s;
-  const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)g.max_n * JTP * sizeof(uint16_t);
-  KTAU_CUDA(cudaFuncSetAttribute(batch_joint_ties_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int jcols = g.max_n <= 1024 ? 64 : 32;
+  const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)g.max_n * (jcols + 1) * sizeof(uint16_t);
+  auto jk = jcols == 64 ? batch_joint_ties_kernel<64> : batch_joint_ties_kernel<32>;
+  KTAU_CUDA(cudaFuncSetAttribute(jk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_joint_ties_kernel, 256, smem));
+  KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jk, 256, smem));
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
   if (grid > g.jt_tiles) grid = g.jt_tiles;
   if (grid < 1) grid = 1;
   KTAU_TRACE("batch_joint_ties_kernel", st);
-  batch_joint_ties_kernel<<<(unsigned)grid, 256, smem, st>>>(g.ds, g.bids, g.nb, g.jt_prefix,
-                                                             g.jt_tiles);
+  jk<<<(unsigned)grid, 256, smem, st>>>(g.ds, g.bids, g.nb, g.jt_prefix, g.jt_tiles);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }

@@ -4,16 +4,16 @@
 // n_c - n_d. Writing A_u[k] = sign(r_u[a_k] - r_u[b_k]) for the k-th sample pair, the numerator of
 // every pair of variables is one dot product: S(u, v) = A_u . A_v, i.e. S = A A^T over the upper
 // triangle. The {-1, 0, +1} entries are exact in FP8 (e4m3) and BF16, every product is exact, and
-// every partial sum is an integer of magnitude at most n_0 <= 523776 < 2^24 (n <= 1024), which an
-// FP32 accumulator holds exactly; the tcgen05 FP8 path was measured to return these sums exactly
-// at |S| = n_0 for n up to 1024 on GB300 (tests/test_gpu_signgemm.py), so FP8 is the default and
+// every partial sum is an integer of magnitude at most n_0 <= 2096128 < 2^24 (n <= 2048), which
+// an FP32 accumulator holds exactly; the tcgen05 FP8 path was measured to return these sums exactly
+// at |S| = n_0 for n up to 2048 on GB300 (tests/test_gpu_signgemm.py), so FP8 is the default and
 // BF16 (twice the bytes, half the rate) stays selectable. n_3 (joint ties) comes from the tie-pair
 // lists of the variables: n_3(u, v) = number of sample pairs tied in u that are also tied in v.
 #pragma once
 #include "ktau_impl.cuh"
 
-#define KTAU_SIGNGEMM_MAX_N 1024
-#define KTAU_SIGNGEMM_FP8_MAX_N 1024
+#define KTAU_SIGNGEMM_MAX_N 2048
+#define KTAU_SIGNGEMM_FP8_MAX_N 2048
 
 bool ktau_signgemm_supported(int64_t n);
 // Operand element size for n and the options (1 = FP8 e4m3, 2 = BF16).

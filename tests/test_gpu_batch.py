@@ -50,7 +50,7 @@ def test_small_batch_matches_oracle(ktau, mode):
     mats = batched_uneven(count=24, m_range=(16, 150), n_range=(20, 300), seed0=100)
     mats[3][5] = 1.0  # a constant variable
     if mode != "signgemm":  # the contraction path is limited to n <= 1024
-        mats.append(uniform_ties(40, 1200, tie_frac=0.1, seed=5))  # long vectors: merge path
+        mats.append(uniform_ties(40, 2100, tie_frac=0.1, seed=5))  # long vectors: merge path
     paths = None if mode == "auto" else [1 if mode == "merge" else 2] * len(mats)
     B, outs = _make(ktau, mats, 64, paths)
     nm, ns = B.paths()

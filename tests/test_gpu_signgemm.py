@@ -46,9 +46,9 @@ def test_uniform_ties_64x200(ktau, bits):
     _check(_run(ktau, X, 64, options={"path": 2, "operand_bits": bits}), oracle_full(X))
 
 
-@pytest.mark.parametrize("n", [2, 3, 17, 64, 100, 127, 128, 129, 200, 256, 300])
+@pytest.mark.parametrize("n", [2, 3, 17, 64, 100, 127, 128, 129, 200, 256, 300, 1100])
 def test_ragged(ktau, n):
-    m = 300  # two 256-row super-tiles, ragged
+    m = 300 if n < 1000 else 90  # two 256-row super-tiles, ragged
     X = uniform_ties(m, n, tie_frac=0.2, seed=n)
     X[10] = X[11]
     X[12] = -X[13]
@@ -56,7 +56,8 @@ def test_ragged(ktau, n):
     _check(_run(ktau, X, 32), oracle_full(X))
 
 
-@pytest.mark.parametrize("n,bits", [(128, 8), (256, 8), (512, 8), (1024, 8), (256, 16)])
+@pytest.mark.parametrize("n,bits", [(128, 8), (256, 8), (512, 8), (1024, 8), (2048, 8),
+                                    (256, 16)])
 def test_extreme_counts(ktau, n, bits):
     """Exactness of the tensor-core sums: |S| = n_0 (identical and reversed rows, the largest
     partial sums), and strongly correlated rows, whose partial sums grow large while each MMA adds
@@ -65,7 +66,7 @@ def test_extreme_counts(ktau, n, bits):
     base = g.random(n).astype(np.float32)
     rows = [base, base, -base, base * 2 + 1, g.random(n).astype(np.float32)]
     rows += [(base + 0.05 * g.random(n)).astype(np.float32) for _ in range(12)]
-    X = np.stack(rows * (3 if n >= 512 else 8))
+    X = np.stack(rows * (2 if n >= 1024 else (3 if n >= 512 else 8)))
     got = _run(ktau, X, 64, options={"path": 2, "operand_bits": bits})
     ref = oracle_full(X)
     _check(got, ref)
