@@ -359,9 +359,9 @@ def run_ours(args):
     kernels = {k: {"launches": c, "avg_ms": t / c, "share": t / max(1e-9, sum(
         x[1] for x in per_kernel.values()))} for k, (c, t) in per_kernel.items()}
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1704_03767_gb300.sharding import max_over_ranks
+
+        total_ms = max_over_ranks(total_ms, device=dev)  # whole-job time = slowest rank
         dist.barrier()
     ms_per_step = total_ms / args.steps
     value = P * world * args.steps / (total_ms / 1e3)
