@@ -95,7 +95,7 @@ struct ktau_trace_scope {
 // root of Eq. 3 are replaced by the product of per-variable factors r_u = 1/sqrt(n_0 - T_u)
 // (computed once per variable in IEEE FP64 by the rank kernel):
 //   tau64 = ((double)S * r_u) * r_v                    two FP64 products, error <= 4 ulp
-//   tau32 = RN_f32 of the FP64 formula S / sqrt(D_u D_v), evaluated as a float-float product
+//   tau32 = RN_f32 of the FP64 formula S / sqrt(D_u D_v), decided from a float-float product
 //           S * r_u * r_v (relative error < 2^-43); when that value lies within 2^-40 of a float
 //           rounding boundary, the FP64 formula itself is evaluated, so the result is always
 //           exactly the round-to-nearest float of the FP64 formula.
@@ -122,49 +122,30 @@ __device__ __forceinline__ double ktau_tau64(int64_t S, double ru, double rv) {
   return __dmul_rn(__dmul_rn((double)S, ru), rv);
 }
 
-__device__ __forceinline__ float ktau_tau32(int64_t S, float2 fu, float2 fv, int64_t n0,
-                                            int64_t Tu, int64_t Tv) {
-  if (isnan(fu.x) || isnan(fv.x)) return __int_as_float(0x7fc00000);
-  if (S == 0) return 0.0f;
-  // S as an exact float-float pair (S fits int32 because |S| <= n_0 < 2^27).
-  const int Si = (int)S;
-  const float sh = __int2float_rn(Si);
-  const float sl = __int2float_rn(Si - __float2int_rn(sh));
-  // t = S * r_u as float-float
-  const float th = __fmul_rn(sh, fu.x);
-  const float tl = __fadd_rn(__fmaf_rn(sh, fu.x, -th), __fmaf_rn(sh, fu.y, __fmul_rn(sl, fu.x)));
-  // p = t * r_v as float-float
-  const float ph = __fmul_rn(th, fv.x);
-  const float pl = __fadd_rn(__fmaf_rn(th, fv.x, -ph), __fmaf_rn(th, fv.y, __fmul_rn(tl, fv.x)));
-  const float f = __fadd_rn(ph, pl);
-  const float d = __fadd_rn(__fsub_rn(ph, f), pl);  // distance of the float-float value from f
-  const uint32_t fb = __float_as_uint(fabsf(f));
-  float half = __uint_as_float(((fb >> 23) - 24u) << 23);  // ulp(f) / 2 (|f| >= 2^-27 here)
-  if ((fb & 0x7fffffu) == 0) half = __fmul_rn(half, 0.5f);  // power of two: closer neighbour below
-  const float margin = __fadd_rn(__fmul_rn(fabsf(f), 0x1p-40f), __fmul_rn(fabsf(d), 0x1p-22f));
-  if (__fadd_rn(fabsf(d), margin) < half) return f;
-  return __double2float_rn(ktau_tau_b_formula(S, n0 - Tu, n0 - Tv));
-}
-
-// Fast part of ktau_tau32 (the float-float product and the boundary test) for a non-NaN
-// variable pair; returns false when the slow FP64 formula is needed.
+// RN_f32 of tau-b: the float-float product S * r_u * r_v approximates tau within 2^-43 relative
+// (and the FP64 formula is within 2^-51 of tau), so when rounding the approximation 2^-40 |tau|
+// lower and higher gives the same float, every value in between -- the FP64 formula's included --
+// rounds to that float (round-to-nearest is monotone). Otherwise (rare) the FP64 formula decides.
+// A constant variable has NaN factors: the test fails and the formula returns NaN.
 __device__ __forceinline__ bool ktau_tau32_fast(int S, float2 fu, float2 fv, float& out) {
   const float sh = __int2float_rn(S);
-  const float sl = __int2float_rn(S - __float2int_rn(sh));
+  const float sl = __int2float_rn(S - __float2int_rn(sh));  // S == sh + sl exactly
   const float th = __fmul_rn(sh, fu.x);
   const float tl = __fadd_rn(__fmaf_rn(sh, fu.x, -th), __fmaf_rn(sh, fu.y, __fmul_rn(sl, fu.x)));
   const float ph = __fmul_rn(th, fv.x);
   const float pl = __fadd_rn(__fmaf_rn(th, fv.x, -ph), __fmaf_rn(th, fv.y, __fmul_rn(tl, fv.x)));
-  const float f = __fadd_rn(ph, pl);
-  const float d = __fadd_rn(__fsub_rn(ph, f), pl);
-  const uint32_t fb = __float_as_uint(fabsf(f));
-  float half = __uint_as_float(((fb >> 23) - 24u) << 23);
-  if ((fb & 0x7fffffu) == 0) half = __fmul_rn(half, 0.5f);
-  const float margin = __fadd_rn(__fmul_rn(fabsf(f), 0x1p-40f), __fmul_rn(fabsf(d), 0x1p-22f));
-  out = S == 0 ? 0.0f : f;
-  // NaN factors (constant variables) take the slow path, which returns NaN.
-  if (isnan(fu.x) || isnan(fv.x)) return false;
-  return S == 0 || __fadd_rn(fabsf(d), margin) < half;
+  const float d = __fmul_rn(fabsf(ph), 0x1p-40f);
+  const float lo = __fadd_rn(ph, __fsub_rn(pl, d));
+  const float hi = __fadd_rn(ph, __fadd_rn(pl, d));
+  out = lo;
+  return lo == hi;
+}
+
+__device__ __forceinline__ float ktau_tau32(int64_t S, float2 fu, float2 fv, int64_t n0,
+                                            int64_t Tu, int64_t Tv) {
+  float f;
+  if (ktau_tau32_fast((int)S, fu, fv, f)) return f;
+  return __double2float_rn(ktau_tau_b_formula(S, n0 - Tu, n0 - Tv));
 }
 
 struct ktau_fac {
