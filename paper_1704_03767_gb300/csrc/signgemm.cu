@@ -521,7 +521,9 @@ __global__ void batch_ties_list_kernel(const ktau_bds* __restrict__ ds,
 // listed in shared memory, and the column variables' ranks are staged transposed (rT[a][j]) 64
 // at a time so that, for each tied pair (a, b), the 32 lanes of a warp check 32 column variables
 // with conflict-free loads. Writes every n_3 of the range (zeros included).
-template <int JCOLS>
+// SPARSE: the output was zeroed beforehand; only rows with ties are visited and only nonzero
+// counts are stored. Otherwise every n_3 of the tile is stored.
+template <int JCOLS, bool SPARSE>
 __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n, int tri,
                                 int64_t y0, int64_t x0, uint64_t p_begin, uint64_t p_end,
                                 int64_t ldo, void* n3out, int count_bits) {
@@ -540,6 +542,7 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
     const int64_t base_off = R.tie_off[y0];
     const int64_t seg = R.tie_off[y0 + rows] - base_off;
     const bool listed = R.tie_off[y0 + rows] <= R.tie_cap && seg <= JCAP;
+    if (SPARSE && seg == 0) return;  // no row of this tile has ties: every n_3 is 0
     for (int i = threadIdx.x; i <= rows; i += blockDim.x)
       s_off[i] = (int)min(R.tie_off[y0 + i] - base_off, (int64_t)JCAP);
     if (listed)
@@ -567,6 +570,7 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
       const int rows_here = tri ? (int)min((int64_t)rows, xs + JCOLS - 1 - y0) : rows;
       for (int i = warp; i < rows_here; i += nwarps) {
         const int64_t y = y0 + i;
+        if (SPARSE && (listed ? s_off[i + 1] == s_off[i] : R.T[y] == 0)) continue;
         int c0 = 0, c1 = 0;
         if (listed) {
           for (int e = s_off[i]; e < s_off[i + 1]; ++e) {
@@ -601,6 +605,7 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
             }
           }
         }
+        if (SPARSE && c0 == 0 && c1 == 0) continue;  // nothing to store (output zeroed)
         const int64_t rowbase = tri ? y * (2 * R.m - y - 1) / 2 - y - 1 : y * ldo;
 #pragma unroll
         for (int h = 0; h < H; ++h) {
@@ -616,6 +621,7 @@ __device__ void joint_ties_tile(const SideArgs& R, const SideArgs& C, int64_t n,
             k = (uint64_t)(rowbase + v);
           }
           const int val = h ? c1 : c0;
+          if (SPARSE && val == 0) continue;
           if (count_bits == 64)
             __stcs((long long*)n3out + k, (long long)val);
           else
@@ -644,7 +650,7 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
       y0 = (t / ncb) * JT;
       x0 = (t % ncb) * JT;
     }
-    joint_ties_tile<JCOLS>(R, C, n, tri, y0, x0, p_begin, p_end, ldo, n3out, count_bits);
+    joint_ties_tile<JCOLS, true>(R, C, n, tri, y0, x0, p_begin, p_end, ldo, n3out, count_bits);
   }
 }
 
@@ -668,8 +674,8 @@ __global__ void __launch_bounds__(256) batch_joint_ties_kernel(
     int64_t yq, xq;
     ktau_tile_coord(w, t - tile_prefix[lo], yq, xq);
     const SideArgs S = side_of_bds(D);
-    joint_ties_tile<JCOLS>(S, S, D.n, 1, yq * JT, xq * JT, 0, (uint64_t)(D.m * (D.m - 1) / 2), 0,
-                           D.out.n3, D.out.count_bits);
+    joint_ties_tile<JCOLS, false>(S, S, D.n, 1, yq * JT, xq * JT, 0,
+                                  (uint64_t)(D.m * (D.m - 1) / 2), 0, D.out.n3, D.out.count_bits);
   }
 }
 
@@ -970,6 +976,13 @@ ktau_status launch_joint_ties_t(const ktau_ranked* A, const ktau_ranked* B, int 
   } else {
     ncb = (B->m + JT - 1) / JT;
     hi = ((A->m + JT - 1) / JT) * ncb;
+  }
+  // n_3 is 0 for every pair with a tie-free variable: zero the output at full write bandwidth and
+  // let the kernel store only the nonzero counts.
+  const size_t count = tri ? (size_t)(p_end - p_begin) : (size_t)A->m * (size_t)ldo;
+  {
+    KTAU_TRACE("n3_zero_fill", st);
+    KTAU_CUDA(cudaMemsetAsync(n3, 0, count * (size_t)(count_bits / 8), st));
   }
   int occ = 0;
   KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
