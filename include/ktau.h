@@ -164,6 +164,21 @@ ktau_status ktau_allpairs_noalloc(const void* values, ktau_dtype dt, int64_t m, 
                                   float* tau32, void* S, void* n3, int32_t count_bits,
                                   void* stream);
 
+/*
+ * ktau_allpairs_host -- ktau_allpairs with HOST output buffers, in passes (Sec. 4.3.1: the range is
+ * split into sub-ranges computed one after another, and each pass's results are copied to the host
+ * while the next pass computes). Device staging is two library-owned buffers per output.
+ *   tau64_h, tau32_h, S_h, n3_h : host buffers of p_end - p_begin elements (any may be NULL);
+ *            page-locked memory (cudaHostAlloc / pinned tensors) gives full copy bandwidth.
+ *   pass_pairs : pairs per pass; 0 picks about a quarter of the range, aligned to 256-row blocks.
+ * Synchronises `stream` before returning (the host buffers are complete on return). Other
+ * arguments and errors as ktau_allpairs.
+ */
+ktau_status ktau_allpairs_host(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                               double* tau64_h, float* tau32_h, void* S_h, void* n3_h,
+                               int32_t count_bits, const ktau_options* opt, uint64_t pass_pairs,
+                               void* stream);
+
 /* Which path ktau_allpairs would take for this handle and options (KTAU_PATH_MERGE or
  * KTAU_PATH_SIGNGEMM) -- the autotuner's choice when opt is NULL or opt->path is AUTO. */
 ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, int32_t* path);

@@ -20,6 +20,7 @@ from .binding import (  # noqa: F401
     batch_desc,
     declared_symbols,
     ktau_allpairs,
+    ktau_allpairs_host,
     ktau_allpairs_noalloc,
     ktau_allpairs_path,
     ktau_device_status,

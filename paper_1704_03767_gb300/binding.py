@@ -67,6 +67,8 @@ _SIGS = {
                       ctypes.c_int),
     "ktau_allpairs_noalloc": ([_vp, ctypes.c_int, _i64, _i64, _i64, _u64, _u64, _vp, _vp, _vp,
                                _vp, _i32, _vp], ctypes.c_int),
+    "ktau_allpairs_host": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(Options),
+                            _u64, _vp], ctypes.c_int),
     "ktau_allpairs_path": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(_i32)], ctypes.c_int),
     "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
     "ktau_device_status": ([_vp], ctypes.c_int),
@@ -222,6 +224,21 @@ def ktau_allpairs_noalloc(values: torch.Tensor, p_begin: int = 0, p_end: int | N
     _check(load().ktau_allpairs_noalloc(values.data_ptr(), dt, m, n, values.stride(0), p_begin,
                                         p_end, _ptr(tau64), _ptr(tau32), _ptr(S), _ptr(n3),
                                         count_bits, _stream(stream)))
+
+
+def ktau_allpairs_host(R: Ranked, p_begin: int = 0, p_end: int | None = None, tau64=None,
+                       tau32=None, S=None, n3=None, count_bits: int = 32, options=None,
+                       pass_pairs: int = 0, stream=None):
+    """ktau_allpairs into HOST tensors (pinned for full bandwidth), in passes whose copies overlap
+    the next pass's compute. Returns when the host tensors are complete."""
+    if p_end is None:
+        p_end = R.pairs
+    for t in (tau64, tau32, S, n3):
+        if t is not None and t.is_cuda:
+            raise ValueError("ktau_allpairs_host takes host tensors")
+    _check(load().ktau_allpairs_host(R.handle, p_begin, p_end, _ptr(tau64), _ptr(tau32), _ptr(S),
+                                     _ptr(n3), count_bits, _options(options), pass_pairs,
+                                     _stream(stream)))
 
 
 def ktau_allpairs_path(R: Ranked, options=None) -> int:

@@ -383,3 +383,93 @@ extern "C" ktau_status ktau_trace_collect(ktau_trace_record* out, int32_t cap, i
   if (count) *count = n < cap ? n : cap;
   return KTAU_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Passes with overlapped device-to-host copies (Sec. 4.3.1).
+// ---------------------------------------------------------------------------------------------
+extern "C" ktau_status ktau_allpairs_host(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                                          double* tau64_h, float* tau32_h, void* S_h, void* n3_h,
+                                          int32_t count_bits, const ktau_options* opt,
+                                          uint64_t pass_pairs, void* stream) {
+  if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  ktau_status s = ktau_check_counts(R->n, count_bits);
+  if (s != KTAU_OK) return s;
+  if ((s = ktau_check_options(opt)) != KTAU_OK) return s;
+  const uint64_t P = (uint64_t)(R->m * (R->m - 1) / 2);
+  if (p_begin > p_end || p_end > P) return ktau_fail(KTAU_EINVAL, "pair range outside the triangle");
+  if (p_begin == p_end) return KTAU_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t total = p_end - p_begin;
+  if (pass_pairs == 0) {
+    // about a quarter of the range, rounded to whole 256-row blocks of the triangle
+    pass_pairs = (total + 3) / 4;
+    const uint64_t rowblock = (uint64_t)R->m * 256;
+    if (pass_pairs > rowblock) pass_pairs = (pass_pairs + rowblock - 1) / rowblock * rowblock;
+  }
+  if (pass_pairs > total) pass_pairs = total;
+  const size_t cb = (size_t)count_bits / 8;
+  const size_t esz[4] = {sizeof(double), sizeof(float), cb, cb};
+  void* hst[4] = {tau64_h, tau32_h, S_h, n3_h};
+  void* dev[2][4] = {{nullptr}};
+  size_t bytes[4];
+  for (int o = 0; o < 4; ++o) bytes[o] = (size_t)pass_pairs * esz[o];
+  for (int b = 0; b < 2 && s == KTAU_OK; ++b)
+    for (int o = 0; o < 4 && s == KTAU_OK; ++o)
+      if (hst[o]) s = ktau_dmalloc(&dev[b][o], bytes[o]);
+  // One copy stream per output array, so that several copy engines move data at once.
+  cudaStream_t cs[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2][4] = {{nullptr}};
+  cudaError_t e = cudaSuccess;
+  if (s == KTAU_OK) {
+    for (int o = 0; o < 4 && e == cudaSuccess; ++o)
+      if (hst[o]) e = cudaStreamCreateWithFlags(&cs[o], cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&computed[b], cudaEventDisableTiming);
+      for (int o = 0; o < 4 && e == cudaSuccess; ++o)
+        if (hst[o]) e = cudaEventCreateWithFlags(&copied[b][o], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) s = ktau_cuda_fail(e, "stream/event creation");
+  }
+  int pass = 0;
+  for (uint64_t lo = p_begin; lo < p_end && s == KTAU_OK; lo += pass_pairs, ++pass) {
+    const uint64_t hi = lo + pass_pairs < p_end ? lo + pass_pairs : p_end;
+    const int b = pass & 1;
+    // the buffer's previous copies must be done before it is overwritten
+    for (int o = 0; o < 4 && pass >= 2; ++o)
+      if (hst[o] && (e = cudaStreamWaitEvent(st, copied[b][o], 0)) != cudaSuccess) {
+        s = ktau_cuda_fail(e, "cudaStreamWaitEvent");
+        break;
+      }
+    if (s != KTAU_OK) break;
+    s = ktau_allpairs(R, lo, hi, (double*)dev[b][0], (float*)dev[b][1], dev[b][2], dev[b][3],
+                      count_bits, opt, stream);
+    if (s != KTAU_OK) break;
+    if ((e = cudaEventRecord(computed[b], st)) != cudaSuccess) {
+      s = ktau_cuda_fail(e, "event");
+      break;
+    }
+    for (int o = 0; o < 4; ++o) {
+      if (!hst[o]) continue;
+      if ((e = cudaStreamWaitEvent(cs[o], computed[b], 0)) != cudaSuccess ||
+          (e = cudaMemcpyAsync((char*)hst[o] + (lo - p_begin) * esz[o], dev[b][o],
+                               (hi - lo) * esz[o], cudaMemcpyDeviceToHost, cs[o])) != cudaSuccess ||
+          (e = cudaEventRecord(copied[b][o], cs[o])) != cudaSuccess) {
+        s = ktau_cuda_fail(e, "device-to-host copy");
+        break;
+      }
+    }
+  }
+  for (int o = 0; o < 4; ++o)
+    if (cs[o]) cudaStreamSynchronize(cs[o]);
+  cudaStreamSynchronize(st);
+  for (int b = 0; b < 2; ++b) {
+    if (computed[b]) cudaEventDestroy(computed[b]);
+    for (int o = 0; o < 4; ++o) {
+      if (copied[b][o]) cudaEventDestroy(copied[b][o]);
+      if (dev[b][o]) ktau_dfree(dev[b][o], bytes[o]);
+    }
+  }
+  for (int o = 0; o < 4; ++o)
+    if (cs[o]) cudaStreamDestroy(cs[o]);
+  return s;
+}
