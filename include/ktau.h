@@ -195,6 +195,16 @@ ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
  * its boundary without exact keys (n > 300; that query's top-k order is not exact). */
 ktau_status ktau_device_status(void* stream);
 
+/* Failure injection for tests of error handling (no GPU fault involved):
+ * ktau_debug_fail_alloc(k): the next k library allocations succeed, every later one fails as if
+ * the device were out of memory (KTAU_ENOMEM); k < 0 switches the injection off.
+ * ktau_debug_wait_timeout(limit_ns, stream): launches one small kernel whose bounded wait (the
+ * same wait the tensor-core kernels use) watches an mbarrier nothing arrives on; after limit_ns it
+ * raises the device status word and returns, so ktau_device_status then reports KTAU_ETIMEOUT and
+ * the context stays usable. */
+ktau_status ktau_debug_fail_alloc(int32_t k);
+ktau_status ktau_debug_wait_timeout(int64_t limit_ns, void* stream);
+
 /* Kernel trace: when enabled, every kernel the library launches is bracketed by CUDA events on
  * its stream (no extra synchronisation). ktau_trace_collect waits for the recorded launches,
  * copies up to `cap` records (kernel name, milliseconds, in launch order) and clears the list.

@@ -23,6 +23,8 @@ from .binding import (  # noqa: F401
     ktau_allpairs_host,
     ktau_allpairs_noalloc,
     ktau_allpairs_path,
+    ktau_debug_fail_alloc,
+    ktau_debug_wait_timeout,
     ktau_device_status,
     ktau_prepare_signs,
     ktau_query,

@@ -72,6 +72,8 @@ _SIGS = {
     "ktau_allpairs_path": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(_i32)], ctypes.c_int),
     "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
     "ktau_device_status": ([_vp], ctypes.c_int),
+    "ktau_debug_fail_alloc": ([_i32], ctypes.c_int),
+    "ktau_debug_wait_timeout": ([_i64, _vp], ctypes.c_int),
     "ktau_trace_enable": ([_i32], ctypes.c_int),
     "ktau_trace_collect": ([ctypes.POINTER(TraceRecord), _i32, ctypes.POINTER(_i32)],
                            ctypes.c_int),
@@ -253,6 +255,14 @@ def ktau_prepare_signs(R: Ranked, stream=None):
 
 def ktau_device_status(stream=None):
     _check(load().ktau_device_status(_stream(stream)))
+
+
+def ktau_debug_fail_alloc(k: int):
+    _check(load().ktau_debug_fail_alloc(k))
+
+
+def ktau_debug_wait_timeout(limit_ns: int, stream=None):
+    _check(load().ktau_debug_wait_timeout(limit_ns, _stream(stream)))
 
 
 def ktau_trace_enable(on: bool = True):

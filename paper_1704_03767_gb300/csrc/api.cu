@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -50,9 +51,25 @@ struct FreeBlock {
 std::vector<FreeBlock>* g_free_blocks = new std::vector<FreeBlock>();  // never destroyed
 }  // namespace
 
+static std::atomic<int> g_fail_alloc_after{-1};
+
+extern "C" ktau_status ktau_debug_fail_alloc(int32_t k) {
+  g_fail_alloc_after.store(k < 0 ? -1 : k);
+  return KTAU_OK;
+}
+
 ktau_status ktau_dmalloc(void** p, size_t bytes) {
   int dev = 0;
   cudaGetDevice(&dev);
+  // injected failure (tests of the error paths)
+  int left = g_fail_alloc_after.load();
+  while (left >= 0) {
+    if (left == 0) {
+      *p = nullptr;
+      return ktau_fail(KTAU_ENOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+    }
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) break;
+  }
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     for (size_t i = 0; i < g_free_blocks->size(); ++i) {

@@ -187,6 +187,30 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 __device__ __forceinline__ bool sg_failed() { return *(volatile unsigned int*)&g_sg_error != 0; }
 
+// The same bounded wait with a caller-chosen limit; used to exercise the timeout path.
+__device__ __noinline__ bool mbar_wait_limit(uint32_t bar, uint32_t parity,
+                                             unsigned long long limit_ns) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    __nanosleep(1000);
+    if (gtimer() - t0 > limit_ns) {
+      atomicExch(&g_sg_error, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+
+// One thread waits on an mbarrier that nothing arrives on until the limit runs out.
+__global__ void wait_timeout_kernel(unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait_limit(smem_u32(&bar), 0u, limit_ns);
+  }
+}
+
 // Operand tiles are re-read by many CTAs: keep them in L2 ahead of the streamed outputs.
 __device__ __forceinline__ uint64_t l2_evict_last_policy() {
   uint64_t pol;
@@ -1224,6 +1248,14 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   if (grid < 1) grid = 1;
   KTAU_TRACE("batch_joint_ties_kernel", st);
   jk<<<(unsigned)grid, 256, smem, st>>>(g.ds, g.bids, g.nb, g.jt_prefix, g.jt_tiles);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_debug_wait_timeout(int64_t limit_ns, void* stream) {
+  if (limit_ns < 0 || limit_ns > 10000000000LL)
+    return ktau_fail(KTAU_EINVAL, "limit must be in [0, 10 s]");
+  wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((unsigned long long)limit_ns);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }

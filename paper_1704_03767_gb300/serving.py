@@ -43,6 +43,8 @@ class Request:
     slot: int = -1
     done: threading.Event = dataclasses.field(default_factory=threading.Event)
 
+    cancelled: bool = False
+
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
@@ -126,6 +128,21 @@ class QueryServer:
             self.pending.append(r)
             self.cv.notify_all()
         return r
+
+    def cancel(self, r: Request) -> bool:
+        """Withdraws a request that has not been admitted yet; True when it was withdrawn (its
+        `error` says so and `done` is set). Admitted requests run to completion."""
+        with self.cv:
+            try:
+                self.pending.remove(r)
+            except ValueError:
+                return False
+            r.cancelled = True
+            r.error = "cancelled"
+            r.finished = time.perf_counter()
+            r.done.set()
+            self.cv.notify_all()
+            return True
 
     def _dispatch(self):
         while True:
