@@ -58,6 +58,13 @@ struct ktau_ranked {
   uint32_t* tie_pairs;
   int64_t tie_cap;
   size_t tie_bytes;
+  // Inverted index of the tied sample pairs (triangular n_3): bucket k (the k-th sample pair in
+  // the Eq. 4 order) lists the variables tied on it; bkt_off[K + 1] prefix, bkt_var[T_sum].
+  // bkt_stat = {sum of s(s-1)/2 over buckets, largest s(s-1)/2, use flag} (device words).
+  int32_t* bkt_off;
+  int32_t* bkt_var;
+  unsigned long long* bkt_stat;
+  size_t bkt_var_bytes;
 };
 
 // ---------------------------------------------------------------------------------------------

@@ -103,15 +103,71 @@ __device__ void expand_row(const uint16_t* s_r, int n, int64_t K, int64_t K_pad,
   }
 }
 
+// EXPAND_ROWS variables per CTA: the sample pairs (a, b) of a 16-byte chunk are the same for every
+// variable, so a thread finds them once (pair_row) and reuses them for all rows of the CTA.
+// Positions k >= K read (0, 0) and store 0, which pads every row to K_pad.
+constexpr int EXPAND_ROWS = 8;
+
 template <int ESIZE>
 __global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
-                                                          int64_t ld, int n, int64_t K,
-                                                          int64_t K_pad, uint8_t* __restrict__ out) {
-  extern __shared__ uint16_t s_r[];
-  const int64_t row = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_r[i] = rank[row * ld + i];
+                                                          int64_t ld, int n, int64_t m, int K,
+                                                          int K_pad, uint8_t* __restrict__ out) {
+  extern __shared__ uint16_t s_r[];  // [EXPAND_ROWS][n]
+  constexpr int PER = 16 / ESIZE;    // elements per 16-byte store
+  const int64_t row0 = (int64_t)blockIdx.x * EXPAND_ROWS;
+  const int rows = (int)min((int64_t)EXPAND_ROWS, m - row0);
+  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
+    const int r = i / n, c = i - r * n;
+    s_r[i] = rank[(row0 + r) * ld + c];
+  }
   __syncthreads();
-  expand_row<ESIZE>(s_r, n, K, K_pad, out + row * K_pad * ESIZE);
+  const int chunks = K_pad / PER;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int k0 = c * PER;
+    int ia[PER], ib[PER];
+    {
+      int a = 0, b = 0;
+      if (k0 < K) {
+        a = pair_row(n, k0);
+        b = k0 - a * (2 * n - a - 1) / 2 + a + 1;
+      }
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        if (k0 + e < K) {
+          ia[e] = a;
+          ib[e] = b;
+          if (++b == n) {
+            ++a;
+            b = a + 1;
+          }
+        } else {
+          ia[e] = ib[e] = 0;
+        }
+      }
+    }
+    for (int r = 0; r < rows; ++r) {
+      const uint16_t* sr = s_r + r * n;
+      uint32_t words[4];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int h = 0; h < PER / 4; ++h) {
+          const int e = w * (PER / 4) + h;
+          const int d = (int)sr[ia[e]] - (int)sr[ib[e]];
+          uint32_t v;
+          if (ESIZE == 1)
+            v = d > 0 ? 0x38u : (d < 0 ? 0xB8u : 0u);
+          else
+            v = d > 0 ? 0x3F80u : (d < 0 ? 0xBF80u : 0u);
+          word |= v << (8 * ESIZE * h);
+        }
+        words[w] = word;
+      }
+      reinterpret_cast<uint4*>(out + (row0 + r) * (int64_t)K_pad * ESIZE)[c] =
+          make_uint4(words[0], words[1], words[2], words[3]);
+    }
+  }
 }
 
 // Batched: rows [0, rows) of a group of datasets (numbered dataset by dataset, prefix over bids),
@@ -437,7 +493,7 @@ constexpr int JCAP = 8192;   // tied sample pairs of one tile's rows listed in s
 // Tied sample pairs of variable y (sorted order: tie groups are runs of equal srank), written
 // to out[0 .. T_y) by one warp. Position k of a group starting at g0 pairs with g0 .. k-1.
 __device__ void warp_list_ties(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
-                               int n, uint32_t* out, int lane) {
+                               int n, uint32_t* out, int lane, int32_t* bkt_cnt = nullptr) {
   int run = 0;
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
@@ -471,6 +527,8 @@ __device__ void warp_list_ties(const uint16_t* __restrict__ perm, const uint16_t
           bb = t;
         }
         out[off + j] = (a << 16) | bb;
+        if (bkt_cnt)  // bucket of sample pair (a, b): its index in the Eq. 4 order
+          atomicAdd(bkt_cnt + (int)(a * (2u * n - a - 1) / 2 + (bb - a - 1)), 1);
       }
     }
     run += __shfl_sync(0xffffffffu, incl, 31);
@@ -509,12 +567,143 @@ __global__ void __launch_bounds__(1024) ties_scan_kernel(const int64_t* __restri
 __global__ void ties_list_kernel(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
                                  const int64_t* __restrict__ T, const int64_t* __restrict__ off,
                                  int64_t ld, int n, int64_t m, int64_t cap,
-                                 uint32_t* __restrict__ pairs) {
+                                 uint32_t* __restrict__ pairs, int32_t* __restrict__ bkt_cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (row >= m) return;
   if (T[row] == 0 || off[row] + T[row] > cap) return;
-  warp_list_ties(perm + row * ld, srank + row * ld, n, pairs + off[row], lane);
+  warp_list_ties(perm + row * ld, srank + row * ld, n, pairs + off[row], lane, bkt_cnt);
+}
+
+// Inclusive prefix of the bucket sizes in place (one CTA), c[K] = total; also the work of the
+// bucket form of n_3 (sum and largest s(s-1)/2) and the flag that selects it.
+__global__ void __launch_bounds__(1024) bucket_scan_kernel(int32_t* __restrict__ c, int64_t K,
+                                                           unsigned long long* __restrict__ stat,
+                                                           unsigned long long lim_total,
+                                                           unsigned long long lim_one) {
+  __shared__ long long wsum[32];
+  __shared__ unsigned long long wwork[32], wmax[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t per = (K + blockDim.x - 1) / blockDim.x;
+  const int64_t b = min(K, tid * per), e = min(K, b + per);
+  long long local = 0;
+  unsigned long long work = 0, big = 0;
+  for (int64_t i = b; i < e; ++i) {
+    const long long v = c[i];
+    local += v;
+    const unsigned long long wv = (unsigned long long)(v * (v - 1) / 2);
+    work += wv;
+    big = wv > big ? wv : big;
+  }
+  long long incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    work += __shfl_xor_sync(0xffffffffu, work, d);
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, big, d);
+    big = o > big ? o : big;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  if (lane == 0) {
+    wwork[warp] = work;
+    wmax[warp] = big;
+  }
+  __syncthreads();
+  long long run = incl - local;
+  for (int w = 0; w < warp; ++w) run += wsum[w];
+  for (int64_t i = b; i < e; ++i) {
+    run += c[i];
+    c[i] = (int32_t)run;
+  }
+  if (tid == 0) {
+    long long tot = 0;
+    unsigned long long W = 0, M = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tot += wsum[w];
+      W += wwork[w];
+      M = wmax[w] > M ? wmax[w] : M;
+    }
+    c[K] = (int32_t)tot;
+    stat[0] = W;
+    stat[1] = M;
+    stat[2] = (W <= lim_total && M <= lim_one) ? 1ull : 0ull;
+  }
+}
+
+// Scatter: bucket ends (inclusive prefix) count down to bucket starts while the variables are
+// placed, so bkt_off ends as the exclusive prefix.
+__global__ void bucket_scatter_kernel(const uint32_t* __restrict__ pairs,
+                                      const int64_t* __restrict__ T, const int64_t* __restrict__ off,
+                                      int n, int64_t m, int64_t cap, int32_t* __restrict__ bkt_off,
+                                      int32_t* __restrict__ bkt_var) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (row >= m) return;
+  if (T[row] == 0 || off[row] + T[row] > cap) return;
+  for (int64_t e = off[row] + lane; e < off[row] + T[row]; e += 32) {
+    const uint32_t ab = pairs[e];
+    const uint32_t a = ab >> 16, bb = ab & 0xffffu;
+    const int key = (int)(a * (2u * n - a - 1) / 2 + (bb - a - 1));
+    const int pos = atomicSub(bkt_off + key, 1) - 1;
+    bkt_var[pos] = (int32_t)row;
+  }
+}
+
+// n_3 from the buckets: every two variables of a bucket share that tied sample pair, so n_3(u, v)
+// is the number of buckets holding both (Table 1: joint ties). The output was zeroed beforehand.
+// A lane takes a bucket of up to 32 variables alone; larger buckets are shared by the warp.
+__device__ __forceinline__ void n3_add(void* n3out, int count_bits, uint64_t k) {
+  if (count_bits == 64)
+    atomicAdd((unsigned long long*)n3out + k, 1ull);
+  else
+    atomicAdd((int*)n3out + k, 1);
+}
+
+__global__ void __launch_bounds__(256) bucket_n3_kernel(const int32_t* __restrict__ bkt_off,
+                                                        const int32_t* __restrict__ bkt_var,
+                                                        const unsigned long long* __restrict__ stat,
+                                                        int64_t K, int64_t m, uint64_t p_begin,
+                                                        uint64_t p_end, void* n3out,
+                                                        int count_bits) {
+  if (stat[2] == 0) return;  // skewed buckets: the tile kernel counts n_3 instead
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  auto emit = [&](int32_t u, int32_t v) {
+    if (u > v) {
+      const int32_t t = u;
+      u = v;
+      v = t;
+    }
+    const uint64_t p = (uint64_t)((int64_t)u * (2 * m - u - 1) / 2 + (v - u - 1));
+    if (p >= p_begin && p < p_end) n3_add(n3out, count_bits, p - p_begin);
+  };
+  for (int64_t k0 = gw * 32; k0 < K; k0 += warps * 32) {
+    const int64_t k = k0 + lane;
+    int32_t lo = 0, s = 0;
+    if (k < K) {
+      lo = bkt_off[k];
+      s = bkt_off[k + 1] - lo;
+    }
+    if (s >= 2 && s <= 32)
+      for (int i = 0; i + 1 < s; ++i) {
+        const int32_t u = bkt_var[lo + i];
+        for (int j = i + 1; j < s; ++j) emit(u, bkt_var[lo + j]);
+      }
+    unsigned big = __ballot_sync(0xffffffffu, s > 32);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const int32_t blo = __shfl_sync(0xffffffffu, lo, src);
+      const int32_t bs = __shfl_sync(0xffffffffu, s, src);
+      for (int i = 0; i + 1 < bs; ++i) {
+        const int32_t u = bkt_var[blo + i];
+        for (int j = i + 1 + lane; j < bs; j += 32) emit(u, bkt_var[blo + j]);
+      }
+    }
+  }
 }
 
 // Batched listing: rows of a group (T, tie_off contiguous over the group's rows).
@@ -662,7 +851,9 @@ __global__ void __launch_bounds__(256) joint_ties_kernel(const SideArgs R, const
                                                          int64_t ncb, int64_t tile_lo,
                                                          int64_t tile_hi, uint64_t p_begin,
                                                          uint64_t p_end, int64_t ldo, void* n3out,
-                                                         int count_bits) {
+                                                         int count_bits,
+                                                         const unsigned long long* bkt_stat) {
+  if (bkt_stat && bkt_stat[2]) return;  // the bucket kernel counts n_3
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
     int64_t y0, x0;
     if (tri) {
@@ -1013,9 +1204,17 @@ ktau_status launch_joint_ties_t(const ktau_ranked* A, const ktau_ranked* B, int 
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
   if (grid > hi - lo) grid = hi - lo;
   if (grid < 1) grid = 1;
+  const unsigned long long* bstat = (tri && A->bkt_stat) ? A->bkt_stat : nullptr;
+  if (bstat) {
+    // Bucket form first; the tile kernel below returns at once when the bucket flag is set.
+    KTAU_TRACE("bucket_n3_kernel", st);
+    bucket_n3_kernel<<<(unsigned)(4 * ktau_sm_count()), 256, 0, st>>>(
+        A->bkt_off, A->bkt_var, A->bkt_stat, A->K, A->m, p_begin, p_end, n3, count_bits);
+    KTAU_CUDA(cudaGetLastError());
+  }
   KTAU_TRACE("joint_ties_kernel", st);
   kern<<<(unsigned)grid, 256, smem, st>>>(side_of(A), side_of(B), A->n, tri, w, ncb, lo, hi,
-                                          p_begin, p_end, ldo, n3, count_bits);
+                                          p_begin, p_end, ldo, n3, count_bits, bstat);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }
@@ -1075,15 +1274,16 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
   R->esize = esize;
   R->sgn_bytes = (size_t)R->m * R->K_pad * R->esize;
   if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
-  const size_t smem = (size_t)n * sizeof(uint16_t);
+  const size_t smem = (size_t)EXPAND_ROWS * n * sizeof(uint16_t);
+  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
   {
   KTAU_TRACE("sign_expand_kernel", st);
   if (R->esize == 1)
-    sign_expand_kernel<1><<<(unsigned)R->m, 256, smem, st>>>(R->rank, R->ld, (int)n, R->K,
-                                                             R->K_pad, (uint8_t*)R->sgn);
+    sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                      (int)R->K_pad, (uint8_t*)R->sgn);
   else
-    sign_expand_kernel<2><<<(unsigned)R->m, 256, smem, st>>>(R->rank, R->ld, (int)n, R->K,
-                                                             R->K_pad, (uint8_t*)R->sgn);
+    sign_expand_kernel<2><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                      (int)R->K_pad, (uint8_t*)R->sgn);
   }
   KTAU_CUDA(cudaGetLastError());
   // Lists of tied sample pairs for n_3: exact capacity from the rank statistics.
@@ -1097,12 +1297,40 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
     ties_scan_kernel<<<1, 1024, 0, st>>>(R->T, R->m, R->tie_off);
   }
   KTAU_CUDA(cudaGetLastError());
+  // Inverted index for the bucket form of n_3 (built when the counts fit 32-bit offsets).
+  const bool buckets = R->stats.T_sum > 0 && R->stats.T_sum < (1ll << 31) && R->m < (1ll << 31);
+  if (buckets) {
+    R->bkt_var_bytes = (size_t)R->stats.T_sum * sizeof(int32_t);
+    if (ktau_dmalloc((void**)&R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t)) != KTAU_OK ||
+        ktau_dmalloc((void**)&R->bkt_var, R->bkt_var_bytes) != KTAU_OK ||
+        ktau_dmalloc((void**)&R->bkt_stat, 4 * sizeof(unsigned long long)) != KTAU_OK)
+      return KTAU_ENOMEM;
+    KTAU_CUDA(cudaMemsetAsync(R->bkt_off, 0, ((size_t)R->K + 1) * sizeof(int32_t), st));
+  }
   {
     KTAU_TRACE("ties_list_kernel", st);
     ties_list_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, st>>>(
-        R->perm, R->srank, R->T, R->tie_off, R->ld, (int)n, R->m, R->tie_cap, R->tie_pairs);
+        R->perm, R->srank, R->T, R->tie_off, R->ld, (int)n, R->m, R->tie_cap, R->tie_pairs,
+        buckets ? R->bkt_off : nullptr);
   }
   KTAU_CUDA(cudaGetLastError());
+  if (buckets) {
+    // Bucket form when its atomic increments stay well below the pair count and no bucket is so
+    // large that one warp would serialise on it.
+    const unsigned long long P = (unsigned long long)(R->m * (R->m - 1) / 2);
+    const unsigned long long lim_total = P / 16 > (1ull << 16) ? P / 16 : (1ull << 16);
+    {
+      KTAU_TRACE("bucket_scan_kernel", st);
+      bucket_scan_kernel<<<1, 1024, 0, st>>>(R->bkt_off, R->K, R->bkt_stat, lim_total, 1ull << 18);
+    }
+    KTAU_CUDA(cudaGetLastError());
+    {
+      KTAU_TRACE("bucket_scatter_kernel", st);
+      bucket_scatter_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, st>>>(
+          R->tie_pairs, R->T, R->tie_off, (int)n, R->m, R->tie_cap, R->bkt_off, R->bkt_var);
+    }
+    KTAU_CUDA(cudaGetLastError());
+  }
   ktau_status s = make_tmap(R);
   if (s != KTAU_OK) return s;
   R->sg_ready = 1;
@@ -1179,8 +1407,14 @@ void ktau_signgemm_release(ktau_ranked* R) {
   ktau_dfree(R->sgn, R->sgn_bytes);
   ktau_dfree(R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t));
   ktau_dfree(R->tie_pairs, R->tie_bytes);
+  ktau_dfree(R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t));
+  ktau_dfree(R->bkt_var, R->bkt_var_bytes);
+  ktau_dfree(R->bkt_stat, 4 * sizeof(unsigned long long));
   R->tie_off = nullptr;
   R->tie_pairs = nullptr;
+  R->bkt_off = nullptr;
+  R->bkt_var = nullptr;
+  R->bkt_stat = nullptr;
   R->sgn = nullptr;
   R->sg_ready = 0;
 }

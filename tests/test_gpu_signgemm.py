@@ -124,3 +124,22 @@ def test_gene_expression_matches_merge_bitwise(ktau):
     assert np.array_equal(n3[idx].cpu().numpy().astype(np.int64), rn3)
     assert_tau32(tau32[idx].cpu().numpy(), rtau)
     R.free()
+
+
+@pytest.mark.parametrize("dups", [0, 1, 3])
+def test_joint_ties_bucket_and_tile_forms(ktau, dups):
+    """n_3 on the triangle: with few shared ties the inverted-index (bucket) form counts it; when
+    `dups` sample columns repeat another column in every variable, a tied sample pair is shared
+    by all 760 variables (one bucket of 288,420 pairs), so the tile form counts it instead. Both
+    must agree with the oracle exactly, also on sub-ranges."""
+    m, n = 760, 96
+    X = uniform_ties(m, n, tie_frac=0.1, seed=40 + dups)
+    for d in range(dups):
+        X[:, 2 * d + 1] = X[:, 2 * d]
+    ref = oracle_full(X)
+    _check(_run(ktau, X, 32), ref)
+    P = m * (m - 1) // 2
+    lo, hi = P // 3 + 5, P // 3 + 20000
+    got = _run(ktau, X, 64, p_begin=lo, p_end=hi)
+    assert np.array_equal(got["n3"].astype(np.int64), ref["n3"][lo:hi])
+    assert np.array_equal(got["S"].astype(np.int64), ref["S"][lo:hi])
