@@ -163,6 +163,181 @@ __device__ void rank_row(const void* __restrict__ values, int64_t off, int n, in
   }
 }
 
+// Short rows (n <= 256): one warp per variable, EPL = np2/32 keys per lane in registers, blocked
+// (lane l holds sorted positions l*EPL .. l*EPL+EPL-1). Same outputs, bit for bit, as rank_row.
+constexpr int RANK_WARPS = 8;
+
+template <int EPL>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[EPL], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32 * EPL; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= EPL) {  // partner in lane ^ (j / EPL), same slot
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int i = lane * EPL + e;
+          const unsigned long long y = __shfl_xor_sync(0xffffffffu, v[e], j / EPL);
+          const bool take_min = ((i & k) == 0) == ((i & j) == 0);
+          v[e] = take_min ? (y < v[e] ? y : v[e]) : (y > v[e] ? y : v[e]);
+        }
+      } else {  // partner in this lane
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int p = e ^ j;
+          if (p > e) {
+            const bool up = ((lane * EPL + e) & k) == 0;
+            const unsigned long long a = v[e], b = v[p];
+            if ((a > b) == up) {
+              v[e] = b;
+              v[p] = a;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int EPL>
+__device__ __forceinline__ void store_u16s(uint16_t* dst, const uint16_t (&x)[EPL]) {
+  if (EPL == 1) {
+    dst[0] = x[0];
+  } else if (EPL == 2) {
+    *reinterpret_cast<uint32_t*>(dst) = (uint32_t)x[0] | ((uint32_t)x[1] << 16);
+  } else if (EPL == 4) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)x[0] | ((uint32_t)x[1] << 16),
+                                                (uint32_t)x[2] | ((uint32_t)x[3] << 16));
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      w[q] = (uint32_t)x[(2 * q) % EPL] | ((uint32_t)x[(2 * q + 1) % EPL] << 16);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int DT, int EPL>
+__global__ void __launch_bounds__(32 * RANK_WARPS) rank_warp_kernel(
+    const void* __restrict__ values, int64_t ld_in, int n, int64_t m, int64_t ld,
+    uint16_t* __restrict__ perm, uint16_t* __restrict__ rank, uint16_t* __restrict__ srank,
+    int64_t* __restrict__ T, int32_t* __restrict__ ndist, int32_t* __restrict__ maxg,
+    double* __restrict__ rs64, float2* __restrict__ rsff, ktau_stats* __restrict__ stats) {
+  __shared__ unsigned long long s_T[RANK_WARPS], s_Tmax[RANK_WARPS];
+  __shared__ unsigned s_g[RANK_WARPS], s_nan[RANK_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row = (int64_t)blockIdx.x * RANK_WARPS + wid;
+  unsigned long long tsum = 0;
+  int gmax = 0;
+  unsigned nan_seen = 0;
+  if (row < m) {
+    unsigned long long v[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int i = lane * EPL + e;
+      v[e] = i < n ? load_key<DT>(values, row * ld_in, i, &nan_seen) : ~0ull;
+    }
+    warp_bitonic<EPL>(v, lane);
+    // Group heads over sorted positions k < n; dense rank = heads up to k, minus one;
+    // first(k) = position of the last head <= k.
+    const unsigned long long prev_last = __shfl_up_sync(0xffffffffu, v[EPL - 1], 1);
+    int heads = 0, last_head = -1;
+    bool head[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int k = lane * EPL + e;
+      const unsigned long long pv = e == 0 ? prev_last : v[e - 1];
+      head[e] = k < n && (k == 0 || (v[e] >> 32) != (pv >> 32));
+      heads += head[e];
+      if (head[e]) last_head = k;
+    }
+    int incl = heads, lmax = last_head;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      const int u = __shfl_up_sync(0xffffffffu, lmax, d);
+      if (lane >= d) {
+        incl += t;
+        lmax = u > lmax ? u : lmax;
+      }
+    }
+    int run = incl - heads;                                  // heads before this lane
+    int first = __shfl_up_sync(0xffffffffu, lmax, 1);        // last head before this lane
+    if (lane == 0) first = -1;
+    uint16_t pk[EPL], sk[EPL], pad[EPL];
+    uint16_t* rrow = rank + row * ld;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int k = lane * EPL + e;
+      pad[e] = 0xffff;
+      if (k < n) {
+        run += head[e];
+        if (head[e]) first = k;
+        const int idx = (int)(v[e] & 0xffffffffu);
+        const int d = run - 1;
+        const int before = k - first;
+        pk[e] = (uint16_t)idx;
+        sk[e] = (uint16_t)d;
+        rrow[idx] = (uint16_t)d;
+        tsum += (unsigned long long)before;
+        gmax = before + 1 > gmax ? before + 1 : gmax;
+      } else {
+        pk[e] = sk[e] = 0xffff;
+      }
+    }
+    // ld is a multiple of 16 and EPL divides 16: a lane's positions are all inside or all
+    // outside the padded row.
+    if (lane * EPL < ld) {
+      store_u16s<EPL>(perm + row * ld + lane * EPL, pk);
+      store_u16s<EPL>(srank + row * ld + lane * EPL, sk);
+      if (lane * EPL >= n) store_u16s<EPL>(rrow + lane * EPL, pad);
+      else if (lane * EPL + EPL > n)
+        for (int e = n - lane * EPL; e < EPL; ++e) rrow[lane * EPL + e] = 0xffff;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      tsum += __shfl_xor_sync(0xffffffffu, tsum, d);
+      const int o = __shfl_xor_sync(0xffffffffu, gmax, d);
+      gmax = o > gmax ? o : gmax;
+    }
+    const int total_heads = __shfl_sync(0xffffffffu, incl, 31);
+    nan_seen = __any_sync(0xffffffffu, nan_seen != 0);
+    if (lane == 0) {
+      T[row] = (int64_t)tsum;
+      // Factor of the tau-b denominator (Eq. 3): 1/sqrt(n_0 - n_1), IEEE FP64.
+      const long long D = (long long)n * (n - 1) / 2 - (long long)tsum;
+      const double r = D > 0 ? __ddiv_rn(1.0, __dsqrt_rn((double)D))
+                             : __longlong_as_double(0x7ff8000000000000LL);
+      const float hi = __double2float_rn(r);
+      rs64[row] = r;
+      rsff[row] = make_float2(hi, D > 0 ? __double2float_rn(r - (double)hi) : hi);
+      ndist[row] = total_heads;
+      maxg[row] = gmax;
+    }
+  }
+  if (lane == 0) {
+    s_T[wid] = tsum;
+    s_Tmax[wid] = tsum;
+    s_g[wid] = (unsigned)gmax;
+    s_nan[wid] = nan_seen;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // one set of statistics atomics per CTA
+    unsigned long long t = 0, tm = 0;
+    unsigned g = 0, nn = 0;
+    for (int w = 0; w < RANK_WARPS; ++w) {
+      t += s_T[w];
+      tm = s_Tmax[w] > tm ? s_Tmax[w] : tm;
+      g = s_g[w] > g ? s_g[w] : g;
+      nn |= s_nan[w];
+    }
+    atomicAdd(&stats->T_sum, t);
+    atomicMax(&stats->T_max, tm);
+    atomicMax(&stats->maxg, g);
+    if (nn) atomicOr(&stats->nan_flag, 1u);
+  }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ values, int64_t ld_in,
                                                    int n, int np2, int64_t ld, uint16_t* perm,
@@ -222,6 +397,26 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
                              ktau_ranked* R, cudaStream_t st) {
   int np2 = 32;
   while (np2 < n) np2 <<= 1;
+  if (m > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "m too large for one launch");
+  if (np2 <= 256) {
+    const unsigned blocks = (unsigned)((m + RANK_WARPS - 1) / RANK_WARPS);
+    const bool f32 = dtype == KTAU_F32;
+    KTAU_TRACE("rank_kernel", st);
+#define KTAU_RANK_WARP(EPL)                                                                    \
+  (f32 ? rank_warp_kernel<KTAU_F32, EPL> : rank_warp_kernel<KTAU_I32, EPL>)<<<               \
+      blocks, 32 * RANK_WARPS, 0, st>>>(values, ld_in, (int)n, m, R->ld, R->perm, R->rank,     \
+                                        R->srank, R->T, R->ndist, R->maxg, R->rs64, R->rsff, \
+                                        R->stats_dev)
+    switch (np2) {
+      case 32: KTAU_RANK_WARP(1); break;
+      case 64: KTAU_RANK_WARP(2); break;
+      case 128: KTAU_RANK_WARP(4); break;
+      default: KTAU_RANK_WARP(8); break;
+    }
+#undef KTAU_RANK_WARP
+    KTAU_CUDA(cudaGetLastError());
+    return KTAU_OK;
+  }
   int threads = np2 / 2 < 32 ? 32 : (np2 / 2 > 512 ? 512 : np2 / 2);
   size_t smem = (size_t)np2 * (sizeof(unsigned long long) + 2 * sizeof(uint16_t));
   if (m > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "m too large for one launch");

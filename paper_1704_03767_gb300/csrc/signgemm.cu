@@ -4,14 +4,17 @@
 //   sign_expand_kernel : A_u[k] = sign(r_u[a] - r_u[b]) for the k-th sample pair (a < b, row-major
 //                        order over the strict upper triangle of the n x n sample-pair matrix),
 //                        encoded as FP8 e4m3 (+1 = 0x38, -1 = 0xB8) or BF16, zero padded to K_pad.
-//   contract_kernel    : persistent, warp-specialised tcgen05 GEMM S = A A^T over the upper
-//                        triangle (or Q D^T for queries). 128 x 256 output tiles; super-tiles of
-//                        256 x 256 are walked through the job-id bijection of Sec. 4.1 (Eq. 13-14)
-//                        and split into two 128-row halves.
+//   contract_kernel    : persistent, warp-specialised tcgen05 GEMM over the upper triangle (or
+//                        the query rectangle). The accumulator is computed transposed, S^T =
+//                        A_cols A_rows^T: TMEM lanes are 128 output columns v and TMEM columns
+//                        are up to 256 output rows u, so a tcgen05.ld register is one row and a
+//                        store across the 32 lanes is contiguous along the packed output row.
+//                        Super-tiles of 256 x 256 are walked through the job-id bijection of
+//                        Sec. 4.1 (Eq. 13-14) and split into two 128-column halves.
 //                        warp 0: TMA producer (cp.async.bulk.tensor, 128B swizzle, 4-stage ring)
 //                        warp 1: TMEM allocation + single-thread tcgen05.mma issue
-//                        warps 2-5: epilogue, tcgen05.ld of the FP32 accumulator (exact integers),
-//                                   tau-b, coalesced stores through smem.
+//                        warps 2-9: epilogue, tcgen05.ld of the FP32 accumulator (exact integers),
+//                                   tau-b, coalesced stores straight from registers.
 //   joint_ties_kernel  : n_3 for every pair from the variables' tie groups (see below).
 //                        Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile run
 //                        under the MMAs of the next. Every mbarrier wait is bounded (about 2 s);
@@ -22,25 +25,30 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "signgemm.cuh"
 
 namespace {
 
-constexpr int BM = 128;            // tile rows (TMEM lanes)
-constexpr int BN = 256;            // tile columns (TMEM columns per accumulator)
+constexpr int BM = 128;            // output columns of a unit (TMEM lanes, MMA M)
+constexpr int BN = 256;            // output rows of a unit, at most (TMEM columns, MMA N)
 constexpr int BKB = 128;           // bytes of K per stage row (one 128B swizzle atom row)
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;  // 16 KB
 constexpr int B_BYTES = BN * BKB;  // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter, each half of the columns
+constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter, each half of the rows
 constexpr int GROUP = 8;           // super-tiles per side of a traversal group (L2 locality)
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int TRS = 33;            // padded row of the epilogue transposition buffer
+// Per-row data of the 32 rows an epilogue warp is storing (broadcast reads from shared memory).
+struct RowInfo {
+  float rhi, rlo;   // float-float 1/sqrt(n_0 - T_u)
+  long long base;   // packed index of (u, 0) (triangle) or u * ldo (rectangle)
+};
 constexpr size_t SMEM_BYTES = 1024 /*align*/ + (size_t)STAGES * STAGE_BYTES +
-                              (size_t)EPI_WARPS * 32 * TRS * 4 + 256 /*barriers*/;
+                              (size_t)EPI_WARPS * 32 * sizeof(RowInfo) + 256 /*barriers*/;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
@@ -336,6 +344,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // ---------------------------------------------------------------------------------------------
 // Contraction kernel
 // ---------------------------------------------------------------------------------------------
+// ktau_tau32_fast for |S| < 2^24, where S is exact in FP32 (the split's low part is zero): the
+// same float-float product and the same rounding test, without the split.
+__device__ __forceinline__ bool tau32_fast_small(int S, float rhi, float rlo, float2 fv,
+                                                 float& out) {
+  const float sh = __int2float_rn(S);
+  const float th = __fmul_rn(sh, rhi);
+  const float tl = __fadd_rn(__fmaf_rn(sh, rhi, -th), __fmul_rn(sh, rlo));
+  const float ph = __fmul_rn(th, fv.x);
+  const float pl = __fadd_rn(__fmaf_rn(th, fv.x, -ph), __fmaf_rn(th, fv.y, __fmul_rn(tl, fv.x)));
+  const float d = __fmul_rn(fabsf(ph), 0x1p-40f);
+  const float lo = __fadd_rn(ph, __fsub_rn(pl, d));
+  const float hi = __fadd_rn(ph, __fadd_rn(pl, d));
+  out = lo;
+  return lo == hi;
+}
+
 struct SideArgs {  // per-variable data of the row side (u) or the column side (v)
   const uint16_t* rank;
   const uint16_t* perm;
@@ -356,7 +380,8 @@ struct ContractArgs {
   int tri;                 // 1: upper triangle of one matrix; 0: rectangle rows x cols
   int64_t wS;              // tri: super-tiles per side
   int64_t wG;              // tri: traversal groups per side
-  int64_t ncb;             // rect: column blocks of BN
+  int64_t ncb;             // rect: column blocks of BM
+  int bnr;                 // output rows per unit: 256, or 128 for short query batches
   int64_t unit_lo, unit_hi;
   uint64_t p_begin, p_end; // tri: pair range
   int64_t ldo;             // rect: output row stride
@@ -379,9 +404,9 @@ struct Prob {
 };
 
 struct Unit {
-  int64_t y0, x0;   // tile origin in the problem's own rows / columns
+  int64_t y0, x0;   // unit origin in the problem's own rows (up to 256) / columns (128)
   bool live;
-  int ta, tb;       // TMA row coordinates of the A and B tiles
+  int ta, tb;       // TMA row coordinates of the A (column variables) and B (row variables) tiles
   int64_t num_kb;
   int bd;           // dataset of a batched launch (-1 otherwise)
 };
@@ -441,18 +466,18 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
     const int64_t lu = u - a.unit_prefix[lo];
     int64_t ys, xs;
     ktau_tile_coord(D.wS, lu >> 1, ys, xs);
-    r.y0 = ys * 256 + (lu & 1) * BM;
-    r.x0 = xs * 256;
-    const int64_t xend = min(r.x0 + (int64_t)BN, D.m);
-    r.live = r.y0 < D.m && min(r.y0 + (int64_t)BM - 1, xend - 2) >= r.y0;
-    r.ta = (int)(D.srow + r.y0);
-    r.tb = (int)(D.srow + r.x0);
+    r.y0 = ys * 256;
+    r.x0 = xs * 256 + (lu & 1) * BM;
+    const int64_t xend = min(r.x0 + (int64_t)BM, D.m);
+    r.live = r.y0 < D.m && r.x0 < D.m && xend - 1 > r.y0;
+    r.ta = (int)(D.srow + r.x0);
+    r.tb = (int)(D.srow + r.y0);
     r.num_kb = D.num_kb;
     return r;
   }
   if (a.tri) {
     // Slot u -> (group of GROUP x GROUP super-tiles, walked by the bijection on the group matrix;
-    // row-major inside the group) -> 256 x 256 super-tile -> 128-row half. Consecutive slots,
+    // row-major inside the group) -> 256 x 256 super-tile -> 128-column half. Consecutive slots,
     // which run at the same time on neighbouring CTAs, stay inside one group and share operand
     // blocks in L2. Slots below the diagonal or past the edge are dead.
     const int64_t s2 = u >> 1;
@@ -460,28 +485,28 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
     int64_t gy, gx;
     ktau_tile_coord(a.wG, gid, gy, gx);
     const int64_t ys = gy * GROUP + loc / GROUP, xs = gx * GROUP + loc % GROUP;
-    r.y0 = ys * 256 + (u & 1) * BM;
-    r.x0 = xs * 256;
-    r.ta = (int)r.y0;
-    r.tb = (int)r.x0;
+    r.y0 = ys * 256;
+    r.x0 = xs * 256 + (u & 1) * BM;
+    r.ta = (int)r.x0;
+    r.tb = (int)r.y0;
     if (ys >= a.wS || xs >= a.wS || ys > xs) {
       r.live = false;
       return r;
     }
     const int64_t m = a.row.m;
-    const int64_t xend = min(r.x0 + (int64_t)BN, m);
-    const int64_t ylast = min(r.y0 + (int64_t)BM - 1, xend - 2);
-    r.live = r.y0 < m && ylast >= r.y0;
+    const int64_t xend = min(r.x0 + (int64_t)BM, m);
+    const int64_t ylast = min(r.y0 + (int64_t)BN - 1, xend - 2);
+    r.live = r.y0 < m && r.x0 < m && ylast >= r.y0;
     if (r.live) {
       const uint64_t pmin = tri_p(m, r.y0, max(r.x0, r.y0 + 1));
       const uint64_t pmax = tri_p(m, ylast, xend - 1);
       r.live = pmax >= a.p_begin && pmin < a.p_end;
     }
   } else {
-    r.y0 = (u / a.ncb) * BM;
-    r.x0 = (u % a.ncb) * BN;
-    r.ta = (int)r.y0;
-    r.tb = (int)r.x0;
+    r.y0 = (u / a.ncb) * a.bnr;
+    r.x0 = (u % a.ncb) * BM;
+    r.ta = (int)r.x0;
+    r.tb = (int)r.y0;
     r.live = r.y0 < a.row.m && r.x0 < a.col.m;
   }
   return r;
@@ -901,8 +926,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* stage_base = smem;
-  int* tbuf_all = (int*)(smem + (size_t)STAGES * STAGE_BYTES);
-  uint64_t* bars = (uint64_t*)((unsigned char*)tbuf_all + (size_t)EPI_WARPS * 32 * TRS * 4);
+  RowInfo* rinfo_all = (RowInfo*)(smem + (size_t)STAGES * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)((unsigned char*)rinfo_all + (size_t)EPI_WARPS * 32 * sizeof(RowInfo));
   // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]; then the TMEM base slot
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -953,11 +978,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          mbar_expect_tx(FULL(stage), STAGE_BYTES);
+          mbar_expect_tx(FULL(stage), (uint32_t)(A_BYTES + a.bnr * BKB));
           const int kx = (int)(kb * BKB);
           tma_load_2d(sa, &tmA, kx, t.ta, FULL(stage), pol);
           tma_load_2d(sb, &tmB, kx, t.tb, FULL(stage), pol);
-          tma_load_2d(sb + BN / 2 * BKB, &tmB, kx, t.tb + BN / 2, FULL(stage), pol);
+          if (a.bnr > BM) tma_load_2d(sb + BM * BKB, &tmB, kx, t.tb + BM, FULL(stage), pol);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -969,8 +994,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t kFmt = ESIZE == 1 ? 0u : 1u;  // E4M3 (f8f6f4) or BF16 (f16)
-      const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(BN >> 3) << 17) |
-                             ((uint32_t)(BM >> 4) << 24);
+      const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
+                             ((uint32_t)(a.bnr >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -1010,9 +1035,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------- Epilogue (warps 2..9) ----------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int half_sel = (warp - 2) >> 2;  // which half of the 256 columns
-    int* tb = tbuf_all + (warp - 2) * 32 * TRS;
+    // Warp w owns TMEM lane quarter q (32 output columns v, one per lane) and one half of the
+    // unit's rows, 32 rows per tcgen05.ld (register j = row u0 + j).
+    const int q = warp & 3;
+    const int half_sel = (warp - 2) >> 2;
+    RowInfo* ri = rinfo_all + (warp - 2) * 32;
+    const int nhalf = a.bnr / 64;  // 32-row chunks per half
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int64_t u = a.unit_lo + blockIdx.x; u < a.unit_hi; u += gridDim.x) {
@@ -1025,52 +1053,48 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int64_t mrow = P.row.m, mcol = P.col.m;
       const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
       const bool wantS = P.out.S != nullptr, s64 = P.out.count_bits == 64;
-      const int64_t ybase = t.y0 + 32 * q;
-      // Per-row data of this warp's 32 rows, one row per lane (broadcast by shuffle below).
-      const int64_t my_y = ybase + lane;
-      const bool my_row_ok = my_y < mrow;
-      const float2 my_rff = my_row_ok ? __ldg(P.row.rsff + my_y) : make_float2(0.f, 0.f);
-      const long long my_base =
-          P.tri ? (long long)(my_y * (2 * mrow - my_y - 1) / 2 - my_y - 1) : (long long)my_y * P.ldo;
-      const int rows_here = (int)min((int64_t)32, mrow - ybase);
-      // Whole 32 x 32 blocks strictly above the diagonal, inside the matrix and inside the pair
-      // range need no per-element checks.
-      bool range_all = true;
-      if (P.tri) {
-        const int64_t ylast = ybase + rows_here - 1;
-        range_all = (uint64_t)(ybase * (2 * mrow - ybase - 1) / 2) >= P.p_begin &&
-                    (uint64_t)(ylast * (2 * mrow - ylast - 1) / 2 + (mrow - ylast - 1)) <= P.p_end;
-      }
-      for (int c = half_sel * (BN / 64); c < (half_sel + 1) * (BN / 64); ++c) {
+      // n_3 output given: store its zeros here; the joint-ties kernels add the nonzero counts.
+      void* const n3z = P.out.n3;
+      const int64_t vbase = t.x0 + 32 * q;
+      const int64_t v = vbase + lane;
+      const bool vin = v < mcol;
+      const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
+      const bool cols_full = vbase + 32 <= mcol;
+      for (int c = half_sel * nhalf; c < (half_sel + 1) * nhalf; ++c) {
         uint32_t r[32];
         tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
-        if (c == (half_sel + 1) * (BN / 64) - 1) {
+        if (c == (half_sel + 1) * nhalf - 1) {
           tc_fence_before();
-          mbar_arrive(TEMPTY(acc));  // accumulator may be overwritten by the next tile
+          mbar_arrive(TEMPTY(acc));  // accumulator may be overwritten by the next unit
         }
-        // transpose: row `lane` of this warp's 32 rows, columns 32c..32c+31
-#pragma unroll
-        for (int j = 0; j < 32; ++j) tb[lane * TRS + j] = __float2int_rn(__uint_as_float(r[j]));
+        const int64_t ub = t.y0 + 32 * c;
+        if (ub >= mrow) continue;
+        {  // lane j describes row ub + j
+          const int64_t y = ub + lane;
+          RowInfo info;
+          const float2 f = y < mrow ? __ldg(P.row.rsff + y) : make_float2(0.f, 0.f);
+          info.rhi = f.x;
+          info.rlo = f.y;
+          info.base = P.tri ? (long long)(y * (2 * mrow - y - 1) / 2 - y - 1) : (long long)y * P.ldo;
+          ri[lane] = info;
+        }
         __syncwarp();
-        const int64_t xc = t.x0 + 32 * c;
-        const int64_t v = xc + lane;
-        const bool vin = v < mcol;
-        const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
-        const bool fast = range_all && rows_here == 32 && xc + 32 <= mcol &&
-                          (!P.tri || xc > ybase + 31);
+        const int rows_here = (int)min((int64_t)32, mrow - ub);
+        bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
+        if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
+          const int64_t ul = ub + 31;
+          fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
+                 (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
+        }
         if (fast && want32 && !want64) {
-#pragma unroll 4
-          for (int i = 0; i < 32; ++i) {
-            const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
-            const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
-            const long long base = __shfl_sync(0xffffffffu, my_base, i);
-            const uint64_t k = (uint64_t)(base + v) - P.p_begin;
-            const int S = tb[i * TRS + lane];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const RowInfo R = ri[j];
+            const uint64_t k = (uint64_t)(R.base + v) - P.p_begin;
+            const int S = __float2int_rn(__uint_as_float(r[j]));
             float tv;
-            if (!ktau_tau32_fast(S, make_float2(rhi, rlo), c_rff, tv)) {
-              const int64_t y = ybase + i;
-              tv = ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, P.row.T[y], P.col.T[v]);
-            }
+            if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv))
+              tv = ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[ub + j], P.col.T[v]);
             __stcs(P.out.tau32 + k, tv);
             if (wantS) {
               if (s64)
@@ -1078,37 +1102,48 @@ __global__ void __launch_bounds__(THREADS, 1)
               else
                 __stcs((int*)P.out.S + k, S);
             }
+            if (n3z) {
+              if (s64)
+                __stcs((long long*)n3z + k, 0ll);
+              else
+                __stcs((int*)n3z + k, 0);
+            }
           }
-        } else {
-          for (int i = 0; i < 32; ++i) {
-            const float rhi = __shfl_sync(0xffffffffu, my_rff.x, i);
-            const float rlo = __shfl_sync(0xffffffffu, my_rff.y, i);
-            const long long base = __shfl_sync(0xffffffffu, my_base, i);
-            const int64_t y = ybase + i;
-            if (i >= rows_here || !vin) continue;
+        } else if (vin) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j >= rows_here) continue;
+            const RowInfo R = ri[j];
+            const int64_t y = ub + j;
             uint64_t k;
             if (P.tri) {
               if (v <= y) continue;
-              const uint64_t p = (uint64_t)(base + v);
+              const uint64_t p = (uint64_t)(R.base + v);
               if (p < P.p_begin || p >= P.p_end) continue;
               k = p - P.p_begin;
             } else {
-              k = (uint64_t)(base + v);
+              k = (uint64_t)(R.base + v);
             }
-            const int S = tb[i * TRS + lane];
+            const int S = __float2int_rn(__uint_as_float(r[j]));
             if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
             if (want32)
               __stcs(P.out.tau32 + k,
-                     ktau_tau32(S, make_float2(rhi, rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
+                     ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
             if (wantS) {
               if (s64)
                 __stcs((long long*)P.out.S + k, (long long)S);
               else
                 __stcs((int*)P.out.S + k, S);
             }
+            if (n3z) {
+              if (s64)
+                __stcs((long long*)n3z + k, 0ll);
+              else
+                __stcs((int*)n3z + k, 0);
+            }
           }
         }
-        __syncwarp();
+        __syncwarp();  // ri is rewritten for the next chunk
       }
       if (++acc == 2) {
         acc = 0;
@@ -1192,13 +1227,8 @@ ktau_status launch_joint_ties_t(const ktau_ranked* A, const ktau_ranked* B, int 
     ncb = (B->m + JT - 1) / JT;
     hi = ((A->m + JT - 1) / JT) * ncb;
   }
-  // n_3 is 0 for every pair with a tie-free variable: zero the output at full write bandwidth and
-  // let the kernel store only the nonzero counts.
-  const size_t count = tri ? (size_t)(p_end - p_begin) : (size_t)A->m * (size_t)ldo;
-  {
-    KTAU_TRACE("n3_zero_fill", st);
-    KTAU_CUDA(cudaMemsetAsync(n3, 0, count * (size_t)(count_bits / 8), st));
-  }
+  // n_3 is 0 for every pair with a tie-free variable: the contraction's epilogue has stored the
+  // zeros, so these kernels store (or add) only the nonzero counts.
   int occ = 0;
   KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
   int64_t grid = (int64_t)(occ > 0 ? occ : 1) * ktau_sm_count();
@@ -1246,9 +1276,10 @@ ktau_status launch_contract_maps(const void* tmap_a, const void* tmap_b, const C
 }
 
 template <int ESIZE>
+// Rows from A, columns from B: the MMA's A operand (TMEM lanes) is the column side.
 ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const ContractArgs& args,
                             int64_t units, cudaStream_t st) {
-  return launch_contract_maps<ESIZE>(A->tmap, B->tmap, args, units, st);
+  return launch_contract_maps<ESIZE>(B->tmap, A->tmap, args, units, st);
 }
 
 }  // namespace
@@ -1259,6 +1290,71 @@ int ktau_sign_esize(int64_t n, const ktau_options* opt) {
   if (opt && opt->operand_bits == 16) return 2;
   return n <= KTAU_SIGNGEMM_FP8_MAX_N ? 1 : 2;
 }
+
+
+// ---------------------------------------------------------------------------------------------
+// Side stream: work that only the n_3 output needs (tie lists, the inverted index, the zero fill
+// and the n_3 kernels) runs on a library-owned stream forked from the caller's stream by an
+// event and joined back by another, so that it overlaps the sign expansion and the contraction.
+// One side stream per device; its fork is taken under a mutex so that concurrent callers cannot
+// interleave the record/wait pair. Callers whose stream is being captured, and small jobs, run
+// everything on their own stream.
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct SideLane {
+  std::mutex mu;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideLane g_side[64];
+
+class SideFork {
+ public:
+  SideFork(cudaStream_t st, bool want) : st_(st) {
+    if (!want) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    lane_ = &g_side[dev];
+    lane_->mu.lock();
+    if (!lane_->s &&
+        (cudaStreamCreateWithFlags(&lane_->s, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&lane_->fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&lane_->join, cudaEventDisableTiming) != cudaSuccess)) {
+      lane_->s = nullptr;
+      lane_->mu.unlock();
+      lane_ = nullptr;
+      return;
+    }
+    if (cudaEventRecord(lane_->fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(lane_->s, lane_->fork, 0) != cudaSuccess) {
+      lane_->mu.unlock();
+      lane_ = nullptr;
+      return;
+    }
+    side_ = lane_->s;
+  }
+  cudaStream_t stream() const { return side_ ? side_ : st_; }
+  // Joins the side stream back into the caller's stream; later work on the caller's stream
+  // waits for everything launched on stream() so far.
+  ktau_status join() {
+    if (!lane_) return KTAU_OK;
+    cudaError_t e = cudaEventRecord(lane_->join, side_);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st_, lane_->join, 0);
+    lane_->mu.unlock();
+    lane_ = nullptr;
+    side_ = nullptr;
+    return e == cudaSuccess ? KTAU_OK : ktau_cuda_fail(e, "side stream join");
+  }
+  ~SideFork() { join(); }
+
+ private:
+  cudaStream_t st_;
+  cudaStream_t side_ = nullptr;
+  SideLane* lane_ = nullptr;
+};
+}  // namespace
 
 ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
   if (R->sg_ready && R->esize == esize) return KTAU_OK;
@@ -1273,43 +1369,35 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
   R->K_pad = (R->K + 127) / 128 * 128;
   R->esize = esize;
   R->sgn_bytes = (size_t)R->m * R->K_pad * R->esize;
-  if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
-  const size_t smem = (size_t)EXPAND_ROWS * n * sizeof(uint16_t);
-  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
-  {
-  KTAU_TRACE("sign_expand_kernel", st);
-  if (R->esize == 1)
-    sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                      (int)R->K_pad, (uint8_t*)R->sgn);
-  else
-    sign_expand_kernel<2><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                      (int)R->K_pad, (uint8_t*)R->sgn);
-  }
-  KTAU_CUDA(cudaGetLastError());
   // Lists of tied sample pairs for n_3: exact capacity from the rank statistics.
   R->tie_cap = (int64_t)R->stats.T_sum;
   R->tie_bytes = (size_t)(R->tie_cap > 0 ? R->tie_cap : 1) * 4;
-  if (ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
-      ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) != KTAU_OK)
-    return KTAU_ENOMEM;
-  {
-    KTAU_TRACE("ties_scan_kernel", st);
-    ties_scan_kernel<<<1, 1024, 0, st>>>(R->T, R->m, R->tie_off);
-  }
-  KTAU_CUDA(cudaGetLastError());
   // Inverted index for the bucket form of n_3 (built when the counts fit 32-bit offsets).
   const bool buckets = R->stats.T_sum > 0 && R->stats.T_sum < (1ll << 31) && R->m < (1ll << 31);
+  if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK ||
+      ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
+      ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) != KTAU_OK)
+    return KTAU_ENOMEM;
   if (buckets) {
     R->bkt_var_bytes = (size_t)R->stats.T_sum * sizeof(int32_t);
     if (ktau_dmalloc((void**)&R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t)) != KTAU_OK ||
         ktau_dmalloc((void**)&R->bkt_var, R->bkt_var_bytes) != KTAU_OK ||
         ktau_dmalloc((void**)&R->bkt_stat, 4 * sizeof(unsigned long long)) != KTAU_OK)
       return KTAU_ENOMEM;
-    KTAU_CUDA(cudaMemsetAsync(R->bkt_off, 0, ((size_t)R->K + 1) * sizeof(int32_t), st));
   }
+  // The tie lists and the index run beside the sign expansion (large matrices only).
+  SideFork side(st, R->m >= 4096);
+  const cudaStream_t ss = side.stream();
   {
-    KTAU_TRACE("ties_list_kernel", st);
-    ties_list_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, st>>>(
+    KTAU_TRACE("ties_scan_kernel", ss);
+    ties_scan_kernel<<<1, 1024, 0, ss>>>(R->T, R->m, R->tie_off);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  if (buckets)
+    KTAU_CUDA(cudaMemsetAsync(R->bkt_off, 0, ((size_t)R->K + 1) * sizeof(int32_t), ss));
+  {
+    KTAU_TRACE("ties_list_kernel", ss);
+    ties_list_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, ss>>>(
         R->perm, R->srank, R->T, R->tie_off, R->ld, (int)n, R->m, R->tie_cap, R->tie_pairs,
         buckets ? R->bkt_off : nullptr);
   }
@@ -1320,18 +1408,32 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
     const unsigned long long P = (unsigned long long)(R->m * (R->m - 1) / 2);
     const unsigned long long lim_total = P / 16 > (1ull << 16) ? P / 16 : (1ull << 16);
     {
-      KTAU_TRACE("bucket_scan_kernel", st);
-      bucket_scan_kernel<<<1, 1024, 0, st>>>(R->bkt_off, R->K, R->bkt_stat, lim_total, 1ull << 18);
+      KTAU_TRACE("bucket_scan_kernel", ss);
+      bucket_scan_kernel<<<1, 1024, 0, ss>>>(R->bkt_off, R->K, R->bkt_stat, lim_total, 1ull << 18);
     }
     KTAU_CUDA(cudaGetLastError());
     {
-      KTAU_TRACE("bucket_scatter_kernel", st);
-      bucket_scatter_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, st>>>(
+      KTAU_TRACE("bucket_scatter_kernel", ss);
+      bucket_scatter_kernel<<<(unsigned)((R->m * 32 + 255) / 256), 256, 0, ss>>>(
           R->tie_pairs, R->T, R->tie_off, (int)n, R->m, R->tie_cap, R->bkt_off, R->bkt_var);
     }
     KTAU_CUDA(cudaGetLastError());
   }
-  ktau_status s = make_tmap(R);
+  const size_t smem = (size_t)EXPAND_ROWS * n * sizeof(uint16_t);
+  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
+  {
+    KTAU_TRACE("sign_expand_kernel", st);
+    if (R->esize == 1)
+      sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                        (int)R->K_pad, (uint8_t*)R->sgn);
+    else
+      sign_expand_kernel<2><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                        (int)R->K_pad, (uint8_t*)R->sgn);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  ktau_status s = side.join();
+  if (s != KTAU_OK) return s;
+  s = make_tmap(R);
   if (s != KTAU_OK) return s;
   R->sg_ready = 1;
   return KTAU_OK;
@@ -1349,6 +1451,7 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.tri = 1;
   a.wS = (m + 255) / 256;
   a.ncb = 0;
+  a.bnr = BN;
   a.p_begin = p_begin;
   a.p_end = p_end;
   a.ldo = 0;
@@ -1364,7 +1467,7 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.unit_lo = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i0 / 256 / GROUP);
   a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / 256 / GROUP + 1);
   const int64_t units = a.unit_hi - a.unit_lo;
-  a.out.n3 = nullptr;
+  // The epilogue zero-fills n_3 over the range; the joint-ties kernels then add nonzero counts.
   s = R->esize == 1 ? launch_contract<1>(R, R, a, units, st) : launch_contract<2>(R, R, a, units, st);
   if (s == KTAU_OK && out.n3)
     s = launch_joint_ties(R, R, 1, p_begin, p_end, 0, out.n3, out.count_bits, st);
@@ -1385,7 +1488,8 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.tri = 0;
   a.wS = 0;
   a.wG = 0;
-  a.ncb = (D->m + BN - 1) / BN;
+  a.ncb = (D->m + BM - 1) / BM;
+  a.bnr = Q->m <= BM ? BM : BN;
   a.p_begin = 0;
   a.p_end = 0;
   a.ldo = ldo;
@@ -1395,8 +1499,7 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.nb = 0;
   a.unit_prefix = nullptr;
   a.unit_lo = 0;
-  a.unit_hi = ((Q->m + BM - 1) / BM) * a.ncb;
-  a.out.n3 = nullptr;
+  a.unit_hi = ((Q->m + a.bnr - 1) / a.bnr) * a.ncb;
   s = Q->esize == 1 ? launch_contract<1>(Q, D, a, a.unit_hi, st)
                     : launch_contract<2>(Q, D, a, a.unit_hi, st);
   if (s == KTAU_OK && out.n3) s = launch_joint_ties(Q, D, 0, 0, 0, ldo, out.n3, out.count_bits, st);
@@ -1468,6 +1571,7 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   a.unit_lo = 0;
   a.unit_hi = g.units;
   a.tri = 1;
+  a.bnr = BN;
   ktau_status s = g.esize == 1 ? launch_contract_maps<1>(g.tmap, g.tmap, a, g.units, st)
                                : launch_contract_maps<2>(g.tmap, g.tmap, a, g.units, st);
   if (s != KTAU_OK) return s;

@@ -51,9 +51,18 @@ def test_uniform_ties_64x200_all_pairs(ktau, count_bits):
     assert got["T"].shape == (64,)
 
 
-def test_tie_counts_and_ranks(ktau):
-    X = uniform_ties(40, 97, seed=4)
-    Xd = torch.from_numpy(X).cuda()
+@pytest.mark.parametrize("n", [2, 5, 31, 32, 33, 64, 97, 128, 200, 255, 256, 257, 1000])
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_tie_counts_and_ranks(ktau, n, dtype):
+    m = 45 if n <= 256 else 12  # ragged against the eight variables of a rank CTA
+    X = uniform_ties(m, n, tie_frac=0.3, seed=4 + n)
+    if dtype == "i32":
+        X = np.floor(X * 7).astype(np.int32) - 3
+    else:
+        X[0, 0], X[0, -1] = -0.0, 0.0  # equal values
+        X[1, 0], X[1, -1] = np.inf, -np.inf
+        X[2, :] = 1.5  # one tie group
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     R = ktau.ktau_rank_prepare(Xd)
     T = ktau.ktau_tie_counts(R).cpu().numpy()
     perm, rank = ktau.ktau_ranked_export(R)
