@@ -47,8 +47,15 @@ struct RowInfo {
   float rhi, rlo;   // float-float 1/sqrt(n_0 - T_u)
   long long base;   // packed index of (u, 0) (triangle) or u * ldo (rectangle)
 };
+constexpr int RI_ROWS = BN / 2;  // rows of one epilogue warp's half of a unit
 constexpr size_t SMEM_BYTES = 1024 /*align*/ + (size_t)STAGES * STAGE_BYTES +
-                              (size_t)EPI_WARPS * 32 * sizeof(RowInfo) + 256 /*barriers*/;
+                              (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo) + 256 /*barriers*/;
+// Pair form (two CTAs of a cluster share one tcgen05.mma.cta_group::2 of M = 256): each CTA
+// holds its 128 column variables (A) and half of the 256 row variables (B) per stage.
+constexpr int STAGES2 = 6;
+constexpr int STAGE2_BYTES = A_BYTES + BM * BKB;  // 32 KB
+constexpr size_t SMEM2_BYTES = 1024 /*align*/ + (size_t)STAGES2 * STAGE2_BYTES +
+                               (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo) + 256 /*barriers*/;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
@@ -290,6 +297,36 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
+// Pair (2-CTA) forms. A TMA load whose completion is signalled on the mbarrier of the leader CTA
+// of the pair (shared::cluster address from mapa).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap, int x, int y,
+                                                 uint32_t cluster_bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(cluster_bar), "l"(pol)
+      : "memory");
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand in the canonical 128-byte-swizzle layout
 // (8-row x 128-byte atoms, 1024 bytes apart along M/N).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
@@ -320,6 +357,29 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+template <int ESIZE>
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  if (ESIZE == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+// Arrives on the mbarrier at this shared-memory offset in both CTAs of the pair once the pair's
+// earlier MMAs have completed.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"((unsigned short)3)
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -358,6 +418,34 @@ __device__ __forceinline__ bool tau32_fast_small(int S, float rhi, float rlo, fl
   const float hi = __fadd_rn(ph, __fadd_rn(pl, d));
   out = lo;
   return lo == hi;
+}
+
+// Register j of a 32-register tcgen05.ld result, for a loop index the compiler cannot unroll
+// (a select chain keeps the array in registers).
+__device__ __forceinline__ uint32_t reg_at(const uint32_t (&r)[32], int j) {
+  uint32_t x = r[0];
+#pragma unroll
+  for (int i = 1; i < 32; ++i) x = j == i ? r[i] : x;
+  return x;
+}
+
+// Interior 32 x 32 block of the epilogue (all pairs valid, 32-bit counts, FP32 tau only): row j
+// of the block is register j; lane = column, so each store is contiguous across the warp. Rows
+// whose FP32 rounding is undecided by the float-float test are flagged in `slow`.
+template <bool WS, bool WN>
+__device__ __forceinline__ void epi_rows32(const uint32_t (&r)[32], const struct RowInfo* rc,
+                                           float2 c_rff, float* o32, int* oS, int* oN,
+                                           uint32_t& slow) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const RowInfo R = rc[j];
+    const int S = __float2int_rn(__uint_as_float(r[j]));
+    float tv;
+    if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv)) slow |= 1u << j;
+    __stcs(o32 + R.base, tv);
+    if (WS) __stcs(oS + R.base, S);
+    if (WN) __stcs(oN + R.base, 0);
+  }
 }
 
 struct SideArgs {  // per-variable data of the row side (u) or the column side (v)
@@ -919,6 +1007,126 @@ __global__ void __launch_bounds__(256) batch_joint_ties_kernel(
   }
 }
 
+// Epilogue of one unit by one epilogue warp (warps 2..9): warp w owns TMEM lane quarter
+// q = w & 3 (32 output columns v, one per lane) and one half of the unit's rows, 32 rows per
+// tcgen05.ld (register j = row u0 + j). The half's row data are fetched into shared memory
+// before the accumulator is waited for. Returns false when a bounded wait gave up.
+__device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit& t, RowInfo* ri,
+                                              uint32_t tmem_base, uint32_t tfull_bar,
+                                              uint32_t tfull_phase, int acc, int warp, int lane,
+                                              uint32_t tempty_bar, bool remote) {
+      const int q = warp & 3;
+      const int half_sel = (warp - 2) >> 2;
+      const int nhalf = a.bnr / 64;  // 32-row chunks per half
+      const Prob P = problem_of(a, t);
+      const int64_t mrow = P.row.m, mcol = P.col.m;
+      const int64_t vbase = t.x0 + 32 * q;
+      const int64_t v = vbase + lane;
+      const bool vin = v < mcol;
+      const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
+      const int64_t hrow0 = t.y0 + 32 * half_sel * nhalf;
+      for (int i = lane; i < 32 * nhalf; i += 32) {
+        const int64_t y = hrow0 + i;
+        RowInfo info;
+        const float2 f = y < mrow ? __ldg(P.row.rsff + y) : make_float2(0.f, 0.f);
+        info.rhi = f.x;
+        info.rlo = f.y;
+        info.base = P.tri ? (long long)(y * (2 * mrow - y - 1) / 2 - y - 1) : (long long)y * P.ldo;
+        ri[i] = info;
+      }
+      __syncwarp();
+      if (!mbar_wait(tfull_bar, tfull_phase)) return false;
+      tc_fence_after();
+      const int64_t n0 = P.n * (P.n - 1) / 2;
+      const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
+      const bool s64 = P.out.count_bits == 64;
+      // n_3 output given: store its zeros here; the joint-ties kernels add the nonzero counts.
+      void* const n3z = P.out.n3;
+      const bool cols_full = vbase + 32 <= mcol;
+      for (int c = half_sel * nhalf; c < (half_sel + 1) * nhalf; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
+        if (c == (half_sel + 1) * nhalf - 1) {
+          // Accumulator may be overwritten by the next unit: one arrive per warp (on the leader
+          // CTA's barrier in the pair form).
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if (remote)
+              mbar_arrive_cluster(tempty_bar);
+            else
+              mbar_arrive(tempty_bar);
+          }
+        }
+        const int64_t ub = t.y0 + 32 * c;
+        if (ub >= mrow) continue;
+        const RowInfo* rc = ri + 32 * (c - half_sel * nhalf);
+        const int rows_here = (int)min((int64_t)32, mrow - ub);
+        bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
+        if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
+          const int64_t ul = ub + 31;
+          fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
+                 (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
+        }
+        if (fast && want32 && !want64 && !s64) {
+          float* const o32 = P.out.tau32 + (v - (int64_t)P.p_begin);
+          int* const oS = P.out.S ? (int*)P.out.S + (v - (int64_t)P.p_begin) : nullptr;
+          int* const oN = n3z ? (int*)n3z + (v - (int64_t)P.p_begin) : nullptr;
+          uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
+          if (oS && oN)
+            epi_rows32<true, true>(r, rc, c_rff, o32, oS, oN, slow);
+          else if (oS)
+            epi_rows32<true, false>(r, rc, c_rff, o32, oS, oN, slow);
+          else if (oN)
+            epi_rows32<false, true>(r, rc, c_rff, o32, oS, oN, slow);
+          else
+            epi_rows32<false, false>(r, rc, c_rff, o32, oS, oN, slow);
+          while (slow) {  // rare: the FP64 formula decides (same thread, stored after the fast value)
+            const int j = __ffs(slow) - 1;
+            slow &= slow - 1;
+            const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
+            o32[rc[j].base] = ktau_tau32(S, make_float2(rc[j].rhi, rc[j].rlo), c_rff, n0,
+                                         P.row.T[ub + j], P.col.T[v]);
+          }
+        } else if (vin) {
+          const bool wantS = P.out.S != nullptr;
+#pragma unroll 1
+          for (int j = 0; j < rows_here; ++j) {
+            const RowInfo R = rc[j];
+            const int64_t y = ub + j;
+            uint64_t k;
+            if (P.tri) {
+              if (v <= y) continue;
+              const uint64_t p = (uint64_t)(R.base + v);
+              if (p < P.p_begin || p >= P.p_end) continue;
+              k = p - P.p_begin;
+            } else {
+              k = (uint64_t)(R.base + v);
+            }
+            const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
+            if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
+            if (want32)
+              __stcs(P.out.tau32 + k,
+                     ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
+            if (wantS) {
+              if (s64)
+                __stcs((long long*)P.out.S + k, (long long)S);
+              else
+                __stcs((int*)P.out.S + k, S);
+            }
+            if (n3z) {
+              if (s64)
+                __stcs((long long*)n3z + k, 0ll);
+              else
+                __stcs((int*)n3z + k, 0);
+            }
+          }
+        }
+      }
+      __syncwarp();  // ri is rewritten for the next unit
+      return true;
+}
+
 template <int ESIZE>
 __global__ void __launch_bounds__(THREADS, 1)
     contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -927,7 +1135,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* stage_base = smem;
   RowInfo* rinfo_all = (RowInfo*)(smem + (size_t)STAGES * STAGE_BYTES);
-  uint64_t* bars = (uint64_t*)((unsigned char*)rinfo_all + (size_t)EPI_WARPS * 32 * sizeof(RowInfo));
+  uint64_t* bars =
+      (uint64_t*)((unsigned char*)rinfo_all + (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo));
   // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]; then the TMEM base slot
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -944,7 +1153,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(TFULL(s), 1);
-      mbar_init(TEMPTY(s), 32 * EPI_WARPS);
+      mbar_init(TEMPTY(s), EPI_WARPS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -1035,116 +1244,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------- Epilogue (warps 2..9) ----------------
-    // Warp w owns TMEM lane quarter q (32 output columns v, one per lane) and one half of the
-    // unit's rows, 32 rows per tcgen05.ld (register j = row u0 + j).
-    const int q = warp & 3;
-    const int half_sel = (warp - 2) >> 2;
-    RowInfo* ri = rinfo_all + (warp - 2) * 32;
-    const int nhalf = a.bnr / 64;  // 32-row chunks per half
     int acc = 0;
     uint32_t acc_phase = 0;
+    RowInfo* ri = rinfo_all + (warp - 2) * RI_ROWS;
     for (int64_t u = a.unit_lo + blockIdx.x; u < a.unit_hi; u += gridDim.x) {
       const Unit t = unit_of(a, u);
       if (!t.live) continue;
-      if (!mbar_wait(TFULL(acc), acc_phase)) break;
-      tc_fence_after();
-      const Prob P = problem_of(a, t);
-      const int64_t n0 = P.n * (P.n - 1) / 2;
-      const int64_t mrow = P.row.m, mcol = P.col.m;
-      const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
-      const bool wantS = P.out.S != nullptr, s64 = P.out.count_bits == 64;
-      // n_3 output given: store its zeros here; the joint-ties kernels add the nonzero counts.
-      void* const n3z = P.out.n3;
-      const int64_t vbase = t.x0 + 32 * q;
-      const int64_t v = vbase + lane;
-      const bool vin = v < mcol;
-      const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
-      const bool cols_full = vbase + 32 <= mcol;
-      for (int c = half_sel * nhalf; c < (half_sel + 1) * nhalf; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
-        if (c == (half_sel + 1) * nhalf - 1) {
-          tc_fence_before();
-          mbar_arrive(TEMPTY(acc));  // accumulator may be overwritten by the next unit
-        }
-        const int64_t ub = t.y0 + 32 * c;
-        if (ub >= mrow) continue;
-        {  // lane j describes row ub + j
-          const int64_t y = ub + lane;
-          RowInfo info;
-          const float2 f = y < mrow ? __ldg(P.row.rsff + y) : make_float2(0.f, 0.f);
-          info.rhi = f.x;
-          info.rlo = f.y;
-          info.base = P.tri ? (long long)(y * (2 * mrow - y - 1) / 2 - y - 1) : (long long)y * P.ldo;
-          ri[lane] = info;
-        }
-        __syncwarp();
-        const int rows_here = (int)min((int64_t)32, mrow - ub);
-        bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
-        if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
-          const int64_t ul = ub + 31;
-          fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
-                 (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
-        }
-        if (fast && want32 && !want64) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const RowInfo R = ri[j];
-            const uint64_t k = (uint64_t)(R.base + v) - P.p_begin;
-            const int S = __float2int_rn(__uint_as_float(r[j]));
-            float tv;
-            if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv))
-              tv = ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[ub + j], P.col.T[v]);
-            __stcs(P.out.tau32 + k, tv);
-            if (wantS) {
-              if (s64)
-                __stcs((long long*)P.out.S + k, (long long)S);
-              else
-                __stcs((int*)P.out.S + k, S);
-            }
-            if (n3z) {
-              if (s64)
-                __stcs((long long*)n3z + k, 0ll);
-              else
-                __stcs((int*)n3z + k, 0);
-            }
-          }
-        } else if (vin) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j >= rows_here) continue;
-            const RowInfo R = ri[j];
-            const int64_t y = ub + j;
-            uint64_t k;
-            if (P.tri) {
-              if (v <= y) continue;
-              const uint64_t p = (uint64_t)(R.base + v);
-              if (p < P.p_begin || p >= P.p_end) continue;
-              k = p - P.p_begin;
-            } else {
-              k = (uint64_t)(R.base + v);
-            }
-            const int S = __float2int_rn(__uint_as_float(r[j]));
-            if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
-            if (want32)
-              __stcs(P.out.tau32 + k,
-                     ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
-            if (wantS) {
-              if (s64)
-                __stcs((long long*)P.out.S + k, (long long)S);
-              else
-                __stcs((int*)P.out.S + k, S);
-            }
-            if (n3z) {
-              if (s64)
-                __stcs((long long*)n3z + k, 0ll);
-              else
-                __stcs((int*)n3z + k, 0);
-            }
-          }
-        }
-        __syncwarp();  // ri is rewritten for the next chunk
-      }
+      if (!epilogue_unit(a, t, ri, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
+                         TEMPTY(acc), false))
+        break;
       if (++acc == 2) {
         acc = 0;
         acc_phase ^= 1u;
@@ -1157,6 +1265,171 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
+                 : "memory");
+  }
+}
+
+
+// Pair form of the triangle contraction: the two CTAs of a cluster compute one 256 x 256
+// super-tile with tcgen05.mma.cta_group::2 (M = 256 output columns, 128 per CTA; N = 256 output
+// rows, whose operand is split 128 / 128 between the CTAs). Per stage each CTA loads 32 KB
+// instead of 48 KB, so six stages fit where four did and every operand byte read from L2 feeds
+// twice the MMA work. The leader CTA (rank 0) issues the MMAs; both CTAs' TMA loads complete on
+// the leader's FULL barrier; the leader's commits arrive on both CTAs' EMPTY and TFULL barriers;
+// both CTAs' epilogue warps release an accumulator on the leader's TEMPTY barrier.
+__device__ __forceinline__ bool pair_live(const ContractArgs& a, int64_t s2) {
+  return unit_of(a, 2 * s2).live || unit_of(a, 2 * s2 + 1).live;
+}
+
+template <int ESIZE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    contract2_kernel(const __grid_constant__ CUtensorMap tmS, const ContractArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* stage_base = smem;
+  RowInfo* rinfo_all = (RowInfo*)(smem + (size_t)STAGES2 * STAGE2_BYTES);
+  uint64_t* bars =
+      (uint64_t*)((unsigned char*)rinfo_all + (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo));
+  // bars: full[STAGES2], empty[STAGES2], tfull[2], tempty[2]; then the TMEM base slot
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES2 + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int64_t cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int64_t s_lo = a.unit_lo >> 1, s_hi = a.unit_hi >> 1;
+  const uint32_t bar0 = smem_u32(bars);
+  auto FULL = [&](int s) { return bar0 + 8u * s; };
+  auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES2 + s); };
+  auto TFULL = [&](int s) { return bar0 + 8u * (2 * STAGES2 + s); };
+  auto TEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES2 + 2 + s); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES2; ++s) {
+      mbar_init(FULL(s), 1);
+      mbar_init(EMPTY(s), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(TFULL(s), 1);
+      mbar_init(TEMPTY(s), 2 * EPI_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers initialised before any cross-CTA signal
+  tc_fence_after();
+  const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmS) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      const uint64_t pol = l2_evict_last_policy();
+      for (int64_t s2 = s_lo + cid; ok && s2 < s_hi; s2 += ncl) {
+        if (!pair_live(a, s2)) continue;
+        const Unit t = unit_of(a, 2 * s2 + rank);
+        const int brow = (int)(t.y0 + (int64_t)BM * rank);  // this CTA's half of the rows
+        for (int64_t kb = 0; kb < t.num_kb; ++kb) {
+          if (!mbar_wait(EMPTY(stage), phase ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE2_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+          if (rank == 0) mbar_expect_tx(FULL(stage), 2u * STAGE2_BYTES);
+          const uint32_t full_leader = cluster_addr(FULL(stage), 0);
+          const int kx = (int)(kb * BKB);
+          tma_load_2d_pair(sa, &tmS, kx, t.ta, full_leader, pol);
+          tma_load_2d_pair(sb, &tmS, kx, brow, full_leader, pol);
+          if (++stage == STAGES2) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // Tail: every stage released by the leader's MMAs, so no commit is still to arrive here.
+      for (int i = 0; ok && i < STAGES2; ++i) {
+        if (!mbar_wait(EMPTY(stage), phase ^ 1u)) break;
+        if (++stage == STAGES2) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (leader CTA) ----------------
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t kFmt = ESIZE == 1 ? 0u : 1u;  // E4M3 (f8f6f4) or BF16 (f16)
+      const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
+                             ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true;
+      for (int64_t s2 = s_lo + cid; ok && s2 < s_hi; s2 += ncl) {
+        if (!pair_live(a, s2)) continue;
+        if (!mbar_wait(TEMPTY(acc), acc_phase ^ 1u)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int64_t kb = 0; kb < a.num_kb; ++kb) {
+          if (!mbar_wait(FULL(stage), phase)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE2_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BKB / 32; ++k)
+            umma_pair<ESIZE>(d_tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                             (kb > 0 || k > 0) ? 1u : 0u);
+          umma_commit_pair(EMPTY(stage));  // frees the stage in both CTAs
+          if (++stage == STAGES2) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit_pair(TFULL(acc));  // accumulator complete in both CTAs
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+    }
+  } else {
+    // ---------------- Epilogue (warps 2..9, both CTAs) ----------------
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    RowInfo* ri = rinfo_all + (warp - 2) * RI_ROWS;
+    for (int64_t s2 = s_lo + cid; s2 < s_hi; s2 += ncl) {
+      if (!pair_live(a, s2)) continue;
+      const Unit t = unit_of(a, 2 * s2 + rank);
+      if (!epilogue_unit(a, t, ri, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
+                         cluster_addr(TEMPTY(acc), 0), true))
+        break;
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+      if (sg_failed()) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs done with TMEM, barriers and each other's shared memory
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
                  : "memory");
   }
 }
@@ -1275,8 +1548,47 @@ ktau_status launch_contract_maps(const void* tmap_a, const void* tmap_b, const C
   return KTAU_OK;
 }
 
+// Pair form over the triangle of one matrix: clusters of two CTAs, as many as fit at once.
 template <int ESIZE>
+ktau_status launch_contract2(const ktau_ranked* R, const ContractArgs& args, int64_t units,
+                             cudaStream_t st) {
+  auto kern = contract2_kernel<ESIZE>;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SMEM2_BYTES));
+  static int max_clusters[64] = {0};
+  int dev = 0;
+  KTAU_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return ktau_fail(KTAU_EINVAL, "device index out of range");
+  if (max_clusters[dev] == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * ktau_sm_count()));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM2_BYTES;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    KTAU_CUDA(cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg));
+    max_clusters[dev] = n > 0 ? n : -1;
+  }
+  if (max_clusters[dev] < 0) return ktau_fail(KTAU_ECUDA, "no two-CTA cluster fits on an SM pair");
+  int64_t clusters = max_clusters[dev];
+  const int64_t supers = (units + 1) / 2;
+  if (clusters > supers) clusters = supers;
+  if (clusters < 1) clusters = 1;
+  KTAU_TRACE("contract_kernel", st);
+  kern<<<(unsigned)(2 * clusters), THREADS, SMEM2_BYTES, st>>>(
+      *reinterpret_cast<const CUtensorMap*>(R->tmap), args);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
 // Rows from A, columns from B: the MMA's A operand (TMEM lanes) is the column side.
+template <int ESIZE>
 ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const ContractArgs& args,
                             int64_t units, cudaStream_t st) {
   return launch_contract_maps<ESIZE>(B->tmap, A->tmap, args, units, st);
@@ -1468,7 +1780,7 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / 256 / GROUP + 1);
   const int64_t units = a.unit_hi - a.unit_lo;
   // The epilogue zero-fills n_3 over the range; the joint-ties kernels then add nonzero counts.
-  s = R->esize == 1 ? launch_contract<1>(R, R, a, units, st) : launch_contract<2>(R, R, a, units, st);
+  s = R->esize == 1 ? launch_contract2<1>(R, a, units, st) : launch_contract2<2>(R, a, units, st);
   if (s == KTAU_OK && out.n3)
     s = launch_joint_ties(R, R, 1, p_begin, p_end, 0, out.n3, out.count_bits, st);
   return s;
