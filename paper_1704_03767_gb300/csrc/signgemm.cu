@@ -52,10 +52,9 @@ constexpr size_t SMEM_BYTES = 1024 /*align*/ + (size_t)STAGES * STAGE_BYTES +
                               (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo) + 256 /*barriers*/;
 // Pair form (two CTAs of a cluster share one tcgen05.mma.cta_group::2 of M = 256): each CTA
 // holds its 128 column variables (A) and half of the 256 row variables (B) per stage.
-constexpr int STAGES2 = 6;
+constexpr int STAGES2 = 7;
 constexpr int STAGE2_BYTES = A_BYTES + BM * BKB;  // 32 KB
-constexpr size_t SMEM2_BYTES = 1024 /*align*/ + (size_t)STAGES2 * STAGE2_BYTES +
-                               (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo) + 256 /*barriers*/;
+constexpr size_t SMEM2_BYTES = 1024 /*align*/ + (size_t)STAGES2 * STAGE2_BYTES + 256 /*barriers*/;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
@@ -429,16 +428,34 @@ __device__ __forceinline__ uint32_t reg_at(const uint32_t (&r)[32], int j) {
   return x;
 }
 
+// Row data of the 32 rows of an epilogue chunk: read from shared memory (written before the
+// accumulator wait), or held by lane j for row j and broadcast with shuffles (all 32 lanes must
+// call it together).
+struct RowsSmem {
+  const RowInfo* rc;
+  __device__ __forceinline__ RowInfo operator()(int j) const { return rc[j]; }
+};
+struct RowsReg {
+  float rhi, rlo;
+  long long base;
+  __device__ __forceinline__ RowInfo operator()(int j) const {
+    RowInfo R;
+    R.rhi = __shfl_sync(0xffffffffu, rhi, j);
+    R.rlo = __shfl_sync(0xffffffffu, rlo, j);
+    R.base = __shfl_sync(0xffffffffu, base, j);
+    return R;
+  }
+};
+
 // Interior 32 x 32 block of the epilogue (all pairs valid, 32-bit counts, FP32 tau only): row j
 // of the block is register j; lane = column, so each store is contiguous across the warp. Rows
 // whose FP32 rounding is undecided by the float-float test are flagged in `slow`.
-template <bool WS, bool WN>
-__device__ __forceinline__ void epi_rows32(const uint32_t (&r)[32], const struct RowInfo* rc,
-                                           float2 c_rff, float* o32, int* oS, int* oN,
-                                           uint32_t& slow) {
+template <bool WS, bool WN, class Rows>
+__device__ __forceinline__ void epi_rows32(const uint32_t (&r)[32], const Rows& rows, float2 c_rff,
+                                           float* o32, int* oS, int* oN, uint32_t& slow) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    const RowInfo R = rc[j];
+    const RowInfo R = rows(j);
     const int S = __float2int_rn(__uint_as_float(r[j]));
     float tv;
     if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv)) slow |= 1u << j;
@@ -1009,122 +1026,139 @@ __global__ void __launch_bounds__(256) batch_joint_ties_kernel(
 
 // Epilogue of one unit by one epilogue warp (warps 2..9): warp w owns TMEM lane quarter
 // q = w & 3 (32 output columns v, one per lane) and one half of the unit's rows, 32 rows per
-// tcgen05.ld (register j = row u0 + j). The half's row data are fetched into shared memory
-// before the accumulator is waited for. Returns false when a bounded wait gave up.
+// tcgen05.ld (register j = row u0 + j). With kSmemRows the half's row data are fetched into
+// shared memory before the accumulator is waited for; otherwise each chunk's rows are held one
+// per lane and broadcast. Returns false when a bounded wait gave up.
+__device__ __forceinline__ RowInfo row_info(const Prob& P, int64_t y) {
+  RowInfo info;
+  const float2 f = y < P.row.m ? __ldg(P.row.rsff + y) : make_float2(0.f, 0.f);
+  info.rhi = f.x;
+  info.rlo = f.y;
+  info.base = P.tri ? (long long)(y * (2 * P.row.m - y - 1) / 2 - y - 1) : (long long)y * P.ldo;
+  return info;
+}
+
+template <bool kSmemRows>
 __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit& t, RowInfo* ri,
                                               uint32_t tmem_base, uint32_t tfull_bar,
                                               uint32_t tfull_phase, int acc, int warp, int lane,
                                               uint32_t tempty_bar, bool remote) {
-      const int q = warp & 3;
-      const int half_sel = (warp - 2) >> 2;
-      const int nhalf = a.bnr / 64;  // 32-row chunks per half
-      const Prob P = problem_of(a, t);
-      const int64_t mrow = P.row.m, mcol = P.col.m;
-      const int64_t vbase = t.x0 + 32 * q;
-      const int64_t v = vbase + lane;
-      const bool vin = v < mcol;
-      const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
-      const int64_t hrow0 = t.y0 + 32 * half_sel * nhalf;
-      for (int i = lane; i < 32 * nhalf; i += 32) {
-        const int64_t y = hrow0 + i;
-        RowInfo info;
-        const float2 f = y < mrow ? __ldg(P.row.rsff + y) : make_float2(0.f, 0.f);
-        info.rhi = f.x;
-        info.rlo = f.y;
-        info.base = P.tri ? (long long)(y * (2 * mrow - y - 1) / 2 - y - 1) : (long long)y * P.ldo;
-        ri[i] = info;
-      }
+  const int q = warp & 3;
+  const int half_sel = (warp - 2) >> 2;
+  const int nhalf = a.bnr / 64;  // 32-row chunks per half
+  const Prob P = problem_of(a, t);
+  const int64_t mrow = P.row.m, mcol = P.col.m;
+  const int64_t vbase = t.x0 + 32 * q;
+  const int64_t v = vbase + lane;
+  const bool vin = v < mcol;
+  const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
+  if (kSmemRows) {
+    const int64_t hrow0 = t.y0 + 32 * half_sel * nhalf;
+    for (int i = lane; i < 32 * nhalf; i += 32) ri[i] = row_info(P, hrow0 + i);
+    __syncwarp();
+  }
+  if (!mbar_wait(tfull_bar, tfull_phase)) return false;
+  tc_fence_after();
+  const int64_t n0 = P.n * (P.n - 1) / 2;
+  const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
+  const bool s64 = P.out.count_bits == 64;
+  // n_3 output given: store its zeros here; the joint-ties kernels add the nonzero counts.
+  void* const n3z = P.out.n3;
+  const bool cols_full = vbase + 32 <= mcol;
+  for (int c = half_sel * nhalf; c < (half_sel + 1) * nhalf; ++c) {
+    const int64_t ub = t.y0 + 32 * c;
+    RowInfo mine;
+    if (!kSmemRows) mine = row_info(P, ub + lane);
+    uint32_t r[32];
+    tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
+    if (c == (half_sel + 1) * nhalf - 1) {
+      // Accumulator may be overwritten by the next unit: one arrive per warp (on the leader
+      // CTA's barrier in the pair form).
+      tc_fence_before();
       __syncwarp();
-      if (!mbar_wait(tfull_bar, tfull_phase)) return false;
-      tc_fence_after();
-      const int64_t n0 = P.n * (P.n - 1) / 2;
-      const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
-      const bool s64 = P.out.count_bits == 64;
-      // n_3 output given: store its zeros here; the joint-ties kernels add the nonzero counts.
-      void* const n3z = P.out.n3;
-      const bool cols_full = vbase + 32 <= mcol;
-      for (int c = half_sel * nhalf; c < (half_sel + 1) * nhalf; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
-        if (c == (half_sel + 1) * nhalf - 1) {
-          // Accumulator may be overwritten by the next unit: one arrive per warp (on the leader
-          // CTA's barrier in the pair form).
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            if (remote)
-              mbar_arrive_cluster(tempty_bar);
-            else
-              mbar_arrive(tempty_bar);
-          }
-        }
-        const int64_t ub = t.y0 + 32 * c;
-        if (ub >= mrow) continue;
-        const RowInfo* rc = ri + 32 * (c - half_sel * nhalf);
-        const int rows_here = (int)min((int64_t)32, mrow - ub);
-        bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
-        if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
-          const int64_t ul = ub + 31;
-          fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
-                 (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
-        }
-        if (fast && want32 && !want64 && !s64) {
-          float* const o32 = P.out.tau32 + (v - (int64_t)P.p_begin);
-          int* const oS = P.out.S ? (int*)P.out.S + (v - (int64_t)P.p_begin) : nullptr;
-          int* const oN = n3z ? (int*)n3z + (v - (int64_t)P.p_begin) : nullptr;
-          uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
-          if (oS && oN)
-            epi_rows32<true, true>(r, rc, c_rff, o32, oS, oN, slow);
-          else if (oS)
-            epi_rows32<true, false>(r, rc, c_rff, o32, oS, oN, slow);
-          else if (oN)
-            epi_rows32<false, true>(r, rc, c_rff, o32, oS, oN, slow);
-          else
-            epi_rows32<false, false>(r, rc, c_rff, o32, oS, oN, slow);
-          while (slow) {  // rare: the FP64 formula decides (same thread, stored after the fast value)
-            const int j = __ffs(slow) - 1;
-            slow &= slow - 1;
-            const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
-            o32[rc[j].base] = ktau_tau32(S, make_float2(rc[j].rhi, rc[j].rlo), c_rff, n0,
-                                         P.row.T[ub + j], P.col.T[v]);
-          }
-        } else if (vin) {
-          const bool wantS = P.out.S != nullptr;
+      if (lane == 0) {
+        if (remote)
+          mbar_arrive_cluster(tempty_bar);
+        else
+          mbar_arrive(tempty_bar);
+      }
+    }
+    if (ub >= mrow) continue;
+    const RowsSmem rs{ri + 32 * (c - half_sel * nhalf)};
+    const RowsReg rr{mine.rhi, mine.rlo, mine.base};
+    const int rows_here = (int)min((int64_t)32, mrow - ub);
+    bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
+    if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
+      const int64_t ul = ub + 31;
+      fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
+             (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
+    }
+    if (fast && want32 && !want64 && !s64) {
+      float* const o32 = P.out.tau32 + (v - (int64_t)P.p_begin);
+      int* const oS = P.out.S ? (int*)P.out.S + (v - (int64_t)P.p_begin) : nullptr;
+      int* const oN = n3z ? (int*)n3z + (v - (int64_t)P.p_begin) : nullptr;
+      uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
+#define KTAU_EPI_ROWS(ROWS)                                                 \
+  if (oS && oN)                                                             \
+    epi_rows32<true, true>(r, ROWS, c_rff, o32, oS, oN, slow);              \
+  else if (oS)                                                              \
+    epi_rows32<true, false>(r, ROWS, c_rff, o32, oS, oN, slow);             \
+  else if (oN)                                                              \
+    epi_rows32<false, true>(r, ROWS, c_rff, o32, oS, oN, slow);             \
+  else                                                                      \
+    epi_rows32<false, false>(r, ROWS, c_rff, o32, oS, oN, slow);
+      if (kSmemRows) {
+        KTAU_EPI_ROWS(rs)
+      } else {
+        KTAU_EPI_ROWS(rr)
+      }
+#undef KTAU_EPI_ROWS
+      while (slow) {  // rare: the FP64 formula decides (same thread, stored after the fast value)
+        const int j = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const RowInfo R = row_info(P, ub + j);
+        const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
+        o32[R.base] = ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[ub + j],
+                                 P.col.T[v]);
+      }
+    } else {
+      const bool wantS = P.out.S != nullptr;
 #pragma unroll 1
-          for (int j = 0; j < rows_here; ++j) {
-            const RowInfo R = rc[j];
-            const int64_t y = ub + j;
-            uint64_t k;
-            if (P.tri) {
-              if (v <= y) continue;
-              const uint64_t p = (uint64_t)(R.base + v);
-              if (p < P.p_begin || p >= P.p_end) continue;
-              k = p - P.p_begin;
-            } else {
-              k = (uint64_t)(R.base + v);
-            }
-            const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
-            if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
-            if (want32)
-              __stcs(P.out.tau32 + k,
-                     ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
-            if (wantS) {
-              if (s64)
-                __stcs((long long*)P.out.S + k, (long long)S);
-              else
-                __stcs((int*)P.out.S + k, S);
-            }
-            if (n3z) {
-              if (s64)
-                __stcs((long long*)n3z + k, 0ll);
-              else
-                __stcs((int*)n3z + k, 0);
-            }
-          }
+      for (int j = 0; j < rows_here; ++j) {
+        const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
+        const int64_t y = ub + j;
+        if (!vin) continue;
+        uint64_t k;
+        if (P.tri) {
+          if (v <= y) continue;
+          const uint64_t p = (uint64_t)(R.base + v);
+          if (p < P.p_begin || p >= P.p_end) continue;
+          k = p - P.p_begin;
+        } else {
+          k = (uint64_t)(R.base + v);
+        }
+        const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
+        if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
+        if (want32)
+          __stcs(P.out.tau32 + k,
+                 ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
+        if (wantS) {
+          if (s64)
+            __stcs((long long*)P.out.S + k, (long long)S);
+          else
+            __stcs((int*)P.out.S + k, S);
+        }
+        if (n3z) {
+          if (s64)
+            __stcs((long long*)n3z + k, 0ll);
+          else
+            __stcs((int*)n3z + k, 0);
         }
       }
-      __syncwarp();  // ri is rewritten for the next unit
-      return true;
+    }
+  }
+  if (kSmemRows) __syncwarp();  // ri is rewritten for the next unit
+  return true;
 }
 
 template <int ESIZE>
@@ -1250,8 +1284,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int64_t u = a.unit_lo + blockIdx.x; u < a.unit_hi; u += gridDim.x) {
       const Unit t = unit_of(a, u);
       if (!t.live) continue;
-      if (!epilogue_unit(a, t, ri, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
-                         TEMPTY(acc), false))
+      if (!epilogue_unit<true>(a, t, ri, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
+                               TEMPTY(acc), false))
         break;
       if (++acc == 2) {
         acc = 0;
@@ -1287,9 +1321,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* stage_base = smem;
-  RowInfo* rinfo_all = (RowInfo*)(smem + (size_t)STAGES2 * STAGE2_BYTES);
-  uint64_t* bars =
-      (uint64_t*)((unsigned char*)rinfo_all + (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo));
+  uint64_t* bars = (uint64_t*)(smem + (size_t)STAGES2 * STAGE2_BYTES);
   // bars: full[STAGES2], empty[STAGES2], tfull[2], tempty[2]; then the TMEM base slot
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES2 + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1410,12 +1442,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     // ---------------- Epilogue (warps 2..9, both CTAs) ----------------
     int acc = 0;
     uint32_t acc_phase = 0;
-    RowInfo* ri = rinfo_all + (warp - 2) * RI_ROWS;
     for (int64_t s2 = s_lo + cid; s2 < s_hi; s2 += ncl) {
       if (!pair_live(a, s2)) continue;
       const Unit t = unit_of(a, 2 * s2 + rank);
-      if (!epilogue_unit(a, t, ri, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
-                         cluster_addr(TEMPTY(acc), 0), true))
+      if (!epilogue_unit<false>(a, t, nullptr, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
+                                cluster_addr(TEMPTY(acc), 0), true))
         break;
       if (++acc == 2) {
         acc = 0;
