@@ -261,8 +261,9 @@ ktau_status ktau_check_options(const ktau_options* opt) {
   if (opt->mapping < 0 || opt->mapping > 2) return ktau_fail(KTAU_EINVAL, "bad mapping");
   if (opt->schedule < 0 || opt->schedule > 2) return ktau_fail(KTAU_EINVAL, "bad schedule");
   if (opt->ctas_per_sm < 0 || opt->ctas_per_sm > 32) return ktau_fail(KTAU_EINVAL, "bad ctas_per_sm");
-  if (opt->operand_bits != 0 && opt->operand_bits != 8 && opt->operand_bits != 16)
-    return ktau_fail(KTAU_EINVAL, "operand_bits must be 0, 8 or 16");
+  if (opt->operand_bits != 0 && opt->operand_bits != 4 && opt->operand_bits != 8 &&
+      opt->operand_bits != 16)
+    return ktau_fail(KTAU_EINVAL, "operand_bits must be 0, 4, 8 or 16");
   return KTAU_OK;
 }
 
@@ -300,7 +301,7 @@ extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uin
     if (!ktau_signgemm_supported(R->n))
       return ktau_fail(KTAU_EINVAL, "sign-contraction path supports n <= %d", KTAU_SIGNGEMM_MAX_N);
     return ktau_signgemm_allpairs(const_cast<ktau_ranked*>(R), p_begin, p_end, out,
-                                  ktau_sign_esize(R->n, opt), st);
+                                  ktau_sign_obits(R->n, opt), st);
   }
   ktau_merge_plan plan;
   ktau_merge_default_plan(R->n, &plan);
@@ -326,7 +327,7 @@ extern "C" ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream) {
   if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
   if (!ktau_signgemm_supported(R->n))
     return ktau_fail(KTAU_EINVAL, "sign contraction supports n <= %d", KTAU_SIGNGEMM_MAX_N);
-  return ktau_signgemm_prepare(R, ktau_sign_esize(R->n, nullptr), (cudaStream_t)stream);
+  return ktau_signgemm_prepare(R, ktau_sign_obits(R->n, nullptr), (cudaStream_t)stream);
 }
 
 ktau_status ktau_query_check_status(cudaStream_t st);

@@ -44,11 +44,12 @@ struct ktau_ranked {
   ktau_stats* stats_dev;
   ktau_stats stats;  // host copy, filled by ktau_rank_prepare
   // Sign expansion for the tensor-core path, built on first use (library-owned):
-  // sgn[m][K_pad] of FP8 e4m3 (esize 1) or BF16 (esize 2) values in {-1, 0, +1}, K = n(n-1)/2,
-  // K_pad = K rounded up to 128; tmap is its TMA descriptor (CUtensorMap, 128-byte box rows).
+  // sgn[m][K_pad] of values in {-1, 0, +1} as FP4 e2m1 (obits 4, two per byte), FP8 e4m3
+  // (obits 8) or BF16 (obits 16), K = n(n-1)/2, K_pad = K rounded up to 128; esize is the
+  // operand's bytes per element in shared memory (1, or 2 for BF16); tmap is its TMA descriptor.
   void* sgn;
   int64_t K, K_pad;
-  int esize;
+  int esize, obits;
   int sg_ready;
   alignas(64) unsigned char tmap[128];
   size_t sgn_bytes;

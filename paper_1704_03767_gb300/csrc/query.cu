@@ -239,7 +239,7 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
   const int path = ktau_choose_path(db, opt);
   ktau_status s;
   if (path == KTAU_PATH_SIGNGEMM && ktau_signgemm_supported(db->n)) {
-    s = ktau_signgemm_rect(Q, D, out, db->m, ktau_sign_esize(db->n, opt), st);
+    s = ktau_signgemm_rect(Q, D, out, db->m, ktau_sign_obits(db->n, opt), st);
   } else {
     ktau_merge_plan plan;
     ktau_merge_default_plan(db->n, &plan);

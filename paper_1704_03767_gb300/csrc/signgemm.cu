@@ -184,6 +184,65 @@ __global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __rest
   }
 }
 
+// FP4 e2m1 form (+1 = 0x2, -1 = 0xA, 0 = 0), two elements per byte, element 2i in the low
+// nibble of byte i; 32 elements per 16-byte store.
+__global__ void __launch_bounds__(256) sign_expand4_kernel(const uint16_t* __restrict__ rank,
+                                                           int64_t ld, int n, int64_t m, int K,
+                                                           int K_pad, uint8_t* __restrict__ out) {
+  extern __shared__ uint16_t s_r[];  // [EXPAND_ROWS][n]
+  constexpr int PER = 32;
+  const int64_t row0 = (int64_t)blockIdx.x * EXPAND_ROWS;
+  const int rows = (int)min((int64_t)EXPAND_ROWS, m - row0);
+  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
+    const int r = i / n, c = i - r * n;
+    s_r[i] = rank[(row0 + r) * ld + c];
+  }
+  __syncthreads();
+  const int chunks = K_pad / PER;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int k0 = c * PER;
+    uint16_t ia[PER], ib[PER];
+    {
+      int a = 0, b = 0;
+      if (k0 < K) {
+        a = pair_row(n, k0);
+        b = k0 - a * (2 * n - a - 1) / 2 + a + 1;
+      }
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        if (k0 + e < K) {
+          ia[e] = (uint16_t)a;
+          ib[e] = (uint16_t)b;
+          if (++b == n) {
+            ++a;
+            b = a + 1;
+          }
+        } else {
+          ia[e] = ib[e] = 0;
+        }
+      }
+    }
+    for (int r = 0; r < rows; ++r) {
+      const uint16_t* sr = s_r + r * n;
+      uint32_t words[4];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const int e = 8 * w + h;
+          const int d = (int)sr[ia[e]] - (int)sr[ib[e]];
+          const uint32_t v = d > 0 ? 0x2u : (d < 0 ? 0xAu : 0u);
+          word |= v << (4 * h);
+        }
+        words[w] = word;
+      }
+      reinterpret_cast<uint4*>(out + (row0 + r) * (int64_t)(K_pad / 2))[c] =
+          make_uint4(words[0], words[1], words[2], words[3]);
+    }
+  }
+}
+
 // Batched: rows [0, rows) of a group of datasets (numbered dataset by dataset, prefix over bids),
 // written into the group's stacked operand (row stride `stride` bytes, dataset rows from srow).
 template <int ESIZE>
@@ -487,6 +546,7 @@ struct ContractArgs {
   int64_t wG;              // tri: traversal groups per side
   int64_t ncb;             // rect: column blocks of BM
   int bnr;                 // output rows per unit: 256, or 128 for short query batches
+  int afmt;                // kind::f8f6f4 operand format: 0 = E4M3, 5 = E2M1 (FP4)
   int64_t unit_lo, unit_hi;
   uint64_t p_begin, p_end; // tri: pair range
   int64_t ldo;             // rect: output row stride
@@ -1221,7 +1281,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          mbar_expect_tx(FULL(stage), (uint32_t)(A_BYTES + a.bnr * BKB));
+          // FP4 boxes count their packed bytes (half the shared-memory footprint)
+          mbar_expect_tx(FULL(stage), (uint32_t)(A_BYTES + a.bnr * BKB) >> (a.afmt == 5 ? 1 : 0));
           const int kx = (int)(kb * BKB);
           tma_load_2d(sa, &tmA, kx, t.ta, FULL(stage), pol);
           tma_load_2d(sb, &tmB, kx, t.tb, FULL(stage), pol);
@@ -1236,7 +1297,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr uint32_t kFmt = ESIZE == 1 ? 0u : 1u;  // E4M3 (f8f6f4) or BF16 (f16)
+      const uint32_t kFmt = ESIZE == 1 ? (uint32_t)a.afmt : 1u;  // E4M3/E2M1 or BF16 (f16)
       const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
                              ((uint32_t)(a.bnr >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
       int stage = 0;
@@ -1376,7 +1437,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
           }
           const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE2_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          if (rank == 0) mbar_expect_tx(FULL(stage), 2u * STAGE2_BYTES);
+          // both CTAs' boxes; FP4 boxes count their packed bytes (half the footprint)
+          if (rank == 0) mbar_expect_tx(FULL(stage), (2u * STAGE2_BYTES) >> (a.afmt == 5 ? 1 : 0));
           const uint32_t full_leader = cluster_addr(FULL(stage), 0);
           const int kx = (int)(kb * BKB);
           tma_load_2d_pair(sa, &tmS, kx, t.ta, full_leader, pol);
@@ -1399,7 +1461,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (leader CTA) ----------------
     if (lane == 0 && rank == 0) {
-      constexpr uint32_t kFmt = ESIZE == 1 ? 0u : 1u;  // E4M3 (f8f6f4) or BF16 (f16)
+      const uint32_t kFmt = ESIZE == 1 ? (uint32_t)a.afmt : 1u;  // E4M3/E2M1 or BF16 (f16)
       const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
       int stage = 0;
@@ -1483,16 +1545,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-ktau_status make_tmap_raw(void* tmap, void* base, int64_t row_bytes_, int64_t rows) {
+// 128 x 128-element boxes with 128-byte swizzle. FP4 rows (fp4 = true) are packed in global
+// memory (row_bytes = K_pad / 2) and land in shared memory as 16-byte containers holding 16
+// elements in their first 8 bytes, one byte of shared memory per element like FP8.
+ktau_status make_tmap_raw(void* tmap, void* base, int64_t row_bytes_, int64_t rows,
+                          bool fp4 = false) {
   CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(tmap);
   PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
   if (!cuTensorMapEncodeTiled) return ktau_fail(KTAU_ECUDA, "cuTensorMapEncodeTiled unavailable");
   const cuuint64_t row_bytes = (cuuint64_t)row_bytes_;
-  cuuint64_t dims[2] = {row_bytes, (cuuint64_t)rows};
+  cuuint64_t dims[2] = {fp4 ? 2 * row_bytes : row_bytes, (cuuint64_t)rows};
   cuuint64_t strides[1] = {row_bytes};
   cuuint32_t box[2] = {(cuuint32_t)BKB, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides,
+  CUresult r = cuTensorMapEncodeTiled(tm, fp4 ? CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B
+                                              : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                                      2, base, dims, strides,
                                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                       CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1502,7 +1570,7 @@ ktau_status make_tmap_raw(void* tmap, void* base, int64_t row_bytes_, int64_t ro
 }
 
 ktau_status make_tmap(ktau_ranked* R) {
-  return make_tmap_raw(R->tmap, R->sgn, R->K_pad * R->esize, R->m);
+  return make_tmap_raw(R->tmap, R->sgn, R->K_pad * R->obits / 8, R->m, R->obits == 4);
 }
 
 SideArgs side_of(const ktau_ranked* R) {
@@ -1634,6 +1702,12 @@ int ktau_sign_esize(int64_t n, const ktau_options* opt) {
   return n <= KTAU_SIGNGEMM_FP8_MAX_N ? 1 : 2;
 }
 
+int ktau_sign_obits(int64_t n, const ktau_options* opt) {
+  if (opt && (opt->operand_bits == 4 || opt->operand_bits == 8 || opt->operand_bits == 16))
+    return opt->operand_bits;
+  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? KTAU_SIGNGEMM_DEFAULT_BITS : 16;
+}
+
 
 // ---------------------------------------------------------------------------------------------
 // Side stream: work that only the n_3 output needs (tie lists, the inverted index, the zero fill
@@ -1699,8 +1773,10 @@ class SideFork {
 };
 }  // namespace
 
-ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
-  if (R->sg_ready && R->esize == esize) return KTAU_OK;
+ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
+  if (obits != 4 && obits != 8 && obits != 16)
+    return ktau_fail(KTAU_EINVAL, "operand bits must be 4, 8 or 16");
+  if (R->sg_ready && R->obits == obits) return KTAU_OK;
   if (R->sg_ready) {  // built for the other operand type: rebuild
     KTAU_CUDA(cudaStreamSynchronize(st));
     ktau_signgemm_release(R);
@@ -1710,8 +1786,9 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
   const int64_t n = R->n;
   R->K = n * (n - 1) / 2;
   R->K_pad = (R->K + 127) / 128 * 128;
-  R->esize = esize;
-  R->sgn_bytes = (size_t)R->m * R->K_pad * R->esize;
+  R->obits = obits;
+  R->esize = obits == 16 ? 2 : 1;
+  R->sgn_bytes = (size_t)R->m * R->K_pad * obits / 8;
   // Lists of tied sample pairs for n_3: exact capacity from the rank statistics.
   R->tie_cap = (int64_t)R->stats.T_sum;
   R->tie_bytes = (size_t)(R->tie_cap > 0 ? R->tie_cap : 1) * 4;
@@ -1766,7 +1843,10 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
   const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
   {
     KTAU_TRACE("sign_expand_kernel", st);
-    if (R->esize == 1)
+    if (R->obits == 4)
+      sign_expand4_kernel<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                      (int)R->K_pad, (uint8_t*)R->sgn);
+    else if (R->esize == 1)
       sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
                                                         (int)R->K_pad, (uint8_t*)R->sgn);
     else
@@ -1783,8 +1863,8 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st) {
 }
 
 ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
-                                   const ktau_out& out, int esize, cudaStream_t st) {
-  ktau_status s = ktau_signgemm_prepare(R, esize, st);
+                                   const ktau_out& out, int obits, cudaStream_t st) {
+  ktau_status s = ktau_signgemm_prepare(R, obits, st);
   if (s != KTAU_OK) return s;
   const int64_t m = R->m;
   ContractArgs a;
@@ -1795,6 +1875,7 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.wS = (m + 255) / 256;
   a.ncb = 0;
   a.bnr = BN;
+  a.afmt = R->obits == 4 ? 5 : 0;
   a.p_begin = p_begin;
   a.p_end = p_end;
   a.ldo = 0;
@@ -1818,10 +1899,10 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
 }
 
 ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
-                               int esize, cudaStream_t st) {
+                               int obits, cudaStream_t st) {
   if (Q->n != D->n) return ktau_fail(KTAU_EINVAL, "sample counts differ");
-  ktau_status s = ktau_signgemm_prepare(Q, esize, st);
-  if (s == KTAU_OK) s = ktau_signgemm_prepare(D, esize, st);
+  ktau_status s = ktau_signgemm_prepare(Q, obits, st);
+  if (s == KTAU_OK) s = ktau_signgemm_prepare(D, obits, st);
   if (s != KTAU_OK) return s;
   ContractArgs a;
   a.row = side_of(Q);
@@ -1833,6 +1914,7 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.wG = 0;
   a.ncb = (D->m + BM - 1) / BM;
   a.bnr = Q->m <= BM ? BM : BN;
+  a.afmt = Q->obits == 4 ? 5 : 0;
   a.p_begin = 0;
   a.p_end = 0;
   a.ldo = ldo;

@@ -14,17 +14,21 @@
 
 #define KTAU_SIGNGEMM_MAX_N 2048
 #define KTAU_SIGNGEMM_FP8_MAX_N 2048
+// Operand bits used when the caller does not choose (operand_bits = 0).
+#define KTAU_SIGNGEMM_DEFAULT_BITS 8
 
 bool ktau_signgemm_supported(int64_t n);
 // Operand element size for n and the options (1 = FP8 e4m3, 2 = BF16).
 int ktau_sign_esize(int64_t n, const ktau_options* opt);
+// Operand bits of the single-matrix and query contraction: 4 (FP4 e2m1), 8 or 16.
+int ktau_sign_obits(int64_t n, const ktau_options* opt);
 // Builds (once per element size) the sign expansion, the tie-pair lists and the TMA descriptor.
-ktau_status ktau_signgemm_prepare(ktau_ranked* R, int esize, cudaStream_t st);
+ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st);
 ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
-                                   const ktau_out& out, int esize, cudaStream_t st);
+                                   const ktau_out& out, int obits, cudaStream_t st);
 // Rectangular form: every row of Q against every row of D (outputs [b][m_db], row stride ldo).
 ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& out, int64_t ldo,
-                               int esize, cudaStream_t st);
+                               int obits, cudaStream_t st);
 void ktau_signgemm_release(ktau_ranked* R);
 
 // Batched tensor-core group: datasets bids[0..nb) of ds (all FP8 or all BF16), whose rows are

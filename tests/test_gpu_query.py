@@ -22,7 +22,7 @@ def ktau():
     return k
 
 
-def _query(ktau, Q, D, k, path=0, count_bits=32):
+def _query(ktau, Q, D, k, path=0, count_bits=32, bits=0):
     Rq = ktau.ktau_rank_prepare(torch.from_numpy(np.ascontiguousarray(Q)).cuda())
     Rd = ktau.ktau_rank_prepare(torch.from_numpy(np.ascontiguousarray(D)).cuda())
     b, m = Q.shape[0], D.shape[0]
@@ -32,7 +32,8 @@ def _query(ktau, Q, D, k, path=0, count_bits=32):
     n3 = torch.empty((b, m), dtype=cdt, device="cuda")
     idx = torch.empty((b, max(k, 1)), dtype=torch.int32, device="cuda")
     tk = torch.empty((b, max(k, 1)), dtype=torch.float64, device="cuda")
-    ktau.ktau_query(Rd, Rq, tau, S, n3, count_bits, k, idx, tk, {"path": path})
+    ktau.ktau_query(Rd, Rq, tau, S, n3, count_bits, k, idx, tk,
+                    {"path": path, "operand_bits": bits})
     ktau.ktau_device_status()
     out = {"tau": tau.cpu().numpy(), "S": S.cpu().numpy().astype(np.int64),
            "n3": n3.cpu().numpy().astype(np.int64), "idx": idx.cpu().numpy()[:, :k],
@@ -51,8 +52,9 @@ def _check(got, Q, D, k):
     assert_tau64(got["tk"].ravel(), ref["topk_tau"].ravel())
 
 
-@pytest.mark.parametrize("n,path", [(100, 0), (200, 0), (100, 1), (1100, 0), (60, 2)])
-def test_query_matches_oracle(ktau, n, path):
+@pytest.mark.parametrize("n,path,bits", [(100, 0, 0), (200, 0, 0), (100, 1, 0), (1100, 0, 0),
+                                         (60, 2, 0), (200, 2, 4), (1100, 2, 4)])
+def test_query_matches_oracle(ktau, n, path, bits):
     D = uniform_ties(300 if n < 1000 else 120, n, tie_frac=0.3, seed=n)
     D[10] = D[11]          # exact |tau| ties -> index order
     D[12] = -D[11]
@@ -60,7 +62,7 @@ def test_query_matches_oracle(ktau, n, path):
     Q = uniform_ties(7, n, tie_frac=0.3, seed=n + 1)
     Q[2] = D[11]
     k = 50
-    _check(_query(ktau, Q, D, k, path), Q, D, k)
+    _check(_query(ktau, Q, D, k, path, bits=bits), Q, D, k)
 
 
 def test_full_sort_and_constant_query(ktau):

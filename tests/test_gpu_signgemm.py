@@ -28,6 +28,7 @@ def _run(ktau, X, count_bits=32, options=SG, p_begin=0, p_end=None):
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     res = ktau.allpairs(Xd, p_begin=p_begin, p_end=p_end, count_bits=count_bits, options=options)
     torch.cuda.synchronize()
+    ktau.ktau_device_status()  # a bounded wait that gave up raises here
     out = {k: v.cpu().numpy() for k, v in res.items() if isinstance(v, torch.Tensor)}
     res["ranked"].free()
     return out
@@ -40,24 +41,25 @@ def _check(got, ref):
     assert_tau32(got["tau32"], ref["tau"])
 
 
-@pytest.mark.parametrize("bits", [8, 16])
+@pytest.mark.parametrize("bits", [4, 8, 16])
 def test_uniform_ties_64x200(ktau, bits):
     X = uniform_ties(64, 200, seed=0)
     _check(_run(ktau, X, 64, options={"path": 2, "operand_bits": bits}), oracle_full(X))
 
 
+@pytest.mark.parametrize("bits", [0, 4])
 @pytest.mark.parametrize("n", [2, 3, 17, 64, 100, 127, 128, 129, 200, 256, 300, 1100])
-def test_ragged(ktau, n):
+def test_ragged(ktau, n, bits):
     m = 300 if n < 1000 else 90  # two 256-row super-tiles, ragged
     X = uniform_ties(m, n, tie_frac=0.2, seed=n)
     X[10] = X[11]
     X[12] = -X[13]
     X[20, : n // 2] = 0.25
-    _check(_run(ktau, X, 32), oracle_full(X))
+    _check(_run(ktau, X, 32, options={"path": 2, "operand_bits": bits}), oracle_full(X))
 
 
 @pytest.mark.parametrize("n,bits", [(128, 8), (256, 8), (512, 8), (1024, 8), (2048, 8),
-                                    (256, 16)])
+                                    (256, 16), (128, 4), (300, 4), (1024, 4), (2048, 4)])
 def test_extreme_counts(ktau, n, bits):
     """Exactness of the tensor-core sums: |S| = n_0 (identical and reversed rows, the largest
     partial sums), and strongly correlated rows, whose partial sums grow large while each MMA adds
@@ -106,15 +108,16 @@ def test_gene_expression_matches_merge_bitwise(ktau):
     Xd = torch.from_numpy(X).cuda()
     R = ktau.ktau_rank_prepare(Xd)
     outs = {}
-    for name, opt in (("sg", SG), ("merge", MERGE)):
+    for name, opt in (("sg", SG), ("sg4", {"path": 2, "operand_bits": 4}), ("merge", MERGE)):
         tau32 = torch.empty(P, dtype=torch.float32, device="cuda")
         S = torch.empty(P, dtype=torch.int32, device="cuda")
         n3 = torch.empty(P, dtype=torch.int32, device="cuda")
         ktau.ktau_allpairs(R, 0, P, None, tau32, S, n3, 32, opt)
         outs[name] = (tau32, S, n3)
     torch.cuda.synchronize()
-    for a, b in zip(outs["sg"], outs["merge"]):
-        assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    for a, b, c in zip(outs["sg"], outs["sg4"], outs["merge"]):
+        assert torch.equal(a.view(torch.int32), c.view(torch.int32))
+        assert torch.equal(b.view(torch.int32), c.view(torch.int32))
     g = np.random.default_rng(0)
     ps = np.unique(np.concatenate([g.integers(0, P, 2000), [0, P - 1]]))
     idx = torch.from_numpy(ps).cuda()
