@@ -186,8 +186,10 @@ ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, in
 
 /* Builds the tensor-core operands of a handle now instead of on first use: the sign expansion
  * A_u[k] = sign(u_a - u_b) over all sample pairs (Sec. 3.1, Algorithm 1), stored as FP8 e4m3
- * (library memory, m * n_0 bytes rounded up to 128 per variable). Asynchronous on `stream`
- * (allocates on first use). EINVAL when n > 1024 (path unsupported). */
+ * (library memory, m * n_0 bytes with n_0 rounded up to 128 per variable). The lists of tied
+ * sample pairs that n_3 needs are built by the first ktau_allpairs call that stores n_3, beside
+ * its contraction. Asynchronous on `stream` (allocates on first use). EINVAL when n > 2048
+ * (path unsupported). */
 ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
 
 /* Synchronises `stream` and reports device-side status words raised since the last call, then

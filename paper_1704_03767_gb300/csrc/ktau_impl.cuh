@@ -66,6 +66,7 @@ struct ktau_ranked {
   int32_t* bkt_var;
   unsigned long long* bkt_stat;
   size_t bkt_var_bytes;
+  int ties_ready;  // tie lists and index built (on first use by an n_3 output)
 };
 
 // ---------------------------------------------------------------------------------------------

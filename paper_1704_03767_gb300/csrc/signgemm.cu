@@ -726,32 +726,50 @@ __device__ void warp_list_ties(const uint16_t* __restrict__ perm, const uint16_t
 }
 
 // Exclusive prefix of the tie counts T over m variables (one CTA): off[i] = sum_{r<i} T[r].
+// Tiles of 4 * blockDim values: each thread loads four consecutive values (coalesced across the
+// CTA), the CTA scans the thread sums, and a running carry links the tiles.
 // A variable's list is stored only when it ends within `cap` entries; the others are walked
 // from their tie groups directly by the joint-ties kernel (same test on both sides).
 __global__ void __launch_bounds__(1024) ties_scan_kernel(const int64_t* __restrict__ T, int64_t m,
                                                          int64_t* __restrict__ off) {
   __shared__ long long wsum[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t per = (m + blockDim.x - 1) / blockDim.x;
-  const int64_t b = min(m, tid * per), e = min(m, b + per);
-  long long local = 0;
-  for (int64_t i = b; i < e; ++i) local += T[i];
-  long long incl = local;
-  for (int d = 1; d < 32; d <<= 1) {
-    const long long t = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += t;
+  __shared__ long long carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  long long carry = 0;
+  for (int64_t base = 0; base < m; base += 4 * (int64_t)blockDim.x) {
+    const int64_t i0 = base + 4 * (int64_t)tid;
+    long long v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = i0 + e < m ? (long long)T[i0 + e] : 0ll;
+    const long long local = v[0] + v[1] + v[2] + v[3];
+    long long incl = local;
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      long long w = lane < nw ? wsum[lane] : 0ll;
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += t;
+      }
+      if (lane < nw) wsum[lane] = w;  // inclusive prefix over warps
+    }
+    __syncthreads();
+    long long run = carry + incl - local + (warp > 0 ? wsum[warp - 1] : 0ll);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (i0 + e < m) off[i0 + e] = run;
+      run += v[e];
+    }
+    if (tid == blockDim.x - 1) carry_s = run;
+    __syncthreads();
+    carry = carry_s;
+    __syncthreads();
   }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  long long before = 0;
-  for (int w = 0; w < warp; ++w) before += wsum[w];
-  long long run = before + incl - local;
-  for (int64_t i = b; i < e; ++i) {
-    off[i] = run;
-    run += T[i];
-  }
-  if (e == m && b < e) off[m] = run;
-  if (m == 0 && tid == 0) off[0] = 0;
+  if (tid == 0) off[m] = carry;
 }
 
 __global__ void ties_list_kernel(const uint16_t* __restrict__ perm, const uint16_t* __restrict__ srank,
@@ -766,56 +784,73 @@ __global__ void ties_list_kernel(const uint16_t* __restrict__ perm, const uint16
 }
 
 // Inclusive prefix of the bucket sizes in place (one CTA), c[K] = total; also the work of the
-// bucket form of n_3 (sum and largest s(s-1)/2) and the flag that selects it.
+// bucket form of n_3 (sum and largest s(s-1)/2) and the flag that selects it. Tiles of
+// 4 * blockDim values as in ties_scan_kernel.
 __global__ void __launch_bounds__(1024) bucket_scan_kernel(int32_t* __restrict__ c, int64_t K,
                                                            unsigned long long* __restrict__ stat,
                                                            unsigned long long lim_total,
                                                            unsigned long long lim_one) {
   __shared__ long long wsum[32];
   __shared__ unsigned long long wwork[32], wmax[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t per = (K + blockDim.x - 1) / blockDim.x;
-  const int64_t b = min(K, tid * per), e = min(K, b + per);
-  long long local = 0;
+  __shared__ long long carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  long long carry = 0;
   unsigned long long work = 0, big = 0;
-  for (int64_t i = b; i < e; ++i) {
-    const long long v = c[i];
-    local += v;
-    const unsigned long long wv = (unsigned long long)(v * (v - 1) / 2);
-    work += wv;
-    big = wv > big ? wv : big;
-  }
-  long long incl = local;
-  for (int d = 1; d < 32; d <<= 1) {
-    const long long t = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += t;
+  for (int64_t base = 0; base < K; base += 4 * (int64_t)blockDim.x) {
+    const int64_t i0 = base + 4 * (int64_t)tid;
+    long long v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      v[e] = i0 + e < K ? (long long)c[i0 + e] : 0ll;
+      const unsigned long long wv = (unsigned long long)(v[e] * (v[e] - 1) / 2);
+      work += wv;
+      big = wv > big ? wv : big;
+    }
+    const long long local = v[0] + v[1] + v[2] + v[3];
+    long long incl = local;
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      long long w = lane < nw ? wsum[lane] : 0ll;
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += t;
+      }
+      if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    long long run = carry + incl - local + (warp > 0 ? wsum[warp - 1] : 0ll);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      run += v[e];
+      if (i0 + e < K) c[i0 + e] = (int32_t)run;
+    }
+    if (tid == blockDim.x - 1) carry_s = run;
+    __syncthreads();
+    carry = carry_s;
+    __syncthreads();
   }
   for (int d = 16; d > 0; d >>= 1) {
     work += __shfl_xor_sync(0xffffffffu, work, d);
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, big, d);
     big = o > big ? o : big;
   }
-  if (lane == 31) wsum[warp] = incl;
   if (lane == 0) {
     wwork[warp] = work;
     wmax[warp] = big;
   }
   __syncthreads();
-  long long run = incl - local;
-  for (int w = 0; w < warp; ++w) run += wsum[w];
-  for (int64_t i = b; i < e; ++i) {
-    run += c[i];
-    c[i] = (int32_t)run;
-  }
   if (tid == 0) {
-    long long tot = 0;
     unsigned long long W = 0, M = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      tot += wsum[w];
+    for (int w = 0; w < nw; ++w) {
       W += wwork[w];
       M = wmax[w] > M ? wmax[w] : M;
     }
-    c[K] = (int32_t)tot;
+    c[K] = (int32_t)carry;
     stat[0] = W;
     stat[1] = M;
     stat[2] = (W <= lim_total && M <= lim_one) ? 1ull : 0ull;
@@ -1789,13 +1824,41 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
   R->obits = obits;
   R->esize = obits == 16 ? 2 : 1;
   R->sgn_bytes = (size_t)R->m * R->K_pad * obits / 8;
-  // Lists of tied sample pairs for n_3: exact capacity from the rank statistics.
+  if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
+  const size_t smem = (size_t)EXPAND_ROWS * n * sizeof(uint16_t);
+  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
+  {
+    KTAU_TRACE("sign_expand_kernel", st);
+    if (R->obits == 4)
+      sign_expand4_kernel<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                      (int)R->K_pad, (uint8_t*)R->sgn);
+    else if (R->esize == 1)
+      sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                        (int)R->K_pad, (uint8_t*)R->sgn);
+    else
+      sign_expand_kernel<2><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                        (int)R->K_pad, (uint8_t*)R->sgn);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  ktau_status s = make_tmap(R);
+  if (s != KTAU_OK) return s;
+  R->sg_ready = 1;
+  return KTAU_OK;
+}
+
+// Lists of tied sample pairs for n_3 and their inverted index, built once per handle on the
+// first call that stores n_3. The kernels are small (at most 256 threads, few registers) so that
+// they can run on the SMs beside the persistent contraction when launched on a side stream.
+ktau_status ktau_signgemm_ties(ktau_ranked* R, cudaStream_t ss) {
+  if (R->ties_ready) return KTAU_OK;
+  const int64_t n = R->n;
+  R->K = n * (n - 1) / 2;
+  // exact capacity from the rank statistics
   R->tie_cap = (int64_t)R->stats.T_sum;
   R->tie_bytes = (size_t)(R->tie_cap > 0 ? R->tie_cap : 1) * 4;
-  // Inverted index for the bucket form of n_3 (built when the counts fit 32-bit offsets).
+  // inverted index for the bucket form of n_3 (built when the counts fit 32-bit offsets)
   const bool buckets = R->stats.T_sum > 0 && R->stats.T_sum < (1ll << 31) && R->m < (1ll << 31);
-  if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK ||
-      ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
+  if (ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
       ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) != KTAU_OK)
     return KTAU_ENOMEM;
   if (buckets) {
@@ -1805,12 +1868,9 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
         ktau_dmalloc((void**)&R->bkt_stat, 4 * sizeof(unsigned long long)) != KTAU_OK)
       return KTAU_ENOMEM;
   }
-  // The tie lists and the index run beside the sign expansion (large matrices only).
-  SideFork side(st, R->m >= 4096);
-  const cudaStream_t ss = side.stream();
   {
     KTAU_TRACE("ties_scan_kernel", ss);
-    ties_scan_kernel<<<1, 1024, 0, ss>>>(R->T, R->m, R->tie_off);
+    ties_scan_kernel<<<1, 256, 0, ss>>>(R->T, R->m, R->tie_off);
   }
   KTAU_CUDA(cudaGetLastError());
   if (buckets)
@@ -1829,7 +1889,7 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
     const unsigned long long lim_total = P / 16 > (1ull << 16) ? P / 16 : (1ull << 16);
     {
       KTAU_TRACE("bucket_scan_kernel", ss);
-      bucket_scan_kernel<<<1, 1024, 0, ss>>>(R->bkt_off, R->K, R->bkt_stat, lim_total, 1ull << 18);
+      bucket_scan_kernel<<<1, 128, 0, ss>>>(R->bkt_off, R->K, R->bkt_stat, lim_total, 1ull << 18);
     }
     KTAU_CUDA(cudaGetLastError());
     {
@@ -1839,26 +1899,7 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
     }
     KTAU_CUDA(cudaGetLastError());
   }
-  const size_t smem = (size_t)EXPAND_ROWS * n * sizeof(uint16_t);
-  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
-  {
-    KTAU_TRACE("sign_expand_kernel", st);
-    if (R->obits == 4)
-      sign_expand4_kernel<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                      (int)R->K_pad, (uint8_t*)R->sgn);
-    else if (R->esize == 1)
-      sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                        (int)R->K_pad, (uint8_t*)R->sgn);
-    else
-      sign_expand_kernel<2><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                        (int)R->K_pad, (uint8_t*)R->sgn);
-  }
-  KTAU_CUDA(cudaGetLastError());
-  ktau_status s = side.join();
-  if (s != KTAU_OK) return s;
-  s = make_tmap(R);
-  if (s != KTAU_OK) return s;
-  R->sg_ready = 1;
+  R->ties_ready = 1;
   return KTAU_OK;
 }
 
@@ -1892,7 +1933,13 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / 256 / GROUP + 1);
   const int64_t units = a.unit_hi - a.unit_lo;
   // The epilogue zero-fills n_3 over the range; the joint-ties kernels then add nonzero counts.
+  // The tie lists (first call only) are built beside the contraction on a side stream.
+  const bool build_ties = out.n3 != nullptr && !R->ties_ready;
+  SideFork side(st, build_ties && m >= 4096);
   s = R->esize == 1 ? launch_contract2<1>(R, a, units, st) : launch_contract2<2>(R, a, units, st);
+  if (s == KTAU_OK && build_ties) s = ktau_signgemm_ties(R, side.stream());
+  const ktau_status sj = side.join();
+  if (s == KTAU_OK) s = sj;
   if (s == KTAU_OK && out.n3)
     s = launch_joint_ties(R, R, 1, p_begin, p_end, 0, out.n3, out.count_bits, st);
   return s;
@@ -1927,6 +1974,8 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.unit_hi = ((Q->m + a.bnr - 1) / a.bnr) * a.ncb;
   s = Q->esize == 1 ? launch_contract<1>(Q, D, a, a.unit_hi, st)
                     : launch_contract<2>(Q, D, a, a.unit_hi, st);
+  if (s == KTAU_OK && out.n3) s = ktau_signgemm_ties(Q, st);
+  if (s == KTAU_OK && out.n3) s = ktau_signgemm_ties(D, st);
   if (s == KTAU_OK && out.n3) s = launch_joint_ties(Q, D, 0, 0, 0, ldo, out.n3, out.count_bits, st);
   return s;
 }
@@ -1945,6 +1994,7 @@ void ktau_signgemm_release(ktau_ranked* R) {
   R->bkt_stat = nullptr;
   R->sgn = nullptr;
   R->sg_ready = 0;
+  R->ties_ready = 0;
 }
 
 ktau_status ktau_signgemm_check_error(cudaStream_t st) {
