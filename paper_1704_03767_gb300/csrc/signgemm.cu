@@ -1464,7 +1464,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       for (int64_t s2 = s_lo + cid; ok && s2 < s_hi; s2 += ncl) {
         if (!pair_live(a, s2)) continue;
         const Unit t = unit_of(a, 2 * s2 + rank);
-        const int brow = (int)(t.y0 + (int64_t)BM * rank);  // this CTA's half of the rows
+        const int brow = t.tb + BM * (int)rank;  // this CTA's half of the rows (operand row)
         for (int64_t kb = 0; kb < t.num_kb; ++kb) {
           if (!mbar_wait(EMPTY(stage), phase ^ 1u)) {
             ok = false;
@@ -1509,7 +1509,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         if (!mbar_wait(TEMPTY(acc), acc_phase ^ 1u)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-        for (int64_t kb = 0; kb < a.num_kb; ++kb) {
+        const int64_t num_kb = unit_of(a, 2 * s2).num_kb;  // per dataset in a batch
+        for (int64_t kb = 0; kb < num_kb; ++kb) {
           if (!mbar_wait(FULL(stage), phase)) {
             ok = false;
             break;
@@ -1684,8 +1685,8 @@ ktau_status launch_contract_maps(const void* tmap_a, const void* tmap_b, const C
 
 // Pair form over the triangle of one matrix: clusters of two CTAs, as many as fit at once.
 template <int ESIZE>
-ktau_status launch_contract2(const ktau_ranked* R, const ContractArgs& args, int64_t units,
-                             cudaStream_t st) {
+ktau_status launch_contract2_map(const void* tmap, const ContractArgs& args, int64_t units,
+                                 cudaStream_t st) {
   auto kern = contract2_kernel<ESIZE>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SMEM2_BYTES));
@@ -1716,9 +1717,15 @@ ktau_status launch_contract2(const ktau_ranked* R, const ContractArgs& args, int
   if (clusters < 1) clusters = 1;
   KTAU_TRACE("contract_kernel", st);
   kern<<<(unsigned)(2 * clusters), THREADS, SMEM2_BYTES, st>>>(
-      *reinterpret_cast<const CUtensorMap*>(R->tmap), args);
+      *reinterpret_cast<const CUtensorMap*>(tmap), args);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
+}
+
+template <int ESIZE>
+ktau_status launch_contract2(const ktau_ranked* R, const ContractArgs& args, int64_t units,
+                             cudaStream_t st) {
+  return launch_contract2_map<ESIZE>(R->tmap, args, units, st);
 }
 
 // Rows from A, columns from B: the MMA's A operand (TMEM lanes) is the column side.
@@ -2047,8 +2054,8 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   a.unit_hi = g.units;
   a.tri = 1;
   a.bnr = BN;
-  ktau_status s = g.esize == 1 ? launch_contract_maps<1>(g.tmap, g.tmap, a, g.units, st)
-                               : launch_contract_maps<2>(g.tmap, g.tmap, a, g.units, st);
+  ktau_status s = g.esize == 1 ? launch_contract2_map<1>(g.tmap, a, g.units, st)
+                               : launch_contract2_map<2>(g.tmap, a, g.units, st);
   if (s != KTAU_OK) return s;
   const int jcols = g.max_n <= 1024 ? 64 : 32;
   const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)g.max_n * (jcols + 1) * sizeof(uint16_t);
