@@ -73,8 +73,9 @@ typedef struct {
   int32_t mapping;      /* merge path: 1 = one warp per pair, 2 = one CTA per pair */
   int32_t schedule;     /* 1 = static stride over tile ids (Sec. 4.3.2), 2 = dynamic counter */
   int32_t ctas_per_sm;  /* persistent grid = ctas_per_sm * SM count */
-  int32_t operand_bits; /* contraction operands: 8 = FP8 e4m3 (default), 4 = FP4 e2m1 (half the
-                           operand memory, same speed), 16 = BF16; all exact for n <= 2048 */
+  int32_t operand_bits; /* contraction operands: 4 = FP4 e2m1, 8 = FP8 e4m3, 16 = BF16, all
+                           exact for n <= 2048; 0 = FP8 for n <= 256, FP4 above (half the
+                           operand bytes) */
   int32_t reserved[2];
 } ktau_options;
 

@@ -22,22 +22,24 @@ namespace {
 
 constexpr int kMergeTq = 16;
 
-// Group kinds: contraction groups (one per operand element size and stride class, stride = K_pad
-// bytes rounded up to a power of two, so stacking wastes at most half of the operand memory),
+// Group kinds: contraction groups (one per operand type and stride class, stride = operand bytes
+// of a row rounded up to a power of two, so stacking wastes at most half of the operand memory),
 // merge with one warp per pair (n <= 1024), merge with one CTA per pair (n > 1024).
 enum GroupKind { kContract = 0, kMergeWarp = 1, kMergeCta = 2 };
 
 struct GroupPlan {
   int kind = kContract;
-  int64_t key = 0;           // contraction: esize * 64 + log2(stride)
+  int64_t key = 0;           // contraction: (operand bits / 4) * 64 + log2(stride)
   std::vector<int32_t> ids;  // indices into the workspace-ordered descriptor table
   int32_t* d_ids = nullptr;
   int64_t* d_row_prefix = nullptr;
   int64_t* d_unit_prefix = nullptr;
   int64_t* d_jt_prefix = nullptr;
   int64_t* d_tile_prefix = nullptr;  // merge group
+  int64_t* d_blk_prefix = nullptr;   // contraction group: sign-expansion blocks per dataset
+  int64_t blocks = 0;
   int64_t row0 = 0, rows = 0, units = 0, jt_tiles = 0, tiles = 0, max_n = 0, stride = 0;
-  int esize = 0;
+  int esize = 0, obits = 0;
   void* sgn = nullptr;
   int64_t* tie_off = nullptr;
   uint32_t* tie_pairs = nullptr;
@@ -131,11 +133,11 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     if (batch_path_for(d, opt) == KTAU_PATH_MERGE) {
       gkey[i] = (int64_t)1 << 40 | (d.n <= 1024 ? 0 : 1);
     } else {
-      const int es = ktau_sign_esize(d.n, opt);
-      const int64_t bytes = (d.n * (d.n - 1) / 2 + 127) / 128 * 128 * es;
-      int lg = 7;
+      const int ob = ktau_sign_obits(d.n, opt);
+      const int64_t bytes = (d.n * (d.n - 1) / 2 + 127) / 128 * 128 * ob / 8;
+      int lg = 6;
       while (((int64_t)1 << lg) < bytes) ++lg;
-      gkey[i] = es * 64 + lg;
+      gkey[i] = (ob / 4) * 64 + lg;
     }
   }
   std::vector<int64_t> keys(gkey);
@@ -212,7 +214,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     GroupPlan& G = B->g[gi];
     if (G.ids.empty()) continue;
     G.row0 = row_prefix[G.ids.front()];
-    std::vector<int64_t> rp(1, 0), up(1, 0), jp(1, 0), tp(1, 0);
+    std::vector<int64_t> rp(1, 0), up(1, 0), jp(1, 0), tp(1, 0), bp(1, 0);
     int64_t kpad_max = 0;
     for (int k : G.ids) {
       ktau_bds& D = B->hds[k];
@@ -223,7 +225,8 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
         D.w = (D.m + D.tq - 1) / D.tq;
         tp.push_back(tp.back() + D.w * (D.w + 1) / 2);
       } else {
-        D.esize = (int)(G.key / 64);
+        D.esize = (int)(G.key / 64) == 4 ? 2 : 1;  // BF16 takes 2 bytes in shared memory
+        bp.push_back(bp.back() + (D.m + KTAU_EXPAND_ROWS - 1) / KTAU_EXPAND_ROWS);
         const int64_t K = D.n * (D.n - 1) / 2;
         const int64_t K_pad = (K + 127) / 128 * 128;
         D.num_kb = K_pad * D.esize / 128;
@@ -248,11 +251,14 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       }
       continue;
     }
-    G.esize = (int)(G.key / 64);
+    G.obits = (int)(G.key / 64) * 4;
+    G.esize = G.obits == 16 ? 2 : 1;
     G.units = up.back();
     G.jt_tiles = jp.back();
-    G.stride = kpad_max * G.esize;
+    G.blocks = bp.back();
+    G.stride = kpad_max * G.obits / 8;
     if ((s = batch_upload(B, &G.d_unit_prefix, up)) != KTAU_OK ||
+        (s = batch_upload(B, &G.d_blk_prefix, bp)) != KTAU_OK ||
         (s = batch_upload(B, &G.d_jt_prefix, jp)) != KTAU_OK ||
         (s = batch_alloc(B, &G.sgn, (size_t)G.rows * G.stride)) != KTAU_OK ||
         (s = batch_alloc(B, (void**)&G.tie_off, ((size_t)G.rows + 1) * 8)) != KTAU_OK) {
@@ -276,7 +282,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       D.tie_pairs = G.tie_pairs;
       D.tie_cap = G.tie_cap;
     }
-    if ((s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows)) != KTAU_OK) {
+    if ((s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows, G.obits)) != KTAU_OK) {
       ktau_batch_free(B);
       return s;
     }
@@ -310,7 +316,10 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
     g.bids = G.d_ids;
     g.nb = (int)G.ids.size();
     g.esize = G.esize;
+    g.obits = G.obits;
     g.row_prefix = G.d_row_prefix;
+    g.blk_prefix = G.d_blk_prefix;
+    g.blocks = G.blocks;
     g.unit_prefix = G.d_unit_prefix;
     g.jt_prefix = G.d_jt_prefix;
     g.rows = G.rows;

@@ -74,130 +74,35 @@ __device__ __forceinline__ int pair_row(int n, long long k) {
   return a;
 }
 
-// One variable's signs: orow[k] for k < K_pad (zero beyond K); s_r holds its n ranks.
-template <int ESIZE>
-__device__ void expand_row(const uint16_t* s_r, int n, int64_t K, int64_t K_pad, uint8_t* orow) {
-  constexpr int PER = 16 / ESIZE;  // elements per 16-byte store
-  const int64_t chunks = K_pad / PER;
-  for (int64_t c = threadIdx.x; c < chunks; c += blockDim.x) {
-    const int64_t k0 = c * PER;
-    uint32_t words[4];
-    if (k0 < K) {
-      int a = pair_row(n, k0);
-      int b = (int)(k0 - (long long)a * (2LL * n - a - 1) / 2) + a + 1;
-      uint32_t acc[PER];
-#pragma unroll
-      for (int e = 0; e < PER; ++e) {
-        uint32_t v = 0;
-        if (k0 + e < K) {
-          const int d = (int)s_r[a] - (int)s_r[b];
-          if (ESIZE == 1)
-            v = d > 0 ? 0x38u : (d < 0 ? 0xB8u : 0u);
-          else
-            v = d > 0 ? 0x3F80u : (d < 0 ? 0xBF80u : 0u);
-          if (++b == n) {
-            ++a;
-            b = a + 1;
-          }
-        }
-        acc[e] = v;
-      }
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        if (ESIZE == 1)
-          words[w] = acc[4 * w] | (acc[4 * w + 1] << 8) | (acc[4 * w + 2] << 16) |
-                     (acc[4 * w + 3] << 24);
-        else
-          words[w] = acc[2 * w] | (acc[2 * w + 1] << 16);
-      }
-    } else {
-      words[0] = words[1] = words[2] = words[3] = 0u;
-    }
-    reinterpret_cast<uint4*>(orow)[c] = make_uint4(words[0], words[1], words[2], words[3]);
-  }
+// Shared-memory rank rows of the expansion kernels are padded: the lanes of a warp read ranks
+// 128 / OB apart (consecutive chunks), which would otherwise share a few banks. Pad slots (one
+// after every 8 ranks for FP8, every 16 for FP4, two after every 8 for BF16) make the 32 reads of
+// one instruction fall on distinct banks.
+// Short rows (n <= 256, PAD = false) are left unpadded: there the extra index arithmetic costs
+// more than the conflicts.
+template <int OB, bool PAD = true>
+__host__ __device__ __forceinline__ int xpad(int i) {
+  if (!PAD) return i;
+  return OB == 8 ? i + (i >> 3) : (OB == 4 ? i + (i >> 4) : i + 2 * (i >> 3));
 }
+template <int OB, bool PAD = true>
+__host__ __device__ __forceinline__ int xrow(int n) { return xpad<OB, PAD>(n) + 1; }
 
-// EXPAND_ROWS variables per CTA: the sample pairs (a, b) of a 16-byte chunk are the same for every
-// variable, so a thread finds them once (pair_row) and reuses them for all rows of the CTA.
-// Positions k >= K read (0, 0) and store 0, which pads every row to K_pad.
-constexpr int EXPAND_ROWS = 8;
+// Signs of up to EXPAND_ROWS variables whose ranks are in shared memory (s_r[r * xrow(n) + xpad(i)]):
+// out[r * row_bytes + k] for k < K_pad, zero beyond K. OB = operand bits: 8 = FP8 e4m3
+// (+1 = 0x38, -1 = 0xB8), 16 = BF16 (0x3F80 / 0xBF80), 4 = FP4 e2m1 (+1 = 0x2, -1 = 0xA, two per
+// byte, element 2i in the low nibble of byte i). The sample pairs (a, b) of a 16-byte chunk are
+// the same for every variable, so a thread finds them once (pair_row) and reuses them; positions
+// k >= K read (0, 0) and store 0.
+constexpr int EXPAND_ROWS = KTAU_EXPAND_ROWS;
 
-template <int ESIZE>
-__global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
-                                                          int64_t ld, int n, int64_t m, int K,
-                                                          int K_pad, uint8_t* __restrict__ out) {
-  extern __shared__ uint16_t s_r[];  // [EXPAND_ROWS][n]
-  constexpr int PER = 16 / ESIZE;    // elements per 16-byte store
-  const int64_t row0 = (int64_t)blockIdx.x * EXPAND_ROWS;
-  const int rows = (int)min((int64_t)EXPAND_ROWS, m - row0);
-  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
-    const int r = i / n, c = i - r * n;
-    s_r[i] = rank[(row0 + r) * ld + c];
-  }
-  __syncthreads();
-  const int chunks = K_pad / PER;
-  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-    const int k0 = c * PER;
-    int ia[PER], ib[PER];
-    {
-      int a = 0, b = 0;
-      if (k0 < K) {
-        a = pair_row(n, k0);
-        b = k0 - a * (2 * n - a - 1) / 2 + a + 1;
-      }
-#pragma unroll
-      for (int e = 0; e < PER; ++e) {
-        if (k0 + e < K) {
-          ia[e] = a;
-          ib[e] = b;
-          if (++b == n) {
-            ++a;
-            b = a + 1;
-          }
-        } else {
-          ia[e] = ib[e] = 0;
-        }
-      }
-    }
-    for (int r = 0; r < rows; ++r) {
-      const uint16_t* sr = s_r + r * n;
-      uint32_t words[4];
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int h = 0; h < PER / 4; ++h) {
-          const int e = w * (PER / 4) + h;
-          const int d = (int)sr[ia[e]] - (int)sr[ib[e]];
-          uint32_t v;
-          if (ESIZE == 1)
-            v = d > 0 ? 0x38u : (d < 0 ? 0xB8u : 0u);
-          else
-            v = d > 0 ? 0x3F80u : (d < 0 ? 0xBF80u : 0u);
-          word |= v << (8 * ESIZE * h);
-        }
-        words[w] = word;
-      }
-      reinterpret_cast<uint4*>(out + (row0 + r) * (int64_t)K_pad * ESIZE)[c] =
-          make_uint4(words[0], words[1], words[2], words[3]);
-    }
-  }
-}
-
-// FP4 e2m1 form (+1 = 0x2, -1 = 0xA, 0 = 0), two elements per byte, element 2i in the low
-// nibble of byte i; 32 elements per 16-byte store.
-__global__ void __launch_bounds__(256) sign_expand4_kernel(const uint16_t* __restrict__ rank,
-                                                           int64_t ld, int n, int64_t m, int K,
-                                                           int K_pad, uint8_t* __restrict__ out) {
-  extern __shared__ uint16_t s_r[];  // [EXPAND_ROWS][n]
-  constexpr int PER = 32;
-  const int64_t row0 = (int64_t)blockIdx.x * EXPAND_ROWS;
-  const int rows = (int)min((int64_t)EXPAND_ROWS, m - row0);
-  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
-    const int r = i / n, c = i - r * n;
-    s_r[i] = rank[(row0 + r) * ld + c];
-  }
-  __syncthreads();
+template <int OB, bool PAD>
+__device__ __forceinline__ void expand_block(const uint16_t* __restrict__ s_r, int rows, int n,
+                                             int K, int K_pad, uint8_t* __restrict__ out,
+                                             int64_t row_bytes) {
+  constexpr int PER = 128 / OB;  // elements per 16-byte store
+  constexpr uint32_t POS = OB == 4 ? 0x2u : (OB == 8 ? 0x38u : 0x3F80u);
+  constexpr uint32_t NEG = OB == 4 ? 0xAu : (OB == 8 ? 0xB8u : 0xBF80u);
   const int chunks = K_pad / PER;
   for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
     const int k0 = c * PER;
@@ -222,50 +127,77 @@ __global__ void __launch_bounds__(256) sign_expand4_kernel(const uint16_t* __res
         }
       }
     }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      ia[e] = (uint16_t)xpad<OB, PAD>(ia[e]);
+      ib[e] = (uint16_t)xpad<OB, PAD>(ib[e]);
+    }
+    const int rs = xrow<OB, PAD>(n);
     for (int r = 0; r < rows; ++r) {
-      const uint16_t* sr = s_r + r * n;
+      const uint16_t* sr = s_r + r * rs;
       uint32_t words[4];
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         uint32_t word = 0;
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          const int e = 8 * w + h;
+        for (int h = 0; h < PER / 4; ++h) {
+          const int e = w * (PER / 4) + h;
           const int d = (int)sr[ia[e]] - (int)sr[ib[e]];
-          const uint32_t v = d > 0 ? 0x2u : (d < 0 ? 0xAu : 0u);
-          word |= v << (4 * h);
+          word |= (d > 0 ? POS : (d < 0 ? NEG : 0u)) << (OB * h);
         }
         words[w] = word;
       }
-      reinterpret_cast<uint4*>(out + (row0 + r) * (int64_t)(K_pad / 2))[c] =
+      reinterpret_cast<uint4*>(out + r * row_bytes)[c] =
           make_uint4(words[0], words[1], words[2], words[3]);
     }
   }
 }
 
-// Batched: rows [0, rows) of a group of datasets (numbered dataset by dataset, prefix over bids),
-// written into the group's stacked operand (row stride `stride` bytes, dataset rows from srow).
-template <int ESIZE>
+template <int OB, bool PAD>
+__global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
+                                                          int64_t ld, int n, int64_t m, int K,
+                                                          int K_pad, uint8_t* __restrict__ out) {
+  extern __shared__ uint16_t s_r[];  // [EXPAND_ROWS][xrow<OB, PAD>(n)]
+  const int64_t row0 = (int64_t)blockIdx.x * EXPAND_ROWS;
+  const int rows = (int)min((int64_t)EXPAND_ROWS, m - row0);
+  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
+    const int r = i / n, c = i - r * n;
+    s_r[r * xrow<OB, PAD>(n) + xpad<OB, PAD>(c)] = rank[(row0 + r) * ld + c];
+  }
+  __syncthreads();
+  const int64_t row_bytes = (int64_t)K_pad * OB / 8;
+  expand_block<OB, PAD>(s_r, rows, n, K, K_pad, out + row0 * row_bytes, row_bytes);
+}
+
+// Batched: blocks of up to EXPAND_ROWS variables of one dataset (numbered dataset by dataset,
+// prefix blk_prefix over bids), written into the group's stacked operand (row stride `stride`
+// bytes, dataset rows from srow). Each row is written up to its own dataset's K_pad.
+template <int OB, bool PAD>
 __global__ void __launch_bounds__(256) batch_sign_expand_kernel(
     const ktau_bds* __restrict__ ds, const int32_t* __restrict__ bids, int nb,
-    const int64_t* __restrict__ row_prefix, int64_t stride, uint8_t* __restrict__ out) {
+    const int64_t* __restrict__ blk_prefix, int64_t stride, uint8_t* __restrict__ out) {
   extern __shared__ uint16_t s_r[];
-  const int64_t r = blockIdx.x;
+  const int64_t blk = blockIdx.x;
   int lo = 0, hi = nb - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (row_prefix[mid] <= r)
+    if (blk_prefix[mid] <= blk)
       lo = mid;
     else
       hi = mid - 1;
   }
   const ktau_bds& D = ds[bids[lo]];
-  const int64_t row = r - row_prefix[lo];
+  const int64_t row0 = (blk - blk_prefix[lo]) * EXPAND_ROWS;
+  const int rows = (int)min((int64_t)EXPAND_ROWS, D.m - row0);
   const int n = (int)D.n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_r[i] = D.rank[row * D.ld + i];
+  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
+    const int r = i / n, c = i - r * n;
+    s_r[r * xrow<OB, PAD>(n) + xpad<OB, PAD>(c)] = D.rank[(row0 + r) * D.ld + c];
+  }
   __syncthreads();
-  const int64_t K = D.n * (D.n - 1) / 2;
-  expand_row<ESIZE>(s_r, n, K, D.num_kb * (BKB / ESIZE), out + (D.srow + row) * stride);
+  const int K = n * (n - 1) / 2;
+  const int K_pad = (K + 127) / 128 * 128;
+  expand_block<OB, PAD>(s_r, rows, n, K, K_pad, out + (D.srow + row0) * stride, stride);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1739,15 +1671,12 @@ ktau_status launch_contract(const ktau_ranked* A, const ktau_ranked* B, const Co
 
 bool ktau_signgemm_supported(int64_t n) { return n >= 2 && n <= KTAU_SIGNGEMM_MAX_N; }
 
-int ktau_sign_esize(int64_t n, const ktau_options* opt) {
-  if (opt && opt->operand_bits == 16) return 2;
-  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? 1 : 2;
-}
-
 int ktau_sign_obits(int64_t n, const ktau_options* opt) {
   if (opt && (opt->operand_bits == 4 || opt->operand_bits == 8 || opt->operand_bits == 16))
     return opt->operand_bits;
-  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? KTAU_SIGNGEMM_DEFAULT_BITS : 16;
+  // FP8 for short vectors; FP4 (half the operand bytes, so more of the operands stay in L2)
+  // once the operand rows are long.
+  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? (n <= 256 ? KTAU_SIGNGEMM_DEFAULT_BITS : 4) : 16;
 }
 
 
@@ -1832,19 +1761,18 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
   R->esize = obits == 16 ? 2 : 1;
   R->sgn_bytes = (size_t)R->m * R->K_pad * obits / 8;
   if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
-  const size_t smem = (size_t)EXPAND_ROWS * n * sizeof(uint16_t);
+  const size_t smem = (size_t)EXPAND_ROWS * xrow<16>((int)n) * sizeof(uint16_t);  // largest pad
   const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
   {
     KTAU_TRACE("sign_expand_kernel", st);
-    if (R->obits == 4)
-      sign_expand4_kernel<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                      (int)R->K_pad, (uint8_t*)R->sgn);
-    else if (R->esize == 1)
-      sign_expand_kernel<1><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                        (int)R->K_pad, (uint8_t*)R->sgn);
-    else
-      sign_expand_kernel<2><<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
-                                                        (int)R->K_pad, (uint8_t*)R->sgn);
+    const bool pad = n > 256;
+    auto kern = R->obits == 4
+                    ? (pad ? sign_expand_kernel<4, true> : sign_expand_kernel<4, false>)
+                    : (R->obits == 8
+                           ? (pad ? sign_expand_kernel<8, true> : sign_expand_kernel<8, false>)
+                           : (pad ? sign_expand_kernel<16, true> : sign_expand_kernel<16, false>));
+    kern<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K, (int)R->K_pad,
+                                     (uint8_t*)R->sgn);
   }
   KTAU_CUDA(cudaGetLastError());
   ktau_status s = make_tmap(R);
@@ -2016,21 +1944,26 @@ ktau_status ktau_signgemm_check_error(cudaStream_t st) {
   return KTAU_OK;
 }
 
-ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows) {
-  return make_tmap_raw(tmap, base, row_bytes, rows);
+ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows,
+                                    int obits) {
+  return make_tmap_raw(tmap, base, row_bytes, rows, obits == 4);
 }
 
 ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   if (g.nb == 0 || g.rows == 0) return KTAU_OK;
-  const size_t smem_r = (size_t)g.max_n * sizeof(uint16_t);
+  const size_t smem_r = (size_t)EXPAND_ROWS * xrow<16>((int)g.max_n) * sizeof(uint16_t);
   {
     KTAU_TRACE("batch_sign_expand_kernel", st);
-    if (g.esize == 1)
-      batch_sign_expand_kernel<1><<<(unsigned)g.rows, 256, smem_r, st>>>(
-          g.ds, g.bids, g.nb, g.row_prefix, g.stride, (uint8_t*)g.sgn);
-    else
-      batch_sign_expand_kernel<2><<<(unsigned)g.rows, 256, smem_r, st>>>(
-          g.ds, g.bids, g.nb, g.row_prefix, g.stride, (uint8_t*)g.sgn);
+    const bool pad = g.max_n > 256;
+    auto kern =
+        g.obits == 4
+            ? (pad ? batch_sign_expand_kernel<4, true> : batch_sign_expand_kernel<4, false>)
+            : (g.obits == 8
+                   ? (pad ? batch_sign_expand_kernel<8, true> : batch_sign_expand_kernel<8, false>)
+                   : (pad ? batch_sign_expand_kernel<16, true>
+                          : batch_sign_expand_kernel<16, false>));
+    kern<<<(unsigned)g.blocks, 256, smem_r, st>>>(g.ds, g.bids, g.nb, g.blk_prefix, g.stride,
+                                                   (uint8_t*)g.sgn);
   }
   KTAU_CUDA(cudaGetLastError());
   {
@@ -2054,6 +1987,7 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   a.unit_hi = g.units;
   a.tri = 1;
   a.bnr = BN;
+  a.afmt = g.obits == 4 ? 5 : 0;
   ktau_status s = g.esize == 1 ? launch_contract2_map<1>(g.tmap, a, g.units, st)
                                : launch_contract2_map<2>(g.tmap, a, g.units, st);
   if (s != KTAU_OK) return s;

@@ -14,12 +14,12 @@
 
 #define KTAU_SIGNGEMM_MAX_N 2048
 #define KTAU_SIGNGEMM_FP8_MAX_N 2048
+// Variables per CTA of the sign-expansion kernels.
+#define KTAU_EXPAND_ROWS 8
 // Operand bits used when the caller does not choose (operand_bits = 0).
 #define KTAU_SIGNGEMM_DEFAULT_BITS 8
 
 bool ktau_signgemm_supported(int64_t n);
-// Operand element size for n and the options (1 = FP8 e4m3, 2 = BF16).
-int ktau_sign_esize(int64_t n, const ktau_options* opt);
 // Operand bits of the single-matrix and query contraction: 4 (FP4 e2m1), 8 or 16.
 int ktau_sign_obits(int64_t n, const ktau_options* opt);
 // Builds (once per element size) the sign expansion, the tie-pair lists and the TMA descriptor.
@@ -37,8 +37,11 @@ struct ktau_sg_group {
   const ktau_bds* ds;
   const int32_t* bids;
   int nb;
-  int esize;
+  int esize;                   // operand bytes per element in shared memory (1, or 2 for BF16)
+  int obits;                   // operand bits in global memory: 4, 8 or 16
   const int64_t* row_prefix;   // [nb + 1] over the group's rows
+  const int64_t* blk_prefix;   // [nb + 1] blocks of EXPAND_ROWS rows per dataset
+  int64_t blocks;
   const int64_t* unit_prefix;  // [nb + 1] contraction units
   const int64_t* jt_prefix;    // [nb + 1] joint-ties tiles
   int64_t rows, units, jt_tiles, max_n;
@@ -50,7 +53,8 @@ struct ktau_sg_group {
   int64_t stride;
   const void* tmap;            // CUtensorMap of sgn (host memory, 128 bytes)
 };
-ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows);
+ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows,
+                                    int obits);
 ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st);
 // Device error word of the contraction kernels (bounded waits that gave up); 0 = none.
 ktau_status ktau_signgemm_check_error(cudaStream_t st);

@@ -22,7 +22,7 @@ def ktau():
     return k
 
 
-def _make(ktau, mats, count_bits=64, paths=None):
+def _make(ktau, mats, count_bits=64, paths=None, options=None):
     descs, outs, keep = [], [], []
     for i, X in enumerate(mats):
         Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
@@ -37,7 +37,7 @@ def _make(ktau, mats, count_bits=64, paths=None):
                                      0 if paths is None else paths[i]))
         outs.append(o)
         keep.append(Xd)
-    B = ktau.Batch(descs, keepalive=keep)
+    B = ktau.Batch(descs, options=options, keepalive=keep)
     return B, outs
 
 
@@ -45,14 +45,15 @@ def _np(o):
     return {k: v.cpu().numpy() for k, v in o.items()}
 
 
-@pytest.mark.parametrize("mode", ["auto", "merge", "signgemm"])
-def test_small_batch_matches_oracle(ktau, mode):
+@pytest.mark.parametrize("mode,bits", [("auto", 0), ("merge", 0), ("signgemm", 0),
+                                       ("signgemm", 4), ("signgemm", 16)])
+def test_small_batch_matches_oracle(ktau, mode, bits):
     mats = batched_uneven(count=24, m_range=(16, 150), n_range=(20, 300), seed0=100)
     mats[3][5] = 1.0  # a constant variable
     if mode != "signgemm":  # the contraction path is limited to n <= 1024
         mats.append(uniform_ties(40, 2100, tie_frac=0.1, seed=5))  # long vectors: merge path
     paths = None if mode == "auto" else [1 if mode == "merge" else 2] * len(mats)
-    B, outs = _make(ktau, mats, 64, paths)
+    B, outs = _make(ktau, mats, 64, paths, {"operand_bits": bits} if bits else None)
     nm, ns = B.paths()
     if mode == "merge":
         assert ns == 0
