@@ -45,6 +45,14 @@ __device__ __forceinline__ unsigned long long team_sum(unsigned long long v,
   return t;
 }
 
+// Team buffers hold element i at word pd(i) = i + i / 32 when lanes own runs of 8 or more
+// (lane l at l * ITEMS): unpadded, the accesses of one instruction would hit every
+// (32 / ITEMS)-th bank; one pad word per 32 spreads them over all banks. Shorter runs are left
+// unpadded (there the index arithmetic costs more than the conflicts). Buffers are sized for
+// the padded form: i + i / 32 + 1 words for n elements.
+template <int ITEMS>
+__device__ __forceinline__ int pd(int i) { return ITEMS >= 8 ? i + (i >> 5) : i; }
+
 // Merge sort of buf[0, n) (ascending) with tmp as the second buffer. With COUNT, each thread
 // accumulates into `cnt` its share of the inversions (pairs i < j with buf[i] > buf[j]).
 // Returns the buffer that holds the sorted sequence. Every thread of the team must call it.
@@ -58,7 +66,7 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
     const int s0 = base + lane * ITEMS;
     uint32_t r[ITEMS];
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) r[i] = (s0 + i < n) ? buf[s0 + i] : kSentinel;
+    for (int i = 0; i < ITEMS; ++i) r[i] = (s0 + i < n) ? buf[pd<ITEMS>(s0 + i)] : kSentinel;
     if (COUNT) {
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i)
@@ -76,7 +84,7 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
-      if (s0 + i < n) buf[s0 + i] = r[i];
+      if (s0 + i < n) buf[pd<ITEMS>(s0 + i)] = r[i];
   }
   team_sync<TEAM>();
   uint32_t* in = buf;
@@ -95,28 +103,28 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
         int lo = max(0, diag - b_len), hi = min(diag, a_len);
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
-          if (in[A + mid] <= in[B + diag - 1 - mid])
+          if (in[pd<ITEMS>(A + mid)] <= in[pd<ITEMS>(B + diag - 1 - mid)])
             lo = mid + 1;
           else
             hi = mid;
         }
         int ai = lo, bi = diag - lo;
         const int todo = min(ITEMS, a_len + b_len - diag);
-        uint32_t va = ai < a_len ? in[A + ai] : kSentinel;
-        uint32_t vb = bi < b_len ? in[B + bi] : kSentinel;
+        uint32_t va = ai < a_len ? in[pd<ITEMS>(A + ai)] : kSentinel;
+        uint32_t vb = bi < b_len ? in[pd<ITEMS>(B + bi)] : kSentinel;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
           if (i < todo) {
             const bool take_b = (ai >= a_len) || (bi < b_len && vb < va);
             if (take_b) {
-              out[o + i] = vb;
+              out[pd<ITEMS>(o + i)] = vb;
               if (COUNT) c += (unsigned)(a_len - ai);  // remaining left elements are larger
               ++bi;
-              vb = bi < b_len ? in[B + bi] : kSentinel;
+              vb = bi < b_len ? in[pd<ITEMS>(B + bi)] : kSentinel;
             } else {
-              out[o + i] = va;
+              out[pd<ITEMS>(o + i)] = va;
               ++ai;
-              va = ai < a_len ? in[A + ai] : kSentinel;
+              va = ai < a_len ? in[pd<ITEMS>(A + ai)] : kSentinel;
             }
           }
         }
@@ -166,7 +174,7 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
                                            long long& n3_out) {
   for (int k = lane; k < n; k += TEAM) {
     const uint32_t w = rank_v[perm_u[k]];
-    buf[k] = u_ties ? (((uint32_t)srank_u[k] << 16) | w) : w;
+    buf[pd<ITEMS>(k)] = u_ties ? (((uint32_t)srank_u[k] << 16) | w) : w;
   }
   team_sync<TEAM>();
   unsigned long long nd = 0, n3 = 0;
@@ -177,19 +185,19 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
     // Step 2: joint ties. In the sorted keys, position k has (k - first index of its key)
     // earlier equal keys.
     for (int k = lane; k < n; k += TEAM) {
-      const uint32_t key = sorted[k];
-      if (k > 0 && sorted[k - 1] == key) {
+      const uint32_t key = sorted[pd<ITEMS>(k)];
+      if (k > 0 && sorted[pd<ITEMS>(k - 1)] == key) {
         int lo = 0, hi = k;
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
-          if (sorted[mid] < key)
+          if (sorted[pd<ITEMS>(mid)] < key)
             lo = mid + 1;
           else
             hi = mid;
         }
         n3 += (unsigned long long)(k - lo);
       }
-      other[k] = key & 0xffffu;
+      other[pd<ITEMS>(k)] = key & 0xffffu;
     }
     team_sync<TEAM>();
     team_merge_sort<TEAM, ITEMS, true>(other, sorted, n, lane, nd);
@@ -385,7 +393,7 @@ ktau_status ktau_launch_batch_merge(const ktau_bds* ds, const int32_t* ids, int 
                                     const int64_t* tile_prefix, int64_t total_tiles, int64_t max_n,
                                     int cta_team, cudaStream_t st) {
   if (nids == 0 || total_tiles == 0) return KTAU_OK;
-  const int cap = (int)((max_n + 3) & ~3LL);
+  const int cap = (int)((max_n + (max_n >> 5) + 1 + 3) & ~3LL);  // pd<ITEMS>(n) + 1, rounded
   const size_t team_bytes = (size_t)2 * cap * sizeof(uint32_t);
   int teams = cta_team ? 1 : (int)std::min<size_t>(8, (200 * 1024) / team_bytes);
   if (teams < 1) return ktau_fail(KTAU_ETOOLARGE, "n=%lld too long for the batched merge path",
@@ -471,7 +479,7 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
 
   const bool cta_team = plan.mapping == 2;
   const int items = cta_team ? 8 : (n <= 256 ? (int)((n + 31) / 32) : 8);
-  a.cap = (int)((n + 3) & ~3LL);
+  a.cap = (int)((n + (n >> 5) + 1 + 3) & ~3LL);  // pd<ITEMS>(n) + 1, rounded
   const size_t team_bytes = (size_t)2 * a.cap * sizeof(uint32_t);
   // Stage the tile's rows in shared memory when they are small next to the per-pair work.
   const size_t stage_bytes = (size_t)3 * tq * R->ld * sizeof(uint16_t);
