@@ -58,9 +58,20 @@ extern "C" ktau_status ktau_debug_fail_alloc(int32_t k) {
   return KTAU_OK;
 }
 
+// Blocks are cached by size class: requests are rounded up to the next of 2^k, 1.25 * 2^k,
+// 1.5 * 2^k, 1.75 * 2^k (at most 25% slack), so work of varying size (query batches, batched
+// datasets) reuses a bounded set of blocks instead of one per distinct size.
+static size_t size_class(size_t bytes) {
+  if (bytes <= 4096) return 4096;
+  int k = 63 - __builtin_clzll((unsigned long long)(bytes - 1));  // 2^k < bytes <= 2^(k+1)
+  const size_t base = (size_t)1 << k, step = base >> 2;
+  return base + ((bytes - base + step - 1) / step) * step;
+}
+
 ktau_status ktau_dmalloc(void** p, size_t bytes) {
   int dev = 0;
   cudaGetDevice(&dev);
+  bytes = size_class(bytes);
   // injected failure (tests of the error paths)
   int left = g_fail_alloc_after.load();
   while (left >= 0) {
@@ -108,7 +119,7 @@ void ktau_dfree(void* p, size_t bytes) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_alloc_mu);
-  g_free_blocks->push_back(FreeBlock{dev, bytes, p});
+  g_free_blocks->push_back(FreeBlock{dev, size_class(bytes), p});
 }
 
 extern "C" {

@@ -79,7 +79,7 @@ class Admission:
 class QueryServer:
     def __init__(self, db: np.ndarray | torch.Tensor, k: int = 100, slots: int = 4,
                  mem_budget: int | None = None, keep_tau: bool = False, options=None,
-                 device: int = 0):
+                 device: int = 0, max_batch: int = 512):
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         dbt = torch.as_tensor(db).to(self.dev, dtype=torch.float32).contiguous()
@@ -97,6 +97,19 @@ class QueryServer:
             mem_budget = int(free * 0.6)
         self.admission = Admission(mem_budget, slots)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        # Per-slot buffers for batches of up to max_batch profiles, allocated once: the request
+        # path then allocates nothing but the batch's ranked handle (from the library's cache).
+        self.max_batch = max_batch
+        self.slot_buf = []
+        for _ in range(slots):
+            self.slot_buf.append({
+                "qh": torch.empty((max_batch, self.n), dtype=torch.float32).pin_memory(),
+                "qd": torch.empty((max_batch, self.n), dtype=torch.float32, device=self.dev),
+                "S": torch.empty((max_batch, self.m_db), dtype=torch.int32, device=self.dev),
+                "idx": torch.empty((max_batch, self.k), dtype=torch.int32, device=self.dev),
+                "tk": torch.empty((max_batch, self.k), dtype=torch.float64, device=self.dev),
+                "idx_h": torch.empty((max_batch, self.k), dtype=torch.int32).pin_memory(),
+                "tk_h": torch.empty((max_batch, self.k), dtype=torch.float64).pin_memory()})
         self.cv = threading.Condition()
         self.pending = collections.deque()
         self.slot_q = [collections.deque() for _ in range(slots)]
@@ -180,7 +193,7 @@ class QueryServer:
                     return
                 r = self.slot_q[i].popleft()
             try:
-                self._run(r, st)
+                self._run(r, st, i)
             except Exception as e:  # reported on the request; the server keeps running
                 r.error = repr(e)
             r.finished = time.perf_counter()
@@ -190,22 +203,33 @@ class QueryServer:
                 self.cv.notify_all()
             r.done.set()
 
-    def _run(self, r: Request, st: torch.cuda.Stream):
+    def _run(self, r: Request, st: torch.cuda.Stream, slot: int):
         b = r.queries.shape[0]
         with torch.cuda.stream(st):
-            qd = torch.from_numpy(r.queries).pin_memory().to(self.dev, non_blocking=True)
+            if b <= self.max_batch:
+                buf = self.slot_buf[slot]
+                buf["qh"][:b].numpy()[...] = r.queries
+                qd = buf["qd"][:b]
+                qd.copy_(buf["qh"][:b], non_blocking=True)
+                S, idx, tk = buf["S"][:b], buf["idx"][:b], buf["tk"][:b]
+                idx_h, tk_h = buf["idx_h"][:b], buf["tk_h"][:b]
+            else:  # larger than the slot buffers: buffers of its own
+                qd = torch.from_numpy(r.queries).pin_memory().to(self.dev, non_blocking=True)
+                S = torch.empty((b, self.m_db), dtype=torch.int32, device=self.dev)
+                idx = torch.empty((b, self.k), dtype=torch.int32, device=self.dev)
+                tk = torch.empty((b, self.k), dtype=torch.float64, device=self.dev)
+                idx_h = torch.empty((b, self.k), dtype=torch.int32).pin_memory()
+                tk_h = torch.empty((b, self.k), dtype=torch.float64).pin_memory()
             R = kb.ktau_rank_prepare(qd, st)
-            S = torch.empty((b, self.m_db), dtype=torch.int32, device=self.dev)
             tau = torch.empty((b, self.m_db), dtype=torch.float64, device=self.dev) \
                 if self.keep_tau else None
-            idx = torch.empty((b, self.k), dtype=torch.int32, device=self.dev)
-            tk = torch.empty((b, self.k), dtype=torch.float64, device=self.dev)
             kb.ktau_query(self.db, R, tau, S, None, 32, self.k, idx, tk, self.options, st)
-            idx_h = idx.to("cpu", non_blocking=True)
-            tk_h = tk.to("cpu", non_blocking=True)
+            idx_h.copy_(idx, non_blocking=True)
+            tk_h.copy_(tk, non_blocking=True)
             R.free_on(st)  # waits for this slot's stream only
-        r.topk_idx = idx_h.numpy()
-        r.topk_tau = tk_h.numpy()
+        # copies: the slot's pinned buffers are reused by its next batch
+        r.topk_idx = idx_h.numpy().copy()
+        r.topk_tau = tk_h.numpy().copy()
         r.tau = tau
 
     def stop(self):
