@@ -11,6 +11,8 @@ arXiv 1704.03767:
   form of Algorithm 1 extended with the tie counts n_1, n_2, n_3.
 * ``pair_counts(u, v, method="knight")`` -- Sec. 3.2 Steps 1-5 with Algorithm 2.
 * ``tau_b`` -- Eq. 3.
+* ``tau_a`` / ``tau_a32`` / ``rn32`` -- tau-a of Sec. 2 ((n_c - n_d) / n_0) in FP64, and a
+  quotient of integers rounded exactly to FP32 (round to nearest, ties to even).
 * ``job_id`` / ``job_coord`` / ``job_coord_formula`` -- Eq. 4-10 (diagonal included).
 * ``rank`` -- the per-variable rank transform of Sec. 3.
 * ``allpairs`` -- Sec. 4.2-4.3 tiled walk of the upper triangle, static thread ranges.
@@ -30,6 +32,9 @@ from .oracle import (  # noqa: F401
     query_topk,
     rank,
     rect,
+    rn32,
+    tau_a,
+    tau_a32,
     tau_b,
     topk_order,
 )

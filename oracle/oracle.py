@@ -104,6 +104,45 @@ def tau_b(S: int, n1: int, n2: int, n: int) -> float:
     return float(_load().ko_tau_b(int(S), int(n1), int(n2), int(n)))
 
 
+def tau_a(S: int, n: int) -> float:
+    """Kendall's tau-a (Sec. 2: (n_c - n_d) / n_0, no tie correction) in FP64: the IEEE quotient
+    of the two integers (Python's int / int is correctly rounded)."""
+    n0 = n * (n - 1) // 2
+    return int(S) / n0
+
+
+def rn32(num: int, den: int) -> np.float32:
+    """num / den rounded to the nearest FP32 value, ties to even, computed exactly with integers
+    (normal range only)."""
+    num, den = int(num), int(den)
+    if den <= 0:
+        raise ValueError("den must be positive")
+    if num == 0:
+        return np.float32(0.0)
+    sign = -1 if num < 0 else 1
+    x = Fraction(abs(num), den)
+    e = abs(num).bit_length() - den.bit_length()  # 2^(e-1) < x < 2^(e+1)
+    while x < Fraction(2) ** e:
+        e -= 1
+    while x >= Fraction(2) ** (e + 1):
+        e += 1
+    if not -126 <= e <= 127:
+        raise ValueError("outside the normal FP32 range")
+    mant = x / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    q = mant.numerator // mant.denominator
+    r = mant - q
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    if q == 1 << 24:
+        q, e = 1 << 23, e + 1
+    return np.float32(sign * float(Fraction(q) * Fraction(2) ** (e - 23)))
+
+
+def tau_a32(S: int, n: int) -> np.float32:
+    """FP32 tau-a: S / n_0 correctly rounded to FP32."""
+    return rn32(int(S), n * (n - 1) // 2)
+
+
 def job_id(m: int, y: int, x: int) -> int:
     return int(_load().ko_job_id(m, y, x))
 

@@ -176,3 +176,56 @@ def test_topk_order(oracle_mod):
     # |tau|^2 * Du = S^2/Dv: 0.9, 0.9, 0, nan, 1.0, 1.0
     assert oracle_mod.topk_order(S, 7, Dv, 6) == [4, 5, 0, 1, 2, 3]
     assert oracle_mod.topk_order(S, 0, Dv, 3) == [0, 1, 2]
+
+
+# ---------------------------------------------------------------------------------------------
+# tau-a (Sec. 2: (n_c - n_d) / n_0) and the exact FP32 rounding of a quotient
+# ---------------------------------------------------------------------------------------------
+def test_rn32_matches_ieee_float32_division(oracle_mod):
+    """Where both operands are exact in FP32, IEEE single division (numpy) is correctly rounded,
+    so it must agree with the exact rounding bit for bit."""
+    g = np.random.default_rng(7)
+    nums = g.integers(-(1 << 24) + 1, 1 << 24, 20000)
+    dens = g.integers(1, 1 << 24, 20000)
+    for a, b in zip(nums, dens):
+        ref = np.float32(a) / np.float32(b)
+        got = oracle_mod.rn32(int(a), int(b))
+        assert got.view(np.uint32) == ref.view(np.uint32), (a, b)
+
+
+def test_rn32_ties_and_nearest_property(oracle_mod):
+    from fractions import Fraction
+
+    # exact midpoints: ties to the even significand
+    assert oracle_mod.rn32((1 << 24) + 1, 1 << 25) == np.float32(0.5)
+    assert oracle_mod.rn32((1 << 24) + 3, 1 << 25) == np.float32(0.5 + 2.0 ** -23)
+    assert oracle_mod.rn32(-((1 << 24) + 1), 1 << 25) == np.float32(-0.5)
+    # nearest-value property in exact arithmetic, with denominators beyond FP32's exact range
+    g = np.random.default_rng(8)
+    for _ in range(3000):
+        den = int(g.integers(1 << 24, 1 << 30))
+        num = int(g.integers(-den, den + 1))
+        if num == 0:
+            continue
+        f = oracle_mod.rn32(num, den)
+        x = Fraction(num, den)
+        fx = Fraction(float(f))
+        for nb in (np.nextafter(f, np.float32(np.inf)), np.nextafter(f, np.float32(-np.inf))):
+            d_nb, d_f = abs(x - Fraction(float(nb))), abs(x - fx)
+            assert d_f < d_nb or (d_f == d_nb and (f.view(np.uint32) & 1) == 0)
+
+
+def test_tau_a_definition(oracle_mod):
+    """tau-a against the definition on tiny inputs, and tau-a = tau-b without ties."""
+    g = np.random.default_rng(9)
+    for _ in range(200):
+        n = int(g.integers(2, 9))
+        u, v = g.integers(0, 4, n), g.integers(0, 4, n)
+        nc = sum(1 for a in range(n) for b in range(a + 1, n) if (u[a] - u[b]) * (v[a] - v[b]) > 0)
+        nd = sum(1 for a in range(n) for b in range(a + 1, n) if (u[a] - u[b]) * (v[a] - v[b]) < 0)
+        c = oracle_mod.pair_counts(u.astype(float), v.astype(float))
+        assert oracle_mod.tau_a(c["S"], n) == (nc - nd) / (n * (n - 1) / 2)
+    u = g.permutation(30).astype(float)
+    v = g.permutation(30).astype(float)
+    c = oracle_mod.pair_counts(u, v)
+    assert abs(oracle_mod.tau_a(c["S"], 30) - oracle_mod.tau_b(c["S"], 0, 0, 30)) < 1e-15
