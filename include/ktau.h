@@ -76,7 +76,11 @@ typedef struct {
   int32_t operand_bits; /* contraction operands: 4 = FP4 e2m1, 8 = FP8 e4m3, 16 = BF16, all
                            exact for n <= 2048; 0 = FP8 for n <= 256, FP4 above (half the
                            operand bytes) */
-  int32_t reserved[2];
+  int32_t statistic;    /* 0 = tau-b (Eq. 3, default); 1 = tau-a = (n_c - n_d) / n_0 (Sec. 2, no
+                           tie correction): tau64 = S / n_0 in IEEE FP64, tau32 = S / n_0
+                           correctly rounded to FP32. ktau_allpairs, ktau_allpairs_path and
+                           ktau_allpairs_host only; ktau_query and ktau_batch_create reject it */
+  int32_t reserved[1];
 } ktau_options;
 
 /* Opaque, library-owned, device-resident ranked matrix (Sec. 3: each variable ranked once):

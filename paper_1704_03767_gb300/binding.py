@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_q", ctypes.c_int32),
                 ("mapping", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("operand_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("statistic", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class TraceRecord(ctypes.Structure):

@@ -275,6 +275,8 @@ ktau_status ktau_check_options(const ktau_options* opt) {
   if (opt->operand_bits != 0 && opt->operand_bits != 4 && opt->operand_bits != 8 &&
       opt->operand_bits != 16)
     return ktau_fail(KTAU_EINVAL, "operand_bits must be 0, 4, 8 or 16");
+  if (opt->statistic != 0 && opt->statistic != 1)
+    return ktau_fail(KTAU_EINVAL, "statistic must be 0 (tau-b) or 1 (tau-a)");
   return KTAU_OK;
 }
 
@@ -305,7 +307,7 @@ extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uin
                      (unsigned long long)p_begin, (unsigned long long)p_end,
                      (unsigned long long)P);
   if (p_begin == p_end) return KTAU_OK;
-  ktau_out out{tau64, tau32, S, n3, count_bits};
+  ktau_out out{tau64, tau32, S, n3, count_bits, opt ? opt->statistic : 0};
   cudaStream_t st = (cudaStream_t)stream;
   const int path = ktau_choose_path(R, opt);
   if (path == KTAU_PATH_SIGNGEMM) {

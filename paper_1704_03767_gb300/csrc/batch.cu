@@ -107,6 +107,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
   if (!descs || count <= 0) return ktau_fail(KTAU_EINVAL, "need count > 0 descriptors");
   ktau_status s = ktau_check_options(opt);
   if (s != KTAU_OK) return s;
+  if (opt && opt->statistic != 0) return ktau_fail(KTAU_EINVAL, "the batched form computes tau-b");
   for (int i = 0; i < count; ++i) {
     const ktau_batch_desc& d = descs[i];
     if (!d.values) return ktau_fail(KTAU_EINVAL, "descriptor %d: values is NULL", i);

@@ -117,6 +117,7 @@ struct ktau_out {
   void* S;
   void* n3;
   int count_bits;
+  int stat;  // 0 = tau-b, 1 = tau-a
 };
 
 __device__ __forceinline__ double ktau_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -163,10 +164,34 @@ struct ktau_fac {
   const int64_t* T;
 };
 
+// tau-a = S / n_0 (no tie correction). FP64: the IEEE quotient of two exact integers. FP32: the
+// quotient correctly rounded to FP32. With S and n_0 below 2^24 that is one IEEE division; above,
+// the FP64 quotient q is rounded to FP32, which can mislead only when q lies exactly on the
+// midpoint m of two floats; then the sign of S - m * n_0 decides (m * n_0 is exact in FP64 for
+// n_0 < 2^28, i.e. n <= 16384).
+__device__ __forceinline__ double ktau_taua64(int64_t S, int64_t n0) {
+  return __ddiv_rn((double)S, (double)n0);
+}
+__device__ __forceinline__ float ktau_taua32(int64_t S, int64_t n0) {
+  if (n0 < (1ll << 24)) return __fdiv_rn((float)S, (float)n0);
+  const double q = __ddiv_rn((double)S, (double)n0);
+  const float f = __double2float_rn(q);
+  const double fd = (double)f;
+  if (fd == q) return f;
+  const float g = nextafterf(f, q > fd ? INFINITY : -INFINITY);
+  const double mid = 0.5 * (fd + (double)g);
+  if (q != mid) return f;
+  const double prod = mid * (double)n0;
+  if ((double)S == prod) return f;  // exact tie: already rounded to even
+  return (double)S > prod ? fmaxf(f, g) : fminf(f, g);
+}
+
 __device__ __forceinline__ void ktau_store(const ktau_out& o, uint64_t k, int64_t S, int64_t n3,
                                            int64_t n0, const ktau_fac& f, int64_t u, int64_t v) {
-  if (o.tau64) o.tau64[k] = ktau_tau64(S, f.rs64[u], f.rs64[v]);
-  if (o.tau32) o.tau32[k] = ktau_tau32(S, f.rsff[u], f.rsff[v], n0, f.T[u], f.T[v]);
+  if (o.tau64) o.tau64[k] = o.stat ? ktau_taua64(S, n0) : ktau_tau64(S, f.rs64[u], f.rs64[v]);
+  if (o.tau32)
+    o.tau32[k] = o.stat ? ktau_taua32(S, n0)
+                        : ktau_tau32(S, f.rsff[u], f.rsff[v], n0, f.T[u], f.T[v]);
   if (o.count_bits == 64) {
     if (o.S) ((long long*)o.S)[k] = S;
     if (o.n3) ((long long*)o.n3)[k] = n3;

@@ -285,9 +285,12 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
       count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, tbuf, tbuf2, lane, red, nd, n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
-        if (a.out.tau64) a.out.tau64[k] = ktau_tau64(S, a.fac.rs64[y], a.facc.rs64[x]);
+        if (a.out.tau64)
+          a.out.tau64[k] = a.out.stat ? ktau_taua64(S, n0)
+                                      : ktau_tau64(S, a.fac.rs64[y], a.facc.rs64[x]);
         if (a.out.tau32)
-          a.out.tau32[k] = ktau_tau32(S, a.fac.rsff[y], a.facc.rsff[x], n0, Tu, Tv);
+          a.out.tau32[k] = a.out.stat ? ktau_taua32(S, n0)
+                                      : ktau_tau32(S, a.fac.rsff[y], a.facc.rsff[x], n0, Tu, Tv);
         if (a.out.count_bits == 64) {
           if (a.out.S) ((long long*)a.out.S)[k] = S;
           if (a.out.n3) ((long long*)a.out.n3)[k] = n3;

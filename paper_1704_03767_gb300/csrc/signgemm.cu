@@ -443,13 +443,17 @@ struct RowsReg {
 // whose FP32 rounding is undecided by the float-float test are flagged in `slow`.
 template <bool WS, bool WN, class Rows>
 __device__ __forceinline__ void epi_rows32(const uint32_t (&r)[32], const Rows& rows, float2 c_rff,
-                                           float* o32, int* oS, int* oN, uint32_t& slow) {
+                                           float* o32, int* oS, int* oN, uint32_t& slow,
+                                           float n0f) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const RowInfo R = rows(j);
     const int S = __float2int_rn(__uint_as_float(r[j]));
     float tv;
-    if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv)) slow |= 1u << j;
+    if (n0f != 0.f)  // tau-a: S / n_0, one IEEE division of exact FP32 integers (n_0 < 2^24)
+      tv = __fdiv_rn((float)S, n0f);
+    else if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv))
+      slow |= 1u << j;
     __stcs(o32 + R.base, tv);
     if (WS) __stcs(oS + R.base, S);
     if (WN) __stcs(oN + R.base, 0);
@@ -1125,15 +1129,16 @@ __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit&
       int* const oS = P.out.S ? (int*)P.out.S + (v - (int64_t)P.p_begin) : nullptr;
       int* const oN = n3z ? (int*)n3z + (v - (int64_t)P.p_begin) : nullptr;
       uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
+      const float n0f = P.out.stat ? (float)n0 : 0.f;
 #define KTAU_EPI_ROWS(ROWS)                                                 \
   if (oS && oN)                                                             \
-    epi_rows32<true, true>(r, ROWS, c_rff, o32, oS, oN, slow);              \
+    epi_rows32<true, true>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);         \
   else if (oS)                                                              \
-    epi_rows32<true, false>(r, ROWS, c_rff, o32, oS, oN, slow);             \
+    epi_rows32<true, false>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);        \
   else if (oN)                                                              \
-    epi_rows32<false, true>(r, ROWS, c_rff, o32, oS, oN, slow);             \
+    epi_rows32<false, true>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);        \
   else                                                                      \
-    epi_rows32<false, false>(r, ROWS, c_rff, o32, oS, oN, slow);
+    epi_rows32<false, false>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);
       if (kSmemRows) {
         KTAU_EPI_ROWS(rs)
       } else {
@@ -1165,10 +1170,14 @@ __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit&
           k = (uint64_t)(R.base + v);
         }
         const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
-        if (want64) __stcs(P.out.tau64 + k, ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
+        if (want64)
+          __stcs(P.out.tau64 + k, P.out.stat ? ktau_taua64(S, n0)
+                                             : ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
         if (want32)
           __stcs(P.out.tau32 + k,
-                 ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y], P.col.T[v]));
+                 P.out.stat ? ktau_taua32(S, n0)
+                            : ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y],
+                                         P.col.T[v]));
         if (wantS) {
           if (s64)
             __stcs((long long*)P.out.S + k, (long long)S);
