@@ -17,6 +17,8 @@ arXiv 1704.03767:
 * ``rank`` -- the per-variable rank transform of Sec. 3.
 * ``allpairs`` -- Sec. 4.2-4.3 tiled walk of the upper triangle, static thread ranges.
 * ``rect`` / ``query_topk`` -- query search of Sec. 1 with exact ordering by |tau|.
+* ``permutation_exceed`` -- permutation test of every pair: exceedances |S(x_i, x_j o sigma)| >=
+  |S(x_i, x_j)| over caller-drawn permutations sigma.
 
 Parity pins for every function are in ``tests/test_oracle_pins.py`` and
 ``tests/test_bijection.py``; no function is "parity unpinned".
@@ -29,6 +31,7 @@ from .oracle import (  # noqa: F401
     job_id,
     lib_path,
     pair_counts,
+    permutation_exceed,
     query_topk,
     rank,
     rect,

@@ -195,6 +195,27 @@ def allpairs(X, method: str = "knight", q: int = 8, threads: int = 1, p_begin: i
     return out
 
 
+def permutation_exceed(X, perms, p_begin: int = 0, p_end: int | None = None) -> np.ndarray:
+    """Permutation test of independence for every pair i < j (Sec. 2: tau measures association;
+    its significance under random relabelling of one variable). For each permutation sigma (a row
+    of `perms`) the samples of the second variable are reordered, x_j -> x_j[sigma], and the pair
+    counts one exceedance when |S(x_i, x_j[sigma])| >= |S(x_i, x_j)|. Counting is Knight's method
+    through rect(); returns the exceedance counts of the packed pairs in [p_begin, p_end)."""
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    P = m * (m - 1) // 2
+    if p_end is None:
+        p_end = P
+    S_obs = allpairs(X, method="knight", p_begin=p_begin, p_end=p_end)["S"]
+    iu, ju = np.triu_indices(m, 1)  # packed order: row-major strict upper triangle
+    iu, ju = iu[p_begin:p_end], ju[p_begin:p_end]
+    exceed = np.zeros(p_end - p_begin, np.int64)
+    for sigma in np.asarray(perms):
+        S_perm = rect(X, X[:, sigma.astype(np.int64)])["S"]  # [i][j]: x_i vs x_j[sigma]
+        exceed += np.abs(S_perm[iu, ju]) >= np.abs(S_obs)
+    return exceed
+
+
 def rect(Q, D) -> dict:
     """Every row of Q against every row of D (Knight counting); arrays of shape [b, mdb]."""
     QQ, DD = _as_f64(Q), _as_f64(D)

@@ -131,3 +131,10 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int = 3) -> np.ndarray
     """Arrival times (s) of a Poisson stream with the given rate."""
     g = _rng(seed)
     return np.cumsum(g.exponential(1.0 / rate_per_s, size=count))
+
+
+def permutations(count: int, n: int, seed: int = 11) -> np.ndarray:
+    """`count` uniformly random permutations of range(n) (PCG64, seeded), uint16 [count, n]: the
+    sample relabellings a permutation test draws, generated here and passed to both sides."""
+    g = _rng(seed)
+    return np.stack([g.permutation(n) for _ in range(count)]).astype(np.uint16)

@@ -229,3 +229,45 @@ def test_tau_a_definition(oracle_mod):
     v = g.permutation(30).astype(float)
     c = oracle_mod.pair_counts(u, v)
     assert abs(oracle_mod.tau_a(c["S"], 30) - oracle_mod.tau_b(c["S"], 0, 0, 30)) < 1e-15
+
+
+# ---------------------------------------------------------------------------------------------
+# Permutation test of every pair
+# ---------------------------------------------------------------------------------------------
+def _mahonian(n):
+    """Number of permutations of n items with k inversions, k = 0..n(n-1)/2 (standard recurrence)."""
+    row = [1]
+    for i in range(2, n + 1):
+        new = [0] * (len(row) + i - 1)
+        for k, c in enumerate(row):
+            for j in range(i):
+                new[k + j] += c
+        row = new
+    return row
+
+
+def test_permutation_exceed_exact_null(oracle_mod):
+    """Over all n! relabellings of a tie-free variable, S = n_0 - 2 * (inversions), so the number
+    of permutations with |S_sigma| >= |S_obs| follows from the Mahonian distribution."""
+    n = 6
+    n0 = n * (n - 1) // 2
+    perms = np.array(list(itertools.permutations(range(n))), dtype=np.uint16)
+    mah = _mahonian(n)
+    g = np.random.default_rng(12)
+    X = np.stack([g.permutation(n) for _ in range(4)]).astype(np.float64)
+    exc = oracle_mod.permutation_exceed(X, perms)
+    S_obs = oracle_mod.allpairs(X)["S"]
+    for s_obs, e in zip(S_obs, exc):
+        expect = sum(c for k, c in enumerate(mah) if abs(n0 - 2 * k) >= abs(s_obs))
+        assert e == expect
+
+
+def test_permutation_exceed_identity_and_ranges(oracle_mod):
+    g = np.random.default_rng(13)
+    X = np.round(g.random((9, 15)), 1)
+    ident = np.tile(np.arange(15, dtype=np.uint16), (3, 1))
+    assert np.all(oracle_mod.permutation_exceed(X, ident) == 3)
+    perms = np.stack([g.permutation(15) for _ in range(5)]).astype(np.uint16)
+    full = oracle_mod.permutation_exceed(X, perms)
+    assert np.array_equal(oracle_mod.permutation_exceed(X, perms, 7, 30), full[7:30])
+    assert np.all((full >= 0) & (full <= 5))
