@@ -203,6 +203,23 @@ ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
  * its boundary without exact keys (n > 300; that query's top-k order is not exact). */
 ktau_status ktau_device_status(void* stream);
 
+/* Permutation test of every pair (Sec. 2: the significance of tau under random relabelling of one
+ * variable's samples). For each of the B permutations sigma_b (perms: device uint16 [B][n], row b
+ * a permutation of 0..n-1 drawn by the caller) and each pair (u, v), u < v, with packed index p
+ * in [p_begin, p_end), adds 1 to exceed[p - p_begin] when |S(u, v o sigma_b)| >= |S(u, v)|, where
+ * S(u, v o sigma) = n_c - n_d between u and v with v's samples reordered by sigma. T_u and T_v do
+ * not change under the relabelling, so this is |tau_b| (and |tau_a|) exceedance exactly. The
+ * two-sided permutation p-value of pair p is (exceed + 1) / (B + 1).
+ *   S_obs  : int32 device array, the observed S of the same range (ktau_allpairs, count_bits 32)
+ *   exceed : uint32 device array of p_end - p_begin counts, accumulated (the caller zeroes it)
+ * Runs on the sign contraction (EINVAL when n > 2048): per permutation one relabelled copy of
+ * the ranks, its sign expansion and one pass of the pair contraction. Entries of perms outside
+ * 0..n-1 give meaningless counts but no out-of-range access. Allocates scratch of one rank and one
+ * operand matrix and returns after the work has finished on `stream`. */
+ktau_status ktau_permutation_exceed(const ktau_ranked* R, const uint16_t* perms, int32_t B,
+                                    uint64_t p_begin, uint64_t p_end, const int32_t* S_obs,
+                                    uint32_t* exceed, void* stream);
+
 /* Failure injection for tests of error handling (no GPU fault involved):
  * ktau_debug_fail_alloc(k): the next k library allocations succeed, every later one fails as if
  * the device were out of memory (KTAU_ENOMEM); k < 0 switches the injection off.

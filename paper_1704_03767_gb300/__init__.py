@@ -24,6 +24,8 @@ from .binding import (  # noqa: F401
     ktau_allpairs_noalloc,
     ktau_allpairs_path,
     ktau_debug_fail_alloc,
+    ktau_permutation_exceed,
+    permutation_pvalues,
     ktau_debug_wait_timeout,
     ktau_device_status,
     ktau_prepare_signs,

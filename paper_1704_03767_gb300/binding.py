@@ -72,6 +72,7 @@ _SIGS = {
     "ktau_allpairs_path": ([_vp, ctypes.POINTER(Options), ctypes.POINTER(_i32)], ctypes.c_int),
     "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
     "ktau_device_status": ([_vp], ctypes.c_int),
+    "ktau_permutation_exceed": ([_vp, _vp, _i32, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
     "ktau_debug_fail_alloc": ([_i32], ctypes.c_int),
     "ktau_debug_wait_timeout": ([_i64, _vp], ctypes.c_int),
     "ktau_trace_enable": ([_i32], ctypes.c_int),
@@ -255,6 +256,35 @@ def ktau_prepare_signs(R: Ranked, stream=None):
 
 def ktau_device_status(stream=None):
     _check(load().ktau_device_status(_stream(stream)))
+
+
+def ktau_permutation_exceed(R: Ranked, perms: torch.Tensor, S_obs: torch.Tensor,
+                            exceed: torch.Tensor, p_begin: int = 0, p_end: int | None = None,
+                            stream=None):
+    """Adds, per pair of [p_begin, p_end), the number of permutations (rows of `perms`, uint16
+    [B, n] on the device) under which |S| of the relabelled pair reaches the observed |S|."""
+    if p_end is None:
+        p_end = R.pairs
+    if perms.dtype != torch.uint16 or perms.dim() != 2 or perms.shape[1] != R.n:
+        raise ValueError("perms must be a uint16 [B, n] tensor")
+    if S_obs.dtype != torch.int32 or exceed.dtype != torch.uint32:
+        raise ValueError("S_obs must be int32 and exceed uint32")
+    _check(load().ktau_permutation_exceed(R.handle, perms.data_ptr(), perms.shape[0], p_begin,
+                                          p_end, S_obs.data_ptr(), exceed.data_ptr(),
+                                          _stream(stream)))
+
+
+def permutation_pvalues(values: torch.Tensor, perms: torch.Tensor, stream=None):
+    """Two-sided permutation p-values (exceed + 1) / (B + 1) of every pair (FP64, packed triangle),
+    with the observed tau-b and S."""
+    res = allpairs(values, want=("tau64", "S"), stream=stream)
+    R = res["ranked"]
+    exceed = torch.zeros(R.pairs, dtype=torch.uint32, device=values.device)
+    ktau_permutation_exceed(R, perms.to(values.device), res["S"], exceed, stream=stream)
+    B = perms.shape[0]
+    res["exceed"] = exceed
+    res["pvalue"] = (exceed.to(torch.float64) + 1.0) / (B + 1.0)
+    return res
 
 
 def ktau_debug_fail_alloc(k: int):

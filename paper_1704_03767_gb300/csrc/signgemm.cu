@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -198,6 +199,21 @@ __global__ void __launch_bounds__(256) batch_sign_expand_kernel(
   const int K = n * (n - 1) / 2;
   const int K_pad = (K + 127) / 128 * 128;
   expand_block<OB, PAD>(s_r, rows, n, K, K_pad, out + (D.srow + row0) * stride, stride);
+}
+
+// Ranks of every variable with its samples relabelled: out[v][k] = rank[v][sigma[k]] for k < n,
+// the padding slots (k >= n) 0xffff as in a ranked handle.
+__global__ void permute_ranks_kernel(const uint16_t* __restrict__ rank, int64_t ld, int n,
+                                     int64_t m, const uint16_t* __restrict__ sigma,
+                                     uint16_t* __restrict__ out) {
+  const int64_t total = m * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / ld;
+    const int k = (int)(i - v * ld);
+    const int src = min((int)sigma[k], n - 1);  // entries outside 0..n-1 cannot read out of the row
+    out[i] = k < n ? rank[v * ld + src] : (uint16_t)0xffffu;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -483,6 +499,10 @@ struct ContractArgs {
   int64_t ncb;             // rect: column blocks of BM
   int bnr;                 // output rows per unit: 256, or 128 for short query batches
   int afmt;                // kind::f8f6f4 operand format: 0 = E4M3, 5 = E2M1 (FP4)
+  // Permutation test (exceed != nullptr): count |S| >= |s_obs[k]| into exceed[k] instead of
+  // storing tau / S / n_3 (triangle, single matrix only).
+  const int32_t* s_obs;
+  uint32_t* exceed;
   int64_t unit_lo, unit_hi;
   uint64_t p_begin, p_end; // tri: pair range
   int64_t ldo;             // rect: output row stride
@@ -502,6 +522,8 @@ struct Prob {
   uint64_t p_begin, p_end;
   int64_t ldo;
   ktau_out out;
+  const int32_t* s_obs;
+  uint32_t* exceed;
 };
 
 struct Unit {
@@ -529,6 +551,8 @@ __device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t)
     p.p_end = a.p_end;
     p.ldo = a.ldo;
     p.out = a.out;
+    p.s_obs = a.s_obs;
+    p.exceed = a.exceed;
   } else {
     const ktau_bds& D = a.bds[t.bd];
     p.row = p.col = side_of_bds(D);
@@ -540,6 +564,8 @@ __device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t)
     p.ldo = 0;
     p.out = D.out;
     p.out.n3 = nullptr;
+    p.s_obs = nullptr;
+    p.exceed = nullptr;
   }
   return p;
 }
@@ -1118,6 +1144,21 @@ __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit&
     const RowsSmem rs{ri + 32 * (c - half_sel * nhalf)};
     const RowsReg rr{mine.rhi, mine.rlo, mine.base};
     const int rows_here = (int)min((int64_t)32, mrow - ub);
+    if (P.exceed) {  // permutation test: one exceedance count per pair, no other output
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j >= rows_here) break;  // warp-uniform
+        const RowInfo R = kSmemRows ? rs(j) : rr(j);
+        const int64_t y = ub + j;
+        if (!vin || (P.tri && v <= y)) continue;
+        const uint64_t p = (uint64_t)(R.base + v);
+        if (P.tri && (p < P.p_begin || p >= P.p_end)) continue;
+        const uint64_t k = P.tri ? p - P.p_begin : p;
+        const int S = __float2int_rn(__uint_as_float(r[j]));
+        if (abs(S) >= abs(P.s_obs[k])) P.exceed[k] += 1u;
+      }
+      continue;
+    }
     bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
     if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
       const int64_t ul = ub + 31;
@@ -1354,7 +1395,8 @@ __device__ __forceinline__ bool pair_live(const ContractArgs& a, int64_t s2) {
 
 template <int ESIZE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    contract2_kernel(const __grid_constant__ CUtensorMap tmS, const ContractArgs a) {
+    contract2_kernel(const __grid_constant__ CUtensorMap tmRow,
+                     const __grid_constant__ CUtensorMap tmCol, const ContractArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* stage_base = smem;
@@ -1397,7 +1439,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmS) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmRow) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmCol) : "memory");
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -1417,8 +1460,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
           if (rank == 0) mbar_expect_tx(FULL(stage), (2u * STAGE2_BYTES) >> (a.afmt == 5 ? 1 : 0));
           const uint32_t full_leader = cluster_addr(FULL(stage), 0);
           const int kx = (int)(kb * BKB);
-          tma_load_2d_pair(sa, &tmS, kx, t.ta, full_leader, pol);
-          tma_load_2d_pair(sb, &tmS, kx, brow, full_leader, pol);
+          tma_load_2d_pair(sa, &tmCol, kx, t.ta, full_leader, pol);
+          tma_load_2d_pair(sb, &tmRow, kx, brow, full_leader, pol);
           if (++stage == STAGES2) {
             stage = 0;
             phase ^= 1u;
@@ -1626,8 +1669,8 @@ ktau_status launch_contract_maps(const void* tmap_a, const void* tmap_b, const C
 
 // Pair form over the triangle of one matrix: clusters of two CTAs, as many as fit at once.
 template <int ESIZE>
-ktau_status launch_contract2_map(const void* tmap, const ContractArgs& args, int64_t units,
-                                 cudaStream_t st) {
+ktau_status launch_contract2_map(const void* tmap_row, const void* tmap_col,
+                                 const ContractArgs& args, int64_t units, cudaStream_t st) {
   auto kern = contract2_kernel<ESIZE>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SMEM2_BYTES));
@@ -1658,7 +1701,8 @@ ktau_status launch_contract2_map(const void* tmap, const ContractArgs& args, int
   if (clusters < 1) clusters = 1;
   KTAU_TRACE("contract_kernel", st);
   kern<<<(unsigned)(2 * clusters), THREADS, SMEM2_BYTES, st>>>(
-      *reinterpret_cast<const CUtensorMap*>(tmap), args);
+      *reinterpret_cast<const CUtensorMap*>(tmap_row),
+      *reinterpret_cast<const CUtensorMap*>(tmap_col), args);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }
@@ -1666,7 +1710,7 @@ ktau_status launch_contract2_map(const void* tmap, const ContractArgs& args, int
 template <int ESIZE>
 ktau_status launch_contract2(const ktau_ranked* R, const ContractArgs& args, int64_t units,
                              cudaStream_t st) {
-  return launch_contract2_map<ESIZE>(R->tmap, args, units, st);
+  return launch_contract2_map<ESIZE>(R->tmap, R->tmap, args, units, st);
 }
 
 // Rows from A, columns from B: the MMA's A operand (TMEM lanes) is the column side.
@@ -1753,6 +1797,24 @@ class SideFork {
 };
 }  // namespace
 
+// Sign expansion of R's ranks into R->sgn (R->K, K_pad, obits and esize set).
+ktau_status launch_sign_expand(const ktau_ranked* R, cudaStream_t st) {
+  const int64_t n = R->n;
+  const size_t smem = (size_t)EXPAND_ROWS * xrow<16>((int)n) * sizeof(uint16_t);  // largest pad
+  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
+  KTAU_TRACE("sign_expand_kernel", st);
+  const bool pad = n > 256;
+  auto kern = R->obits == 4
+                  ? (pad ? sign_expand_kernel<4, true> : sign_expand_kernel<4, false>)
+                  : (R->obits == 8
+                         ? (pad ? sign_expand_kernel<8, true> : sign_expand_kernel<8, false>)
+                         : (pad ? sign_expand_kernel<16, true> : sign_expand_kernel<16, false>));
+  kern<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K, (int)R->K_pad,
+                                   (uint8_t*)R->sgn);
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
 ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
   if (obits != 4 && obits != 8 && obits != 16)
     return ktau_fail(KTAU_EINVAL, "operand bits must be 4, 8 or 16");
@@ -1770,21 +1832,9 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
   R->esize = obits == 16 ? 2 : 1;
   R->sgn_bytes = (size_t)R->m * R->K_pad * obits / 8;
   if (ktau_dmalloc(&R->sgn, R->sgn_bytes) != KTAU_OK) return KTAU_ENOMEM;
-  const size_t smem = (size_t)EXPAND_ROWS * xrow<16>((int)n) * sizeof(uint16_t);  // largest pad
-  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
-  {
-    KTAU_TRACE("sign_expand_kernel", st);
-    const bool pad = n > 256;
-    auto kern = R->obits == 4
-                    ? (pad ? sign_expand_kernel<4, true> : sign_expand_kernel<4, false>)
-                    : (R->obits == 8
-                           ? (pad ? sign_expand_kernel<8, true> : sign_expand_kernel<8, false>)
-                           : (pad ? sign_expand_kernel<16, true> : sign_expand_kernel<16, false>));
-    kern<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K, (int)R->K_pad,
-                                     (uint8_t*)R->sgn);
-  }
-  KTAU_CUDA(cudaGetLastError());
-  ktau_status s = make_tmap(R);
+  ktau_status s = launch_sign_expand(R, st);
+  if (s != KTAU_OK) return s;
+  s = make_tmap(R);
   if (s != KTAU_OK) return s;
   R->sg_ready = 1;
   return KTAU_OK;
@@ -1847,10 +1897,8 @@ ktau_status ktau_signgemm_ties(ktau_ranked* R, cudaStream_t ss) {
   return KTAU_OK;
 }
 
-ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
-                                   const ktau_out& out, int obits, cudaStream_t st) {
-  ktau_status s = ktau_signgemm_prepare(R, obits, st);
-  if (s != KTAU_OK) return s;
+// Contraction arguments of the triangle of one matrix over the pairs [p_begin, p_end).
+ContractArgs tri_args(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end, const ktau_out& out) {
   const int64_t m = R->m;
   ContractArgs a;
   a.row = a.col = side_of(R);
@@ -1875,6 +1923,17 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   a.wG = (a.wS + GROUP - 1) / GROUP;
   a.unit_lo = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i0 / 256 / GROUP);
   a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / 256 / GROUP + 1);
+  a.s_obs = nullptr;
+  a.exceed = nullptr;
+  return a;
+}
+
+ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                                   const ktau_out& out, int obits, cudaStream_t st) {
+  ktau_status s = ktau_signgemm_prepare(R, obits, st);
+  if (s != KTAU_OK) return s;
+  const int64_t m = R->m;
+  const ContractArgs a = tri_args(R, p_begin, p_end, out);
   const int64_t units = a.unit_hi - a.unit_lo;
   // The epilogue zero-fills n_3 over the range; the joint-ties kernels then add nonzero counts.
   // The tie lists (first call only) are built beside the contraction on a side stream.
@@ -1905,6 +1964,8 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.wG = 0;
   a.ncb = (D->m + BM - 1) / BM;
   a.bnr = Q->m <= BM ? BM : BN;
+  a.s_obs = nullptr;
+  a.exceed = nullptr;
   a.afmt = Q->obits == 4 ? 5 : 0;
   a.p_begin = 0;
   a.p_end = 0;
@@ -1997,8 +2058,8 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   a.tri = 1;
   a.bnr = BN;
   a.afmt = g.obits == 4 ? 5 : 0;
-  ktau_status s = g.esize == 1 ? launch_contract2_map<1>(g.tmap, a, g.units, st)
-                               : launch_contract2_map<2>(g.tmap, a, g.units, st);
+  ktau_status s = g.esize == 1 ? launch_contract2_map<1>(g.tmap, g.tmap, a, g.units, st)
+                               : launch_contract2_map<2>(g.tmap, g.tmap, a, g.units, st);
   if (s != KTAU_OK) return s;
   const int jcols = g.max_n <= 1024 ? 64 : 32;
   const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)g.max_n * (jcols + 1) * sizeof(uint16_t);
@@ -2021,4 +2082,65 @@ extern "C" ktau_status ktau_debug_wait_timeout(int64_t limit_ns, void* stream) {
   wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((unsigned long long)limit_ns);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Permutation test of every pair
+// ---------------------------------------------------------------------------------------------
+extern "C" ktau_status ktau_permutation_exceed(const ktau_ranked* Rc, const uint16_t* perms,
+                                               int32_t B, uint64_t p_begin, uint64_t p_end,
+                                               const int32_t* S_obs, uint32_t* exceed,
+                                               void* stream) {
+  if (!Rc) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  if (B < 0) return ktau_fail(KTAU_EINVAL, "B must be >= 0");
+  if (B > 0 && !perms) return ktau_fail(KTAU_EINVAL, "perms is NULL");
+  if (!S_obs || !exceed) return ktau_fail(KTAU_EINVAL, "S_obs and exceed are required");
+  if (!ktau_signgemm_supported(Rc->n))
+    return ktau_fail(KTAU_EINVAL, "the permutation test runs on the sign contraction: n <= %d",
+                     KTAU_SIGNGEMM_MAX_N);
+  const uint64_t P = (uint64_t)(Rc->m * (Rc->m - 1) / 2);
+  if (p_begin > p_end || p_end > P) return ktau_fail(KTAU_EINVAL, "pair range outside the triangle");
+  if (p_begin == p_end || B == 0) return KTAU_OK;
+  ktau_ranked* R = const_cast<ktau_ranked*>(Rc);
+  cudaStream_t st = (cudaStream_t)stream;
+  ktau_status s = ktau_signgemm_prepare(R, ktau_sign_obits(R->n, nullptr), st);
+  if (s != KTAU_OK) return s;
+  // The relabelled copy: its own ranks and signs, everything else shared with R.
+  ktau_ranked Rp = *R;
+  const size_t rank_bytes = (size_t)R->m * R->ld * sizeof(uint16_t);
+  Rp.rank = nullptr;
+  Rp.sgn = nullptr;
+  if (ktau_dmalloc((void**)&Rp.rank, rank_bytes) != KTAU_OK) return KTAU_ENOMEM;
+  if (ktau_dmalloc(&Rp.sgn, R->sgn_bytes) != KTAU_OK) {
+    ktau_dfree(Rp.rank, rank_bytes);
+    return KTAU_ENOMEM;
+  }
+  s = make_tmap(&Rp);
+  ContractArgs a = tri_args(R, p_begin, p_end, ktau_out{nullptr, nullptr, nullptr, nullptr, 32, 0});
+  a.col = side_of(&Rp);
+  a.s_obs = S_obs;
+  a.exceed = exceed;
+  const int64_t units = a.unit_hi - a.unit_lo;
+  const int64_t total = R->m * R->ld;
+  const unsigned pblocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+  for (int32_t b = 0; b < B && s == KTAU_OK; ++b) {
+    {
+      KTAU_TRACE("permute_ranks_kernel", st);
+      permute_ranks_kernel<<<pblocks, 256, 0, st>>>(R->rank, R->ld, (int)R->n, R->m,
+                                                   perms + (size_t)b * R->n, Rp.rank);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = ktau_cuda_fail(e, "permute_ranks_kernel");
+    if (s == KTAU_OK) s = launch_sign_expand(&Rp, st);
+    if (s == KTAU_OK)
+      s = R->esize == 1 ? launch_contract2_map<1>(R->tmap, Rp.tmap, a, units, st)
+                        : launch_contract2_map<2>(R->tmap, Rp.tmap, a, units, st);
+  }
+  // The scratch goes back to the cache only once the work that uses it has finished.
+  const cudaError_t e = cudaStreamSynchronize(st);
+  ktau_dfree(Rp.sgn, R->sgn_bytes);
+  ktau_dfree(Rp.rank, rank_bytes);
+  if (s == KTAU_OK && e != cudaSuccess) s = ktau_cuda_fail(e, "cudaStreamSynchronize");
+  if (s == KTAU_OK) s = ktau_signgemm_check_error(st);
+  return s;
 }
