@@ -43,8 +43,12 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-query", action="store_true")
-    ap.add_argument("--query-batches", type=int, default=300,
+    ap.add_argument("--query-batches", type=int, default=2000,
                     help="batches per offered load in the serving measurement")
+    ap.add_argument("--no-merge", action="store_true",
+                    help="skip the merge-path (Knight) measurement")
+    ap.add_argument("--no-perm", action="store_true",
+                    help="skip the permutation-test measurement")
     return ap.parse_args()
 
 
@@ -112,6 +116,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu capture, or None
+    when the kernel's source has changed since that capture (its SHA-256 is recorded beside the
+    figure)."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))[kernel]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, KeyError, ValueError):
+        return None
+    if hashlib.sha256(src).hexdigest() != rec["sha256"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -137,9 +157,16 @@ def cpu_baseline(X, seconds: float):
     t0 = time.perf_counter()
     oracle.allpairs(Xd, method="knight", threads=threads, p_begin=0, p_end=sample)
     dt = time.perf_counter() - t0
+    # the same oracle on one core, on a sample a quarter as long in time
+    one = max(2000, int(sample / threads / 4))
+    t1 = time.perf_counter()
+    oracle.allpairs(Xd, method="knight", threads=1, p_begin=0, p_end=one)
+    dt1 = time.perf_counter() - t1
     return {"value": sample / dt, "unit": "pairs/s", "cores": threads, "kind": "oracle",
             "sample": f"first {sample} packed pairs (rows 0..) of the same m=16384 x n=128 matrix, "
-                      f"Knight counting, {dt:.1f} s"}
+                      f"Knight counting, {dt:.1f} s",
+            "single_core": {"value": one / dt1, "unit": "pairs/s", "cores": 1,
+                            "sample": f"first {one} packed pairs, {dt1:.1f} s"}}
 
 
 def bench_batched(ktau, steps: int, warmup: int) -> dict:
@@ -201,6 +228,83 @@ def bench_batched(ktau, steps: int, warmup: int) -> dict:
             "speedup_vs_plain": plain_ms / ms}
 
 
+def bench_merge(ktau, clocks_mhz: float | None) -> dict:
+    """The Knight merge path (K-b) on its own: the long heavy-tie profiles it is the path for
+    (2048 x 4096 int32, values 0..63, int64 counts + FP64 tau) and the bench matrix, each timed
+    by the library's per-kernel CUDA events. Roof: one compare-and-count merge step per int32
+    lane per clock (152 SMs x 128 lanes at the sampled SM clock)."""
+    import torch
+
+    from synthetic import gene_expression, heavy_ties_ordinal
+
+    dev = torch.device("cuda")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f = (clocks_mhz or 2070.0) * 1e6
+    peak = sms * 128 * f / 1e9
+    out = {}
+    cases = (("heavy_ties_2048x4096_int32", heavy_ties_ordinal(2048, 4096, seed=0), 64),
+             ("gene_expression_16384x128", gene_expression(M, N, seed=0), 32))
+    for name, X, bits in cases:
+        m, n = X.shape
+        P = m * (m - 1) // 2
+        Xd = torch.from_numpy(X).to(dev)
+        R = ktau.ktau_rank_prepare(Xd)
+        cdt = torch.int64 if bits == 64 else torch.int32
+        S = torch.empty(P, dtype=cdt, device=dev)
+        n3 = torch.empty(P, dtype=cdt, device=dev)
+        t64 = torch.empty(P, dtype=torch.float64, device=dev) if bits == 64 else None
+        t32 = None if bits == 64 else torch.empty(P, dtype=torch.float32, device=dev)
+        opts = {"path": 1}
+        ktau.ktau_allpairs(R, 0, P, t64, t32, S, n3, bits, opts)  # warm-up
+        torch.cuda.synchronize()
+        reps = 2
+        ktau.ktau_trace_collect()
+        ktau.ktau_trace_enable(True)
+        for _ in range(reps):
+            ktau.ktau_allpairs(R, 0, P, t64, t32, S, n3, bits, opts)
+        torch.cuda.synchronize()
+        ktau.ktau_trace_enable(False)
+        tr = ktau.ktau_trace_collect()
+        ktau.ktau_device_status()
+        ms = sum(t for k, t in tr if k.startswith("merge")) / reps
+        lg = max(1, (n - 1).bit_length())
+        steps = n * lg  # Step 3 compare-and-count steps per pair
+        ach = P * steps / (ms / 1e3) / 1e9
+        out[name] = {"m": m, "n": n, "pairs": P, "count_bits": bits, "kernel_ms": ms,
+                     "pairs_per_s": P / (ms / 1e3), "ns_per_pair": ms * 1e6 / P,
+                     "sample_comparisons_per_s": P * (n * (n - 1) // 2) / (ms / 1e3),
+                     "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                                  "unit": "G merge-steps/s vs int32 lane-ops/s", "frac": ach / peak,
+                                  "steps_per_pair": steps}}
+        R.free()
+        del Xd, S, n3, t64, t32
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_permutation(ktau, Xd, P: int, B: int = 8) -> dict:
+    """Permutation test on the bench matrix: B relabellings, each a full pass over the
+    134,209,536 pairs (relabelled ranks, their sign expansion, pair contraction counting
+    exceedances)."""
+    import torch
+
+    from synthetic import permutations
+
+    R = ktau.ktau_rank_prepare(Xd)
+    S = torch.empty(P, dtype=torch.int32, device=Xd.device)
+    ktau.ktau_allpairs(R, 0, P, None, None, S, None, 32)
+    exc = torch.zeros(P, dtype=torch.uint32, device=Xd.device)
+    perms = torch.from_numpy(permutations(B, N, seed=5)).to(Xd.device)
+    ktau.ktau_permutation_exceed(R, perms[:1], S, exc)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ktau.ktau_permutation_exceed(R, perms, S, exc)  # returns when finished
+    dt = time.perf_counter() - t0
+    R.free()
+    return {"permutations": B, "seconds": dt, "ms_per_permutation": dt * 1e3 / B,
+            "pair_permutations_per_s": P * B / dt}
+
+
 def bench_query(ktau, batches_per_load: int) -> dict:
     """Serving: resident 65536 x 256 database, batches of 1..512 profiles (log-uniform),
     exact tau-b against every row + top-100; closed-loop capacity, then Poisson streams at 0.3,
@@ -229,6 +333,31 @@ def bench_query(ktau, batches_per_load: int) -> dict:
            "closed_loop": {"batches_per_s": cap_batches, "queries_per_s": profiles / dt,
                            "pairs_per_s": profiles * 65536 / dt},
            "open_loop": []}
+    # Plain launch of the same batches, one after another on one stream (no continuous
+    # batching): H2D, rank, query + top-k, D2H, synchronise.
+    import numpy as np
+    import torch
+
+    import paper_1704_03767_gb300 as kb
+
+    lat_plain = []
+    tq = time.perf_counter()
+    for q in batches:
+        ts = time.perf_counter()
+        qd = torch.from_numpy(q).cuda()
+        Rq = kb.ktau_rank_prepare(qd)
+        b = q.shape[0]
+        Sq = torch.empty((b, 65536), dtype=torch.int32, device="cuda")
+        idx = torch.empty((b, 100), dtype=torch.int32, device="cuda")
+        tk = torch.empty((b, 100), dtype=torch.float64, device="cuda")
+        kb.ktau_query(srv.db, Rq, None, Sq, None, 32, 100, idx, tk)
+        idx.cpu(), tk.cpu()
+        Rq.free()
+        lat_plain.append((time.perf_counter() - ts) * 1e3)
+    dtp = time.perf_counter() - tq
+    out["plain_launch"] = {"batches_per_s": len(batches) / dtp, "queries_per_s": profiles / dtp,
+                           "p50_ms": percentile(lat_plain, 50), "p99_ms": percentile(lat_plain, 99)}
+    out["speedup_vs_plain"] = (profiles / dt) / (profiles / dtp)
     for load in (0.3, 0.6, 0.9):
         t1 = time.perf_counter()
         rs = run_open_loop(srv, batches, rate_per_s=load * cap_batches)
@@ -390,9 +519,37 @@ def run_ours(args):
         achieved = flops / (kern_avg_ms / 1e3) / 1e12
         bf16 = (peaks or {}).get("bf16_tflops", 1921.4)
         peak = 2.0 * bf16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s (FP8 e4m3, of measured BF16 x 2)", "frac": achieved / peak,
-                "traffic": None, "kernel": "contract_kernel<1>", "kernel_ms": kern_avg_ms}
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": _traffic("contract2_kernel"),
+                "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops (burst) x 2, the "
+                               "nominal FP8/BF16 ratio; FP8 e4m3 operands",
+                "kernel": "contract2_kernel<1> (2-CTA tcgen05 pair)", "kernel_ms": kern_avg_ms}
+
+    # tau-a (Sec. 2, no tie correction) on the same workload: the whole step without n_3.
+    taua = None
+    if world == 1:
+        opts_a = dict(opts, statistic=1)
+        for _ in range(2):
+            R = ktau.ktau_rank_prepare(Xd, stream)
+            ktau.ktau_allpairs(R, 0, P, None, tau32, S, None, 32, opts_a, stream)
+            R.free()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a0.record(stream)
+            R = ktau.ktau_rank_prepare(Xd, stream)
+            if path_id == 2:
+                ktau.ktau_prepare_signs(R, stream)
+            ktau.ktau_allpairs(R, 0, P, None, tau32, S, None, 32, opts_a, stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            a_ms += a0.elapsed_time(a1)
+            R.free()
+        ktau.ktau_device_status(stream)
+        taua = {"outputs": "FP32 tau-a + int32 S (no n_3)", "ms_per_step": a_ms / args.steps,
+                "pairs_per_s": P * args.steps / (a_ms / 1e3)}
 
     e2e = None
     if not args.no_e2e:
@@ -429,6 +586,12 @@ def run_ours(args):
     query = None
     if not args.no_query and world == 1:
         query = bench_query(ktau, args.query_batches)
+    perm = None
+    if not args.no_perm and world == 1 and path_id == 2:
+        perm = bench_permutation(ktau, Xd, P)
+    merge = None
+    if not args.no_merge and world == 1:
+        merge = bench_merge(ktau, clocks.get("sm_mhz"))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -448,7 +611,8 @@ def run_ours(args):
         "kernels": kernels,
         "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "sample_comparisons_per_s": value * (N * (N - 1) // 2),
-        "batched": batched, "query": query,
+        "batched": batched, "query": query, "merge_path": merge, "tau_a": taua,
+        "permutation_test": perm,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -1145,17 +1145,31 @@ __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit&
     const RowsReg rr{mine.rhi, mine.rlo, mine.base};
     const int rows_here = (int)min((int64_t)32, mrow - ub);
     if (P.exceed) {  // permutation test: one exceedance count per pair, no other output
+      // Groups of 8 rows: first every observed S of the group (independent loads), then the
+      // comparisons and fire-and-forget atomic increments (each pair has one thread per launch).
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (j >= rows_here) break;  // warp-uniform
-        const RowInfo R = kSmemRows ? rs(j) : rr(j);
-        const int64_t y = ub + j;
-        if (!vin || (P.tri && v <= y)) continue;
-        const uint64_t p = (uint64_t)(R.base + v);
-        if (P.tri && (p < P.p_begin || p >= P.p_end)) continue;
-        const uint64_t k = P.tri ? p - P.p_begin : p;
-        const int S = __float2int_rn(__uint_as_float(r[j]));
-        if (abs(S) >= abs(P.s_obs[k])) P.exceed[k] += 1u;
+      for (int h = 0; h < 4; ++h) {
+        int so[8];
+        uint64_t kk[8];
+        uint32_t valid = 0;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = 8 * h + jj;
+          const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
+          const int64_t y = ub + j;
+          const uint64_t p = (uint64_t)(R.base + v);
+          kk[jj] = P.tri ? p - P.p_begin : p;
+          so[jj] = 0;
+          if (j < rows_here && vin && (!P.tri || (v > y && p >= P.p_begin && p < P.p_end))) {
+            valid |= 1u << jj;
+            so[jj] = __ldg(P.s_obs + kk[jj]);
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int S = __float2int_rn(__uint_as_float(r[8 * h + jj]));
+          if (((valid >> jj) & 1u) && abs(S) >= abs(so[jj])) atomicAdd(P.exceed + kk[jj], 1u);
+        }
       }
       continue;
     }
