@@ -53,6 +53,27 @@ __device__ __forceinline__ unsigned long long team_sum(unsigned long long v,
 template <int ITEMS>
 __device__ __forceinline__ int pd(int i) { return ITEMS >= 8 ? i + (i >> 5) : i; }
 
+// Team-wide exclusive max-scan of one int per thread (lane order); -1 for the first lane.
+template <int TEAM>
+__device__ __forceinline__ int team_excl_max(int v, unsigned long long* red) {
+  const int lane = threadIdx.x & 31, wid = (threadIdx.x % TEAM) >> 5;
+  int incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl = max(incl, t);
+  }
+  int excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = -1;
+  if (TEAM == 32) return excl;
+  int* w = reinterpret_cast<int*>(red);  // TEAM / 32 warp maxima
+  __syncthreads();
+  if (lane == 31) w[wid] = incl;
+  __syncthreads();
+  for (int i = 0; i < wid; ++i) excl = max(excl, w[i]);
+  __syncthreads();
+  return excl;
+}
+
 // Merge sort of buf[0, n) (ascending) with tmp as the second buffer. With COUNT, each thread
 // accumulates into `cnt` its share of the inversions (pairs i < j with buf[i] > buf[j]).
 // Returns the buffer that holds the sorted sequence. Every thread of the team must call it.
@@ -182,22 +203,40 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
     unsigned long long unused = 0;
     uint32_t* sorted = team_merge_sort<TEAM, ITEMS, false>(buf, tmp, n, lane, unused);
     uint32_t* other = sorted == buf ? tmp : buf;
-    // Step 2: joint ties. In the sorted keys, position k has (k - first index of its key)
-    // earlier equal keys.
-    for (int k = lane; k < n; k += TEAM) {
-      const uint32_t key = sorted[pd<ITEMS>(k)];
-      if (k > 0 && sorted[pd<ITEMS>(k - 1)] == key) {
-        int lo = 0, hi = k;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (sorted[pd<ITEMS>(mid)] < key)
-            lo = mid + 1;
-          else
-            hi = mid;
-        }
-        n3 += (unsigned long long)(k - lo);
+    // Step 2: joint ties. In the sorted keys, position k has (k - first index of its run of
+    // equal keys) earlier equal keys.
+    if (TEAM > 32) {
+      // Long vectors: each lane takes a contiguous segment; the last run head of every earlier
+      // segment (team max-scan) is where its first run started.
+      const int per = (n + TEAM - 1) / TEAM;
+      const int kb = min(n, lane * per), ke = min(n, kb + per);
+      int last = -1;
+      for (int k = kb; k < ke; ++k)
+        if (k == 0 || sorted[pd<ITEMS>(k)] != sorted[pd<ITEMS>(k - 1)]) last = k;
+      int first = team_excl_max<TEAM>(last, red);
+      for (int k = kb; k < ke; ++k) {
+        const uint32_t key = sorted[pd<ITEMS>(k)];
+        if (k == 0 || key != sorted[pd<ITEMS>(k - 1)]) first = k;
+        n3 += (unsigned long long)(k - first);
+        other[pd<ITEMS>(k)] = key & 0xffffu;
       }
-      other[pd<ITEMS>(k)] = key & 0xffffu;
+    } else {
+      // Short vectors, few ties: the first index of a tied key by binary search.
+      for (int k = lane; k < n; k += TEAM) {
+        const uint32_t key = sorted[pd<ITEMS>(k)];
+        if (k > 0 && sorted[pd<ITEMS>(k - 1)] == key) {
+          int lo = 0, hi = k;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sorted[pd<ITEMS>(mid)] < key)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          n3 += (unsigned long long)(k - lo);
+        }
+        other[pd<ITEMS>(k)] = key & 0xffffu;
+      }
     }
     team_sync<TEAM>();
     team_merge_sort<TEAM, ITEMS, true>(other, sorted, n, lane, nd);
@@ -481,7 +520,7 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
   }
 
   const bool cta_team = plan.mapping == 2;
-  const int items = cta_team ? 8 : (n <= 256 ? (int)((n + 31) / 32) : 8);
+  const int items = cta_team ? (n > 2048 ? 16 : 8) : (n <= 256 ? (int)((n + 31) / 32) : 8);
   a.cap = (int)((n + (n >> 5) + 1 + 3) & ~3LL);  // pd<ITEMS>(n) + 1, rounded
   const size_t team_bytes = (size_t)2 * a.cap * sizeof(uint32_t);
   // Stage the tile's rows in shared memory when they are small next to the per-pair work.
@@ -503,7 +542,9 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
   }
   const size_t smem = (a.stage ? stage_bytes : 0) + (size_t)teams * team_bytes;
   const int cps = plan.ctas_per_sm;
-  if (cta_team) return launch_one<256, 8>(a, threads, smem, cps, tiles, st);
+  if (cta_team)
+    return items == 16 ? launch_one<256, 16>(a, threads, smem, cps, tiles, st)
+                       : launch_one<256, 8>(a, threads, smem, cps, tiles, st);
   switch (items) {
     case 1: return launch_one<32, 1>(a, threads, smem, cps, tiles, st);
     case 2: return launch_one<32, 2>(a, threads, smem, cps, tiles, st);
