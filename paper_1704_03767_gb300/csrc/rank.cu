@@ -217,117 +217,120 @@ __device__ __forceinline__ void store_u16s(uint16_t* dst, const uint16_t (&x)[EP
   }
 }
 
+// Rank transform of one variable by one warp (see rank_warp_kernel); `off` is the element offset
+// of its values, `row` its row in the outputs. Accumulates the warp's statistics.
 template <int DT, int EPL>
-__global__ void __launch_bounds__(32 * RANK_WARPS) rank_warp_kernel(
-    const void* __restrict__ values, int64_t ld_in, int n, int64_t m, int64_t ld,
-    uint16_t* __restrict__ perm, uint16_t* __restrict__ rank, uint16_t* __restrict__ srank,
-    int64_t* __restrict__ T, int32_t* __restrict__ ndist, int32_t* __restrict__ maxg,
-    double* __restrict__ rs64, float2* __restrict__ rsff, ktau_stats* __restrict__ stats) {
-  __shared__ unsigned long long s_T[RANK_WARPS], s_Tmax[RANK_WARPS];
-  __shared__ unsigned s_g[RANK_WARPS], s_nan[RANK_WARPS];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row = (int64_t)blockIdx.x * RANK_WARPS + wid;
-  unsigned long long tsum = 0;
-  int gmax = 0;
-  unsigned nan_seen = 0;
-  if (row < m) {
-    unsigned long long v[EPL];
+__device__ __forceinline__ void rank_warp_row(const void* __restrict__ values, int64_t off, int n,
+                                              int64_t ld, int64_t row, uint16_t* __restrict__ perm,
+                                              uint16_t* __restrict__ rank,
+                                              uint16_t* __restrict__ srank, int64_t* __restrict__ T,
+                                              int32_t* __restrict__ ndist,
+                                              int32_t* __restrict__ maxg, double* __restrict__ rs64,
+                                              float2* __restrict__ rsff, unsigned long long& tsum,
+                                              int& gmax, unsigned& nan_seen, int lane) {
+  unsigned long long v[EPL];
 #pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      const int i = lane * EPL + e;
-      v[e] = i < n ? load_key<DT>(values, row * ld_in, i, &nan_seen) : ~0ull;
-    }
-    warp_bitonic<EPL>(v, lane);
-    // Group heads over sorted positions k < n; dense rank = heads up to k, minus one;
-    // first(k) = position of the last head <= k.
-    const unsigned long long prev_last = __shfl_up_sync(0xffffffffu, v[EPL - 1], 1);
-    int heads = 0, last_head = -1;
-    bool head[EPL];
+  for (int e = 0; e < EPL; ++e) {
+    const int i = lane * EPL + e;
+    v[e] = i < n ? load_key<DT>(values, off, i, &nan_seen) : ~0ull;
+  }
+  warp_bitonic<EPL>(v, lane);
+  // Group heads over sorted positions k < n; dense rank = heads up to k, minus one;
+  // first(k) = position of the last head <= k.
+  const unsigned long long prev_last = __shfl_up_sync(0xffffffffu, v[EPL - 1], 1);
+  int heads = 0, last_head = -1;
+  bool head[EPL];
 #pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      const int k = lane * EPL + e;
-      const unsigned long long pv = e == 0 ? prev_last : v[e - 1];
-      head[e] = k < n && (k == 0 || (v[e] >> 32) != (pv >> 32));
-      heads += head[e];
-      if (head[e]) last_head = k;
-    }
-    int incl = heads, lmax = last_head;
+  for (int e = 0; e < EPL; ++e) {
+    const int k = lane * EPL + e;
+    const unsigned long long pv = e == 0 ? prev_last : v[e - 1];
+    head[e] = k < n && (k == 0 || (v[e] >> 32) != (pv >> 32));
+    heads += head[e];
+    if (head[e]) last_head = k;
+  }
+  int incl = heads, lmax = last_head;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, d);
-      const int u = __shfl_up_sync(0xffffffffu, lmax, d);
-      if (lane >= d) {
-        incl += t;
-        lmax = u > lmax ? u : lmax;
-      }
-    }
-    int run = incl - heads;                                  // heads before this lane
-    int first = __shfl_up_sync(0xffffffffu, lmax, 1);        // last head before this lane
-    if (lane == 0) first = -1;
-    uint16_t pk[EPL], sk[EPL], pad[EPL];
-    uint16_t* rrow = rank + row * ld;
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      const int k = lane * EPL + e;
-      pad[e] = 0xffff;
-      if (k < n) {
-        run += head[e];
-        if (head[e]) first = k;
-        const int idx = (int)(v[e] & 0xffffffffu);
-        const int d = run - 1;
-        const int before = k - first;
-        pk[e] = (uint16_t)idx;
-        sk[e] = (uint16_t)d;
-        rrow[idx] = (uint16_t)d;
-        tsum += (unsigned long long)before;
-        gmax = before + 1 > gmax ? before + 1 : gmax;
-      } else {
-        pk[e] = sk[e] = 0xffff;
-      }
-    }
-    // ld is a multiple of 16 and EPL divides 16: a lane's positions are all inside or all
-    // outside the padded row.
-    if (lane * EPL < ld) {
-      store_u16s<EPL>(perm + row * ld + lane * EPL, pk);
-      store_u16s<EPL>(srank + row * ld + lane * EPL, sk);
-      if (lane * EPL >= n) store_u16s<EPL>(rrow + lane * EPL, pad);
-      else if (lane * EPL + EPL > n)
-        for (int e = n - lane * EPL; e < EPL; ++e) rrow[lane * EPL + e] = 0xffff;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      tsum += __shfl_xor_sync(0xffffffffu, tsum, d);
-      const int o = __shfl_xor_sync(0xffffffffu, gmax, d);
-      gmax = o > gmax ? o : gmax;
-    }
-    const int total_heads = __shfl_sync(0xffffffffu, incl, 31);
-    nan_seen = __any_sync(0xffffffffu, nan_seen != 0);
-    if (lane == 0) {
-      T[row] = (int64_t)tsum;
-      // Factor of the tau-b denominator (Eq. 3): 1/sqrt(n_0 - n_1), IEEE FP64.
-      const long long D = (long long)n * (n - 1) / 2 - (long long)tsum;
-      const double r = D > 0 ? __ddiv_rn(1.0, __dsqrt_rn((double)D))
-                             : __longlong_as_double(0x7ff8000000000000LL);
-      const float hi = __double2float_rn(r);
-      rs64[row] = r;
-      rsff[row] = make_float2(hi, D > 0 ? __double2float_rn(r - (double)hi) : hi);
-      ndist[row] = total_heads;
-      maxg[row] = gmax;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    const int u = __shfl_up_sync(0xffffffffu, lmax, d);
+    if (lane >= d) {
+      incl += t;
+      lmax = u > lmax ? u : lmax;
     }
   }
+  int run = incl - heads;                                  // heads before this lane
+  int first = __shfl_up_sync(0xffffffffu, lmax, 1);        // last head before this lane
+  if (lane == 0) first = -1;
+  uint16_t pk[EPL], sk[EPL], pad[EPL];
+  uint16_t* rrow = rank + row * ld;
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int k = lane * EPL + e;
+    pad[e] = 0xffff;
+    if (k < n) {
+      run += head[e];
+      if (head[e]) first = k;
+      const int idx = (int)(v[e] & 0xffffffffu);
+      const int d = run - 1;
+      const int before = k - first;
+      pk[e] = (uint16_t)idx;
+      sk[e] = (uint16_t)d;
+      rrow[idx] = (uint16_t)d;
+      tsum += (unsigned long long)before;
+      gmax = before + 1 > gmax ? before + 1 : gmax;
+    } else {
+      pk[e] = sk[e] = 0xffff;
+    }
+  }
+  // ld is a multiple of 16 and EPL divides 16: a lane's positions are all inside or all
+  // outside the padded row.
+  if (lane * EPL < ld) {
+    store_u16s<EPL>(perm + row * ld + lane * EPL, pk);
+    store_u16s<EPL>(srank + row * ld + lane * EPL, sk);
+    if (lane * EPL >= n) store_u16s<EPL>(rrow + lane * EPL, pad);
+    else if (lane * EPL + EPL > n)
+      for (int e = n - lane * EPL; e < EPL; ++e) rrow[lane * EPL + e] = 0xffff;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    tsum += __shfl_xor_sync(0xffffffffu, tsum, d);
+    const int o = __shfl_xor_sync(0xffffffffu, gmax, d);
+    gmax = o > gmax ? o : gmax;
+  }
+  const int total_heads = __shfl_sync(0xffffffffu, incl, 31);
+  nan_seen = __any_sync(0xffffffffu, nan_seen != 0);
+  if (lane == 0) {
+    T[row] = (int64_t)tsum;
+    // Factor of the tau-b denominator (Eq. 3): 1/sqrt(n_0 - n_1), IEEE FP64.
+    const long long D = (long long)n * (n - 1) / 2 - (long long)tsum;
+    const double r = D > 0 ? __ddiv_rn(1.0, __dsqrt_rn((double)D))
+                           : __longlong_as_double(0x7ff8000000000000LL);
+    const float hi = __double2float_rn(r);
+    rs64[row] = r;
+    rsff[row] = make_float2(hi, D > 0 ? __double2float_rn(r - (double)hi) : hi);
+    ndist[row] = total_heads;
+    maxg[row] = gmax;
+  }
+}
+
+// Per-CTA statistics: one set of atomics for the CTA's warps.
+__device__ __forceinline__ void rank_warp_stats(unsigned long long tsum, int gmax, unsigned nan_seen,
+                                                ktau_stats* stats) {
+  __shared__ unsigned long long s_T[RANK_WARPS];
+  __shared__ unsigned s_g[RANK_WARPS], s_nan[RANK_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     s_T[wid] = tsum;
-    s_Tmax[wid] = tsum;
     s_g[wid] = (unsigned)gmax;
     s_nan[wid] = nan_seen;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {  // one set of statistics atomics per CTA
+  if (threadIdx.x == 0) {
     unsigned long long t = 0, tm = 0;
     unsigned g = 0, nn = 0;
     for (int w = 0; w < RANK_WARPS; ++w) {
       t += s_T[w];
-      tm = s_Tmax[w] > tm ? s_Tmax[w] : tm;
+      tm = s_T[w] > tm ? s_T[w] : tm;
       g = s_g[w] > g ? s_g[w] : g;
       nn |= s_nan[w];
     }
@@ -336,6 +339,71 @@ __global__ void __launch_bounds__(32 * RANK_WARPS) rank_warp_kernel(
     atomicMax(&stats->maxg, g);
     if (nn) atomicOr(&stats->nan_flag, 1u);
   }
+}
+
+template <int DT, int EPL>
+__global__ void __launch_bounds__(32 * RANK_WARPS) rank_warp_kernel(
+    const void* __restrict__ values, int64_t ld_in, int n, int64_t m, int64_t ld,
+    uint16_t* __restrict__ perm, uint16_t* __restrict__ rank, uint16_t* __restrict__ srank,
+    int64_t* __restrict__ T, int32_t* __restrict__ ndist, int32_t* __restrict__ maxg,
+    double* __restrict__ rs64, float2* __restrict__ rsff, ktau_stats* __restrict__ stats) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row = (int64_t)blockIdx.x * RANK_WARPS + wid;
+  unsigned long long tsum = 0;
+  int gmax = 0;
+  unsigned nan_seen = 0;
+  if (row < m)
+    rank_warp_row<DT, EPL>(values, row * ld_in, n, ld, row, perm, rank, srank, T, ndist, maxg,
+                           rs64, rsff, tsum, gmax, nan_seen, lane);
+  rank_warp_stats(tsum, gmax, nan_seen, stats);
+}
+
+// Batched form for the variables of datasets with n <= 256: one warp per variable, the dataset
+// found from the prefix of row counts; variables of longer datasets are left to batch_rank_kernel.
+__global__ void __launch_bounds__(32 * RANK_WARPS) batch_rank_warp_kernel(
+    const ktau_bds* __restrict__ ds, int count, const int64_t* __restrict__ row_prefix,
+    int64_t total_rows, ktau_stats* __restrict__ stats) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * RANK_WARPS + wid;
+  unsigned long long tsum = 0;
+  int gmax = 0;
+  unsigned nan_seen = 0;
+  if (r < total_rows) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // largest d with row_prefix[d] <= r
+      const int mid = (lo + hi + 1) >> 1;
+      if (row_prefix[mid] <= r)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const ktau_bds& D = ds[lo];
+    const int64_t row = r - row_prefix[lo];
+    const int n = (int)D.n;
+    if (n <= 256) {
+      const bool f32 = D.dtype == KTAU_F32;
+#define KTAU_BATCH_WARP_ROW(EPL)                                                                 \
+  if (f32)                                                                                       \
+    rank_warp_row<KTAU_F32, EPL>(D.values, row * D.ld_in, n, D.ld, row, D.perm, D.rank, D.srank, \
+                                 D.T, D.ndist, D.maxg, D.rs64, D.rsff, tsum, gmax, nan_seen,     \
+                                 lane);                                                          \
+  else                                                                                           \
+    rank_warp_row<KTAU_I32, EPL>(D.values, row * D.ld_in, n, D.ld, row, D.perm, D.rank, D.srank, \
+                                 D.T, D.ndist, D.maxg, D.rs64, D.rsff, tsum, gmax, nan_seen,     \
+                                 lane);
+      if (n <= 32) {
+        KTAU_BATCH_WARP_ROW(1)
+      } else if (n <= 64) {
+        KTAU_BATCH_WARP_ROW(2)
+      } else if (n <= 128) {
+        KTAU_BATCH_WARP_ROW(4)
+      } else {
+        KTAU_BATCH_WARP_ROW(8)
+      }
+#undef KTAU_BATCH_WARP_ROW
+    }
+  }
+  rank_warp_stats(tsum, gmax, nan_seen, stats);
 }
 
 template <int DT>
@@ -365,6 +433,7 @@ __global__ void __launch_bounds__(256) batch_rank_kernel(const ktau_bds* __restr
       hi = mid - 1;
   }
   const ktau_bds& D = ds[lo];
+  if (D.n <= 256) return;  // ranked by batch_rank_warp_kernel
   const int64_t row = r - row_prefix[lo];
   int np2 = 32;
   while (np2 < D.n) np2 <<= 1;
@@ -387,8 +456,16 @@ ktau_status ktau_launch_batch_rank(const ktau_bds* ds, int count, const int64_t*
   KTAU_CUDA(cudaFuncSetAttribute(batch_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   if (total_rows > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "too many rows in one batch");
-  KTAU_TRACE("batch_rank_kernel", st);
-  batch_rank_kernel<<<(unsigned)total_rows, 256, smem, st>>>(ds, count, row_prefix, stats);
+  {
+    KTAU_TRACE("batch_rank_warp_kernel", st);
+    batch_rank_warp_kernel<<<(unsigned)((total_rows + RANK_WARPS - 1) / RANK_WARPS),
+                             32 * RANK_WARPS, 0, st>>>(ds, count, row_prefix, total_rows, stats);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  if (max_n > 256) {
+    KTAU_TRACE("batch_rank_kernel", st);
+    batch_rank_kernel<<<(unsigned)total_rows, 256, smem, st>>>(ds, count, row_prefix, stats);
+  }
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }
