@@ -1,0 +1,82 @@
+"""Edge cases at the limits of the ABI: the longest vectors (n = KTAU_MAX_N) on the merge path,
+a large matrix (300,000 variables) with a pair range at the end of the triangle on both paths
+(64-bit pair indices, tile walks far from the origin), and inputs just beyond the limits."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import assert_tau32, assert_tau64, oracle_full, oracle_sampled
+from synthetic import uniform_ties
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ktau():
+    from paper_1704_03767_gb300 import build as kb
+
+    kb.build()
+    import paper_1704_03767_gb300 as k
+
+    k.load()
+    return k
+
+
+def test_longest_vectors_merge_path(ktau):
+    n = 16384  # KTAU_MAX_N
+    X = uniform_ties(5, n, tie_frac=0.3, seed=31)
+    X[1] = X[0]
+    X[2] = -X[0]
+    Xd = torch.from_numpy(X).cuda()
+    res = ktau.allpairs(Xd, count_bits=64, options={"path": 1})
+    torch.cuda.synchronize()
+    ktau.ktau_device_status()
+    got = {k: v.cpu().numpy() for k, v in res.items() if isinstance(v, torch.Tensor)}
+    res["ranked"].free()
+    ref = oracle_full(X)
+    assert np.array_equal(got["S"], ref["S"])
+    assert np.array_equal(got["n3"], ref["n3"])
+    assert_tau64(got["tau64"], ref["tau"])
+    assert_tau32(got["tau32"], ref["tau"])
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_large_matrix_tail_range(ktau, path):
+    m, n = 300_000, 32
+    X = uniform_ties(m, n, tie_frac=0.3, seed=32)
+    X[m - 1] = X[m - 2]
+    Xd = torch.from_numpy(X).cuda()
+    R = ktau.ktau_rank_prepare(Xd)
+    P = m * (m - 1) // 2
+    lo, hi = P - 70_000, P
+    tau64 = torch.empty(hi - lo, dtype=torch.float64, device="cuda")
+    tau32 = torch.empty(hi - lo, dtype=torch.float32, device="cuda")
+    S = torch.empty(hi - lo, dtype=torch.int64, device="cuda")
+    n3 = torch.empty(hi - lo, dtype=torch.int64, device="cuda")
+    ktau.ktau_allpairs(R, lo, hi, tau64, tau32, S, n3, 64, {"path": path})
+    torch.cuda.synchronize()
+    ktau.ktau_device_status()
+    R.free()
+    g = np.random.default_rng(33)
+    ps = np.unique(np.concatenate([g.integers(lo, hi, 400), [lo, hi - 1]]))
+    rS, rn3, rtau = oracle_sampled(X, ps)
+    idx = ps - lo
+    assert np.array_equal(S.cpu().numpy()[idx], rS)
+    assert np.array_equal(n3.cpu().numpy()[idx], rn3)
+    assert_tau64(tau64.cpu().numpy()[idx], rtau)
+    assert_tau32(tau32.cpu().numpy()[idx], rtau)
+
+
+def test_beyond_limits_rejected(ktau):
+    X = torch.zeros((2, 16385), dtype=torch.float32, device="cuda")  # n > KTAU_MAX_N
+    with pytest.raises(ktau.KtauError):
+        ktau.ktau_rank_prepare(X)
+    X = torch.zeros((3, 1), dtype=torch.float32, device="cuda")  # n < 2
+    with pytest.raises(ktau.KtauError):
+        ktau.ktau_rank_prepare(X)
+    Xd = torch.from_numpy(uniform_ties(10, 3000, seed=34)).cuda()
+    R = ktau.ktau_rank_prepare(Xd)
+    out = torch.empty(45, dtype=torch.int32, device="cuda")
+    with pytest.raises(ktau.KtauError):  # sign contraction: n <= 2048
+        ktau.ktau_allpairs(R, 0, 45, None, None, out, None, 32, {"path": 2})
+    R.free()
