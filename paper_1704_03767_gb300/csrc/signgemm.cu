@@ -497,7 +497,7 @@ struct ContractArgs {
   int64_t wS;              // tri: super-tiles per side
   int64_t wG;              // tri: traversal groups per side
   int64_t ncb;             // rect: column blocks of BM
-  int bnr;                 // output rows per unit: 256, or 128 for short query batches
+  int bnr;                 // output rows per unit: 256, or 128 / 64 for short query batches
   int afmt;                // kind::f8f6f4 operand format: 0 = E4M3, 5 = E2M1 (FP4)
   // Permutation test (exceed != nullptr): count |S| >= |s_obs[k]| into exceed[k] instead of
   // storing tau / S / n_3 (triangle, single matrix only).
@@ -1312,8 +1312,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          // FP4 boxes count their packed bytes (half the shared-memory footprint)
-          mbar_expect_tx(FULL(stage), (uint32_t)(A_BYTES + a.bnr * BKB) >> (a.afmt == 5 ? 1 : 0));
+          // one or two 128-row boxes of rows; FP4 boxes count their packed bytes (half the
+          // shared-memory footprint)
+          mbar_expect_tx(FULL(stage),
+                         (uint32_t)(A_BYTES + (a.bnr > BM ? 2 : 1) * BM * BKB) >> (a.afmt == 5 ? 1 : 0));
           const int kx = (int)(kb * BKB);
           tma_load_2d(sa, &tmA, kx, t.ta, FULL(stage), pol);
           tma_load_2d(sb, &tmB, kx, t.tb, FULL(stage), pol);
@@ -1866,15 +1868,24 @@ ktau_status ktau_signgemm_ties(ktau_ranked* R, cudaStream_t ss) {
   R->tie_bytes = (size_t)(R->tie_cap > 0 ? R->tie_cap : 1) * 4;
   // inverted index for the bucket form of n_3 (built when the counts fit 32-bit offsets)
   const bool buckets = R->stats.T_sum > 0 && R->stats.T_sum < (1ll << 31) && R->m < (1ll << 31);
-  if (ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) != KTAU_OK ||
-      ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) != KTAU_OK)
-    return KTAU_ENOMEM;
-  if (buckets) {
+  bool ok = ktau_dmalloc((void**)&R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t)) == KTAU_OK &&
+            ktau_dmalloc((void**)&R->tie_pairs, R->tie_bytes) == KTAU_OK;
+  if (ok && buckets) {
     R->bkt_var_bytes = (size_t)R->stats.T_sum * sizeof(int32_t);
-    if (ktau_dmalloc((void**)&R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t)) != KTAU_OK ||
-        ktau_dmalloc((void**)&R->bkt_var, R->bkt_var_bytes) != KTAU_OK ||
-        ktau_dmalloc((void**)&R->bkt_stat, 4 * sizeof(unsigned long long)) != KTAU_OK)
-      return KTAU_ENOMEM;
+    ok = ktau_dmalloc((void**)&R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t)) == KTAU_OK &&
+         ktau_dmalloc((void**)&R->bkt_var, R->bkt_var_bytes) == KTAU_OK &&
+         ktau_dmalloc((void**)&R->bkt_stat, 4 * sizeof(unsigned long long)) == KTAU_OK;
+  }
+  if (!ok) {  // give back what was allocated; a later call starts again
+    ktau_dfree(R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t));
+    ktau_dfree(R->tie_pairs, R->tie_bytes);
+    ktau_dfree(R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t));
+    ktau_dfree(R->bkt_var, R->bkt_var_bytes);
+    R->tie_off = nullptr;
+    R->tie_pairs = nullptr;
+    R->bkt_off = nullptr;
+    R->bkt_var = nullptr;
+    return KTAU_ENOMEM;
   }
   {
     KTAU_TRACE("ties_scan_kernel", ss);
@@ -1977,7 +1988,7 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.wS = 0;
   a.wG = 0;
   a.ncb = (D->m + BM - 1) / BM;
-  a.bnr = Q->m <= BM ? BM : BN;
+  a.bnr = Q->m <= 64 ? 64 : (Q->m <= BM ? BM : BN);  // MMA N: multiple of 16, up to 256
   a.s_obs = nullptr;
   a.exceed = nullptr;
   a.afmt = Q->obits == 4 ? 5 : 0;
