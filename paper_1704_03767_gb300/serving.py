@@ -9,9 +9,12 @@ budget still unreserved; each slot is a thread with its own CUDA stream that run
     host->device copy of the profiles, ktau_rank_prepare, ktau_query (exact tau-b against every
     database row + exact top-k by |tau|), device->host copy of the top-k
 
-so batches that arrive while others are on the GPU overlap with them. The result of a batch
-does not depend on what else is in flight: every kernel writes only that batch's buffers and the
-counts are exact integers formed into tau by one fixed epilogue.
+so batches that arrive while others are on the GPU overlap with them. When several batches are
+pending, consecutive ones (in arrival order, up to max_batch profiles and within the memory budget)
+are merged into one launch and their rows split back afterwards: under load this amortises the
+per-launch host work. The result of a batch does not depend on what else is in flight or merged
+with it: every query row is scored against the database on its own (exact integer counts formed
+into tau by one fixed epilogue, top-k per row).
 
 All computation is in libktau.so; this module is host-side scheduling only.
 """
@@ -79,7 +82,7 @@ class Admission:
 class QueryServer:
     def __init__(self, db: np.ndarray | torch.Tensor, k: int = 100, slots: int = 4,
                  mem_budget: int | None = None, keep_tau: bool = False, options=None,
-                 device: int = 0, max_batch: int = 512):
+                 device: int = 0, max_batch: int = 512, merge: bool = True):
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         dbt = torch.as_tensor(db).to(self.dev, dtype=torch.float32).contiguous()
@@ -100,6 +103,7 @@ class QueryServer:
         # Per-slot buffers for batches of up to max_batch profiles, allocated once: the request
         # path then allocates nothing but the batch's ranked handle (from the library's cache).
         self.max_batch = max_batch
+        self.merge = merge
         self.slot_buf = []
         for _ in range(slots):
             self.slot_buf.append({
@@ -164,12 +168,24 @@ class QueryServer:
                     self.cv.wait()
                 if not self.running and not self.pending:
                     return
-                r = self.pending[0]
-                need = self.footprint(r.queries.shape[0])
+                # The head request, plus the consecutive ones behind it that fit in one launch.
+                group = [self.pending[0]]
+                rows = group[0].queries.shape[0]
+                if self.merge and rows <= self.max_batch:
+                    for r in list(self.pending)[1:]:
+                        b = r.queries.shape[0]
+                        if rows + b > self.max_batch:
+                            break
+                        group.append(r)
+                        rows += b
+                need = self.footprint(rows)
+                if need > self.admission.budget and len(group) > 1:
+                    group, rows = group[:1], group[0].queries.shape[0]
+                    need = self.footprint(rows)
                 try:
                     slot = self.admission.try_admit(need)
                 except ValueError as e:
-                    self.pending.popleft()
+                    r = self.pending.popleft()
                     r.error = str(e)
                     r.finished = time.perf_counter()
                     r.done.set()
@@ -177,9 +193,12 @@ class QueryServer:
                 if slot is None:
                     self.cv.wait()
                     continue
-                self.pending.popleft()
-                r.reserved, r.slot, r.admitted = need, slot, time.perf_counter()
-                self.slot_q[slot].append(r)
+                now = time.perf_counter()
+                for r in group:
+                    self.pending.popleft()
+                    r.slot, r.admitted = slot, now
+                group[0].reserved = need
+                self.slot_q[slot].append(group)
                 self.cv.notify_all()
 
     def _slot(self, i: int):
@@ -191,30 +210,40 @@ class QueryServer:
                     self.cv.wait()
                 if not self.slot_q[i]:
                     return
-                r = self.slot_q[i].popleft()
+                group = self.slot_q[i].popleft()
             try:
-                self._run(r, st, i)
-            except Exception as e:  # reported on the request; the server keeps running
-                r.error = repr(e)
-            r.finished = time.perf_counter()
+                self._run(group, st, i)
+            except Exception as e:  # reported on the requests; the server keeps running
+                for r in group:
+                    r.error = repr(e)
+            now = time.perf_counter()
             with self.cv:
-                self.admission.release(r.slot, r.reserved)
-                self.timeline.append((r.rid, r.slot, r.admitted, r.finished))
+                self.admission.release(i, group[0].reserved)
+                for r in group:
+                    r.finished = now
+                    self.timeline.append((r.rid, r.slot, r.admitted, r.finished))
                 self.cv.notify_all()
-            r.done.set()
+            for r in group:
+                r.done.set()
 
-    def _run(self, r: Request, st: torch.cuda.Stream, slot: int):
-        b = r.queries.shape[0]
+    def _run(self, group, st: torch.cuda.Stream, slot: int):
+        sizes = [r.queries.shape[0] for r in group]
+        b = sum(sizes)
         with torch.cuda.stream(st):
             if b <= self.max_batch:
                 buf = self.slot_buf[slot]
-                buf["qh"][:b].numpy()[...] = r.queries
+                qh = buf["qh"][:b].numpy()
+                o = 0
+                for r, sz in zip(group, sizes):
+                    qh[o:o + sz] = r.queries
+                    o += sz
                 qd = buf["qd"][:b]
                 qd.copy_(buf["qh"][:b], non_blocking=True)
                 S, idx, tk = buf["S"][:b], buf["idx"][:b], buf["tk"][:b]
                 idx_h, tk_h = buf["idx_h"][:b], buf["tk_h"][:b]
-            else:  # larger than the slot buffers: buffers of its own
-                qd = torch.from_numpy(r.queries).pin_memory().to(self.dev, non_blocking=True)
+            else:  # one request larger than the slot buffers: buffers of its own
+                qd = torch.from_numpy(group[0].queries).pin_memory().to(self.dev,
+                                                                         non_blocking=True)
                 S = torch.empty((b, self.m_db), dtype=torch.int32, device=self.dev)
                 idx = torch.empty((b, self.k), dtype=torch.int32, device=self.dev)
                 tk = torch.empty((b, self.k), dtype=torch.float64, device=self.dev)
@@ -227,10 +256,13 @@ class QueryServer:
             idx_h.copy_(idx, non_blocking=True)
             tk_h.copy_(tk, non_blocking=True)
             R.free_on(st)  # waits for this slot's stream only
-        # copies: the slot's pinned buffers are reused by its next batch
-        r.topk_idx = idx_h.numpy().copy()
-        r.topk_tau = tk_h.numpy().copy()
-        r.tau = tau
+        # copies: the slot's pinned buffers are reused by its next launch
+        o = 0
+        for r, sz in zip(group, sizes):
+            r.topk_idx = idx_h[o:o + sz].numpy().copy()
+            r.topk_tau = tk_h[o:o + sz].numpy().copy()
+            r.tau = tau[o:o + sz] if tau is not None else None
+            o += sz
 
     def stop(self):
         with self.cv:

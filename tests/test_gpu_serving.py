@@ -37,7 +37,8 @@ def test_results_alone_equal_results_in_the_mix(ktau):
         assert r.error is None, r.error
         ref.append((r.topk_idx.copy(), r.topk_tau.copy()))
     alone.stop()
-    # in the mix: 4 slots, everything submitted at once
+    # in the mix: 4 slots, everything submitted at once; pending batches are merged into
+    # shared launches (rows of several requests in one contraction) ...
     mix = QueryServer(D, k=25, slots=4)
     reqs = [mix.submit(q) for q in batches]
     for r in reqs:
@@ -46,11 +47,23 @@ def test_results_alone_equal_results_in_the_mix(ktau):
     for r, (ri, rt) in zip(reqs, ref):
         assert np.array_equal(r.topk_idx, ri)
         assert np.array_equal(r.topk_tau.view(np.int64), rt.view(np.int64))
-    # continuous batching: some batches ran concurrently
-    tl = sorted(mix.timeline, key=lambda t: t[2])
-    overlaps = sum(1 for a, b in zip(tl, tl[1:]) if b[2] < a[3])
-    assert overlaps > 0
+    launches = {}
+    for rid, slot, adm, fin in mix.timeline:
+        launches.setdefault((slot, adm), []).append(rid)
+    assert max(len(v) for v in launches.values()) > 1  # some launch served several requests
     mix.stop()
+    # ... and without merging, batches run concurrently on different slots.
+    sep = QueryServer(D, k=25, slots=4, merge=False)
+    reqs2 = [sep.submit(q) for q in batches]
+    for r, (ri, rt) in zip(reqs2, ref):
+        r.done.wait()
+        assert r.error is None, r.error
+        assert np.array_equal(r.topk_idx, ri)
+        assert np.array_equal(r.topk_tau.view(np.int64), rt.view(np.int64))
+    tl = sorted(sep.timeline, key=lambda t: t[2])
+    overlaps = sum(1 for a, b in zip(tl, tl[1:]) if b[2] < a[3] and b[1] != a[1])
+    assert overlaps > 0
+    sep.stop()
     # exact top-k against the oracle for one small batch
     i = int(np.argmin(sizes))
     o = oracle.query_topk(batches[i], D, 25)
