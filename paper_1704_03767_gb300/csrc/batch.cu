@@ -62,6 +62,13 @@ struct ktau_batch {
   std::vector<std::pair<void*, size_t>> allocs;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // Groups run on kLanes streams forked from the caller's stream after the rank transform and
+  // joined back at the end, so that groups too small to fill the GPU overlap (every group owns its
+  // operands, tie lists and outputs).
+  static constexpr int kLanes = 4;
+  cudaStream_t lane[kLanes] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kLanes] = {};
 };
 
 static ktau_status batch_alloc(ktau_batch* B, void** p, size_t bytes) {
@@ -95,6 +102,11 @@ extern "C" ktau_status ktau_batch_free(ktau_batch* B) {
   cudaDeviceSynchronize();
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
+  for (int l = 0; l < ktau_batch::kLanes; ++l) {
+    if (B->lane[l]) cudaStreamDestroy(B->lane[l]);
+    if (B->join[l]) cudaEventDestroy(B->join[l]);
+  }
+  if (B->fork) cudaEventDestroy(B->fork);
   for (auto& a : B->allocs) ktau_dfree(a.first, a.second);
   delete B;
   return KTAU_OK;
@@ -295,6 +307,15 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     return s;
   }
   KTAU_CUDA(cudaMemset(B->d_stats, 0, sizeof(ktau_stats)));
+  cudaError_t e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+  for (int l = 0; l < ktau_batch::kLanes && e == cudaSuccess; ++l) {
+    e = cudaStreamCreateWithFlags(&B->lane[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->join[l], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    ktau_batch_free(B);
+    return ktau_cuda_fail(e, "batch streams");
+  }
   *out = B;
   return KTAU_OK;
 }
@@ -305,11 +326,16 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
   ktau_status s = ktau_launch_batch_rank(B->d_ds, B->count, B->d_row_prefix, B->total_rows,
                                          B->max_n, B->d_stats, st);
   if (s != KTAU_OK) return s;
+  // fork: every lane waits for the ranks
+  KTAU_CUDA(cudaEventRecord(B->fork, st));
+  for (int l = 0; l < ktau_batch::kLanes; ++l) KTAU_CUDA(cudaStreamWaitEvent(B->lane[l], B->fork, 0));
+  int gi = 0;
   for (GroupPlan& G : B->g) {
     if (G.ids.empty() || s != KTAU_OK) continue;
+    cudaStream_t ls = B->lane[gi++ % ktau_batch::kLanes];
     if (G.kind != kContract) {
       s = ktau_launch_batch_merge(B->d_ds, G.d_ids, (int)G.ids.size(), G.d_tile_prefix, G.tiles,
-                                  G.max_n, G.kind == kMergeCta ? 1 : 0, st);
+                                  G.max_n, G.kind == kMergeCta ? 1 : 0, ls);
       continue;
     }
     ktau_sg_group g;
@@ -334,7 +360,14 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
     g.sgn = G.sgn;
     g.stride = G.stride;
     g.tmap = G.tmap;
-    s = ktau_signgemm_batch(g, st);
+    s = ktau_signgemm_batch(g, ls);
+  }
+  // join: the caller's stream waits for every lane (also after an error, so that no lane is left
+  // forked, e.g. inside a graph capture)
+  for (int l = 0; l < ktau_batch::kLanes; ++l) {
+    cudaError_t e = cudaEventRecord(B->join[l], B->lane[l]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B->join[l], 0);
+    if (e != cudaSuccess && s == KTAU_OK) s = ktau_cuda_fail(e, "batch join");
   }
   return s;
 }
