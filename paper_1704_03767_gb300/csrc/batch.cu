@@ -65,7 +65,8 @@ struct ktau_batch {
   // Groups run on kLanes streams forked from the caller's stream after the rank transform and
   // joined back at the end, so that groups too small to fill the GPU overlap (every group owns its
   // operands, tie lists and outputs).
-  static constexpr int kLanes = 4;
+  static constexpr int kLanes = 8;
+  std::vector<int> lane_of;  // lane of each group: largest groups first, each to the least loaded
   cudaStream_t lane[kLanes] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kLanes] = {};
@@ -316,6 +317,31 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     ktau_batch_free(B);
     return ktau_cuda_fail(e, "batch streams");
   }
+  // Lane assignment: work estimate of a group = contraction tiles x K blocks (+ merge tiles x n),
+  // largest first to the least loaded lane.
+  {
+    std::vector<std::pair<double, int>> work;
+    for (size_t gi = 0; gi < B->g.size(); ++gi) {
+      const GroupPlan& G = B->g[gi];
+      double w = 0;
+      if (G.kind == kContract)
+        w = (double)G.units * (double)G.stride + (double)G.rows * (double)G.stride;
+      else
+        w = (double)G.tiles * (double)G.max_n * 64.0;
+      work.push_back({w, (int)gi});
+    }
+    std::sort(work.begin(), work.end(), [](const std::pair<double, int>& a,
+                                           const std::pair<double, int>& b) { return a.first > b.first; });
+    B->lane_of.assign(B->g.size(), 0);
+    double load[ktau_batch::kLanes] = {0};
+    for (const auto& wi : work) {
+      int best = 0;
+      for (int l = 1; l < ktau_batch::kLanes; ++l)
+        if (load[l] < load[best]) best = l;
+      load[best] += wi.first;
+      B->lane_of[wi.second] = best;
+    }
+  }
   *out = B;
   return KTAU_OK;
 }
@@ -329,10 +355,10 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
   // fork: every lane waits for the ranks
   KTAU_CUDA(cudaEventRecord(B->fork, st));
   for (int l = 0; l < ktau_batch::kLanes; ++l) KTAU_CUDA(cudaStreamWaitEvent(B->lane[l], B->fork, 0));
-  int gi = 0;
-  for (GroupPlan& G : B->g) {
+  for (size_t gi = 0; gi < B->g.size(); ++gi) {
+    GroupPlan& G = B->g[gi];
     if (G.ids.empty() || s != KTAU_OK) continue;
-    cudaStream_t ls = B->lane[gi++ % ktau_batch::kLanes];
+    cudaStream_t ls = B->lane[B->lane_of[gi]];
     if (G.kind != kContract) {
       s = ktau_launch_batch_merge(B->d_ds, G.d_ids, (int)G.ids.size(), G.d_tile_prefix, G.tiles,
                                   G.max_n, G.kind == kMergeCta ? 1 : 0, ls);
