@@ -443,7 +443,9 @@ def run_ours(args):
     path_used = {1: "merge", 2: "signgemm"}[path_id]
 
     def step(ev=None):
-        R = ktau.ktau_rank_prepare(Xd, stream)
+        # The statistics (NaN flag, tie counts) are read by ktau_allpairs, so the sign expansion
+        # is enqueued while the rank transform finishes.
+        R = ktau.ktau_rank_prepare_async(Xd, stream)
         if path_id == 2:
             ktau.ktau_prepare_signs(R, stream)  # sign expansion + tie lists (part of the step)
         if ev:
@@ -539,7 +541,7 @@ def run_ours(args):
         for _ in range(args.steps):
             flush.zero_()
             a0.record(stream)
-            R = ktau.ktau_rank_prepare(Xd, stream)
+            R = ktau.ktau_rank_prepare_async(Xd, stream)
             if path_id == 2:
                 ktau.ktau_prepare_signs(R, stream)
             ktau.ktau_allpairs(R, 0, P, None, tau32, S, None, 32, opts_a, stream)

@@ -109,6 +109,17 @@ int32_t ktau_abi_version(void);
 ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int64_t n, int64_t ld,
                               void* stream, ktau_ranked** out);
 
+/* ktau_rank_prepare without the synchronisation: the NaN flag and the tie statistics are copied
+ * to pinned host memory behind an event on `stream`, and the first call that needs them
+ * (ktau_allpairs, ktau_allpairs_host, ktau_allpairs_path, ktau_query, ktau_permutation_exceed)
+ * waits for that copy, so work enqueued in between (ktau_prepare_signs) overlaps the rank
+ * transform's completion. A NaN is reported by that first call (KTAU_ENAN, and again by every
+ * later call on the handle). `values` must stay valid until the rank transform has run on
+ * `stream`. The first use must not race with another call on the same handle. Errors as
+ * ktau_rank_prepare except ENAN. */
+ktau_status ktau_rank_prepare_async(const void* values, ktau_dtype dt, int64_t m, int64_t n,
+                                    int64_t ld, void* stream, ktau_ranked** out);
+
 /* Releases a handle (NULL is accepted). Synchronises the device before freeing. */
 ktau_status ktau_ranked_free(ktau_ranked* R);
 /* Releases a handle whose every use was enqueued on `stream`: synchronises that stream only

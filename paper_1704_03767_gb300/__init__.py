@@ -32,6 +32,7 @@ from .binding import (  # noqa: F401
     ktau_query,
     ktau_query_scratch_bytes,
     ktau_rank_prepare,
+    ktau_rank_prepare_async,
     ktau_ranked_export,
     ktau_tie_counts,
     ktau_trace_collect,

@@ -58,6 +58,8 @@ _SIGS = {
     "ktau_abi_version": ([], _i32),
     "ktau_rank_prepare": ([_vp, ctypes.c_int, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)],
                           ctypes.c_int),
+    "ktau_rank_prepare_async": ([_vp, ctypes.c_int, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)],
+                                ctypes.c_int),
     "ktau_ranked_free": ([_vp], ctypes.c_int),
     "ktau_ranked_free_on": ([_vp, _vp], ctypes.c_int),
     "ktau_ranked_shape": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
@@ -174,6 +176,17 @@ class Ranked:
 
 def ktau_rank_prepare(values: torch.Tensor, stream=None) -> Ranked:
     """Rank transform of every row of a CUDA float32/int32 matrix (row-major, unit column stride)."""
+    return _rank_prepare(values, stream, "ktau_rank_prepare")
+
+
+def ktau_rank_prepare_async(values: torch.Tensor, stream=None) -> Ranked:
+    """ktau_rank_prepare without synchronising the stream: a NaN is reported (KtauError, status 2)
+    by the first call that uses the handle. `values` must stay alive until the stream has run
+    the rank transform."""
+    return _rank_prepare(values, stream, "ktau_rank_prepare_async")
+
+
+def _rank_prepare(values: torch.Tensor, stream, fn: str) -> Ranked:
     if values.dim() != 2 or not values.is_cuda:
         raise ValueError("values must be a 2-D CUDA tensor")
     if values.dtype == torch.float32:
@@ -186,8 +199,8 @@ def ktau_rank_prepare(values: torch.Tensor, stream=None) -> Ranked:
         raise ValueError("values must have unit column stride")
     m, n = values.shape
     h = ctypes.c_void_p()
-    _check(load().ktau_rank_prepare(values.data_ptr(), dt, m, n, values.stride(0), _stream(stream),
-                                    ctypes.byref(h)))
+    _check(getattr(load(), fn)(values.data_ptr(), dt, m, n, values.stride(0), _stream(stream),
+                               ctypes.byref(h)))
     return Ranked(h.value, m, n, values.device)
 
 

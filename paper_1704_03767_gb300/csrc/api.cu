@@ -142,8 +142,48 @@ const char* ktau_status_string(ktau_status s) {
 
 int32_t ktau_abi_version(void) { return KTAU_ABI_VERSION; }
 
-ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int64_t n, int64_t ld,
-                              void* stream, ktau_ranked** out) {
+}  // extern "C"
+
+// Pinned host slots for the statistics of asynchronously prepared handles (one page-locked
+// allocation made on first use, slots recycled when their handle releases them).
+namespace {
+constexpr int kPinSlots = 4096;
+std::mutex g_pin_mu;
+ktau_stats* g_pin = nullptr;
+std::vector<int> g_pin_free;
+
+ktau_stats* pin_take() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (!g_pin) {
+    if (cudaHostAlloc((void**)&g_pin, kPinSlots * sizeof(ktau_stats), cudaHostAllocPortable) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      g_pin = nullptr;
+      return nullptr;
+    }
+    for (int i = kPinSlots - 1; i >= 0; --i) g_pin_free.push_back(i);
+  }
+  if (g_pin_free.empty()) return nullptr;
+  const int i = g_pin_free.back();
+  g_pin_free.pop_back();
+  return g_pin + i;
+}
+
+void pin_give(ktau_stats* p) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back((int)(p - g_pin));
+}
+
+// Releases the pinned slot and event of a handle whose copy has completed (or never started).
+void stats_release(ktau_ranked* R) {
+  if (R->stats_pin) pin_give(R->stats_pin);
+  if (R->stats_ev) cudaEventDestroy(R->stats_ev);
+  R->stats_pin = nullptr;
+  R->stats_ev = nullptr;
+}
+
+ktau_status rank_prepare_impl(const void* values, ktau_dtype dt, int64_t m, int64_t n,
+                              int64_t ld, void* stream, bool async, ktau_ranked** out) {
   if (!out) return ktau_fail(KTAU_EINVAL, "out is NULL");
   *out = nullptr;
   if (!values) return ktau_fail(KTAU_EINVAL, "values is NULL");
@@ -188,7 +228,19 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
     s = ktau_cuda_fail(e, "cudaMemsetAsync");
   }
   if (s == KTAU_OK) s = ktau_launch_rank(values, (int)dt, m, n, ld, R, st);
-  if (s == KTAU_OK) {
+  ktau_stats* pin = (s == KTAU_OK && async) ? pin_take() : nullptr;
+  if (pin) {
+    R->stats_pin = pin;
+    if ((e = cudaEventCreateWithFlags(&R->stats_ev, cudaEventDisableTiming)) != cudaSuccess) {
+      R->stats_ev = nullptr;
+      s = ktau_cuda_fail(e, "cudaEventCreate");
+    } else if ((e = cudaMemcpyAsync(pin, R->stats_dev, sizeof(ktau_stats),
+                                    cudaMemcpyDeviceToHost, st)) != cudaSuccess) {
+      s = ktau_cuda_fail(e, "cudaMemcpyAsync(stats)");
+    } else if ((e = cudaEventRecord(R->stats_ev, st)) != cudaSuccess) {
+      s = ktau_cuda_fail(e, "cudaEventRecord(stats)");
+    }
+  } else if (s == KTAU_OK) {
     if ((e = cudaMemcpyAsync(&R->stats, R->stats_dev, sizeof(ktau_stats), cudaMemcpyDeviceToHost,
                              st)) != cudaSuccess)
       s = ktau_cuda_fail(e, "cudaMemcpyAsync(stats)");
@@ -199,6 +251,7 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
   }
   if (s != KTAU_OK) {
     cudaStreamSynchronize(st);
+    stats_release(R);
     ktau_dfree(R->block, R->block_bytes);
     free(R);
     return s;
@@ -207,9 +260,37 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
   return KTAU_OK;
 }
 
+}  // namespace
+
+ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int64_t n, int64_t ld,
+                              void* stream, ktau_ranked** out) {
+  return rank_prepare_impl(values, dt, m, n, ld, stream, false, out);
+}
+
+ktau_status ktau_rank_prepare_async(const void* values, ktau_dtype dt, int64_t m, int64_t n,
+                                    int64_t ld, void* stream, ktau_ranked** out) {
+  return rank_prepare_impl(values, dt, m, n, ld, stream, true, out);
+}
+
+ktau_status ktau_ranked_stats(const ktau_ranked* Rc) {
+  if (!Rc) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  ktau_ranked* R = const_cast<ktau_ranked*>(Rc);
+  if (R->stats_pin) {
+    const cudaError_t e = cudaEventSynchronize(R->stats_ev);
+    if (e != cudaSuccess) return ktau_cuda_fail(e, "statistics copy");
+    R->stats = *R->stats_pin;
+    stats_release(R);
+  }
+  if (R->stats.nan_flag) return ktau_fail(KTAU_ENAN, "NaN in the input matrix");
+  return KTAU_OK;
+}
+
+extern "C" {
+
 ktau_status ktau_ranked_free(ktau_ranked* R) {
   if (!R) return KTAU_OK;
   cudaDeviceSynchronize();  // no kernel may still use the handle's memory when it is recycled
+  stats_release(R);
   if (R->block) ktau_dfree(R->block, R->block_bytes);
   ktau_signgemm_release(R);
   free(R);
@@ -219,6 +300,7 @@ ktau_status ktau_ranked_free(ktau_ranked* R) {
 ktau_status ktau_ranked_free_on(ktau_ranked* R, void* stream) {
   if (!R) return KTAU_OK;
   KTAU_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  stats_release(R);
   if (R->block) ktau_dfree(R->block, R->block_bytes);
   ktau_signgemm_release(R);
   free(R);
@@ -300,6 +382,7 @@ extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uin
   if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
   ktau_status s = ktau_check_counts(R->n, count_bits);
   if (s != KTAU_OK) return s;
+  if ((s = ktau_ranked_stats(R)) != KTAU_OK) return s;
   if ((s = ktau_check_options(opt)) != KTAU_OK) return s;
   const uint64_t P = (uint64_t)(R->m * (R->m - 1) / 2);
   if (p_begin > p_end || p_end > P)
@@ -332,6 +415,7 @@ extern "C" ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_optio
   if (!R || !path) return ktau_fail(KTAU_EINVAL, "NULL argument");
   ktau_status s = ktau_check_options(opt);
   if (s != KTAU_OK) return s;
+  if ((s = ktau_ranked_stats(R)) != KTAU_OK) return s;
   *path = ktau_choose_path(R, opt);
   return KTAU_OK;
 }
@@ -425,6 +509,7 @@ extern "C" ktau_status ktau_allpairs_host(const ktau_ranked* R, uint64_t p_begin
   if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
   ktau_status s = ktau_check_counts(R->n, count_bits);
   if (s != KTAU_OK) return s;
+  if ((s = ktau_ranked_stats(R)) != KTAU_OK) return s;
   if ((s = ktau_check_options(opt)) != KTAU_OK) return s;
   const uint64_t P = (uint64_t)(R->m * (R->m - 1) / 2);
   if (p_begin > p_end || p_end > P) return ktau_fail(KTAU_EINVAL, "pair range outside the triangle");

@@ -8,8 +8,8 @@
 // tiles and units. Contraction groups stack their sign expansions into one operand tensor (one
 // TMA descriptor per group, each dataset using only its own K blocks).
 //
-// Run (ktau_batch_run): rank kernel over every row of every dataset; per contraction group:
-// sign expansion, tie lists, contraction, joint ties; one launch per merge group.
+// Run (ktau_batch_run): per group, on the group's lane: rank kernel over the group's rows; per
+// contraction group: sign expansion, tie lists, contraction, joint ties; one launch per merge group.
 // Nothing is allocated and nothing waits on the host, so the sequence can be graph-captured.
 #include <algorithm>
 #include <cstring>
@@ -54,7 +54,6 @@ struct ktau_batch {
   int device = 0;
   std::vector<ktau_bds> hds;  // workspace order
   ktau_bds* d_ds = nullptr;
-  int64_t* d_row_prefix = nullptr;
   int64_t total_rows = 0, max_n = 0;
   uint64_t pairs = 0;
   std::vector<GroupPlan> g;  // in workspace order
@@ -62,8 +61,7 @@ struct ktau_batch {
   std::vector<std::pair<void*, size_t>> allocs;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // Groups run on kLanes streams forked from the caller's stream after the rank transform and
-  // joined back at the end, so that groups too small to fill the GPU overlap (every group owns its
+  // Groups run on kLanes streams forked from the caller's stream and joined back at the end, so that groups too small to fill the GPU overlap (every group owns its
   // operands, tie lists and outputs).
   static constexpr int kLanes = 8;
   std::vector<int> lane_of;  // lane of each group: largest groups first, each to the least loaded
@@ -230,9 +228,10 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     G.row0 = row_prefix[G.ids.front()];
     std::vector<int64_t> rp(1, 0), up(1, 0), jp(1, 0), tp(1, 0), bp(1, 0);
     int64_t kpad_max = 0;
+    for (int k : G.ids) G.max_n = std::max<int64_t>(G.max_n, B->hds[k].n);
+    const int erows = ktau_expand_rows(G.max_n);
     for (int k : G.ids) {
       ktau_bds& D = B->hds[k];
-      G.max_n = std::max<int64_t>(G.max_n, D.n);
       rp.push_back(rp.back() + D.m);
       if (G.kind != kContract) {
         D.tq = G.kind == kMergeWarp ? kMergeTq : 4;
@@ -240,7 +239,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
         tp.push_back(tp.back() + D.w * (D.w + 1) / 2);
       } else {
         D.esize = (int)(G.key / 64) == 4 ? 2 : 1;  // BF16 takes 2 bytes in shared memory
-        bp.push_back(bp.back() + (D.m + KTAU_EXPAND_ROWS - 1) / KTAU_EXPAND_ROWS);
+        bp.push_back(bp.back() + (D.m + erows - 1) / erows);
         const int64_t K = D.n * (D.n - 1) / 2;
         const int64_t K_pad = (K + 127) / 128 * 128;
         D.num_kb = K_pad * D.esize / 128;
@@ -302,7 +301,6 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     }
   }
   if ((s = batch_upload(B, &B->d_ds, B->hds)) != KTAU_OK ||
-      (s = batch_upload(B, &B->d_row_prefix, row_prefix)) != KTAU_OK ||
       (s = batch_alloc(B, (void**)&B->d_stats, sizeof(ktau_stats))) != KTAU_OK) {
     ktau_batch_free(B);
     return s;
@@ -349,16 +347,19 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
 extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
   if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  ktau_status s = ktau_launch_batch_rank(B->d_ds, B->count, B->d_row_prefix, B->total_rows,
-                                         B->max_n, B->d_stats, st);
-  if (s != KTAU_OK) return s;
-  // fork: every lane waits for the ranks
+  ktau_status s = KTAU_OK;
+  // fork: every lane starts after the caller's earlier work
   KTAU_CUDA(cudaEventRecord(B->fork, st));
   for (int l = 0; l < ktau_batch::kLanes; ++l) KTAU_CUDA(cudaStreamWaitEvent(B->lane[l], B->fork, 0));
   for (size_t gi = 0; gi < B->g.size(); ++gi) {
     GroupPlan& G = B->g[gi];
     if (G.ids.empty() || s != KTAU_OK) continue;
     cudaStream_t ls = B->lane[B->lane_of[gi]];
+    // Rank transform of the group's own variables on its lane (a group's datasets are consecutive
+    // in the descriptor table), so that a lane's counting starts as soon as its own ranks are done.
+    s = ktau_launch_batch_rank(B->d_ds + G.ids.front(), (int)G.ids.size(), G.d_row_prefix, G.rows,
+                               G.max_n, B->d_stats, ls);
+    if (s != KTAU_OK) continue;
     if (G.kind != kContract) {
       s = ktau_launch_batch_merge(B->d_ds, G.d_ids, (int)G.ids.size(), G.d_tile_prefix, G.tiles,
                                   G.max_n, G.kind == kMergeCta ? 1 : 0, ls);

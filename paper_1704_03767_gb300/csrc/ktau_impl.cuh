@@ -42,7 +42,11 @@ struct ktau_ranked {
   double* rs64;
   float2* rsff;
   ktau_stats* stats_dev;
-  ktau_stats stats;  // host copy, filled by ktau_rank_prepare
+  ktau_stats stats;  // host copy, filled by ktau_rank_prepare (see ktau_ranked_stats)
+  // ktau_rank_prepare_async: the statistics are copied into a pinned host slot behind stats_ev
+  // and read on first use; stats_pin is null once `stats` holds them.
+  ktau_stats* stats_pin;
+  cudaEvent_t stats_ev;
   // Sign expansion for the tensor-core path, built on first use (library-owned):
   // sgn[m][K_pad] of values in {-1, 0, +1} as FP4 e2m1 (obits 4, two per byte), FP8 e4m3
   // (obits 8) or BF16 (obits 16), K = n(n-1)/2, K_pad = K rounded up to 128; esize is the
@@ -68,6 +72,10 @@ struct ktau_ranked {
   size_t bkt_var_bytes;
   int ties_ready;  // tie lists and index built (on first use by an n_3 output)
 };
+
+// The handle's rank statistics on the host: waits for the copy of an asynchronously prepared
+// handle on its first use (one thread at a time); ENAN when the matrix held a NaN.
+ktau_status ktau_ranked_stats(const ktau_ranked* R);
 
 // ---------------------------------------------------------------------------------------------
 // Error reporting (thread-local message, see ktau_last_error).

@@ -286,6 +286,8 @@ ktau_status ktau_query_validate(const ktau_ranked* db, const ktau_ranked* querie
   ktau_status s = ktau_check_counts(db->n, count_bits);
   if (s != KTAU_OK) return s;
   if ((s = ktau_check_options(opt)) != KTAU_OK) return s;
+  if ((s = ktau_ranked_stats(db)) != KTAU_OK || (s = ktau_ranked_stats(queries)) != KTAU_OK)
+    return s;
   if (opt && opt->statistic != 0) return ktau_fail(KTAU_EINVAL, "the query form computes tau-b");
   if (k < 0 || k > TK_MAXK || k > db->m)
     return ktau_fail(KTAU_EINVAL, "k must be in [0, min(m_db, %d)]", TK_MAXK);

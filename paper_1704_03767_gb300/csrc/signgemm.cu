@@ -1,9 +1,9 @@
 // K-c: exact sign-matrix contraction on the GB300 tensor cores (see signgemm.cuh).
 //
 // Kernels
-//   sign_expand_kernel : A_u[k] = sign(r_u[a] - r_u[b]) for the k-th sample pair (a < b, row-major
-//                        order over the strict upper triangle of the n x n sample-pair matrix),
-//                        encoded as FP8 e4m3 (+1 = 0x38, -1 = 0xB8) or BF16, zero padded to K_pad.
+//   sign_expand_kernel : A_u[k] = sign(r_u[(i + d) mod n] - r_u[i]) for the k-th sample pair
+//                        (i, d) in circulant order (below), encoded as FP8 e4m3, FP4 e2m1 or
+//                        BF16, zero padded to K_pad.
 //   contract_kernel    : persistent, warp-specialised tcgen05 GEMM over the upper triangle (or
 //                        the query rectangle). The accumulator is computed transposed, S^T =
 //                        A_cols A_rows^T: TMEM lanes are 128 output columns v and TMEM columns
@@ -63,121 +63,244 @@ __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
 // ---------------------------------------------------------------------------------------------
 // Sign expansion
 // ---------------------------------------------------------------------------------------------
-// First sample index a of pair k in row-major order over a < b (row a holds n-1-a pairs).
-__device__ __forceinline__ int pair_row(int n, long long k) {
-  const float nf = (float)n - 0.5f;
-  int a = (int)floorf(nf - sqrtf(fmaxf(nf * nf - 2.0f * (float)k, 0.0f)));
-  if (a < 0) a = 0;
-  if (a > n - 2) a = n - 2;
-  auto start = [n](long long r) { return r * (2LL * n - r - 1) / 2; };
-  while (a > 0 && start(a) > k) --a;
-  while (a < n - 2 && start(a + 1) <= k) ++a;
-  return a;
+// Order of the sample pairs in the operands (circulant order): position k < K holds the pair
+// (i, (i + d) mod n) with d = k / n + 1 and i = k mod n. Offsets d = 1 .. floor((n - 1) / 2) take
+// every i; for even n the offset n / 2 takes i < n / 2 only, which is exactly k < K = n (n - 1) / 2.
+// Every unordered sample pair appears once, and the sign is taken in the same direction for every
+// variable, so A_u . A_v is n_c - n_d (Algorithm 1 sums over the pairs in any order). In this order
+// eight consecutive positions read two contiguous runs of ranks, r[i0 ..] and r[i0 + d ..], except
+// where i passes n - 1 inside the eight (then d advances and the partner run skips one sample).
+//
+// A CTA expands up to ktau_expand_rows(n) variables. Each variable's ranks sit in shared memory
+// as eight copies of the ranks repeated past n, copy c holding r[(x + c) mod n] at x, so a run that
+// starts anywhere is one aligned 16-byte load from copy (start mod 8). A thread takes eight
+// positions at a time for every variable of the CTA: b - a for the two runs in packed 16-bit lanes
+// gives the signs of eight pairs in eight adds (ranks are below 2048: bit 15 of each lane of
+// b - a + 0x7fff is b > a, of b - a + 0x8000 is b >= a), which are then packed into the operand
+// encoding: FP8 e4m3 (+1 = 0x38, -1 = 0xB8), BF16 (0x3F80 / 0xBF80) or FP4 e2m1 (+1 = 0x2,
+// -1 = 0xA, element b of the eight in the high nibble of byte b, element 4 + b in the low nibble).
+// Positions K <= k < K_pad are zero.
+__host__ __device__ __forceinline__ int expand_copy_len(int n) { return (n + 24 + 7) & ~7; }
+__host__ __device__ __forceinline__ size_t expand_smem(int64_t max_n) {
+  return (size_t)ktau_expand_rows(max_n) * 8 * expand_copy_len((int)max_n) * sizeof(uint16_t);
 }
 
-// Shared-memory rank rows of the expansion kernels are padded: the lanes of a warp read ranks
-// 128 / OB apart (consecutive chunks), which would otherwise share a few banks. Pad slots (one
-// after every 8 ranks for FP8, every 16 for FP4, two after every 8 for BF16) make the 32 reads of
-// one instruction fall on distinct banks.
-// Short rows (n <= 256, PAD = false) are left unpadded: there the extra index arithmetic costs
-// more than the conflicts.
-template <int OB, bool PAD = true>
-__host__ __device__ __forceinline__ int xpad(int i) {
-  if (!PAD) return i;
-  return OB == 8 ? i + (i >> 3) : (OB == 4 ? i + (i >> 4) : i + 2 * (i >> 3));
+// prmt.b32 in its default mode: a selector nibble with bit 3 set fills the result byte with the
+// sign bit of the selected byte (0xFF or 0x00).
+__device__ __forceinline__ uint32_t prmt_sx(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
 }
-template <int OB, bool PAD = true>
-__host__ __device__ __forceinline__ int xrow(int n) { return xpad<OB, PAD>(n) + 1; }
 
-// Signs of up to EXPAND_ROWS variables whose ranks are in shared memory (s_r[r * xrow(n) + xpad(i)]):
-// out[r * row_bytes + k] for k < K_pad, zero beyond K. OB = operand bits: 8 = FP8 e4m3
-// (+1 = 0x38, -1 = 0xB8), 16 = BF16 (0x3F80 / 0xBF80), 4 = FP4 e2m1 (+1 = 0x2, -1 = 0xA, two per
-// byte, element 2i in the low nibble of byte i). The sample pairs (a, b) of a 16-byte chunk are
-// the same for every variable, so a thread finds them once (pair_row) and reuses them; positions
-// k >= K read (0, 0) and store 0.
-constexpr int EXPAND_ROWS = KTAU_EXPAND_ROWS;
-
-template <int OB, bool PAD>
-__device__ __forceinline__ void expand_block(const uint16_t* __restrict__ s_r, int rows, int n,
-                                             int K, int K_pad, uint8_t* __restrict__ out,
-                                             int64_t row_bytes) {
-  constexpr int PER = 128 / OB;  // elements per 16-byte store
-  constexpr uint32_t POS = OB == 4 ? 0x2u : (OB == 8 ? 0x38u : 0x3F80u);
-  constexpr uint32_t NEG = OB == 4 ? 0xAu : (OB == 8 ? 0xB8u : 0xBF80u);
-  const int chunks = K_pad / PER;
-  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-    const int k0 = c * PER;
-    uint16_t ia[PER], ib[PER];
-    {
-      int a = 0, b = 0;
-      if (k0 < K) {
-        a = pair_row(n, k0);
-        b = k0 - a * (2 * n - a - 1) / 2 + a + 1;
-      }
+// Operand bytes of eight signs from the flag words: bit 15 / 31 of G[t] = (b > a) for elements
+// 2t / 2t + 1, of E[t] = (b >= a). The flags become byte masks (sign-filling byte permutes), and
+// two logic ops per word give the codes: ne = gt | !ge selects the magnitude bits, !ge the sign.
+template <int OB>
+__device__ __forceinline__ void encode_store(const uint32_t (&G)[4], const uint32_t (&E)[4],
+                                             uint8_t* __restrict__ dst) {
+  if (OB == 4) {
+    const uint32_t mg0 = prmt_sx(G[0], G[1], 0xFDB9u), mg1 = prmt_sx(G[2], G[3], 0xFDB9u);
+    const uint32_t me0 = prmt_sx(E[0], E[1], 0xFDB9u), me1 = prmt_sx(E[2], E[3], 0xFDB9u);
+    // nibble masks: element b in the high nibble of byte b, element 4 + b in the low nibble
+    const uint32_t hg = (mg0 & 0xF0F0F0F0u) | (mg1 & 0x0F0F0F0Fu);
+    const uint32_t he = (me0 & 0xF0F0F0F0u) | (me1 & 0x0F0F0F0Fu);
+    *reinterpret_cast<uint32_t*>(dst) = ((hg | ~he) & 0x22222222u) | (~he & 0x88888888u);
+  } else if (OB == 8) {
+    uint32_t w[2];
 #pragma unroll
-      for (int e = 0; e < PER; ++e) {
-        if (k0 + e < K) {
-          ia[e] = (uint16_t)a;
-          ib[e] = (uint16_t)b;
-          if (++b == n) {
-            ++a;
-            b = a + 1;
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t mg = prmt_sx(G[2 * h], G[2 * h + 1], 0xFDB9u);
+      const uint32_t me = prmt_sx(E[2 * h], E[2 * h + 1], 0xFDB9u);
+      w[h] = ((mg | ~me) & 0x38383838u) | (~me & 0x80808080u);
+    }
+    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t mg = prmt_sx(G[t], G[t], 0xBB99u), me = prmt_sx(E[t], E[t], 0xBB99u);
+      w[t] = ((mg | ~me) & 0x3F803F80u) | (~me & 0x80008000u);
+    }
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Eight ranks r[(x0 + e) mod n], e < 8, of one variable as four packed words: one 16-byte load
+// where they are an aligned run of the row, else one by one.
+__device__ __forceinline__ void load_rank_run(const uint16_t* __restrict__ src, int n, int x0,
+                                              uint32_t* w) {
+  int x = x0;
+  while (x >= n) x -= n;
+  if ((x & 7) == 0 && x + 8 <= n) {
+    const uint4 v = *reinterpret_cast<const uint4*>(src + x);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    uint32_t h[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      int xe = x + 2 * t + e;
+      while (xe >= n) xe -= n;
+      h[e] = src[xe];
+    }
+    w[t] = h[0] | (h[1] << 16);
+  }
+}
+
+// Signs of `rows` <= RR variables (ranks rank[r * ld + x]) into out[r * row_bytes + ...],
+// positions [0, K_pad). s_r: 8 * expand_copy_len(n) uint16 per variable, 16-byte aligned.
+template <int OB, int RR>
+__device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, int64_t ld,
+                                             int rows, int n, int K, int K_pad,
+                                             uint8_t* __restrict__ out, int64_t row_bytes,
+                                             uint16_t* __restrict__ s_r) {
+  const int LS = expand_copy_len(n);
+  const int RS = 8 * LS;   // elements per variable
+  const int CH = LS / 8 - 1;  // 8-element chunks of every copy that are read (x < LS - 8)
+  // the eight copies, chunk by chunk: chunk y of copy c = r[(8y + c + e) mod n], e < 8
+  for (int idx = threadIdx.x; idx < rows * CH; idx += blockDim.x) {
+    const int r = idx / CH, y = idx - r * CH;
+    const uint16_t* src = rank + (int64_t)r * ld;
+    uint32_t w[8];
+    load_rank_run(src, n, 8 * y, w);
+    load_rank_run(src, n, 8 * y + 8, w + 4);
+    uint16_t* dst = s_r + r * RS + 8 * y;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      uint32_t o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int u = j + (c >> 1);
+        o[j] = (c & 1) ? __funnelshift_r(w[u], w[u + 1], 16) : w[u];
+      }
+      *reinterpret_cast<uint4*>(dst + c * LS) = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+  }
+  __syncthreads();
+
+  constexpr int UB = OB;  // bytes of eight elements
+  const int units = K_pad >> 3;
+  const float inv_n = 1.0f / (float)n;
+  for (int q = threadIdx.x; q < units; q += blockDim.x) {
+    const int k0 = q << 3;
+    uint8_t* dst = out + (int64_t)q * UB;
+    if (k0 >= K) {  // padding
+      for (int r = 0; r < rows; ++r) {
+        if (OB == 4)
+          *reinterpret_cast<uint32_t*>(dst + r * row_bytes) = 0u;
+        else if (OB == 8)
+          *reinterpret_cast<uint2*>(dst + r * row_bytes) = make_uint2(0u, 0u);
+        else
+          *reinterpret_cast<uint4*>(dst + r * row_bytes) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      continue;
+    }
+    if (n < 8 || K - k0 < 8) {
+      // short rows (the eight positions may span several offsets) and the last, partly valid
+      // eight of a row: pairs one by one from copy 0, positions k >= K compare equal (sign 0)
+      for (int r = 0; r < rows; ++r) {
+        const uint16_t* row = s_r + r * RS;
+        uint32_t A[4] = {0u, 0u, 0u, 0u}, B[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = k0 + e;
+          if (k < K) {
+            const int i = k % n, j = (i + k / n + 1) % n;
+            A[e >> 1] |= (uint32_t)row[i] << (16 * (e & 1));
+            B[e >> 1] |= (uint32_t)row[j] << (16 * (e & 1));
           }
-        } else {
-          ia[e] = ib[e] = 0;
         }
-      }
-    }
+        uint32_t G[4], E[4];
 #pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      ia[e] = (uint16_t)xpad<OB, PAD>(ia[e]);
-      ib[e] = (uint16_t)xpad<OB, PAD>(ib[e]);
-    }
-    const int rs = xrow<OB, PAD>(n);
-    for (int r = 0; r < rows; ++r) {
-      const uint16_t* sr = s_r + r * rs;
-      uint32_t words[4];
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int h = 0; h < PER / 4; ++h) {
-          const int e = w * (PER / 4) + h;
-          const int d = (int)sr[ia[e]] - (int)sr[ib[e]];
-          word |= (d > 0 ? POS : (d < 0 ? NEG : 0u)) << (OB * h);
+        for (int t = 0; t < 4; ++t) {
+          G[t] = B[t] - A[t] + 0x7FFF7FFFu;
+          E[t] = B[t] - A[t] + 0x80008000u;
         }
-        words[w] = word;
+        encode_store<OB>(G, E, dst + r * row_bytes);
       }
-      reinterpret_cast<uint4*>(out + r * row_bytes)[c] =
-          make_uint4(words[0], words[1], words[2], words[3]);
+      continue;
+    }
+    int d = (int)((float)k0 * inv_n);  // k0 / n, possibly one off
+    int i0 = k0 - d * n;
+    if (i0 < 0) {
+      --d;
+      i0 += n;
+    } else if (i0 >= n) {
+      ++d;
+      i0 -= n;
+    }
+    int s = i0 + d + 1;  // partner run r[s ..], reduced mod n
+    if (s >= n) s -= n;
+    const int c = n - i0;  // elements 0 .. c-1 take offset d + 1, the rest d + 2 (one sample on)
+    const int offA = (i0 & 7) * LS + (i0 & ~7);
+    const int offX = (s & 7) * LS + (s & ~7);
+    if (c >= 8) {
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        if (r >= rows) break;
+        const uint16_t* row = s_r + r * RS;
+        const uint4 a4 = *reinterpret_cast<const uint4*>(row + offA);
+        const uint4 b4 = *reinterpret_cast<const uint4*>(row + offX);
+        const uint32_t G[4] = {b4.x - a4.x + 0x7FFF7FFFu, b4.y - a4.y + 0x7FFF7FFFu,
+                               b4.z - a4.z + 0x7FFF7FFFu, b4.w - a4.w + 0x7FFF7FFFu};
+        const uint32_t E[4] = {b4.x - a4.x + 0x80008000u, b4.y - a4.y + 0x80008000u,
+                               b4.z - a4.z + 0x80008000u, b4.w - a4.w + 0x80008000u};
+        encode_store<OB>(G, E, dst + r * row_bytes);
+      }
+    } else {
+      const int offY = ((s + 1) & 7) * LS + ((s + 1) & ~7);
+      uint32_t sel[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        sel[t] = 0x3210u + (2 * t + 1 >= c ? 0x4400u : 0u) + (2 * t >= c ? 0x0044u : 0u);
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        if (r >= rows) break;
+        const uint16_t* row = s_r + r * RS;
+        const uint4 a4 = *reinterpret_cast<const uint4*>(row + offA);
+        const uint4 x4 = *reinterpret_cast<const uint4*>(row + offX);
+        const uint4 y4 = *reinterpret_cast<const uint4*>(row + offY);
+        const uint32_t A[4] = {a4.x, a4.y, a4.z, a4.w};
+        const uint32_t B[4] = {__byte_perm(x4.x, y4.x, sel[0]), __byte_perm(x4.y, y4.y, sel[1]),
+                               __byte_perm(x4.z, y4.z, sel[2]), __byte_perm(x4.w, y4.w, sel[3])};
+        uint32_t G[4], E[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          G[t] = B[t] - A[t] + 0x7FFF7FFFu;
+          E[t] = B[t] - A[t] + 0x80008000u;
+        }
+        encode_store<OB>(G, E, dst + r * row_bytes);
+      }
     }
   }
 }
 
-template <int OB, bool PAD>
+template <int OB, int RR>
 __global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
                                                           int64_t ld, int n, int64_t m, int K,
                                                           int K_pad, uint8_t* __restrict__ out) {
-  extern __shared__ uint16_t s_r[];  // [EXPAND_ROWS][xrow<OB, PAD>(n)]
-  const int64_t row0 = (int64_t)blockIdx.x * EXPAND_ROWS;
-  const int rows = (int)min((int64_t)EXPAND_ROWS, m - row0);
-  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
-    const int r = i / n, c = i - r * n;
-    s_r[r * xrow<OB, PAD>(n) + xpad<OB, PAD>(c)] = rank[(row0 + r) * ld + c];
-  }
-  __syncthreads();
+  extern __shared__ __align__(16) uint16_t s_r[];
+  const int64_t row0 = (int64_t)blockIdx.x * RR;
+  const int rows = (int)min((int64_t)RR, m - row0);
   const int64_t row_bytes = (int64_t)K_pad * OB / 8;
-  expand_block<OB, PAD>(s_r, rows, n, K, K_pad, out + row0 * row_bytes, row_bytes);
+  expand_block<OB, RR>(rank + row0 * ld, ld, rows, n, K, K_pad, out + row0 * row_bytes, row_bytes,
+                   s_r);
 }
 
-// Batched: blocks of up to EXPAND_ROWS variables of one dataset (numbered dataset by dataset,
-// prefix blk_prefix over bids), written into the group's stacked operand (row stride `stride`
-// bytes, dataset rows from srow). Each row is written up to its own dataset's K_pad.
-template <int OB, bool PAD>
+// Batched: blocks of up to RR variables of one dataset (numbered dataset by dataset, prefix
+// blk_prefix over bids), written into the group's stacked operand (row stride `stride` bytes,
+// dataset rows from srow). Each row is written up to its own dataset's K_pad.
+template <int OB, int RR>
 __global__ void __launch_bounds__(256) batch_sign_expand_kernel(
     const ktau_bds* __restrict__ ds, const int32_t* __restrict__ bids, int nb,
     const int64_t* __restrict__ blk_prefix, int64_t stride, uint8_t* __restrict__ out) {
-  extern __shared__ uint16_t s_r[];
+  extern __shared__ __align__(16) uint16_t s_r[];
   const int64_t blk = blockIdx.x;
   int lo = 0, hi = nb - 1;
   while (lo < hi) {
@@ -188,17 +311,13 @@ __global__ void __launch_bounds__(256) batch_sign_expand_kernel(
       hi = mid - 1;
   }
   const ktau_bds& D = ds[bids[lo]];
-  const int64_t row0 = (blk - blk_prefix[lo]) * EXPAND_ROWS;
-  const int rows = (int)min((int64_t)EXPAND_ROWS, D.m - row0);
+  const int64_t row0 = (blk - blk_prefix[lo]) * RR;
+  const int rows = (int)min((int64_t)RR, D.m - row0);
   const int n = (int)D.n;
-  for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
-    const int r = i / n, c = i - r * n;
-    s_r[r * xrow<OB, PAD>(n) + xpad<OB, PAD>(c)] = D.rank[(row0 + r) * D.ld + c];
-  }
-  __syncthreads();
   const int K = n * (n - 1) / 2;
   const int K_pad = (K + 127) / 128 * 128;
-  expand_block<OB, PAD>(s_r, rows, n, K, K_pad, out + (D.srow + row0) * stride, stride);
+  expand_block<OB, RR>(D.rank + row0 * D.ld, D.ld, rows, n, K, K_pad, out + (D.srow + row0) * stride,
+                   stride, s_r);
 }
 
 // Ranks of every variable with its samples relabelled: out[v][k] = rank[v][sigma[k]] for k < n,
@@ -1816,15 +1935,18 @@ class SideFork {
 // Sign expansion of R's ranks into R->sgn (R->K, K_pad, obits and esize set).
 ktau_status launch_sign_expand(const ktau_ranked* R, cudaStream_t st) {
   const int64_t n = R->n;
-  const size_t smem = (size_t)EXPAND_ROWS * xrow<16>((int)n) * sizeof(uint16_t);  // largest pad
-  const unsigned eblocks = (unsigned)((R->m + EXPAND_ROWS - 1) / EXPAND_ROWS);
+  const size_t smem = expand_smem(n);
+  const int rows = ktau_expand_rows(n);
+  const unsigned eblocks = (unsigned)((R->m + rows - 1) / rows);
   KTAU_TRACE("sign_expand_kernel", st);
-  const bool pad = n > 256;
+  auto pick = [rows](auto k8, auto k4, auto k2) { return rows == 8 ? k8 : (rows == 4 ? k4 : k2); };
   auto kern = R->obits == 4
-                  ? (pad ? sign_expand_kernel<4, true> : sign_expand_kernel<4, false>)
-                  : (R->obits == 8
-                         ? (pad ? sign_expand_kernel<8, true> : sign_expand_kernel<8, false>)
-                         : (pad ? sign_expand_kernel<16, true> : sign_expand_kernel<16, false>));
+                  ? pick(sign_expand_kernel<4, 8>, sign_expand_kernel<4, 4>, sign_expand_kernel<4, 2>)
+                  : (R->obits == 8 ? pick(sign_expand_kernel<8, 8>, sign_expand_kernel<8, 4>,
+                                          sign_expand_kernel<8, 2>)
+                                   : pick(sign_expand_kernel<16, 8>, sign_expand_kernel<16, 4>,
+                                          sign_expand_kernel<16, 2>));
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K, (int)R->K_pad,
                                    (uint8_t*)R->sgn);
   KTAU_CUDA(cudaGetLastError());
@@ -2046,17 +2168,20 @@ ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, i
 
 ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   if (g.nb == 0 || g.rows == 0) return KTAU_OK;
-  const size_t smem_r = (size_t)EXPAND_ROWS * xrow<16>((int)g.max_n) * sizeof(uint16_t);
+  const size_t smem_r = expand_smem(g.max_n);
   {
     KTAU_TRACE("batch_sign_expand_kernel", st);
-    const bool pad = g.max_n > 256;
-    auto kern =
-        g.obits == 4
-            ? (pad ? batch_sign_expand_kernel<4, true> : batch_sign_expand_kernel<4, false>)
-            : (g.obits == 8
-                   ? (pad ? batch_sign_expand_kernel<8, true> : batch_sign_expand_kernel<8, false>)
-                   : (pad ? batch_sign_expand_kernel<16, true>
-                          : batch_sign_expand_kernel<16, false>));
+    const int rows = ktau_expand_rows(g.max_n);
+    auto pick = [rows](auto k8, auto k4, auto k2) { return rows == 8 ? k8 : (rows == 4 ? k4 : k2); };
+    auto kern = g.obits == 4 ? pick(batch_sign_expand_kernel<4, 8>, batch_sign_expand_kernel<4, 4>,
+                                    batch_sign_expand_kernel<4, 2>)
+                             : (g.obits == 8 ? pick(batch_sign_expand_kernel<8, 8>,
+                                                    batch_sign_expand_kernel<8, 4>,
+                                                    batch_sign_expand_kernel<8, 2>)
+                                             : pick(batch_sign_expand_kernel<16, 8>,
+                                                    batch_sign_expand_kernel<16, 4>,
+                                                    batch_sign_expand_kernel<16, 2>));
+    KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     kern<<<(unsigned)g.blocks, 256, smem_r, st>>>(g.ds, g.bids, g.nb, g.blk_prefix, g.stride,
                                                    (uint8_t*)g.sgn);
   }
@@ -2126,6 +2251,8 @@ extern "C" ktau_status ktau_permutation_exceed(const ktau_ranked* Rc, const uint
   const uint64_t P = (uint64_t)(Rc->m * (Rc->m - 1) / 2);
   if (p_begin > p_end || p_end > P) return ktau_fail(KTAU_EINVAL, "pair range outside the triangle");
   if (p_begin == p_end || B == 0) return KTAU_OK;
+  ktau_status st0 = ktau_ranked_stats(Rc);
+  if (st0 != KTAU_OK) return st0;
   ktau_ranked* R = const_cast<ktau_ranked*>(Rc);
   cudaStream_t st = (cudaStream_t)stream;
   ktau_status s = ktau_signgemm_prepare(R, ktau_sign_obits(R->n, nullptr), st);

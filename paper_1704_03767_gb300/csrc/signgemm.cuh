@@ -14,8 +14,10 @@
 
 #define KTAU_SIGNGEMM_MAX_N 2048
 #define KTAU_SIGNGEMM_FP8_MAX_N 2048
-// Variables per CTA of the sign-expansion kernels.
-#define KTAU_EXPAND_ROWS 8
+// Variables per CTA of the sign-expansion kernels (their shared memory grows with n).
+__host__ __device__ inline int ktau_expand_rows(int64_t n) {
+  return n <= 512 ? 8 : (n <= 1024 ? 4 : 2);
+}
 // Operand bits used when the caller does not choose (operand_bits = 0).
 #define KTAU_SIGNGEMM_DEFAULT_BITS 8
 
@@ -40,7 +42,7 @@ struct ktau_sg_group {
   int esize;                   // operand bytes per element in shared memory (1, or 2 for BF16)
   int obits;                   // operand bits in global memory: 4, 8 or 16
   const int64_t* row_prefix;   // [nb + 1] over the group's rows
-  const int64_t* blk_prefix;   // [nb + 1] blocks of EXPAND_ROWS rows per dataset
+  const int64_t* blk_prefix;   // [nb + 1] blocks of ktau_expand_rows(max_n) rows per dataset
   int64_t blocks;
   const int64_t* unit_prefix;  // [nb + 1] contraction units
   const int64_t* jt_prefix;    // [nb + 1] joint-ties tiles
