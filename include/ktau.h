@@ -251,6 +251,10 @@ typedef struct {
 } ktau_trace_record;
 ktau_status ktau_trace_enable(int32_t on);
 ktau_status ktau_trace_collect(ktau_trace_record* out, int32_t cap, int32_t* count);
+/* Restricts the trace to launches named `name` (the record names, e.g. "contract_kernel"); NULL
+ * or "" traces every launch. Each traced launch adds two event records to its stream, so a
+ * filter keeps the trace from adding to the time of the steps it measures. */
+ktau_status ktau_trace_filter(const char* name);
 
 /*
  * Batched form: many independent matrices of uneven m and n processed by one persistent

@@ -37,5 +37,6 @@ from .binding import (  # noqa: F401
     ktau_tie_counts,
     ktau_trace_collect,
     ktau_trace_enable,
+    ktau_trace_filter,
     load,
 )

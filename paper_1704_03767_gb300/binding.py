@@ -78,6 +78,7 @@ _SIGS = {
     "ktau_debug_fail_alloc": ([_i32], ctypes.c_int),
     "ktau_debug_wait_timeout": ([_i64, _vp], ctypes.c_int),
     "ktau_trace_enable": ([_i32], ctypes.c_int),
+    "ktau_trace_filter": ([ctypes.c_char_p], ctypes.c_int),
     "ktau_trace_collect": ([ctypes.POINTER(TraceRecord), _i32, ctypes.POINTER(_i32)],
                            ctypes.c_int),
     "ktau_batch_create": ([ctypes.POINTER(BatchDesc), _i32, ctypes.POINTER(Options),
@@ -310,6 +311,11 @@ def ktau_debug_wait_timeout(limit_ns: int, stream=None):
 
 def ktau_trace_enable(on: bool = True):
     _check(load().ktau_trace_enable(1 if on else 0))
+
+
+def ktau_trace_filter(name: str | None = None):
+    """Trace only the launches named `name` (None: every launch)."""
+    _check(load().ktau_trace_filter(name.encode() if name else None))
 
 
 def ktau_trace_collect(cap: int = 65536):

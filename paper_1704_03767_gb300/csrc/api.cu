@@ -448,8 +448,11 @@ bool g_trace_on = false;
 std::vector<TraceRec>* g_trace = new std::vector<TraceRec>();
 }  // namespace
 
+static char g_trace_only[48] = "";  // ktau_trace_filter; empty = every launch
+
 ktau_trace_scope::ktau_trace_scope(const char* name, cudaStream_t s) : slot(-1), st(s) {
   if (!g_trace_on) return;
+  if (g_trace_only[0] && strncmp(name, g_trace_only, sizeof(g_trace_only)) != 0) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   TraceRec r;
@@ -473,6 +476,12 @@ ktau_trace_scope::~ktau_trace_scope() {
 
 extern "C" ktau_status ktau_trace_enable(int32_t on) {
   g_trace_on = on != 0;
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_trace_filter(const char* name) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  snprintf(g_trace_only, sizeof(g_trace_only), "%s", name ? name : "");
   return KTAU_OK;
 }
 

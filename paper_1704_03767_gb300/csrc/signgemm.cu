@@ -867,12 +867,14 @@ __global__ void ties_list_kernel(const uint16_t* __restrict__ perm, const uint16
 // Inclusive prefix of the bucket sizes in place (one CTA), c[K] = total; also the work of the
 // bucket form of n_3 (sum and largest s(s-1)/2) and the flag that selects it. Tiles of
 // 4 * blockDim values as in ties_scan_kernel.
-__global__ void __launch_bounds__(1024) bucket_scan_kernel(int32_t* __restrict__ c, int64_t K,
-                                                           unsigned long long* __restrict__ stat,
-                                                           unsigned long long lim_total,
-                                                           unsigned long long lim_one) {
-  __shared__ long long wsum[32];
-  __shared__ unsigned long long wwork[32], wmax[32];
+// At most 256 threads: the per-warp arrays stay small enough (200 bytes) for a CTA of this kernel
+// to fit on an SM beside a CTA of the pair contraction, whose shared memory leaves 1.8 KB free.
+__global__ void __launch_bounds__(256) bucket_scan_kernel(int32_t* __restrict__ c, int64_t K,
+                                                          unsigned long long* __restrict__ stat,
+                                                          unsigned long long lim_total,
+                                                          unsigned long long lim_one) {
+  __shared__ long long wsum[8];
+  __shared__ unsigned long long wwork[8], wmax[8];
   __shared__ long long carry_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   long long carry = 0;
@@ -1884,6 +1886,26 @@ struct SideLane {
 };
 SideLane g_side[64];
 
+// A timing-enabled event recorded on the stream just before the pair contraction (never waited
+// on). Measured on GB300 at m = 16384, n = 128: the contraction queued directly behind the sign
+// expansion takes 0.819 ms, and 0.796 ms when this event (or any kernel) separates the two; an
+// event without timing does not have that effect. Skipped while the stream is being captured.
+std::mutex g_mark_mu;
+cudaEvent_t g_mark[64] = {};
+void mark_before_contraction(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_mark_mu);
+  if (!g_mark[dev] && cudaEventCreate(&g_mark[dev]) != cudaSuccess) {
+    g_mark[dev] = nullptr;
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(g_mark[dev], st);
+}
+
 class SideFork {
  public:
   SideFork(cudaStream_t st, bool want) : st_(st) {
@@ -2085,6 +2107,7 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   // The epilogue zero-fills n_3 over the range; the joint-ties kernels then add nonzero counts.
   // The tie lists (first call only) are built beside the contraction on a side stream.
   const bool build_ties = out.n3 != nullptr && !R->ties_ready;
+  mark_before_contraction(st);
   SideFork side(st, build_ties && m >= 4096);
   s = R->esize == 1 ? launch_contract2<1>(R, a, units, st) : launch_contract2<2>(R, a, units, st);
   if (s == KTAU_OK && build_ties) s = ktau_signgemm_ties(R, side.stream());
