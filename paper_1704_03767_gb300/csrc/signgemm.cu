@@ -81,6 +81,9 @@ __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
 // -1 = 0xA, element b of the eight in the high nibble of byte b, element 4 + b in the low nibble).
 // Positions K <= k < K_pad are zero.
 __host__ __device__ __forceinline__ int expand_copy_len(int n) { return (n + 24 + 7) & ~7; }
+// 16 warps per CTA: at n > 1024 a CTA holds 66 KB of rank copies, three CTAs per SM, and the
+// shared-memory load latency needs the 48 resident warps that gives.
+constexpr int kExpandThreads = 512;
 __host__ __device__ __forceinline__ size_t expand_smem(int64_t max_n) {
   return (size_t)ktau_expand_rows(max_n) * 8 * expand_copy_len((int)max_n) * sizeof(uint16_t);
 }
@@ -282,7 +285,7 @@ __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, 
 }
 
 template <int OB, int RR>
-__global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __restrict__ rank,
+__global__ void __launch_bounds__(kExpandThreads) sign_expand_kernel(const uint16_t* __restrict__ rank,
                                                           int64_t ld, int n, int64_t m, int K,
                                                           int K_pad, uint8_t* __restrict__ out) {
   extern __shared__ __align__(16) uint16_t s_r[];
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(256) sign_expand_kernel(const uint16_t* __rest
 // blk_prefix over bids), written into the group's stacked operand (row stride `stride` bytes,
 // dataset rows from srow). Each row is written up to its own dataset's K_pad.
 template <int OB, int RR>
-__global__ void __launch_bounds__(256) batch_sign_expand_kernel(
+__global__ void __launch_bounds__(kExpandThreads) batch_sign_expand_kernel(
     const ktau_bds* __restrict__ ds, const int32_t* __restrict__ bids, int nb,
     const int64_t* __restrict__ blk_prefix, int64_t stride, uint8_t* __restrict__ out) {
   extern __shared__ __align__(16) uint16_t s_r[];
@@ -1969,8 +1972,8 @@ ktau_status launch_sign_expand(const ktau_ranked* R, cudaStream_t st) {
                                    : pick(sign_expand_kernel<16, 8>, sign_expand_kernel<16, 4>,
                                           sign_expand_kernel<16, 2>));
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<eblocks, 256, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K, (int)R->K_pad,
-                                   (uint8_t*)R->sgn);
+  kern<<<eblocks, kExpandThreads, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                              (int)R->K_pad, (uint8_t*)R->sgn);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }
@@ -2205,8 +2208,8 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
                                                     batch_sign_expand_kernel<16, 4>,
                                                     batch_sign_expand_kernel<16, 2>));
     KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
-    kern<<<(unsigned)g.blocks, 256, smem_r, st>>>(g.ds, g.bids, g.nb, g.blk_prefix, g.stride,
-                                                   (uint8_t*)g.sgn);
+    kern<<<(unsigned)g.blocks, kExpandThreads, smem_r, st>>>(g.ds, g.bids, g.nb, g.blk_prefix,
+                                                              g.stride, (uint8_t*)g.sgn);
   }
   KTAU_CUDA(cudaGetLastError());
   {
