@@ -201,8 +201,9 @@ ktau_status ktau_allpairs_host(const ktau_ranked* R, uint64_t p_begin, uint64_t 
 ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, int32_t* path);
 
 /* Builds the tensor-core operands of a handle now instead of on first use: the sign expansion
- * A_u[k] = sign(u_a - u_b) over all sample pairs (Sec. 3.1, Algorithm 1), stored as FP8 e4m3
- * (library memory, m * n_0 bytes with n_0 rounded up to 128 per variable). The lists of tied
+ * A_u[k] = sign(u_b - u_a) over all sample pairs (Sec. 3.1, Algorithm 1; the pairs in an internal
+ * order shared by every variable), stored as FP8 e4m3 for n <= 256 and FP4 e2m1 above (library
+ * memory, m * n_0 or m * n_0 / 2 bytes with n_0 rounded up to 128 per variable). The lists of tied
  * sample pairs that n_3 needs are built by the first ktau_allpairs call that stores n_3, beside
  * its contraction. Asynchronous on `stream` (allocates on first use). EINVAL when n > 2048
  * (path unsupported). */
