@@ -35,6 +35,9 @@ __device__ __forceinline__ unsigned long long load_key(const void* values, int64
 
 // Rank transform of one variable (row `row` of the outputs) by one CTA; `off` is the element
 // offset of its values. Shared memory: np2 keys + 2 x np2 uint16.
+template <int EPL>
+__device__ __forceinline__ void cta_bitonic_hybrid(unsigned long long* sm_keys, int np2);
+
 template <int DT>
 __device__ void rank_row(const void* __restrict__ values, int64_t off, int n, int np2,
                          int64_t ld, int64_t row, uint16_t* perm, uint16_t* rank, uint16_t* srank,
@@ -54,20 +57,30 @@ __device__ void rank_row(const void* __restrict__ values, int64_t off, int n, in
     sm_keys[i] = i < n ? load_key<DT>(values, off, i, &nan_seen) : ~0ull;
   __syncthreads();
 
-  // Bitonic sort of np2 keys, ascending.
-  for (int k = 2; k <= np2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < np2 / 2; i += nt) {
-        int lo = 2 * i - (i & (j - 1));  // index with bit j clear
-        int hi = lo + j;
-        bool up = (lo & k) == 0;
-        unsigned long long a = sm_keys[lo], b = sm_keys[hi];
-        if ((a > b) == up) {
-          sm_keys[lo] = b;
-          sm_keys[hi] = a;
+  // Bitonic sort of np2 keys, ascending: warp blocks in registers where np2 = blockDim * EPL
+  // for EPL in 2..8, the whole network through shared memory otherwise.
+  const int epl = np2 / nt;
+  if (epl * nt == np2 && epl >= 2 && epl <= 8) {
+    switch (epl) {
+      case 2: cta_bitonic_hybrid<2>(sm_keys, np2); break;
+      case 4: cta_bitonic_hybrid<4>(sm_keys, np2); break;
+      default: cta_bitonic_hybrid<8>(sm_keys, np2); break;
+    }
+  } else {
+    for (int k = 2; k <= np2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < np2 / 2; i += nt) {
+          int lo = 2 * i - (i & (j - 1));  // index with bit j clear
+          int hi = lo + j;
+          bool up = (lo & k) == 0;
+          unsigned long long a = sm_keys[lo], b = sm_keys[hi];
+          if ((a > b) == up) {
+            sm_keys[lo] = b;
+            sm_keys[hi] = a;
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
 
@@ -196,6 +209,86 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[EPL], int l
         }
       }
     }
+  }
+}
+
+// Bitonic merge of a bitonic sequence of 32 * EPL keys held by a warp (position lane * EPL + e)
+// into ascending (up) or descending order: the steps j = 16 EPL .. 1 of one phase.
+template <int EPL>
+__device__ __forceinline__ void warp_merge(unsigned long long (&v)[EPL], int lane, bool up) {
+#pragma unroll
+  for (int j = 16 * EPL; j > 0; j >>= 1) {
+    if (j >= EPL) {
+      const bool lower = (lane & (j / EPL)) == 0;  // this lane holds the lower position
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, v[e], j / EPL);
+        v[e] = (lower == up) ? (y < v[e] ? y : v[e]) : (y > v[e] ? y : v[e]);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int p = e ^ j;
+        if (p > e) {
+          const unsigned long long a = v[e], b = v[p];
+          if ((a > b) == up) {
+            v[e] = b;
+            v[p] = a;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Reverses the order of the warp's 32 * EPL keys (position p -> 32 EPL - 1 - p).
+template <int EPL>
+__device__ __forceinline__ void warp_reverse(unsigned long long (&v)[EPL], int lane) {
+  unsigned long long r[EPL];
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) r[e] = __shfl_sync(0xffffffffu, v[EPL - 1 - e], 31 - lane);
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) v[e] = r[e];
+}
+
+// Bitonic sort of sm_keys[0, np2) ascending by a CTA whose warps each own one block of 32 * EPL
+// consecutive keys (np2 = blockDim.x * EPL): the phases up to the block size and, in later
+// phases, the steps inside a block run in registers with shuffles; only the steps across blocks
+// go through shared memory, with one barrier each. The compare-exchange network is the standard
+// one (position i pairs with i ^ j, ascending where i & k == 0), so the result is the same.
+template <int EPL>
+__device__ __forceinline__ void cta_bitonic_hybrid(unsigned long long* sm_keys, int np2) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int B = 32 * EPL;
+  const int base = wid * B;
+  unsigned long long v[EPL];
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) v[e] = sm_keys[base + lane * EPL + e];
+  warp_bitonic<EPL>(v, lane);               // block ascending
+  if (base & B) warp_reverse<EPL>(v, lane);  // odd blocks descending, as the network leaves them
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) sm_keys[base + lane * EPL + e] = v[e];
+  __syncthreads();
+  for (int k = 2 * B; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j >= B; j >>= 1) {
+      for (int i = threadIdx.x; i < np2 / 2; i += blockDim.x) {
+        const int lo = 2 * i - (i & (j - 1));  // index with bit j clear
+        const int hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const unsigned long long a = sm_keys[lo], b = sm_keys[hi];
+        if ((a > b) == up) {
+          sm_keys[lo] = b;
+          sm_keys[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) v[e] = sm_keys[base + lane * EPL + e];
+    warp_merge<EPL>(v, lane, (base & k) == 0);
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) sm_keys[base + lane * EPL + e] = v[e];
+    __syncthreads();
   }
 }
 
