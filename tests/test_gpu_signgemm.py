@@ -48,7 +48,8 @@ def test_uniform_ties_64x200(ktau, bits):
 
 
 @pytest.mark.parametrize("bits", [0, 4])
-@pytest.mark.parametrize("n", [2, 3, 17, 64, 100, 127, 128, 129, 200, 256, 300, 1100])
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 9, 15, 16, 17, 64, 100, 127, 128, 129, 200, 256, 300,
+                               1100])
 def test_ragged(ktau, n, bits):
     m = 300 if n < 1000 else 90  # two 256-row super-tiles, ragged
     X = uniform_ties(m, n, tie_frac=0.2, seed=n)
