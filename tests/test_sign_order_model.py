@@ -99,3 +99,22 @@ def test_operand_codes():
             me = prmt_sign_fill(E[t], E[t], 0xBB99)
             w = ((mg | (~me & M32)) & 0x3F803F80) | ((~me & M32) & 0x80008000)
             assert w & 0xFFFF == bf16[signs[2 * t]] and w >> 16 == bf16[signs[2 * t + 1]]
+
+
+def test_circulant_sign_product_equals_oracle_S():
+    """S = A A^T with the signs in circulant order equals the oracle's definition counts on data
+    with ties (Algorithm 1's sum does not depend on the order of the sample pairs)."""
+    import oracle
+
+    g = np.random.default_rng(4)
+    for n in (7, 8, 9, 40):
+        X = np.round(g.random((6, n)) * 6) / 6  # heavy ties
+        K = n * (n - 1) // 2
+        A = np.zeros((6, K), dtype=np.int64)
+        for k in range(K):
+            i, j = circulant_pair(k, n)
+            A[:, k] = np.sign(X[:, j] - X[:, i])
+        S = A @ A.T
+        for u in range(6):
+            for v in range(u + 1, 6):
+                assert S[u, v] == oracle.pair_counts(X[u], X[v], "definition")["S"]
