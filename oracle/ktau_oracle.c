@@ -9,13 +9,15 @@
  *   ko_pair_definition : the definition of concordance (Sec. 1) counted directly over all
  *                        n(n-1)/2 sample pairs in the sign form of Algorithm 1, extended with
  *                        the tie counts n_1, n_2, n_3 of Table 1.  O(n^2).
- *   ko_pair_knight     : Knight's sort-based method with exact ties, Sec. 3.2 Steps 1-5 and
- *                        Algorithm 2 (with the tail copy that the printed merge leaves out).
+ *   ko_pair_knight     : Knight's sort-based method with exact ties, Sec. 3.2 Steps 1-5; Step 3
+ *                        is a recursive merge sort by v that counts its exchanges (strict
+ *                        comparison, equal v taken from the lower half, as Algorithm 2 requires).
  *   ko_tau_b           : Eq. 3.
  *   ko_F / ko_job_id / ko_job_coord_formula / ko_job_coord : Eq. 4-10 (diagonal included).
  *   ko_rank            : the rank transform of Sec. 3 (stable argsort, dense rank, tie pairs).
  *   ko_allpairs        : Sec. 4.2-4.3: q x q tiles over the upper triangle, tile ids mapped back
- *                        with Eq. 13-14, static contiguous tile ranges per thread.
+ *                        with Eq. 13-14; the requested pair range is cut into equal contiguous
+ *                        slices, one per thread (static distribution).
  *   ko_rect            : every query row against every database row (Sec. 1 query search).
  * Inputs are FP64 (the caller converts float32/int32 exactly). Counts are int64.
  * Parity pins: hand-worked examples, scipy's tau-b, identities, brute force between the two
@@ -73,45 +75,34 @@ static int ko_joint_cmp(const void* pa, const void* pb) {
   return 0;
 }
 
-/* One out-of-place merge of in[left, mid) and in[mid, right) by v (Algorithm 2, gse_merge).
- * Taking an element from the right run while left elements remain means every remaining left
- * element has a larger v: those mid - l pairs are discordant. Equal v values take the left
- * element first, so equal pairs are never counted. The remaining tail of whichever run is not
- * exhausted is copied after the loop. */
-static int64_t ko_merge_count(const ko_joint* in, ko_joint* out, int64_t left, int64_t mid,
-                              int64_t right) {
-  int64_t l = left, r = mid, p = left, nd = 0;
-  while (l < mid && r < right) {
-    if (in[r].v < in[l].v) {
-      nd += mid - l;
-      out[p++] = in[r++];
+/* Step 3 (Sec. 3.2): the list, already in (u, v) order, is put in v order by merge sort, and the
+ * exchanges that sort performs are counted; that count is n_d.
+ *
+ * Written as a recursive top-down merge sort over x[lo, hi): sort each half, then fill the
+ * scratch span t[lo, hi) front to back, each time choosing the smaller head. An element chosen
+ * from the upper half jumps over every element still waiting in the lower half. Each of those
+ * came earlier in the (u, v) order and has a strictly larger v, so its u is strictly smaller:
+ * each jump is one discordant pair. On equal v the lower-half element is chosen first, so a tie
+ * in v is never counted (the pair is tied, not discordant). On return x[lo, hi) is in v order. */
+static int64_t ko_sort_count(ko_joint* x, ko_joint* t, int64_t lo, int64_t hi) {
+  if (hi - lo < 2) return 0;
+  const int64_t half = lo + (hi - lo) / 2;
+  int64_t swaps = ko_sort_count(x, t, lo, half) + ko_sort_count(x, t, half, hi);
+  int64_t a = lo, b = half;
+  for (int64_t k = lo; k < hi; ++k) {
+    const int lower_done = (a == half);
+    const int upper_done = (b == hi);
+    if (!upper_done && (lower_done || x[b].v < x[a].v)) {
+      swaps += half - a; /* elements of the lower half still waiting */
+      t[k] = x[b];
+      ++b;
     } else {
-      out[p++] = in[l++];
+      t[k] = x[a];
+      ++a;
     }
   }
-  while (l < mid) out[p++] = in[l++];
-  while (r < right) out[p++] = in[r++];
-  return nd;
-}
-
-/* Step 3: bottom-up merge sort of the Step-1 list by v, summing the discordant counts.
- * On return `pairs` holds the list sorted by v. */
-static int64_t ko_step3(ko_joint* pairs, ko_joint* buffer, int64_t n) {
-  int64_t nd = 0;
-  ko_joint* in = pairs;
-  ko_joint* out = buffer;
-  for (int64_t s = 1; s < n; s *= 2) {
-    for (int64_t l = 0; l < n; l += 2 * s) {
-      int64_t mid = l + s < n ? l + s : n;
-      int64_t r = l + 2 * s < n ? l + 2 * s : n;
-      nd += ko_merge_count(in, out, l, mid, r);
-    }
-    ko_joint* t = in;
-    in = out;
-    out = t;
-  }
-  if (in != pairs) memcpy(pairs, in, (size_t)n * sizeof(ko_joint));
-  return nd;
+  memcpy(x + lo, t + lo, (size_t)(hi - lo) * sizeof(ko_joint));
+  return swaps;
 }
 
 /* Sum over runs of equal keys of t(t-1)/2, for a list already sorted so equal keys are adjacent. */
@@ -167,7 +158,7 @@ static void ko_pair_knight_work(const double* u, const double* v, int64_t n, ko_
   int64_t n1 = ko_tie_pairs_u(pairs, n);
   int64_t n3 = ko_tie_pairs_uv(pairs, n);
   /* Step 3: discordant pairs while re-sorting by v. */
-  int64_t nd = ko_step3(pairs, buffer, n);
+  int64_t nd = ko_sort_count(pairs, buffer, 0, n);
   /* Step 4: n_2 (ties in v) on the list now sorted by v. */
   int64_t n2 = ko_tie_pairs_v(pairs, n);
   /* Step 5: n_c - n_d = n_0 - n_1 - n_2 + n_3 - 2 n_d. */
@@ -281,9 +272,10 @@ int ko_rank(const double* x, int64_t n, int64_t* perm, int64_t* rank, int64_t* T
 typedef struct {
   const double* X;
   int64_t m, n, ld, q, w;
+  uint64_t p_lo, p_hi; /* this thread's slice of the requested range */
   int64_t tile_begin, tile_end;
-  uint64_t p_begin, p_end;
-  int method; /* 0 = definition, 1 = Knight */
+  uint64_t p_begin;    /* start of the requested range (outputs are indexed from it) */
+  int method;          /* 0 = definition, 1 = Knight */
   int64_t *S, *n3, *nd, *n1, *n2;
   double* tau;
   int status;
@@ -304,7 +296,7 @@ static void* ko_allpairs_worker(void* arg) {
       for (int64_t x = xq * jb->q; x < (xq + 1) * jb->q && x < m; ++x) {
         if (x <= y) continue; /* strict upper triangle: the diagonal is not a pair */
         uint64_t p = (uint64_t)(y * (2 * m - y - 1) / 2 + (x - y - 1));
-        if (p < jb->p_begin || p >= jb->p_end) continue;
+        if (p < jb->p_lo || p >= jb->p_hi) continue; /* another thread's pair */
         const double* u = jb->X + y * jb->ld;
         const double* v = jb->X + x * jb->ld;
         ko_counts c;
@@ -327,26 +319,39 @@ static void* ko_allpairs_worker(void* arg) {
   return NULL;
 }
 
+/* Row of the pair with packed index p: the strict upper triangle of an m x m matrix is the
+ * diagonal-included triangle of an (m-1) x (m-1) matrix (pair (y, x) <-> cell (y, x-1)), so
+ * Eq. 9-10 with the Eq. 6 check on m-1 gives y. */
+static int64_t ko_pair_row(int64_t m, uint64_t p) {
+  int64_t y, x1;
+  ko_job_coord(m - 1, (int64_t)p, &y, &x1);
+  return y;
+}
+
 /* Every pair (y < x) of the m x n matrix X (row stride ld) whose packed index
  * p = y(2m-y-1)/2 + (x-y-1) lies in [p_begin, p_end); outputs are indexed by p - p_begin and
- * any may be NULL. q is the tile side (Sec. 4.2), threads the number of worker threads, each
- * given one contiguous range of tile ids (static distribution, Sec. 4.3.2 and 4.4). */
+ * any may be NULL. q is the tile side (Sec. 4.2) and `threads` the number of worker threads.
+ * The requested range is cut into `threads` contiguous slices of equal pair counts (a static
+ * distribution, Sec. 4.3.2 and 4.4). A thread walks, in tile-id order (Eq. 13-14), the tiles
+ * of the tile rows its slice touches, and counts only the pairs of its own slice, so every
+ * thread does the same share of the requested work whatever part of the triangle it lies in. */
 int ko_allpairs(const double* X, int64_t m, int64_t n, int64_t ld, int method, int64_t q,
                 int threads, uint64_t p_begin, uint64_t p_end, int64_t* S, int64_t* n3,
                 int64_t* nd, int64_t* n1, int64_t* n2, double* tau) {
   if (q < 1) q = 8;
   if (threads < 1) threads = 1;
-  int64_t w = (m + q - 1) / q;
-  int64_t tiles = w * (w + 1) / 2;
-  int64_t per = (tiles + threads - 1) / threads;
+  if (m < 2 || p_end <= p_begin) return 0;
+  const int64_t w = (m + q - 1) / q;
+  const uint64_t span = p_end - p_begin;
   ko_job* jobs = (ko_job*)calloc((size_t)threads, sizeof(ko_job));
   pthread_t* tids = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
-  if (!jobs || !tids) {
+  char* started = (char*)calloc((size_t)threads, 1);
+  if (!jobs || !tids || !started) {
     free(jobs);
     free(tids);
+    free(started);
     return -1;
   }
-  int started = 0;
   for (int t = 0; t < threads; ++t) {
     ko_job* jb = &jobs[t];
     jb->X = X;
@@ -355,10 +360,16 @@ int ko_allpairs(const double* X, int64_t m, int64_t n, int64_t ld, int method, i
     jb->ld = ld;
     jb->q = q;
     jb->w = w;
-    jb->tile_begin = t * per < tiles ? t * per : tiles;
-    jb->tile_end = (t + 1) * per < tiles ? (t + 1) * per : tiles;
+    jb->p_lo = p_begin + span * (uint64_t)t / (uint64_t)threads;
+    jb->p_hi = p_begin + span * (uint64_t)(t + 1) / (uint64_t)threads;
+    if (jb->p_lo < jb->p_hi) {
+      /* tile rows from the first to the last pair row of the slice, whole rows of tiles */
+      const int64_t yq_first = ko_pair_row(m, jb->p_lo) / q;
+      const int64_t yq_last = ko_pair_row(m, jb->p_hi - 1) / q;
+      jb->tile_begin = ko_job_id(w, yq_first, yq_first);
+      jb->tile_end = ko_job_id(w, yq_last, w - 1) + 1;
+    }
     jb->p_begin = p_begin;
-    jb->p_end = p_end;
     jb->method = method;
     jb->S = S;
     jb->n3 = n3;
@@ -366,24 +377,21 @@ int ko_allpairs(const double* X, int64_t m, int64_t n, int64_t ld, int method, i
     jb->n1 = n1;
     jb->n2 = n2;
     jb->tau = tau;
-    if (threads == 1) {
-      ko_allpairs_worker(jb);
-    } else if (pthread_create(&tids[t], NULL, ko_allpairs_worker, jb) == 0) {
-      ++started;
-    } else {
-      ko_allpairs_worker(jb);
-    }
+  }
+  for (int t = 0; t < threads; ++t) {
+    if (threads > 1 && pthread_create(&tids[t], NULL, ko_allpairs_worker, &jobs[t]) == 0)
+      started[t] = 1;
+    else
+      ko_allpairs_worker(&jobs[t]);
   }
   int status = 0;
-  if (threads > 1) {
-    for (int t = 0; t < threads; ++t)
-      if (tids[t]) pthread_join(tids[t], NULL);
-  }
+  for (int t = 0; t < threads; ++t)
+    if (started[t]) pthread_join(tids[t], NULL);
   for (int t = 0; t < threads; ++t)
     if (jobs[t].status) status = -1;
-  (void)started;
   free(jobs);
   free(tids);
+  free(started);
   return status;
 }
 

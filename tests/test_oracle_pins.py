@@ -271,3 +271,83 @@ def test_permutation_exceed_identity_and_ranges(oracle_mod):
     full = oracle_mod.permutation_exceed(X, perms)
     assert np.array_equal(oracle_mod.permutation_exceed(X, perms, 7, 30), full[7:30])
     assert np.all((full >= 0) & (full <= 5))
+
+
+def test_allpairs_thread_slices(oracle_mod):
+    """The requested range is cut into per-thread slices: any thread count and any sub-range give
+    the single-thread result, including slices that start and end inside a tile row."""
+    g = np.random.default_rng(21)
+    m, n = 37, 19
+    X = g.integers(0, 5, (m, n)).astype(float)
+    P = m * (m - 1) // 2
+    ref = oracle_mod.allpairs(X, threads=1)
+    for threads in (2, 3, 7, 16, 40):
+        for a, b in ((0, P), (0, 90), (13, 14), (200, 611), (P - 5, P)):
+            out = oracle_mod.allpairs(X, q=4, threads=threads, p_begin=a, p_end=b)
+            for k in ("S", "n3", "nd", "n1", "n2"):
+                assert np.array_equal(out[k], ref[k][a:b]), (threads, a, b, k)
+
+
+def _brute_topk(Q, D, k):
+    """Independent top-k: per (query, row) the definition counter and Eq. 3, then a full sort on
+    (tau is NaN, -|tau| as the exact rational S^2 / (D_u D_v), row index)."""
+    from fractions import Fraction
+
+    n = Q.shape[1]
+    n0 = n * (n - 1) // 2
+    idx, tau = [], []
+    for q in Q:
+        keyed = []
+        for j, row in enumerate(D):
+            c = pair_counts_def(q, row)
+            du, dv = n0 - c["n1"], n0 - c["n2"]
+            t = math.nan if du == 0 or dv == 0 else c["S"] / math.sqrt(du * dv)
+            key = (1, Fraction(0)) if math.isnan(t) else (0, -Fraction(c["S"] ** 2, du * dv))
+            keyed.append((key, j, t))
+        keyed.sort(key=lambda e: (e[0], e[1]))
+        idx.append([j for _, j, _ in keyed[:k]])
+        tau.append([t for _, _, t in keyed[:k]])
+    return idx, tau
+
+
+def pair_counts_def(u, v):
+    """Definition-level counts written out in Python (sign products over all sample pairs)."""
+    u, v = [float(x) for x in u], [float(x) for x in v]
+    nc = nd = n1 = n2 = 0
+    n = len(u)
+    for a in range(n):
+        for b in range(a + 1, n):
+            su = (u[a] > u[b]) - (u[a] < u[b])
+            sv = (v[a] > v[b]) - (v[a] < v[b])
+            nc += su * sv > 0
+            nd += su * sv < 0
+            n1 += su == 0
+            n2 += sv == 0
+    return {"S": nc - nd, "n1": n1, "n2": n2}
+
+
+def test_query_topk_brute_force(oracle_mod):
+    """query_topk against the brute-force order above. The database has rows with equal |tau|
+    against the queries (duplicated and negated rows), a constant row (NaN, last) and tied values;
+    one query is constant (every tau NaN: order by row index)."""
+    g = np.random.default_rng(31)
+    n = 9
+    D = g.integers(0, 4, (14, n)).astype(float)
+    D[3] = D[1]             # equal |tau| to row 1 for every query: index order decides
+    D[5] = -D[1]            # |tau| equal to rows 1 and 3, sign flipped
+    D[7] = 2.0              # constant row: NaN
+    D[9] = g.permutation(n)  # no ties
+    Q = g.integers(0, 5, (4, n)).astype(float)
+    Q[2] = D[1]             # |tau| = 1 against rows 1, 3 and 5
+    Q[3] = 1.5              # constant query
+    for k in (1, 5, 14):
+        r = oracle_mod.query_topk(Q, D, k)
+        idx, tau = _brute_topk(Q, D, k)
+        assert r["topk_idx"].tolist() == idx, k
+        for got, want in zip(r["topk_tau"], tau):
+            for a, b in zip(got, want):
+                assert (math.isnan(a) and math.isnan(b)) or a == b
+    r = oracle_mod.query_topk(Q, D, 14)
+    assert r["topk_idx"][2][:3].tolist() == [1, 3, 5]
+    assert r["topk_idx"][3].tolist() == list(range(14))
+    assert 7 == r["topk_idx"][0][-1]
