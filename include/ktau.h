@@ -159,20 +159,21 @@ ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end
 
 /*
  * ktau_allpairs_noalloc -- ktau_allpairs (merge path) for one matrix straight from its values,
- * allocating nothing. The paper has no counterpart: this entry point is for callers that may not
- * allocate device memory when they need the result, such as code running while its stream is
- * captured into a CUDA graph, plug-ins confined to a memory budget owned by a host framework's
- * allocator, or latency-critical loops where cudaMalloc/cudaFree (which can synchronise the
- * device) are not allowed.
+ * allocating nothing. The paper has no counterpart. It serves callers that cannot allocate device
+ * memory where they need the result: plug-ins of a host framework that owns the device memory
+ * through its own allocator and budget (a cudaMalloc behind its back can fail or break its
+ * accounting), and real-time loops that forbid cudaMalloc/cudaFree because those calls can
+ * synchronise the device and stall.
  *   values, dt, m, n, ld : as ktau_rank_prepare. [p_begin, p_end), tau64, tau32, S, n3,
  *            count_bits : as ktau_allpairs. All caller-owned; the library allocates nothing.
  * Working memory is a fixed array of KTAU_NOALLOC_SCRATCH_BYTES compiled into the library (every
  * GPU that loads the library holds it until the process exits). It must hold the ranked matrix,
  * 3*m*ld16*2 + 32*m bytes (ld16 = n rounded up to 16, arrays padded to 256 bytes) plus 256; larger
  * inputs fail with KTAU_ETOOLARGE (m <= 16384 at n = 128 fits). The first call on a device looks
- * up the array's device address, so make that first call before any stream capture. Every call
- * uses the same array: calls whose GPU work overlaps (other streams, other threads) race and must
- * be serialised by the caller. Synchronises `stream` once to read the NaN flag (KTAU_ENAN).
+ * up the array's device address (set-up, once per device), so make that first call before any
+ * stream capture. Every call uses the same array, which keeps the previous call's contents: calls
+ * whose GPU work overlaps (other streams, other threads) race and must be serialised by the
+ * caller. Synchronises `stream` once, after the rank transform, to read the NaN flag (KTAU_ENAN).
  * Errors: EINVAL, ETOOLARGE, ENAN, ECUDA.
  */
 #define KTAU_NOALLOC_SCRATCH_BYTES (16u << 20)

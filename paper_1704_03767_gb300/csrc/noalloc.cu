@@ -1,9 +1,9 @@
 // ktau_allpairs_noalloc: the rank transform and the Knight merge path for one matrix, with every
 // byte of working memory taken from a fixed array compiled into the library instead of being
-// allocated. It exists for callers that may not allocate device memory at the point where they
-// need the result -- code that runs while its stream is being captured into a CUDA graph,
-// plug-ins that must stay inside a memory budget owned by a host framework's allocator, or
-// real-time loops that forbid cudaMalloc/cudaFree (which can synchronise the device).
+// allocated. It exists for callers that cannot allocate device memory at the point where they
+// need the result: plug-ins that must stay inside a memory budget owned by a host framework's
+// allocator, and real-time loops that forbid cudaMalloc/cudaFree (which can synchronise the
+// device). The call synchronises its stream once, to read the NaN flag of the rank transform.
 //
 // The working memory is the ranked matrix (permutation, dense ranks, ranks in sorted order, tie
 // counts, denominator factors, statistics): for m variables of n samples it needs
