@@ -120,6 +120,14 @@ ktau_status ktau_rank_prepare(const void* values, ktau_dtype dt, int64_t m, int6
 ktau_status ktau_rank_prepare_async(const void* values, ktau_dtype dt, int64_t m, int64_t n,
                                     int64_t ld, void* stream, ktau_ranked** out);
 
+/* ktau_rank_prepare from HOST values: values_h is a host pointer (page-locked memory gives full
+ * copy bandwidth), m x n row-major with row stride ld elements, dtype dt. The values are copied
+ * into a library-owned device staging buffer on `stream` and ranked from there; the staging
+ * buffer goes back to the library's cache before the call returns, so values_h may be reused at
+ * once. Synchronises `stream`. Errors as ktau_rank_prepare. */
+ktau_status ktau_rank_prepare_host(const void* values_h, ktau_dtype dt, int64_t m, int64_t n,
+                                   int64_t ld, void* stream, ktau_ranked** out);
+
 /* Releases a handle (NULL is accepted). Synchronises the device before freeing. */
 ktau_status ktau_ranked_free(ktau_ranked* R);
 /* Releases a handle whose every use was enqueued on `stream`: synchronises that stream only
@@ -233,6 +241,14 @@ ktau_status ktau_permutation_exceed(const ktau_ranked* R, const uint16_t* perms,
                                     uint64_t p_begin, uint64_t p_end, const int32_t* S_obs,
                                     uint32_t* exceed, void* stream);
 
+/* Two-sided permutation p-values of the pairs whose exceedance counts ktau_permutation_exceed
+ * accumulated over B permutations: pvalue[i] = (exceed[i] + 1) / (B + 1) in IEEE FP64 (the
+ * observed labelling counted as one of B + 1 equally likely ones; Sec. 2 motivates tau as a
+ * test statistic). exceed: uint32 device array of `count` counts; pvalue: FP64 device array of
+ * `count`. Asynchronous on `stream`. Errors: EINVAL (NULL arrays with count > 0, B < 0), ECUDA. */
+ktau_status ktau_permutation_pvalues(const uint32_t* exceed, int32_t B, uint64_t count,
+                                     double* pvalue, void* stream);
+
 /* Failure injection for tests of error handling (no GPU fault involved):
  * ktau_debug_fail_alloc(k): the next k library allocations succeed, every later one fails as if
  * the device were out of memory (KTAU_ENOMEM); k < 0 switches the injection off.
@@ -297,6 +313,33 @@ ktau_status ktau_batch_paths(const ktau_batch* B, int32_t* n_merge, int32_t* n_s
 /* Total pairs over all datasets. */
 ktau_status ktau_batch_pairs(const ktau_batch* B, uint64_t* pairs);
 ktau_status ktau_batch_free(ktau_batch* B);
+
+/*
+ * ktau_allpairs_batched -- the batched form as one call, with all scratch in a workspace the caller
+ * owns (the pass and tile scheduling of Sec. 4.2-4.3 generalised to a list of job matrices):
+ * rank transform and every pair of every dataset, exactly as ktau_batch_create + ktau_batch_run
+ * would compute them, bit for bit.
+ *   descs, count, opt : as ktau_batch_create (the descriptors are read during the call only).
+ *   workspace : caller-owned device memory, 256-byte aligned, of at least ktau_workspace_size()
+ *            bytes for the same descriptors and options. It holds the ranked datasets, their
+ *            operands and the plan's tables, and must stay untouched until the work has finished
+ *            on `stream`. Its contents need no initialisation.
+ *   nan_flag : NULL or a device uint32 that receives this call's NaN flag (nonzero when some
+ *            dataset holds a NaN; that dataset's outputs are then meaningless).
+ * Allocates nothing, creates no stream and never synchronises: the plan's tables reach the device
+ * as parameters of small kernel launches on `stream` (no memcpy, no staging), and every group runs
+ * on `stream`, one after another, so the call can also be captured into a CUDA graph. For repeated
+ * launches of the same datasets, ktau_batch_create + ktau_batch_graph_launch spread the groups over
+ * several streams and replay them as one CUDA graph.
+ * Errors: EINVAL (as ktau_batch_create; workspace NULL, unaligned or too small), ETOOLARGE, ECUDA.
+ */
+ktau_status ktau_allpairs_batched(const ktau_batch_desc* descs, int32_t count,
+                                  const ktau_options* opt, void* workspace, size_t workspace_bytes,
+                                  uint32_t* nan_flag, void* stream);
+/* Bytes of workspace ktau_allpairs_batched needs for these descriptors and options (host only; no
+ * device work, nothing allocated). */
+ktau_status ktau_workspace_size(const ktau_batch_desc* descs, int32_t count,
+                                const ktau_options* opt, size_t* bytes);
 
 /*
  * ktau_query -- query-based search (Sec. 1): exact tau-b of every query profile against every

@@ -60,6 +60,8 @@ _SIGS = {
                           ctypes.c_int),
     "ktau_rank_prepare_async": ([_vp, ctypes.c_int, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)],
                                 ctypes.c_int),
+    "ktau_rank_prepare_host": ([_vp, ctypes.c_int, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)],
+                               ctypes.c_int),
     "ktau_ranked_free": ([_vp], ctypes.c_int),
     "ktau_ranked_free_on": ([_vp, _vp], ctypes.c_int),
     "ktau_ranked_shape": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
@@ -75,6 +77,7 @@ _SIGS = {
     "ktau_prepare_signs": ([_vp, _vp], ctypes.c_int),
     "ktau_device_status": ([_vp], ctypes.c_int),
     "ktau_permutation_exceed": ([_vp, _vp, _i32, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
+    "ktau_permutation_pvalues": ([_vp, _i32, _u64, _vp, _vp], ctypes.c_int),
     "ktau_debug_fail_alloc": ([_i32], ctypes.c_int),
     "ktau_debug_wait_timeout": ([_i64, _vp], ctypes.c_int),
     "ktau_trace_enable": ([_i32], ctypes.c_int),
@@ -89,6 +92,10 @@ _SIGS = {
     "ktau_batch_paths": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
     "ktau_batch_pairs": ([_vp, ctypes.POINTER(_u64)], ctypes.c_int),
     "ktau_batch_free": ([_vp], ctypes.c_int),
+    "ktau_allpairs_batched": ([ctypes.POINTER(BatchDesc), _i32, ctypes.POINTER(Options), _vp,
+                               ctypes.c_size_t, _vp, _vp], ctypes.c_int),
+    "ktau_workspace_size": ([ctypes.POINTER(BatchDesc), _i32, ctypes.POINTER(Options),
+                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "ktau_query": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(Options), _vp],
                    ctypes.c_int),
     "ktau_query_scratch_bytes": ([_vp, _i64, _i32, ctypes.POINTER(ctypes.c_size_t)],
@@ -187,8 +194,17 @@ def ktau_rank_prepare_async(values: torch.Tensor, stream=None) -> Ranked:
     return _rank_prepare(values, stream, "ktau_rank_prepare_async")
 
 
-def _rank_prepare(values: torch.Tensor, stream, fn: str) -> Ranked:
-    if values.dim() != 2 or not values.is_cuda:
+def ktau_rank_prepare_host(values: torch.Tensor, stream=None, device=None) -> Ranked:
+    """Rank transform of a HOST float32/int32 matrix (pinned for full copy bandwidth): the library
+    copies it to the device and ranks it there."""
+    if values.dim() != 2 or values.is_cuda:
+        raise ValueError("values must be a 2-D host tensor")
+    return _rank_prepare(values, stream, "ktau_rank_prepare_host",
+                         device or torch.device("cuda", torch.cuda.current_device()))
+
+
+def _rank_prepare(values: torch.Tensor, stream, fn: str, device=None) -> Ranked:
+    if values.dim() != 2 or (device is None and not values.is_cuda):
         raise ValueError("values must be a 2-D CUDA tensor")
     if values.dtype == torch.float32:
         dt = KTAU_F32
@@ -202,7 +218,7 @@ def _rank_prepare(values: torch.Tensor, stream, fn: str) -> Ranked:
     h = ctypes.c_void_p()
     _check(getattr(load(), fn)(values.data_ptr(), dt, m, n, values.stride(0), _stream(stream),
                                ctypes.byref(h)))
-    return Ranked(h.value, m, n, values.device)
+    return Ranked(h.value, m, n, device or values.device)
 
 
 def ktau_tie_counts(R: Ranked, T: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -295,10 +311,20 @@ def permutation_pvalues(values: torch.Tensor, perms: torch.Tensor, stream=None):
     R = res["ranked"]
     exceed = torch.zeros(R.pairs, dtype=torch.uint32, device=values.device)
     ktau_permutation_exceed(R, perms.to(values.device), res["S"], exceed, stream=stream)
-    B = perms.shape[0]
     res["exceed"] = exceed
-    res["pvalue"] = (exceed.to(torch.float64) + 1.0) / (B + 1.0)
+    res["pvalue"] = ktau_permutation_pvalues(exceed, perms.shape[0], stream=stream)
     return res
+
+
+def ktau_permutation_pvalues(exceed: torch.Tensor, B: int, pvalue=None, stream=None):
+    """(exceed + 1) / (B + 1) per pair, computed by the library (FP64 CUDA tensor)."""
+    if exceed.dtype != torch.uint32 or not exceed.is_cuda:
+        raise ValueError("exceed must be a uint32 CUDA tensor")
+    if pvalue is None:
+        pvalue = torch.empty(exceed.numel(), dtype=torch.float64, device=exceed.device)
+    _check(load().ktau_permutation_pvalues(exceed.data_ptr(), B, exceed.numel(),
+                                           pvalue.data_ptr(), _stream(stream)))
+    return pvalue
 
 
 def ktau_debug_fail_alloc(k: int):
@@ -398,6 +424,25 @@ def batch_desc(values: torch.Tensor, tau64=None, tau32=None, S=None, n3=None,
     dt = KTAU_F32 if values.dtype == torch.float32 else KTAU_I32
     return BatchDesc(values.data_ptr(), dt, count_bits, m, n, values.stride(0), _ptr(tau64),
                      _ptr(tau32), _ptr(S), _ptr(n3), path, 0)
+
+
+def ktau_workspace_size(descs, options=None) -> int:
+    """Bytes of device workspace ktau_allpairs_batched needs for these descriptors."""
+    arr = (BatchDesc * len(descs))(*descs)
+    v = ctypes.c_size_t()
+    _check(load().ktau_workspace_size(arr, len(descs), _options(options), ctypes.byref(v)))
+    return v.value
+
+
+def ktau_allpairs_batched(descs, workspace: torch.Tensor, nan_flag=None, options=None,
+                          stream=None):
+    """Every dataset of `descs` in one call, with all scratch in `workspace` (a CUDA uint8 tensor
+    of at least ktau_workspace_size bytes, 256-byte aligned); `nan_flag` is an optional CUDA
+    int32/uint32 tensor of one element that receives the call's NaN flag."""
+    arr = (BatchDesc * len(descs))(*descs)
+    _check(load().ktau_allpairs_batched(arr, len(descs), _options(options), workspace.data_ptr(),
+                                        workspace.numel() * workspace.element_size(),
+                                        _ptr(nan_flag), _stream(stream)))
 
 
 def ktau_query(db: Ranked, queries: Ranked, tau=None, S=None, n3=None, count_bits: int = 32,

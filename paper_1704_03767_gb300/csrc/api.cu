@@ -272,6 +272,35 @@ ktau_status ktau_rank_prepare_async(const void* values, ktau_dtype dt, int64_t m
   return rank_prepare_impl(values, dt, m, n, ld, stream, true, out);
 }
 
+ktau_status ktau_rank_prepare_host(const void* values_h, ktau_dtype dt, int64_t m, int64_t n,
+                                   int64_t ld, void* stream, ktau_ranked** out) {
+  if (!out) return ktau_fail(KTAU_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!values_h) return ktau_fail(KTAU_EINVAL, "values is NULL");
+  if (dt != KTAU_F32 && dt != KTAU_I32) return ktau_fail(KTAU_EINVAL, "unknown dtype %d", (int)dt);
+  if (m < 1 || n < 2 || ld < n)
+    return ktau_fail(KTAU_EINVAL, "need m >= 1, n >= 2 and ld >= n");
+  if (n > KTAU_MAX_N || m > KTAU_MAX_M)
+    return ktau_fail(KTAU_ETOOLARGE, "m=%lld x n=%lld beyond the limits", (long long)m,
+                     (long long)n);
+  cudaStream_t st = (cudaStream_t)stream;
+  // Staging copy of the values (4-byte elements, rows packed to n), released once the rank
+  // transform has read it: ktau_rank_prepare synchronises the stream before returning.
+  const size_t row = (size_t)n * 4, bytes = (size_t)m * row;
+  void* dv = nullptr;
+  ktau_status s = ktau_dmalloc(&dv, bytes);
+  if (s != KTAU_OK) return s;
+  const cudaError_t e = cudaMemcpy2DAsync(dv, row, values_h, (size_t)ld * 4, row, (size_t)m,
+                                          cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess)
+    s = ktau_cuda_fail(e, "cudaMemcpy2DAsync(values)");
+  else
+    s = rank_prepare_impl(dv, dt, m, n, n, stream, false, out);
+  cudaStreamSynchronize(st);
+  ktau_dfree(dv, bytes);
+  return s;
+}
+
 ktau_status ktau_ranked_stats(const ktau_ranked* Rc) {
   if (!Rc) return ktau_fail(KTAU_EINVAL, "handle is NULL");
   ktau_ranked* R = const_cast<ktau_ranked*>(Rc);

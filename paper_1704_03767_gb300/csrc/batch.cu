@@ -68,11 +68,71 @@ struct ktau_batch {
   cudaStream_t lane[kLanes] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kLanes] = {};
+  // Where device memory comes from: the library's allocator (a plan, ktau_batch_create), a
+  // caller's workspace carved front to back (ktau_allpairs_batched), or nowhere (measure: only
+  // the sizes are added up, for ktau_workspace_size). In the workspace modes nothing is
+  // allocated, no stream is created, every group runs on the caller's stream and the descriptor
+  // tables are copied with cudaMemcpyAsync on it.
+  enum Source { kLibrary = 0, kWorkspace = 1, kMeasure = 2 };
+  int source = kLibrary;
+  char* arena = nullptr;
+  size_t arena_cap = 0, arena_used = 0;
+  cudaStream_t copy_st = nullptr;
 };
+
+// Host-to-device copy of a plan table without a memcpy: the bytes travel as the by-value
+// parameter of a one-block kernel, 32 KB per launch. Launch parameters are copied when the launch
+// is enqueued, so the call neither stages through pinned memory nor waits for the stream, and the
+// host buffer may be released as soon as it returns.
+constexpr int kUploadChunk = 32736;  // + 16 header bytes stays within the 32764-byte limit
+struct UploadChunk {
+  unsigned char* dst;
+  unsigned int bytes;
+  unsigned int pad;
+  alignas(16) unsigned char data[kUploadChunk];
+};
+
+__global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
+  const unsigned full = c.bytes & ~15u;
+  if (((uintptr_t)c.dst & 15) == 0) {
+    for (unsigned i = threadIdx.x * 16; i < full; i += blockDim.x * 16)
+      *reinterpret_cast<uint4*>(c.dst + i) = *reinterpret_cast<const uint4*>(c.data + i);
+  } else {
+    for (unsigned i = threadIdx.x; i < full; i += blockDim.x) c.dst[i] = c.data[i];
+  }
+  for (unsigned i = full + threadIdx.x; i < c.bytes; i += blockDim.x) c.dst[i] = c.data[i];
+}
+
+static ktau_status upload_by_launch(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  static thread_local UploadChunk* chunk = new UploadChunk();  // 32 KB, kept per host thread
+  for (size_t off = 0; off < bytes; off += kUploadChunk) {
+    const size_t len = bytes - off < (size_t)kUploadChunk ? bytes - off : (size_t)kUploadChunk;
+    chunk->dst = (unsigned char*)dst + off;
+    chunk->bytes = (unsigned int)len;
+    memcpy(chunk->data, (const unsigned char*)src + off, len);
+    upload_kernel<<<1, 256, 0, st>>>(*chunk);
+    KTAU_CUDA(cudaGetLastError());
+  }
+  return KTAU_OK;
+}
 
 static ktau_status batch_alloc(ktau_batch* B, void** p, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   if (bytes == 0) bytes = 256;
+  if (B->source == ktau_batch::kMeasure) {
+    // A stand-in address, 256-byte aligned, that is never dereferenced.
+    *p = (void*)((uintptr_t)0x100000 + B->arena_used);
+    B->arena_used += bytes;
+    return KTAU_OK;
+  }
+  if (B->source == ktau_batch::kWorkspace) {
+    if (B->arena_used + bytes > B->arena_cap)
+      return ktau_fail(KTAU_EINVAL, "workspace of %zu bytes is too small (ktau_workspace_size)",
+                       B->arena_cap);
+    *p = B->arena + B->arena_used;
+    B->arena_used += bytes;
+    return KTAU_OK;
+  }
   ktau_status s = ktau_dmalloc(p, bytes);
   if (s == KTAU_OK) B->allocs.push_back({*p, bytes});
   return s;
@@ -81,8 +141,11 @@ static ktau_status batch_alloc(ktau_batch* B, void** p, size_t bytes) {
 template <class T>
 static ktau_status batch_upload(ktau_batch* B, T** dst, const std::vector<T>& v) {
   ktau_status s = batch_alloc(B, (void**)dst, v.size() * sizeof(T));
-  if (s != KTAU_OK) return s;
-  if (!v.empty()) KTAU_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (s != KTAU_OK || v.empty() || B->source == ktau_batch::kMeasure) return s;
+  if (B->source == ktau_batch::kWorkspace)
+    return upload_by_launch(*dst, v.data(), v.size() * sizeof(T), B->copy_st);
+  else
+    KTAU_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return KTAU_OK;
 }
 
@@ -98,6 +161,10 @@ ktau_status ktau_check_options(const ktau_options* opt);
 
 extern "C" ktau_status ktau_batch_free(ktau_batch* B) {
   if (!B) return KTAU_OK;
+  if (B->source != ktau_batch::kLibrary) {  // owns no device memory, stream or graph
+    delete B;
+    return KTAU_OK;
+  }
   cudaDeviceSynchronize();
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
@@ -111,11 +178,34 @@ extern "C" ktau_status ktau_batch_free(ktau_batch* B) {
   return KTAU_OK;
 }
 
+static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t count,
+                                       const ktau_options* opt, ktau_batch* B);
+
+// Validates the descriptors and lays the plan out (B->source says where memory comes from). On
+// failure B is released.
+static ktau_status batch_build(const ktau_batch_desc* descs, int32_t count,
+                               const ktau_options* opt, ktau_batch* B) {
+  if (!descs || count <= 0) {
+    ktau_batch_free(B);
+    return ktau_fail(KTAU_EINVAL, "need count > 0 descriptors");
+  }
+  ktau_status s = batch_build_checked(descs, count, opt, B);
+  if (s != KTAU_OK) ktau_batch_free(B);
+  return s;
+}
+
 extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t count,
                                          const ktau_options* opt, ktau_batch** out) {
   if (!out) return ktau_fail(KTAU_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!descs || count <= 0) return ktau_fail(KTAU_EINVAL, "need count > 0 descriptors");
+  ktau_batch* B = new ktau_batch();
+  ktau_status s = batch_build(descs, count, opt, B);
+  if (s == KTAU_OK) *out = B;
+  return s;
+}
+
+static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t count,
+                                       const ktau_options* opt, ktau_batch* B) {
   ktau_status s = ktau_check_options(opt);
   if (s != KTAU_OK) return s;
   if (opt && opt->statistic != 0) return ktau_fail(KTAU_EINVAL, "the batched form computes tau-b");
@@ -134,7 +224,6 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       return ktau_fail(KTAU_EINVAL, "descriptor %d: contraction path needs n <= %d", i,
                        KTAU_SIGNGEMM_MAX_N);
   }
-  ktau_batch* B = new ktau_batch();
   B->count = count;
   cudaGetDevice(&B->device);
   // Group of every dataset; workspace order = group order (contraction groups by stride class,
@@ -186,7 +275,6 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
   const int64_t R = B->total_rows;
   char* ws = nullptr;
   if ((s = batch_alloc(B, (void**)&ws, rank_bytes + (size_t)R * 32 + 4096)) != KTAU_OK) {
-    ktau_batch_free(B);
     return s;
   }
   int64_t* T_all = (int64_t*)(ws + rank_bytes);
@@ -253,13 +341,11 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     G.rows = rp.back();
     if ((s = batch_upload(B, &G.d_ids, G.ids)) != KTAU_OK ||
         (s = batch_upload(B, &G.d_row_prefix, rp)) != KTAU_OK) {
-      ktau_batch_free(B);
       return s;
     }
     if (G.kind != kContract) {
       G.tiles = tp.back();
       if ((s = batch_upload(B, &G.d_tile_prefix, tp)) != KTAU_OK) {
-        ktau_batch_free(B);
         return s;
       }
       continue;
@@ -275,7 +361,6 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
         (s = batch_upload(B, &G.d_jt_prefix, jp)) != KTAU_OK ||
         (s = batch_alloc(B, &G.sgn, (size_t)G.rows * G.stride)) != KTAU_OK ||
         (s = batch_alloc(B, (void**)&G.tie_off, ((size_t)G.rows + 1) * 8)) != KTAU_OK) {
-      ktau_batch_free(B);
       return s;
     }
     // Tie lists: room for 2n tied pairs per variable on average; variables beyond the capacity
@@ -283,7 +368,6 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     G.tie_cap = 0;
     for (int k : G.ids) G.tie_cap += B->hds[k].m * 2 * B->hds[k].n;
     if ((s = batch_alloc(B, (void**)&G.tie_pairs, (size_t)G.tie_cap * 4)) != KTAU_OK) {
-      ktau_batch_free(B);
       return s;
     }
     int64_t srow = 0;
@@ -295,15 +379,21 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       D.tie_pairs = G.tie_pairs;
       D.tie_cap = G.tie_cap;
     }
-    if ((s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows, G.obits)) != KTAU_OK) {
-      ktau_batch_free(B);
+    if (B->source != ktau_batch::kMeasure &&
+        (s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows, G.obits)) != KTAU_OK) {
       return s;
     }
   }
   if ((s = batch_upload(B, &B->d_ds, B->hds)) != KTAU_OK ||
       (s = batch_alloc(B, (void**)&B->d_stats, sizeof(ktau_stats))) != KTAU_OK) {
-    ktau_batch_free(B);
     return s;
+  }
+  if (B->source == ktau_batch::kMeasure) return KTAU_OK;
+  if (B->source == ktau_batch::kWorkspace) {
+    // Groups run one after another on the caller's stream; the statistics start at zero.
+    B->lane_of.assign(B->g.size(), 0);
+    KTAU_CUDA(cudaMemsetAsync(B->d_stats, 0, sizeof(ktau_stats), B->copy_st));
+    return KTAU_OK;
   }
   KTAU_CUDA(cudaMemset(B->d_stats, 0, sizeof(ktau_stats)));
   cudaError_t e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
@@ -311,10 +401,7 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
     e = cudaStreamCreateWithFlags(&B->lane[l], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->join[l], cudaEventDisableTiming);
   }
-  if (e != cudaSuccess) {
-    ktau_batch_free(B);
-    return ktau_cuda_fail(e, "batch streams");
-  }
+  if (e != cudaSuccess) return ktau_cuda_fail(e, "batch streams");
   // Lane assignment: work estimate of a group = contraction tiles x K blocks (+ merge tiles x n),
   // largest first to the least loaded lane.
   {
@@ -340,7 +427,6 @@ extern "C" ktau_status ktau_batch_create(const ktau_batch_desc* descs, int32_t c
       B->lane_of[wi.second] = best;
     }
   }
-  *out = B;
   return KTAU_OK;
 }
 
@@ -348,13 +434,17 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
   if (!B) return ktau_fail(KTAU_EINVAL, "batch is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   ktau_status s = KTAU_OK;
+  const bool lanes = B->fork != nullptr;  // a plan made by ktau_batch_create
   // fork: every lane starts after the caller's earlier work
-  KTAU_CUDA(cudaEventRecord(B->fork, st));
-  for (int l = 0; l < ktau_batch::kLanes; ++l) KTAU_CUDA(cudaStreamWaitEvent(B->lane[l], B->fork, 0));
+  if (lanes) {
+    KTAU_CUDA(cudaEventRecord(B->fork, st));
+    for (int l = 0; l < ktau_batch::kLanes; ++l)
+      KTAU_CUDA(cudaStreamWaitEvent(B->lane[l], B->fork, 0));
+  }
   for (size_t gi = 0; gi < B->g.size(); ++gi) {
     GroupPlan& G = B->g[gi];
     if (G.ids.empty() || s != KTAU_OK) continue;
-    cudaStream_t ls = B->lane[B->lane_of[gi]];
+    cudaStream_t ls = lanes ? B->lane[B->lane_of[gi]] : st;
     // Rank transform of the group's own variables on its lane (a group's datasets are consecutive
     // in the descriptor table), so that a lane's counting starts as soon as its own ranks are done.
     s = ktau_launch_batch_rank(B->d_ds + G.ids.front(), (int)G.ids.size(), G.d_row_prefix, G.rows,
@@ -391,7 +481,7 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
   }
   // join: the caller's stream waits for every lane (also after an error, so that no lane is left
   // forked, e.g. inside a graph capture)
-  for (int l = 0; l < ktau_batch::kLanes; ++l) {
+  for (int l = 0; lanes && l < ktau_batch::kLanes; ++l) {
     cudaError_t e = cudaEventRecord(B->join[l], B->lane[l]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B->join[l], 0);
     if (e != cudaSuccess && s == KTAU_OK) s = ktau_cuda_fail(e, "batch join");
@@ -446,4 +536,44 @@ extern "C" ktau_status ktau_batch_pairs(const ktau_batch* B, uint64_t* pairs) {
   if (!B || !pairs) return ktau_fail(KTAU_EINVAL, "NULL argument");
   *pairs = B->pairs;
   return KTAU_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// One call over many datasets with the scratch in the caller's workspace.
+// ---------------------------------------------------------------------------------------------
+extern "C" ktau_status ktau_workspace_size(const ktau_batch_desc* descs, int32_t count,
+                                           const ktau_options* opt, size_t* bytes) {
+  if (!bytes) return ktau_fail(KTAU_EINVAL, "bytes is NULL");
+  *bytes = 0;
+  ktau_batch* B = new ktau_batch();
+  B->source = ktau_batch::kMeasure;
+  ktau_status s = batch_build(descs, count, opt, B);
+  if (s != KTAU_OK) return s;
+  *bytes = B->arena_used;
+  ktau_batch_free(B);
+  return KTAU_OK;
+}
+
+extern "C" ktau_status ktau_allpairs_batched(const ktau_batch_desc* descs, int32_t count,
+                                             const ktau_options* opt, void* workspace,
+                                             size_t workspace_bytes, uint32_t* nan_flag,
+                                             void* stream) {
+  if (!workspace) return ktau_fail(KTAU_EINVAL, "workspace is NULL");
+  if ((uintptr_t)workspace & 255) return ktau_fail(KTAU_EINVAL, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ktau_batch* B = new ktau_batch();
+  B->source = ktau_batch::kWorkspace;
+  B->arena = (char*)workspace;
+  B->arena_cap = workspace_bytes;
+  B->copy_st = st;
+  ktau_status s = batch_build(descs, count, opt, B);
+  if (s != KTAU_OK) return s;
+  s = ktau_batch_run(B, stream);
+  if (s == KTAU_OK && nan_flag) {
+    const cudaError_t e = cudaMemcpyAsync(nan_flag, &B->d_stats->nan_flag, sizeof(uint32_t),
+                                          cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) s = ktau_cuda_fail(e, "cudaMemcpyAsync(nan_flag)");
+  }
+  ktau_batch_free(B);
+  return s;
 }

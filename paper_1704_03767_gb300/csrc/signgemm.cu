@@ -2322,3 +2322,28 @@ extern "C" ktau_status ktau_permutation_exceed(const ktau_ranked* Rc, const uint
   if (s == KTAU_OK) s = ktau_signgemm_check_error(st);
   return s;
 }
+
+// Two-sided permutation p-values from the exceedance counts: p = (count + 1) / (B + 1), the
+// observed labelling counted as one of the B + 1 equally likely ones (IEEE FP64 quotient).
+__global__ void permutation_pvalue_kernel(const uint32_t* __restrict__ exceed, uint64_t count,
+                                          double den, double* __restrict__ pvalue) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    pvalue[i] = __ddiv_rn((double)exceed[i] + 1.0, den);
+}
+
+extern "C" ktau_status ktau_permutation_pvalues(const uint32_t* exceed, int32_t B, uint64_t count,
+                                                double* pvalue, void* stream) {
+  if (B < 0) return ktau_fail(KTAU_EINVAL, "B must be >= 0");
+  if (count == 0) return KTAU_OK;
+  if (!exceed || !pvalue) return ktau_fail(KTAU_EINVAL, "exceed and pvalue are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t blocks = std::min<uint64_t>((count + 255) / 256, (uint64_t)ktau_sm_count() * 8);
+  {
+    KTAU_TRACE("permutation_pvalue_kernel", st);
+    permutation_pvalue_kernel<<<(unsigned)blocks, 256, 0, st>>>(exceed, count, (double)B + 1.0,
+                                                                pvalue);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}

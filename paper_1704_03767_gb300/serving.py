@@ -6,7 +6,7 @@ Clients submit batches of query profiles (b x n) at any time. A dispatcher admit
 batches in arrival order whenever a stream slot is free and the batch's device memory fits the
 budget still unreserved; each slot is a thread with its own CUDA stream that runs
 
-    host->device copy of the profiles, ktau_rank_prepare, ktau_query (exact tau-b against every
+    host->device copy of the profiles, ktau_rank_prepare_async, ktau_query (exact tau-b against every
     database row + exact top-k by |tau|), device->host copy of the top-k
 
 so batches that arrive while others are on the GPU overlap with them. When several batches are
@@ -249,7 +249,9 @@ class QueryServer:
                 tk = torch.empty((b, self.k), dtype=torch.float64, device=self.dev)
                 idx_h = torch.empty((b, self.k), dtype=torch.int32).pin_memory()
                 tk_h = torch.empty((b, self.k), dtype=torch.float64).pin_memory()
-            R = kb.ktau_rank_prepare(qd, st)
+            # No host round trip between the rank transform and the query: the statistics copy is
+            # read when ktau_query needs it.
+            R = kb.ktau_rank_prepare_async(qd, st)
             tau = torch.empty((b, self.m_db), dtype=torch.float64, device=self.dev) \
                 if self.keep_tau else None
             kb.ktau_query(self.db, R, tau, S, None, 32, self.k, idx, tk, self.options, st)

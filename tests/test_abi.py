@@ -76,3 +76,32 @@ def test_argument_validation_without_gpu(lib):
     assert lib.ktau_allpairs(None, 0, 1, None, None, None, None, 32, None, None) == 1
     assert lib.ktau_query(None, None, None, None, None, 32, 0, None, None, None, None) == 1
     assert lib.ktau_ranked_free(None) == 0
+
+
+def test_workspace_size_without_gpu(lib):
+    """ktau_workspace_size is host arithmetic only: it runs without a GPU, grows with the
+    datasets, and covers at least the three rank arrays of every dataset."""
+    import paper_1704_03767_gb300 as ktau
+
+    def desc(m, n, path=1):
+        return ktau.BatchDesc(0x1000, 0, 32, m, n, n, None, None, None, None, path, 0)
+
+    small = ktau.ktau_workspace_size([desc(10, 20)])
+    big = ktau.ktau_workspace_size([desc(10, 20), desc(300, 500)])
+    assert small >= 3 * 10 * 32 * 2 and big > small
+    # contraction datasets also hold their sign operands (n_0 rounded up to 128 bytes per row)
+    sg = ktau.ktau_workspace_size([desc(300, 100, 2)])
+    assert sg >= 300 * ((100 * 99 // 2 + 127) // 128 * 128)
+    size = ctypes.c_size_t()
+    assert lib.ktau_workspace_size(None, 1, None, ctypes.byref(size)) == 1
+    arr = (ktau.BatchDesc * 1)(desc(1, 20))  # m < 2
+    assert lib.ktau_workspace_size(arr, 1, None, ctypes.byref(size)) == 1
+    arr = (ktau.BatchDesc * 1)(desc(10, 20))
+    assert lib.ktau_workspace_size(arr, 1, None, None) == 1
+    # the batched call rejects a missing or unaligned workspace before any device work
+    assert lib.ktau_allpairs_batched(arr, 1, None, None, 1 << 20, None, None) == 1
+    assert lib.ktau_allpairs_batched(arr, 1, None, 0x1001, 1 << 20, None, None) == 1
+    # p-values: B < 0 and NULL arrays
+    assert lib.ktau_permutation_pvalues(None, -1, 5, None, None) == 1
+    assert lib.ktau_permutation_pvalues(None, 3, 5, None, None) == 1
+    assert lib.ktau_permutation_pvalues(None, 3, 0, None, None) == 0

@@ -141,3 +141,92 @@ def test_thousand_uneven_datasets_sampled(ktau):
         assert_tau64(o["tau64"][idx].cpu().numpy(), rtau)
         assert_tau32(o["tau32"][idx].cpu().numpy(), rtau)
     B.free()
+
+
+def _bits(a):
+    return a.view(np.int32 if a.itemsize == 4 else np.int64)
+
+
+def _descs_like(ktau, mats, count_bits=32, paths=None):
+    """Fresh outputs and descriptors for the one-call form (same datasets as a plan)."""
+    descs, outs, keep = [], [], []
+    for i, X in enumerate(mats):
+        Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        m = X.shape[0]
+        P = m * (m - 1) // 2
+        cdt = torch.int64 if count_bits == 64 else torch.int32
+        o = {"tau64": torch.full((P,), -3.0, dtype=torch.float64, device="cuda"),
+             "tau32": torch.full((P,), -3.0, dtype=torch.float32, device="cuda"),
+             "S": torch.full((P,), -9, dtype=cdt, device="cuda"),
+             "n3": torch.full((P,), -9, dtype=cdt, device="cuda")}
+        descs.append(ktau.batch_desc(Xd, o["tau64"], o["tau32"], o["S"], o["n3"], count_bits,
+                                     0 if paths is None else paths[i]))
+        outs.append(o)
+        keep.append(Xd)
+    return descs, outs, keep
+
+
+def _workspace(nbytes):
+    # 256-byte aligned view into a byte tensor (torch's allocator aligns to 512 bytes anyway)
+    return torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")[:nbytes]
+
+
+@pytest.mark.parametrize("paths", [None, "merge"])
+def test_batched_call_matches_plan(ktau, paths):
+    """ktau_allpairs_batched (scratch in the caller's workspace, one stream) gives the plan's
+    outputs bit for bit, twice in a row on the same workspace, and a graph captured around it
+    replays the same outputs."""
+    mats = batched_uneven(count=40, m_range=(16, 260), n_range=(20, 1400), seed0=300)
+    mats[2][4] = 2.0  # constant variable
+    pth = None if paths is None else [1] * len(mats)
+    B, ref_outs = _make(ktau, mats, 32, pth)
+    s = torch.cuda.Stream()
+    B.run(s)
+    B.check(s)
+    ref = [_np(o) for o in ref_outs]
+    B.free()
+    descs, outs, keep = _descs_like(ktau, mats, 32, pth)
+    nbytes = ktau.ktau_workspace_size(descs)
+    ws = _workspace(nbytes)
+    assert ws.data_ptr() % 256 == 0
+    flag = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    for rep in range(2):
+        for o in outs:
+            for t in o.values():
+                t.fill_(-4)
+        ktau.ktau_allpairs_batched(descs, ws, flag, stream=s)
+        s.synchronize()
+        assert int(flag.item()) == 0
+        for o, r in zip(outs, ref):
+            g = _np(o)
+            for k in g:
+                assert np.array_equal(_bits(g[k]), _bits(r[k])), (rep, k)
+    # capture the call into a graph and replay it
+    for o in outs:
+        for t in o.values():
+            t.fill_(-4)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ktau.ktau_allpairs_batched(descs, ws, flag, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        got = _np(o)
+        for k in got:
+            assert np.array_equal(_bits(got[k]), _bits(r[k])), ("graph", k)
+    del g
+    ktau.ktau_device_status(s)
+
+
+def test_batched_call_nan_and_small_workspace(ktau):
+    mats = [uniform_ties(20, 30, seed=1), uniform_ties(25, 40, seed=2)]
+    mats[1][3, 4] = np.nan
+    descs, outs, keep = _descs_like(ktau, mats)
+    nbytes = ktau.ktau_workspace_size(descs)
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ktau.ktau_allpairs_batched(descs, _workspace(nbytes), flag)
+    torch.cuda.synchronize()
+    assert int(flag.item()) != 0
+    with pytest.raises(ktau.KtauError) as ei:
+        ktau.ktau_allpairs_batched(descs, _workspace(nbytes - 256), flag)
+    assert ei.value.status == 1 and "workspace" in ei.value.message

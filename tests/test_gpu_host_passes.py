@@ -60,3 +60,29 @@ def test_host_passes_benchmark_size(ktau):
     assert torch.equal(Sd.cpu(), S)
     assert torch.isfinite(t32).all() and t32.abs().max() <= 1.0
     R.free()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_rank_prepare_from_host(ktau, dtype):
+    """ktau_rank_prepare_host (host values, strided rows, pinned or pageable) gives the same ranked
+    matrix as ktau_rank_prepare on the device copy, and rejects a NaN."""
+    X = uniform_ties(70, 150, tie_frac=0.3, seed=9)
+    if dtype == "i32":
+        X = (X * 50).astype(np.int32)
+    wide = np.zeros((70, 160), dtype=X.dtype)
+    wide[:, :150] = X
+    host = torch.from_numpy(wide)[:, :150]  # row stride 160
+    for h in (host, host.pin_memory()):
+        Rh = ktau.ktau_rank_prepare_host(h)
+        Rd = ktau.ktau_rank_prepare(torch.from_numpy(X).cuda())
+        for a, b in zip(ktau.ktau_ranked_export(Rh), ktau.ktau_ranked_export(Rd)):
+            assert torch.equal(a, b)
+        assert torch.equal(ktau.ktau_tie_counts(Rh), ktau.ktau_tie_counts(Rd))
+        Rh.free()
+        Rd.free()
+    if dtype == "f32":
+        bad = torch.from_numpy(X.copy())
+        bad[3, 7] = float("nan")
+        with pytest.raises(ktau.KtauError) as ei:
+            ktau.ktau_rank_prepare_host(bad)
+        assert ei.value.status == 2
