@@ -139,39 +139,53 @@ def _peaks():
         return None
 
 
-def fp8_gemm_peak(dev) -> dict:
-    """Dense FP8 e4m3 tensor rate of this GPU, measured as MEASURED_PEAKS.json measures BF16: a
-    cuBLAS GEMM (torch._scaled_mm, unit scales, BF16 output) of 8192^3, best of 10 launches, 2 N^3
-    flops each. Taken before the timed region."""
+def _gemm_peak(f, n: int) -> float:
+    """Best of 10 launches of f (an n^3 GEMM) in TFLOP/s (2 n^3 flops each)."""
     import torch
 
-    n = 8192
-    a = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
-    b = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
-    one = torch.tensor(1.0, device=dev)
     for _ in range(3):
-        torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16)
+        f()
     best = float("inf")
     for _ in range(10):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16)
+        f()
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
+def tensor_peaks(dev) -> dict:
+    """Dense low-precision tensor rates of this GPU, measured as MEASURED_PEAKS.json measures BF16:
+    cuBLAS GEMMs (torch._scaled_mm, BF16 output) of 8192^3, best of 10 launches. FP8: e4m3 with
+    unit tensor scales. FP4: e2m1 with one e4m3 scale per 16 elements (the FP4 tensor format that
+    torch exposes; the contraction uses e2m1 with one power-of-two scale per 32 elements, the same
+    FP4 MMA rate class). Taken before the timed region."""
+    import torch
+
+    n = 8192
+    out = {"how": "torch._scaled_mm, 8192^3, best of 10 (burst), BF16 output"}
+    a = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+    b = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+    one = torch.tensor(1.0, device=dev)
+    out["fp8_tflops"] = _gemm_peak(
+        lambda: torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16), n)
     del a, b
+    try:
+        a4 = torch.randint(0, 256, (n, n // 2), device=dev, dtype=torch.uint8).view(
+            torch.float4_e2m1fn_x2)
+        b4 = torch.randint(0, 256, (n, n // 2), device=dev, dtype=torch.uint8).view(
+            torch.float4_e2m1fn_x2)
+        sa = torch.ones((n, n // 16), device=dev).to(torch.float8_e4m3fn)
+        sb = torch.ones((n, n // 16), device=dev).to(torch.float8_e4m3fn)
+        out["fp4_tflops"] = _gemm_peak(
+            lambda: torch._scaled_mm(a4, b4.t(), sa, sb, out_dtype=torch.bfloat16), n)
+        del a4, b4, sa, sb
+    except (RuntimeError, AttributeError, TypeError) as e:  # FP4 GEMM not exposed by this torch
+        out["fp4_error"] = str(e).splitlines()[0][:200]
     torch.cuda.empty_cache()
-    return {"tflops": 2.0 * n ** 3 / (best / 1e3) / 1e12, "ms": best,
-            "how": "torch._scaled_mm e4m3 x e4m3 -> bf16, 8192^3, best of 10 (burst)"}
-
-
-def _timed_oracle(Xd, threads: int, p_end: int):
-    """Wall and process CPU seconds of one oracle run over the first p_end pairs."""
-    import oracle
-
-    c0, t0 = time.process_time(), time.perf_counter()
-    oracle.allpairs(Xd, method="knight", threads=threads, p_begin=0, p_end=p_end)
-    return time.perf_counter() - t0, time.process_time() - c0
+    return out
 
 
 def cpu_baseline(X, seconds: float):
@@ -468,7 +482,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    fp8_peak = fp8_gemm_peak(dev)
+    tpeaks = tensor_peaks(dev)
     R0 = ktau.ktau_rank_prepare(Xd, stream)
     path_id = ktau.ktau_allpairs_path(R0, opts)
     R0.free()
@@ -554,19 +568,31 @@ def run_ours(args):
                 "traffic": None, "kernel": "merge_pairs_kernel",
                 "kernel_ms": kern_avg_ms}
     else:
-        # Algorithmic work of the contraction: n_0 multiply-adds (2 flops) per pair, FP8 e4m3
-        # operands; peak = the dense FP8 GEMM rate measured on this GPU before the timed region.
+        # Algorithmic work of the contraction: n_0 multiply-adds (2 flops) per pair. Its
+        # operands are FP4 e2m1 (block-scaled MMA), so the tensor roof is the FP4 GEMM rate
+        # measured on this GPU (the FP8 rate x 3, the nominal FP4/FP8 ratio, when torch exposes
+        # no FP4 GEMM). The HBM view: the
+        # stored outputs (12 bytes per pair) and the operands read once.
         flops = 2.0 * P * (N * (N - 1) // 2)
         kern_avg_ms = dominant_ms
         achieved = flops / (kern_avg_ms / 1e3) / 1e12
         bf16 = (peaks or {}).get("bf16_tflops", 1899.7)
-        peak = fp8_peak["tflops"]
+        if "fp4_tflops" in tpeaks:
+            peak, src = tpeaks["fp4_tflops"], "FP4 e2m1 cuBLAS GEMM on this GPU (" + tpeaks["how"] + ")"
+        else:
+            peak, src = 3.0 * tpeaks["fp8_tflops"], "FP8 cuBLAS GEMM on this GPU x 3 (nominal ratio)"
+        alg_bytes = 12.0 * P + M * ((N * (N - 1) // 2 + 255) // 256 * 128)
+        hbm = (peaks or {}).get("hbm_gbs", 6779.7)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _traffic("contract2_kernel"),
-                "peak_source": "of measured: dense FP8 e4m3 cuBLAS GEMM on this GPU (" +
-                               fp8_peak["how"] + "); FP8 e4m3 operands",
-                "frac_vs_bf16_x2": achieved / (2.0 * bf16),
-                "kernel": "contract2_kernel<1> (2-CTA tcgen05 pair)", "kernel_ms": kern_avg_ms}
+                "peak_source": "of measured: " + src + "; the kernel's operands are FP4 e2m1",
+                "frac_vs_fp8": achieved / tpeaks["fp8_tflops"],
+                "fp8_tflops": tpeaks["fp8_tflops"],
+                "hbm_view": {"algorithmic_bytes": alg_bytes,
+                             "achieved_gbs": alg_bytes / (kern_avg_ms / 1e3) / 1e9, "peak_gbs": hbm,
+                             "frac": alg_bytes / (kern_avg_ms / 1e3) / 1e9 / hbm},
+                "kernel": "contract2_kernel<1, MX> (2-CTA tcgen05 kind::mxf4 pair)",
+                "kernel_ms": kern_avg_ms}
 
     # tau-a (Sec. 2, no tie correction) on the same workload: the whole step without n_3.
     taua = None

@@ -73,9 +73,9 @@ typedef struct {
   int32_t mapping;      /* merge path: 1 = one warp per pair, 2 = one CTA per pair */
   int32_t schedule;     /* 1 = static stride over tile ids (Sec. 4.3.2), 2 = dynamic counter */
   int32_t ctas_per_sm;  /* persistent grid = ctas_per_sm * SM count */
-  int32_t operand_bits; /* contraction operands: 4 = FP4 e2m1, 8 = FP8 e4m3, 16 = BF16, all
-                           exact for n <= 2048; 0 = FP8 for n <= 256, FP4 above (half the
-                           operand bytes) */
+  int32_t operand_bits; /* contraction operands: 4 = FP4 e2m1 (the triangle's pair kernel reads
+                           them with the block-scaled FP4 MMA, scale factors 1), 8 = FP8 e4m3,
+                           16 = BF16, all exact for n <= 2048; 0 = FP4 */
   int32_t statistic;    /* 0 = tau-b (Eq. 3, default); 1 = tau-a = (n_c - n_d) / n_0 (Sec. 2, no
                            tie correction): tau64 = S / n_0 in IEEE FP64, tau32 = S / n_0
                            correctly rounded to FP32. ktau_allpairs, ktau_allpairs_path and
@@ -211,8 +211,8 @@ ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, in
 
 /* Builds the tensor-core operands of a handle now instead of on first use: the sign expansion
  * A_u[k] = sign(u_b - u_a) over all sample pairs (Sec. 3.1, Algorithm 1; the pairs in an internal
- * order shared by every variable), stored as FP8 e4m3 for n <= 256 and FP4 e2m1 above (library
- * memory, m * n_0 or m * n_0 / 2 bytes with n_0 rounded up to 128 per variable). The lists of tied
+ * order shared by every variable), stored as packed FP4 e2m1 (library memory, m * n_0 / 2 bytes
+ * with n_0 rounded up to 256 per variable). The lists of tied
  * sample pairs that n_3 needs are built by the first ktau_allpairs call that stores n_3, beside
  * its contraction. Asynchronous on `stream` (allocates on first use). EINVAL when n > 2048
  * (path unsupported). */

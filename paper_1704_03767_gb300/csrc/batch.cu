@@ -41,6 +41,7 @@ struct GroupPlan {
   int64_t row0 = 0, rows = 0, units = 0, jt_tiles = 0, tiles = 0, max_n = 0, stride = 0;
   int esize = 0, obits = 0;
   void* sgn = nullptr;
+  alignas(64) unsigned char tmap_b[128];  // row-operand boxes (FP4: 120 rows)
   int64_t* tie_off = nullptr;
   uint32_t* tie_pairs = nullptr;
   int64_t tie_cap = 0;
@@ -235,7 +236,7 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
       gkey[i] = (int64_t)1 << 40 | (d.n <= 1024 ? 0 : 1);
     } else {
       const int ob = ktau_sign_obits(d.n, opt);
-      const int64_t bytes = (d.n * (d.n - 1) / 2 + 127) / 128 * 128 * ob / 8;
+      const int64_t bytes = ktau_kpad(d.n * (d.n - 1) / 2, ob) * ob / 8;
       int lg = 6;
       while (((int64_t)1 << lg) < bytes) ++lg;
       gkey[i] = (ob / 4) * 64 + lg;
@@ -326,13 +327,16 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
         D.w = (D.m + D.tq - 1) / D.tq;
         tp.push_back(tp.back() + D.w * (D.w + 1) / 2);
       } else {
-        D.esize = (int)(G.key / 64) == 4 ? 2 : 1;  // BF16 takes 2 bytes in shared memory
+        const int gobits = (int)(G.key / 64) * 4;
+        D.esize = gobits == 16 ? 2 : 1;  // BF16 takes 2 bytes in shared memory
         bp.push_back(bp.back() + (D.m + erows - 1) / erows);
         const int64_t K = D.n * (D.n - 1) / 2;
-        const int64_t K_pad = (K + 127) / 128 * 128;
-        D.num_kb = K_pad * D.esize / 128;
+        const int64_t K_pad = ktau_kpad(K, gobits);
+        // stage rows of 128 bytes: 128 FP8 / 64 BF16 elements, or 256 packed FP4 elements
+        D.num_kb = gobits == 4 ? K_pad / 256 : K_pad * D.esize / 128;
         kpad_max = std::max(kpad_max, K_pad);
-        D.wS = (D.m + 255) / 256;
+        const int st = ktau_pair_tile(gobits);  // super-tile side of the pair contraction
+        D.wS = (D.m + st - 1) / st;
         up.push_back(up.back() + D.wS * (D.wS + 1));
         const int64_t w = (D.m + 255) / 256;
         jp.push_back(jp.back() + w * (w + 1) / 2);
@@ -380,7 +384,9 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
       D.tie_cap = G.tie_cap;
     }
     if (B->source != ktau_batch::kMeasure &&
-        (s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows, G.obits)) != KTAU_OK) {
+        ((s = ktau_signgemm_make_tmap(G.tmap, G.sgn, G.stride, G.rows, G.obits, 128)) != KTAU_OK ||
+         (s = ktau_signgemm_make_tmap(G.tmap_b, G.sgn, G.stride, G.rows, G.obits,
+                                      ktau_pair_tile(G.obits) / 2)) != KTAU_OK)) {
       return s;
     }
   }
@@ -477,6 +483,7 @@ extern "C" ktau_status ktau_batch_run(ktau_batch* B, void* stream) {
     g.sgn = G.sgn;
     g.stride = G.stride;
     g.tmap = G.tmap;
+    g.tmap_b = G.tmap_b;
     s = ktau_signgemm_batch(g, ls);
   }
   // join: the caller's stream waits for every lane (also after an error, so that no lane is left

@@ -56,6 +56,11 @@ struct ktau_ranked {
   int esize, obits;
   int sg_ready;
   alignas(64) unsigned char tmap[128];
+  // FP4 only: the same rows as plain bytes, for the block-scaled (kind::mxf4) pair contraction,
+  // which reads the packed e2m1 elements directly (tmap expands them to one byte each): boxes of
+  // 128 rows (column operand) and of 120 rows (row operand).
+  alignas(64) unsigned char tmap_mx[128];
+  alignas(64) unsigned char tmap_mxb[128];
   size_t sgn_bytes;
   // Lists of tied sample pairs for n_3 (tie_off[m+1] = prefix of T, tie_pairs[(a << 16) | b]);
   // a variable is listed when its list ends within tie_cap entries.

@@ -57,6 +57,26 @@ constexpr int STAGES2 = 7;
 constexpr int STAGE2_BYTES = A_BYTES + BM * BKB;  // 32 KB
 constexpr size_t SMEM2_BYTES = 1024 /*align*/ + (size_t)STAGES2 * STAGE2_BYTES + 256 /*barriers*/;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
+constexpr int kMxFmt = 9;  // ContractArgs::afmt of block-scaled FP4 operands
+// Block-scaled FP4 pair kernel: TMEM holds two accumulators and the scale factors, so its MMA is
+// N = 240 rows (accumulators at columns 0 and 256, scale factors at columns 496..511) and its
+// super-tiles are 240 x 240. The column operand is still loaded as 256 rows (M = 256 of the pair);
+// the 16 columns past the super-tile are the next super-tile's first columns, whose counts (and
+// hence outputs) are identical, so storing them again is harmless.
+constexpr int MXT = 240;       // super-tile side
+constexpr int MXB = MXT / 2;   // row-operand rows per CTA
+constexpr uint32_t kSfCol = 496;
+// Pair kernel with block-scaled FP4: stages of 16 KB (column operand) + 15 KB (120 rows), and a
+// 32-row slot of row data per epilogue warp (broadcast reads instead of shuffles).
+constexpr int STAGE2_MX_BYTES = 128 * 128 + MXB * 128;
+// Epilogue warps of the pair kernel: four per TMEM lane quarter, each a quarter of the unit's rows
+// (more warps in flight hide the latency of the per-output arithmetic and stores).
+constexpr int PAIR_EW = 8;
+constexpr int PAIR_THREADS = 64 + 32 * PAIR_EW;
+constexpr size_t SMEM2_MX_BYTES = 1024 + (size_t)7 * STAGE2_MX_BYTES +
+                                  (size_t)PAIR_EW * 32 * 16 /*row slots*/ + 256 /*barriers*/;
+static_assert(SMEM2_MX_BYTES <= 232448, "shared memory of the block-scaled pair kernel");
+static_assert(STAGE2_MX_BYTES % 1024 == 0, "stages start on 1024-byte swizzle atoms");
 
 __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
 
@@ -318,7 +338,7 @@ __global__ void __launch_bounds__(kExpandThreads) batch_sign_expand_kernel(
   const int rows = (int)min((int64_t)RR, D.m - row0);
   const int n = (int)D.n;
   const int K = n * (n - 1) / 2;
-  const int K_pad = (K + 127) / 128 * 128;
+  const int K_pad = (int)ktau_kpad(K, OB);
   expand_block<OB, RR>(D.rank + row0 * D.ld, D.ld, rows, n, K, K_pad, out + (D.srow + row0) * stride,
                    stride, s_r);
 }
@@ -441,8 +461,11 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) 
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+// Arrive on a barrier of the leader CTA without release semantics: used to hand an accumulator
+// back, where the only ordering needed is that of the TMEM reads, which tcgen05.wait::ld has
+// already completed; a release arrive would also wait for the warp's global stores.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
                : "memory");
 }
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -502,6 +525,18 @@ __device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t a, uint64_t 
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
   }
 }
+// Block-scaled FP4 pair MMA (kind::mxf4, one UE8M0 scale per 32 elements along K): packed e2m1
+// operands, K = 64 per instruction (32 bytes of each operand row); the scale factors are read
+// from TMEM at sfa / sfb.
+__device__ __forceinline__ void umma_pair_mx(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                             uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5],"
+      " p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate));
+}
 // Arrives on the mbarrier at this shared-memory offset in both CTAs of the pair once the pair's
 // earlier MMAs have completed.
 __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
@@ -529,14 +564,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Writes the same 32-bit word into 16 consecutive columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t w) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1};" ::"r"(taddr), "r"(w)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------------------------
 // Contraction kernel
 // ---------------------------------------------------------------------------------------------
 // ktau_tau32_fast for |S| < 2^24, where S is exact in FP32 (the split's low part is zero): the
-// same float-float product and the same rounding test, without the split.
-__device__ __forceinline__ bool tau32_fast_small(int S, float rhi, float rlo, float2 fv,
+// same float-float product and the same rounding test, without the split. sh is S as FP32 (the
+// accumulator's exact sum).
+__device__ __forceinline__ bool tau32_fast_small(float sh, float rhi, float rlo, float2 fv,
                                                  float& out) {
-  const float sh = __int2float_rn(S);
   const float th = __fmul_rn(sh, rhi);
   const float tl = __fadd_rn(__fmaf_rn(sh, rhi, -th), __fmul_rn(sh, rlo));
   const float ph = __fmul_rn(th, fv.x);
@@ -579,21 +625,21 @@ struct RowsReg {
 // Interior 32 x 32 block of the epilogue (all pairs valid, 32-bit counts, FP32 tau only): row j
 // of the block is register j; lane = column, so each store is contiguous across the warp. Rows
 // whose FP32 rounding is undecided by the float-float test are flagged in `slow`.
-template <bool WS, bool WN, class Rows>
-__device__ __forceinline__ void epi_rows32(const uint32_t (&r)[32], const Rows& rows, float2 c_rff,
-                                           float* o32, int* oS, int* oN, uint32_t& slow,
-                                           float n0f) {
+template <bool WS, bool WN, int NR, class Rows>
+__device__ __forceinline__ void epi_rows32(const uint32_t (&sv)[32], const Rows& rows,
+                                           float2 c_rff, float* o32, int* oS, int* oN,
+                                           uint32_t& slow, float n0f) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
+  for (int j = 0; j < NR; ++j) {
     const RowInfo R = rows(j);
-    const int S = __float2int_rn(__uint_as_float(r[j]));
+    const float sh = __uint_as_float(sv[j]);  // the exact integer sum
     float tv;
     if (n0f != 0.f)  // tau-a: S / n_0, one IEEE division of exact FP32 integers (n_0 < 2^24)
-      tv = __fdiv_rn((float)S, n0f);
-    else if (!tau32_fast_small(S, R.rhi, R.rlo, c_rff, tv))
+      tv = __fdiv_rn(sh, n0f);
+    else if (!tau32_fast_small(sh, R.rhi, R.rlo, c_rff, tv))
       slow |= 1u << j;
     __stcs(o32 + R.base, tv);
-    if (WS) __stcs(oS + R.base, S);
+    if (WS) __stcs(oS + R.base, __float2int_rn(sh));
     if (WN) __stcs(oN + R.base, 0);
   }
 }
@@ -616,11 +662,13 @@ struct ContractArgs {
   SideArgs row, col;
   int64_t n, num_kb;
   int tri;                 // 1: upper triangle of one matrix; 0: rectangle rows x cols
+  int st;                  // tri: super-tile side (256, or MXT for block-scaled FP4)
   int64_t wS;              // tri: super-tiles per side
   int64_t wG;              // tri: traversal groups per side
   int64_t ncb;             // rect: column blocks of BM
   int bnr;                 // output rows per unit: 256, or 128 / 64 for short query batches
-  int afmt;                // kind::f8f6f4 operand format: 0 = E4M3, 5 = E2M1 (FP4)
+  int afmt;                // kind::f8f6f4 operand format: 0 = E4M3, 5 = E2M1 (FP4), or kMxFmt:
+                           // packed E2M1 through kind::mxf4 (pair kernel only)
   // Permutation test (exceed != nullptr): count |S| >= |s_obs[k]| into exceed[k] instead of
   // storing tau / S / n_3 (triangle, single matrix only).
   const int32_t* s_obs;
@@ -650,6 +698,9 @@ struct Prob {
 
 struct Unit {
   int64_t y0, x0;   // unit origin in the problem's own rows (up to 256) / columns (128)
+  int64_t yend;     // first row past the unit (the super-tile's or the matrix's end)
+  int64_t xend;     // first column past the unit's super-tile (columns beyond it repeat the next
+                    // super-tile's outputs: stored twice with equal values, counted once)
   bool live;
   int ta, tb;       // TMA row coordinates of the A (column variables) and B (row variables) tiles
   int64_t num_kb;
@@ -715,8 +766,10 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
     const int64_t lu = u - a.unit_prefix[lo];
     int64_t ys, xs;
     ktau_tile_coord(D.wS, lu >> 1, ys, xs);
-    r.y0 = ys * 256;
-    r.x0 = xs * 256 + (lu & 1) * BM;
+    r.y0 = ys * a.st;
+    r.x0 = xs * a.st + (lu & 1) * BM;
+    r.yend = min(r.y0 + (int64_t)a.st, D.m);
+    r.xend = min((xs + 1) * (int64_t)a.st, D.m);
     const int64_t xend = min(r.x0 + (int64_t)BM, D.m);
     r.live = r.y0 < D.m && r.x0 < D.m && xend - 1 > r.y0;
     r.ta = (int)(D.srow + r.x0);
@@ -734,17 +787,19 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
     int64_t gy, gx;
     ktau_tile_coord(a.wG, gid, gy, gx);
     const int64_t ys = gy * GROUP + loc / GROUP, xs = gx * GROUP + loc % GROUP;
-    r.y0 = ys * 256;
-    r.x0 = xs * 256 + (u & 1) * BM;
+    r.y0 = ys * a.st;
+    r.x0 = xs * a.st + (u & 1) * BM;
     r.ta = (int)r.x0;
     r.tb = (int)r.y0;
+    r.yend = min(r.y0 + (int64_t)a.st, a.row.m);
+    r.xend = min((xs + 1) * (int64_t)a.st, a.row.m);
     if (ys >= a.wS || xs >= a.wS || ys > xs) {
       r.live = false;
       return r;
     }
     const int64_t m = a.row.m;
     const int64_t xend = min(r.x0 + (int64_t)BM, m);
-    const int64_t ylast = min(r.y0 + (int64_t)BN - 1, xend - 2);
+    const int64_t ylast = min(r.yend - 1, xend - 2);
     r.live = r.y0 < m && r.x0 < m && ylast >= r.y0;
     if (r.live) {
       const uint64_t pmin = tri_p(m, r.y0, max(r.x0, r.y0 + 1));
@@ -756,6 +811,8 @@ __device__ __forceinline__ Unit unit_of(const ContractArgs& a, int64_t u) {
     r.x0 = (u % a.ncb) * BM;
     r.ta = (int)r.x0;
     r.tb = (int)r.y0;
+    r.yend = min(r.y0 + (int64_t)a.bnr, a.row.m);
+    r.xend = min(r.x0 + (int64_t)BM, a.col.m);
     r.live = r.y0 < a.row.m && r.x0 < a.col.m;
   }
   return r;
@@ -1219,157 +1276,213 @@ __device__ __forceinline__ RowInfo row_info(const Prob& P, int64_t y) {
   return info;
 }
 
+// The per-unit constants of one epilogue warp.
+struct EpiCtx {
+  Prob P;
+  int64_t mrow, mcol, vbase, v, n0;
+  int64_t yend;  // rows at or past yend are not this unit's
+  bool vown;     // this lane's column belongs to the unit's super-tile (counted once)
+  bool vin, want64, want32, s64, cols_full;
+  float2 c_rff;
+  void* n3z;  // n_3 output given: store its zeros here; the joint-ties kernels add the rest
+};
+
+__device__ __forceinline__ EpiCtx epi_ctx(const ContractArgs& a, const Unit& t, int q, int lane) {
+  EpiCtx e;
+  e.P = problem_of(a, t);
+  e.mrow = e.P.row.m;
+  e.mcol = e.P.col.m;
+  e.yend = t.yend;
+  e.vown = t.x0 + 32 * q + lane < t.xend;
+  e.vbase = t.x0 + 32 * q;
+  e.v = e.vbase + lane;
+  e.vin = e.v < e.mcol;
+  e.c_rff = e.vin ? __ldg(e.P.col.rsff + e.v) : make_float2(0.f, 0.f);
+  e.n0 = e.P.n * (e.P.n - 1) / 2;
+  e.want64 = e.P.out.tau64 != nullptr;
+  e.want32 = e.P.out.tau32 != nullptr;
+  e.s64 = e.P.out.count_bits == 64;
+  e.n3z = e.P.out.n3;
+  e.cols_full = e.vbase + 32 <= e.mcol;
+  return e;
+}
+
+// Outputs of one 32-row chunk (rows ub .. ub + 31, register j = row ub + j) of one epilogue
+// warp's 32 columns, from the integer counts r.
 template <bool kSmemRows>
+__device__ __forceinline__ void epi_chunk(const EpiCtx& E, const RowInfo* rc, const RowInfo& mine,
+                                          int64_t ub, const uint32_t (&r)[32]) {
+  const Prob& P = E.P;
+  const int64_t mrow = E.mrow, v = E.v, vbase = E.vbase, n0 = E.n0;
+  const bool vin = E.vin;
+  const float2 c_rff = E.c_rff;
+  const RowsSmem rs{rc};
+  const RowsReg rr{mine.rhi, mine.rlo, mine.base};
+  const int rows_here = (int)min((int64_t)32, E.yend - ub);
+  if (P.exceed) {  // permutation test: one exceedance count per pair, no other output
+    // Groups of 8 rows: first every observed S of the group (independent loads), then the
+    // comparisons and fire-and-forget atomic increments (each pair has one thread per launch).
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int so[8];
+      uint64_t kk[8];
+      uint32_t valid = 0;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = 8 * h + jj;
+        const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
+        const int64_t y = ub + j;
+        const uint64_t p = (uint64_t)(R.base + v);
+        kk[jj] = P.tri ? p - P.p_begin : p;
+        so[jj] = 0;
+        if (j < rows_here && vin && E.vown &&
+            (!P.tri || (v > y && p >= P.p_begin && p < P.p_end))) {
+          valid |= 1u << jj;
+          so[jj] = __ldg(P.s_obs + kk[jj]);
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int S = __float2int_rn(__uint_as_float(r[8 * h + jj]));
+        if (((valid >> jj) & 1u) && abs(S) >= abs(so[jj])) atomicAdd(P.exceed + kk[jj], 1u);
+      }
+    }
+    return;
+  }
+  // Interior blocks of 32 rows, or of 16 (the last chunk of a 240-row super-tile)
+  bool fast = (rows_here == 32 || rows_here == 16) && E.cols_full &&
+              (!P.tri || vbase > ub + rows_here - 1);
+  if (fast && P.tri) {  // every pair of these rows inside the pair range
+    const int64_t ul = ub + rows_here - 1;
+    fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
+           (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
+  }
+  if (fast && E.want32 && !E.want64 && !E.s64) {
+    float* const o32 = P.out.tau32 + (v - (int64_t)P.p_begin);
+    int* const oS = P.out.S ? (int*)P.out.S + (v - (int64_t)P.p_begin) : nullptr;
+    int* const oN = E.n3z ? (int*)E.n3z + (v - (int64_t)P.p_begin) : nullptr;
+    uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
+    const float n0f = P.out.stat ? (float)n0 : 0.f;
+#define KTAU_EPI_ROWS_N(ROWS, NR)                                           \
+  if (oS && oN)                                                             \
+    epi_rows32<true, true, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);     \
+  else if (oS)                                                              \
+    epi_rows32<true, false, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);    \
+  else if (oN)                                                              \
+    epi_rows32<false, true, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);    \
+  else                                                                      \
+    epi_rows32<false, false, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);
+#define KTAU_EPI_ROWS(ROWS)        \
+  if (rows_here == 32) {           \
+    KTAU_EPI_ROWS_N(ROWS, 32)      \
+  } else {                         \
+    KTAU_EPI_ROWS_N(ROWS, 16)      \
+  }
+    if (kSmemRows) {
+      KTAU_EPI_ROWS(rs)
+    } else {
+      KTAU_EPI_ROWS(rr)
+    }
+#undef KTAU_EPI_ROWS
+#undef KTAU_EPI_ROWS_N
+    while (slow) {  // rare: the FP64 formula decides (same thread, stored after the fast value)
+      const int j = __ffs(slow) - 1;
+      slow &= slow - 1;
+      const RowInfo R = row_info(P, ub + j);
+      const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
+      o32[R.base] = ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[ub + j],
+                               P.col.T[v]);
+    }
+  } else {
+    const bool wantS = P.out.S != nullptr;
+#pragma unroll 1
+    for (int j = 0; j < rows_here; ++j) {
+      const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
+      const int64_t y = ub + j;
+      if (!vin) continue;
+      uint64_t k;
+      if (P.tri) {
+        if (v <= y) continue;
+        const uint64_t p = (uint64_t)(R.base + v);
+        if (p < P.p_begin || p >= P.p_end) continue;
+        k = p - P.p_begin;
+      } else {
+        k = (uint64_t)(R.base + v);
+      }
+      const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
+      if (E.want64)
+        __stcs(P.out.tau64 + k, P.out.stat ? ktau_taua64(S, n0)
+                                           : ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
+      if (E.want32)
+        __stcs(P.out.tau32 + k,
+               P.out.stat ? ktau_taua32(S, n0)
+                          : ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y],
+                                       P.col.T[v]));
+      if (wantS) {
+        if (E.s64)
+          __stcs((long long*)P.out.S + k, (long long)S);
+        else
+          __stcs((int*)P.out.S + k, S);
+      }
+      if (E.n3z) {
+        if (E.s64)
+          __stcs((long long*)E.n3z + k, 0ll);
+        else
+          __stcs((int*)E.n3z + k, 0);
+      }
+    }
+  }
+}
+
+// Releases an accumulator once this warp's tcgen05.ld of it have completed: one arrive per warp
+// (on the leader CTA's barrier in the pair form).
+__device__ __forceinline__ void release_acc(uint32_t tempty_bar, bool remote, int lane) {
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) {
+    if (remote)
+      mbar_arrive_cluster_relaxed(tempty_bar);
+    else
+      mbar_arrive(tempty_bar);
+  }
+}
+
+// kSlot (with !kSmemRows): ri is this warp's 32-entry slot; each chunk's row data go there
+// (one entry per lane) and are read back by broadcast.
+template <bool kSmemRows, bool kSlot = false, int EW = EPI_WARPS>
 __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit& t, RowInfo* ri,
                                               uint32_t tmem_base, uint32_t tfull_bar,
                                               uint32_t tfull_phase, int acc, int warp, int lane,
                                               uint32_t tempty_bar, bool remote) {
   const int q = warp & 3;
-  const int half_sel = (warp - 2) >> 2;
-  const int nhalf = a.bnr / 64;  // 32-row chunks per half
-  const Prob P = problem_of(a, t);
-  const int64_t mrow = P.row.m, mcol = P.col.m;
-  const int64_t vbase = t.x0 + 32 * q;
-  const int64_t v = vbase + lane;
-  const bool vin = v < mcol;
-  const float2 c_rff = vin ? __ldg(P.col.rsff + v) : make_float2(0.f, 0.f);
+  const int half_sel = (warp - 2) >> 2;     // which part of the rows (EW / 4 parts)
+  const int nhalf = a.bnr / 32 / (EW / 4);  // 32-row chunks per part
+  const EpiCtx E = epi_ctx(a, t, q, lane);
   if (kSmemRows) {
     const int64_t hrow0 = t.y0 + 32 * half_sel * nhalf;
-    for (int i = lane; i < 32 * nhalf; i += 32) ri[i] = row_info(P, hrow0 + i);
+    for (int i = lane; i < 32 * nhalf; i += 32) ri[i] = row_info(E.P, hrow0 + i);
     __syncwarp();
   }
   if (!mbar_wait(tfull_bar, tfull_phase)) return false;
   tc_fence_after();
-  const int64_t n0 = P.n * (P.n - 1) / 2;
-  const bool want64 = P.out.tau64 != nullptr, want32 = P.out.tau32 != nullptr;
-  const bool s64 = P.out.count_bits == 64;
-  // n_3 output given: store its zeros here; the joint-ties kernels add the nonzero counts.
-  void* const n3z = P.out.n3;
-  const bool cols_full = vbase + 32 <= mcol;
+  RowInfo next;  // this lane's row of the next chunk, loaded one chunk ahead
+  if (!kSmemRows) next = row_info(E.P, t.y0 + 32 * half_sel * nhalf + lane);
   for (int c = half_sel * nhalf; c < (half_sel + 1) * nhalf; ++c) {
     const int64_t ub = t.y0 + 32 * c;
-    RowInfo mine;
-    if (!kSmemRows) mine = row_info(P, ub + lane);
+    const RowInfo mine = next;
+    if (!kSmemRows && c + 1 < (half_sel + 1) * nhalf) next = row_info(E.P, ub + 32 + lane);
     uint32_t r[32];
     tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
-    if (c == (half_sel + 1) * nhalf - 1) {
-      // Accumulator may be overwritten by the next unit: one arrive per warp (on the leader
-      // CTA's barrier in the pair form).
-      tc_fence_before();
+    // the accumulator may be overwritten by the next unit once the last chunk is read
+    if (c == (half_sel + 1) * nhalf - 1) release_acc(tempty_bar, remote, lane);
+    if (ub >= E.yend) continue;
+    if (kSlot) {
+      ri[lane] = mine;
       __syncwarp();
-      if (lane == 0) {
-        if (remote)
-          mbar_arrive_cluster(tempty_bar);
-        else
-          mbar_arrive(tempty_bar);
-      }
-    }
-    if (ub >= mrow) continue;
-    const RowsSmem rs{ri + 32 * (c - half_sel * nhalf)};
-    const RowsReg rr{mine.rhi, mine.rlo, mine.base};
-    const int rows_here = (int)min((int64_t)32, mrow - ub);
-    if (P.exceed) {  // permutation test: one exceedance count per pair, no other output
-      // Groups of 8 rows: first every observed S of the group (independent loads), then the
-      // comparisons and fire-and-forget atomic increments (each pair has one thread per launch).
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        int so[8];
-        uint64_t kk[8];
-        uint32_t valid = 0;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = 8 * h + jj;
-          const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
-          const int64_t y = ub + j;
-          const uint64_t p = (uint64_t)(R.base + v);
-          kk[jj] = P.tri ? p - P.p_begin : p;
-          so[jj] = 0;
-          if (j < rows_here && vin && (!P.tri || (v > y && p >= P.p_begin && p < P.p_end))) {
-            valid |= 1u << jj;
-            so[jj] = __ldg(P.s_obs + kk[jj]);
-          }
-        }
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int S = __float2int_rn(__uint_as_float(r[8 * h + jj]));
-          if (((valid >> jj) & 1u) && abs(S) >= abs(so[jj])) atomicAdd(P.exceed + kk[jj], 1u);
-        }
-      }
-      continue;
-    }
-    bool fast = rows_here == 32 && cols_full && (!P.tri || vbase > ub + 31);
-    if (fast && P.tri) {  // every pair of these 32 rows inside the pair range
-      const int64_t ul = ub + 31;
-      fast = (uint64_t)(ub * (2 * mrow - ub - 1) / 2) >= P.p_begin &&
-             (uint64_t)(ul * (2 * mrow - ul - 1) / 2 + (mrow - ul - 1)) <= P.p_end;
-    }
-    if (fast && want32 && !want64 && !s64) {
-      float* const o32 = P.out.tau32 + (v - (int64_t)P.p_begin);
-      int* const oS = P.out.S ? (int*)P.out.S + (v - (int64_t)P.p_begin) : nullptr;
-      int* const oN = n3z ? (int*)n3z + (v - (int64_t)P.p_begin) : nullptr;
-      uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
-      const float n0f = P.out.stat ? (float)n0 : 0.f;
-#define KTAU_EPI_ROWS(ROWS)                                                 \
-  if (oS && oN)                                                             \
-    epi_rows32<true, true>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);         \
-  else if (oS)                                                              \
-    epi_rows32<true, false>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);        \
-  else if (oN)                                                              \
-    epi_rows32<false, true>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);        \
-  else                                                                      \
-    epi_rows32<false, false>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);
-      if (kSmemRows) {
-        KTAU_EPI_ROWS(rs)
-      } else {
-        KTAU_EPI_ROWS(rr)
-      }
-#undef KTAU_EPI_ROWS
-      while (slow) {  // rare: the FP64 formula decides (same thread, stored after the fast value)
-        const int j = __ffs(slow) - 1;
-        slow &= slow - 1;
-        const RowInfo R = row_info(P, ub + j);
-        const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
-        o32[R.base] = ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[ub + j],
-                                 P.col.T[v]);
-      }
+      epi_chunk<true>(E, ri, mine, ub, r);
+      __syncwarp();  // the slot is rewritten for the next chunk
     } else {
-      const bool wantS = P.out.S != nullptr;
-#pragma unroll 1
-      for (int j = 0; j < rows_here; ++j) {
-        const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
-        const int64_t y = ub + j;
-        if (!vin) continue;
-        uint64_t k;
-        if (P.tri) {
-          if (v <= y) continue;
-          const uint64_t p = (uint64_t)(R.base + v);
-          if (p < P.p_begin || p >= P.p_end) continue;
-          k = p - P.p_begin;
-        } else {
-          k = (uint64_t)(R.base + v);
-        }
-        const int S = __float2int_rn(__uint_as_float(reg_at(r, j)));
-        if (want64)
-          __stcs(P.out.tau64 + k, P.out.stat ? ktau_taua64(S, n0)
-                                             : ktau_tau64(S, P.row.rs64[y], P.col.rs64[v]));
-        if (want32)
-          __stcs(P.out.tau32 + k,
-                 P.out.stat ? ktau_taua32(S, n0)
-                            : ktau_tau32(S, make_float2(R.rhi, R.rlo), c_rff, n0, P.row.T[y],
-                                         P.col.T[v]));
-        if (wantS) {
-          if (s64)
-            __stcs((long long*)P.out.S + k, (long long)S);
-          else
-            __stcs((int*)P.out.S + k, S);
-        }
-        if (n3z) {
-          if (s64)
-            __stcs((long long*)n3z + k, 0ll);
-          else
-            __stcs((int*)n3z + k, 0);
-        }
-      }
+      epi_chunk<kSmemRows>(E, ri + 32 * (c - half_sel * nhalf), mine, ub, r);
     }
   }
   if (kSmemRows) __syncwarp();  // ri is rewritten for the next unit
@@ -1533,14 +1646,21 @@ __device__ __forceinline__ bool pair_live(const ContractArgs& a, int64_t s2) {
   return unit_of(a, 2 * s2).live || unit_of(a, 2 * s2 + 1).live;
 }
 
-template <int ESIZE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+// MX: block-scaled FP4 operands (kind::mxf4, packed e2m1 rows of 256 elements per 128-byte stage
+// row, every scale factor 1.0, i.e. every byte of TMEM columns kSfCol.. is 0x7F = 2^0), MMA
+// N = MXT rows: 240 x 240 super-tiles, the row operand loaded as 120 rows per CTA (tmRow's boxes
+// are 120 rows high).
+template <int ESIZE, bool MX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1)
     contract2_kernel(const __grid_constant__ CUtensorMap tmRow,
                      const __grid_constant__ CUtensorMap tmCol, const ContractArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* stage_base = smem;
-  uint64_t* bars = (uint64_t*)(smem + (size_t)STAGES2 * STAGE2_BYTES);
+  constexpr int kStageBytes = MX ? STAGE2_MX_BYTES : STAGE2_BYTES;
+  RowInfo* const rslots = (RowInfo*)(smem + (size_t)STAGES2 * kStageBytes);  // MX only
+  uint64_t* bars =
+      (uint64_t*)(smem + (size_t)STAGES2 * kStageBytes + (MX ? PAIR_EW * 32 * 16 : 0));
   // bars: full[STAGES2], empty[STAGES2], tfull[2], tempty[2]; then the TMEM base slot
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES2 + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1560,7 +1680,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(TFULL(s), 1);
-      mbar_init(TEMPTY(s), 2 * EPI_WARPS);
+      mbar_init(TEMPTY(s), 2 * PAIR_EW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -1575,6 +1695,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   cluster_sync();  // both CTAs' barriers initialised before any cross-CTA signal
   tc_fence_after();
   const uint32_t tmem_base = *(volatile uint32_t*)tmem_slot;
+  if (MX) {
+    // Scale factors 1.0 in both CTAs before the first MMA: warps 2..5 cover the four lane
+    // quarters (a warp reaches the TMEM lanes of quarter warp % 4), columns 496..511.
+    if (warp >= 2 && warp < 6) {
+      tmem_fill16(tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + kSfCol, 0x7F7F7F7Fu);
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+  }
+  constexpr int kAccs = 2;       // accumulators in TMEM, at columns 0 and BN
+  constexpr int kRows = MX ? MXT : BN;    // MMA N: output rows of a unit
+  constexpr int kBrows = kRows / 2;       // row-operand rows loaded per CTA
 
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
@@ -1588,16 +1723,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       for (int64_t s2 = s_lo + cid; ok && s2 < s_hi; s2 += ncl) {
         if (!pair_live(a, s2)) continue;
         const Unit t = unit_of(a, 2 * s2 + rank);
-        const int brow = t.tb + BM * (int)rank;  // this CTA's half of the rows (operand row)
+        const int brow = t.tb + kBrows * (int)rank;  // this CTA's half of the rows (operand row)
         for (int64_t kb = 0; kb < t.num_kb; ++kb) {
           if (!mbar_wait(EMPTY(stage), phase ^ 1u)) {
             ok = false;
             break;
           }
-          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE2_BYTES);
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * kStageBytes);
           const uint32_t sb = sa + A_BYTES;
-          // both CTAs' boxes; FP4 boxes count their packed bytes (half the footprint)
-          if (rank == 0) mbar_expect_tx(FULL(stage), (2u * STAGE2_BYTES) >> (a.afmt == 5 ? 1 : 0));
+          // both CTAs' boxes; FP4 boxes expanded by the TMA count their packed bytes (half the
+          // footprint); block-scaled FP4 boxes are plain bytes
+          if (rank == 0)
+            mbar_expect_tx(FULL(stage),
+                           (2u * (A_BYTES + kBrows * BKB)) >> (!MX && a.afmt == 5 ? 1 : 0));
           const uint32_t full_leader = cluster_addr(FULL(stage), 0);
           const int kx = (int)(kb * BKB);
           tma_load_2d_pair(sa, &tmCol, kx, t.ta, full_leader, pol);
@@ -1621,8 +1759,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     // ---------------- MMA issuer (leader CTA) ----------------
     if (lane == 0 && rank == 0) {
       const uint32_t kFmt = ESIZE == 1 ? (uint32_t)a.afmt : 1u;  // E4M3/E2M1 or BF16 (f16)
-      const uint32_t idesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
-                             ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+      // kind::f8f6f4 / f16: F32 accumulator (bit 4), A and B formats, N / 8, M / 16.
+      // kind::mxf4: scale-factor ids 0, A and B E2M1 (1), N / 8, UE8M0 scales (bit 23), M / 16.
+      const uint32_t idesc =
+          MX ? (1u << 7) | (1u << 10) | ((uint32_t)(kRows >> 3) << 17) | (1u << 23) |
+                   ((uint32_t)((2 * BM) >> 4) << 24)
+             : (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(kRows >> 3) << 17) |
+                   ((uint32_t)((2 * BM) >> 4) << 24);
+      const uint32_t sf = tmem_base + kSfCol;
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -1640,12 +1784,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE2_BYTES);
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * kStageBytes);
           const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-          for (int k = 0; k < BKB / 32; ++k)
-            umma_pair<ESIZE>(d_tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
-                             (kb > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < BKB / 32; ++k) {
+            if (MX)
+              umma_pair_mx(d_tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, sf, sf,
+                           (kb > 0 || k > 0) ? 1u : 0u);
+            else
+              umma_pair<ESIZE>(d_tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                               (kb > 0 || k > 0) ? 1u : 0u);
+          }
           umma_commit_pair(EMPTY(stage));  // frees the stage in both CTAs
           if (++stage == STAGES2) {
             stage = 0;
@@ -1654,23 +1803,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         }
         if (!ok) break;
         umma_commit_pair(TFULL(acc));  // accumulator complete in both CTAs
-        if (++acc == 2) {
+        if (++acc == kAccs) {
           acc = 0;
           acc_phase ^= 1u;
         }
       }
     }
   } else {
-    // ---------------- Epilogue (warps 2..9, both CTAs) ----------------
+    // ---------------- Epilogue (warps 2.., both CTAs) ----------------
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int64_t s2 = s_lo + cid; s2 < s_hi; s2 += ncl) {
       if (!pair_live(a, s2)) continue;
       const Unit t = unit_of(a, 2 * s2 + rank);
-      if (!epilogue_unit<false>(a, t, nullptr, tmem_base, TFULL(acc), acc_phase, acc, warp, lane,
-                                cluster_addr(TEMPTY(acc), 0), true))
-        break;
-      if (++acc == 2) {
+      const bool ok =
+          MX ? epilogue_unit<false, true, PAIR_EW>(a, t, rslots + 32 * (warp - 2), tmem_base,
+                                                   TFULL(acc), acc_phase, acc, warp, lane,
+                                                   cluster_addr(TEMPTY(acc), 0), true)
+             : epilogue_unit<false, false, PAIR_EW>(a, t, nullptr, tmem_base, TFULL(acc),
+                                                    acc_phase, acc, warp, lane,
+                                                    cluster_addr(TEMPTY(acc), 0), true);
+      if (!ok) break;
+      if (++acc == kAccs) {
         acc = 0;
         acc_phase ^= 1u;
       }
@@ -1709,14 +1863,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // memory (row_bytes = K_pad / 2) and land in shared memory as 16-byte containers holding 16
 // elements in their first 8 bytes, one byte of shared memory per element like FP8.
 ktau_status make_tmap_raw(void* tmap, void* base, int64_t row_bytes_, int64_t rows,
-                          bool fp4 = false) {
+                          bool fp4 = false, int box_rows = BM) {
   CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(tmap);
   PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
   if (!cuTensorMapEncodeTiled) return ktau_fail(KTAU_ECUDA, "cuTensorMapEncodeTiled unavailable");
   const cuuint64_t row_bytes = (cuuint64_t)row_bytes_;
   cuuint64_t dims[2] = {fp4 ? 2 * row_bytes : row_bytes, (cuuint64_t)rows};
   cuuint64_t strides[1] = {row_bytes};
-  cuuint32_t box[2] = {(cuuint32_t)BKB, (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)BKB, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = cuTensorMapEncodeTiled(tm, fp4 ? CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B
                                               : CU_TENSOR_MAP_DATA_TYPE_UINT8,
@@ -1730,7 +1884,11 @@ ktau_status make_tmap_raw(void* tmap, void* base, int64_t row_bytes_, int64_t ro
 }
 
 ktau_status make_tmap(ktau_ranked* R) {
-  return make_tmap_raw(R->tmap, R->sgn, R->K_pad * R->obits / 8, R->m, R->obits == 4);
+  ktau_status s = make_tmap_raw(R->tmap, R->sgn, R->K_pad * R->obits / 8, R->m, R->obits == 4);
+  if (s == KTAU_OK && R->obits == 4) s = make_tmap_raw(R->tmap_mx, R->sgn, R->K_pad / 2, R->m);
+  if (s == KTAU_OK && R->obits == 4)
+    s = make_tmap_raw(R->tmap_mxb, R->sgn, R->K_pad / 2, R->m, false, MXB);
+  return s;
 }
 
 SideArgs side_of(const ktau_ranked* R) {
@@ -1811,18 +1969,20 @@ ktau_status launch_contract_maps(const void* tmap_a, const void* tmap_b, const C
 template <int ESIZE>
 ktau_status launch_contract2_map(const void* tmap_row, const void* tmap_col,
                                  const ContractArgs& args, int64_t units, cudaStream_t st) {
-  auto kern = contract2_kernel<ESIZE>;
-  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)SMEM2_BYTES));
-  static int max_clusters[64] = {0};
+  const bool mx = ESIZE == 1 && args.afmt == kMxFmt;
+  auto kern = mx ? contract2_kernel<1, true> : contract2_kernel<ESIZE, false>;
+  const size_t smem = mx ? SMEM2_MX_BYTES : SMEM2_BYTES;
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  static int max_clusters_by[2][64] = {{0}};
+  int* const max_clusters = max_clusters_by[mx ? 1 : 0];
   int dev = 0;
   KTAU_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return ktau_fail(KTAU_EINVAL, "device index out of range");
   if (max_clusters[dev] == 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * ktau_sm_count()));
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM2_BYTES;
+    cfg.blockDim = dim3(PAIR_THREADS);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
     attr.val.clusterDim.x = 2;
@@ -1840,17 +2000,27 @@ ktau_status launch_contract2_map(const void* tmap_row, const void* tmap_col,
   if (clusters > supers) clusters = supers;
   if (clusters < 1) clusters = 1;
   KTAU_TRACE("contract_kernel", st);
-  kern<<<(unsigned)(2 * clusters), THREADS, SMEM2_BYTES, st>>>(
+  kern<<<(unsigned)(2 * clusters), PAIR_THREADS, smem, st>>>(
       *reinterpret_cast<const CUtensorMap*>(tmap_row),
       *reinterpret_cast<const CUtensorMap*>(tmap_col), args);
   KTAU_CUDA(cudaGetLastError());
   return KTAU_OK;
 }
 
+// Tensor maps of a handle's operands for the pair kernel with these arguments: the row operand
+// (u, the MMA's B) and the column operand (v, the MMA's A).
+const void* pair_tmap_row(const ktau_ranked* R, const ContractArgs& args) {
+  return args.afmt == kMxFmt ? (const void*)R->tmap_mxb : (const void*)R->tmap;
+}
+const void* pair_tmap_col(const ktau_ranked* R, const ContractArgs& args) {
+  return args.afmt == kMxFmt ? (const void*)R->tmap_mx : (const void*)R->tmap;
+}
+
 template <int ESIZE>
 ktau_status launch_contract2(const ktau_ranked* R, const ContractArgs& args, int64_t units,
                              cudaStream_t st) {
-  return launch_contract2_map<ESIZE>(R->tmap, R->tmap, args, units, st);
+  return launch_contract2_map<ESIZE>(pair_tmap_row(R, args), pair_tmap_col(R, args), args, units,
+                                     st);
 }
 
 // Rows from A, columns from B: the MMA's A operand (TMEM lanes) is the column side.
@@ -1867,9 +2037,9 @@ bool ktau_signgemm_supported(int64_t n) { return n >= 2 && n <= KTAU_SIGNGEMM_MA
 int ktau_sign_obits(int64_t n, const ktau_options* opt) {
   if (opt && (opt->operand_bits == 4 || opt->operand_bits == 8 || opt->operand_bits == 16))
     return opt->operand_bits;
-  // FP8 for short vectors; FP4 (half the operand bytes, so more of the operands stay in L2)
-  // once the operand rows are long.
-  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? (n <= 256 ? KTAU_SIGNGEMM_DEFAULT_BITS : 4) : 16;
+  // FP4: half the operand bytes of FP8, and the pair contraction reads them with the
+  // block-scaled FP4 MMA (measured on GB300 at 16384 x 128: 0.72 ms against 0.79 ms with FP8).
+  return n <= KTAU_SIGNGEMM_FP8_MAX_N ? KTAU_SIGNGEMM_DEFAULT_BITS : 16;
 }
 
 
@@ -1990,7 +2160,7 @@ ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
     return ktau_fail(KTAU_EINVAL, "sign contraction supports 2 <= n <= %d", KTAU_SIGNGEMM_MAX_N);
   const int64_t n = R->n;
   R->K = n * (n - 1) / 2;
-  R->K_pad = (R->K + 127) / 128 * 128;
+  R->K_pad = ktau_kpad(R->K, obits);
   R->obits = obits;
   R->esize = obits == 16 ? 2 : 1;
   R->sgn_bytes = (size_t)R->m * R->K_pad * obits / 8;
@@ -2075,12 +2245,14 @@ ContractArgs tri_args(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end, co
   ContractArgs a;
   a.row = a.col = side_of(R);
   a.n = R->n;
-  a.num_kb = R->K_pad * R->esize / BKB;
+  // FP4 operands go through the block-scaled pair kernel: 256 packed elements per stage row
+  a.num_kb = R->obits == 4 ? R->K_pad / 2 / BKB : R->K_pad * R->esize / BKB;
   a.tri = 1;
-  a.wS = (m + 255) / 256;
+  a.st = ktau_pair_tile(R->obits);
+  a.wS = (m + a.st - 1) / a.st;
   a.ncb = 0;
   a.bnr = BN;
-  a.afmt = R->obits == 4 ? 5 : 0;
+  a.afmt = R->obits == 4 ? kMxFmt : 0;
   a.p_begin = p_begin;
   a.p_end = p_end;
   a.ldo = 0;
@@ -2093,8 +2265,8 @@ ContractArgs tri_args(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end, co
   ktau_tile_coord(m - 1, (int64_t)p_begin, i0, j0);
   ktau_tile_coord(m - 1, (int64_t)(p_end - 1), i1, j1);
   a.wG = (a.wS + GROUP - 1) / GROUP;
-  a.unit_lo = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i0 / 256 / GROUP);
-  a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / 256 / GROUP + 1);
+  a.unit_lo = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i0 / a.st / GROUP);
+  a.unit_hi = 2 * GROUP * GROUP * ktau_rowstart(a.wG, i1 / a.st / GROUP + 1);
   a.s_obs = nullptr;
   a.exceed = nullptr;
   return a;
@@ -2133,6 +2305,7 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   a.n = Q->n;
   a.num_kb = Q->K_pad * Q->esize / BKB;
   a.tri = 0;
+  a.st = 256;
   a.wS = 0;
   a.wG = 0;
   a.ncb = (D->m + BM - 1) / BM;
@@ -2187,10 +2360,15 @@ ktau_status ktau_signgemm_check_error(cudaStream_t st) {
   return KTAU_OK;
 }
 
+// Batched groups run on the pair kernel only: FP4 rows are mapped as plain bytes for the
+// block-scaled MMA.
 ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows,
-                                    int obits) {
-  return make_tmap_raw(tmap, base, row_bytes, rows, obits == 4);
+                                    int obits, int box_rows) {
+  (void)obits;
+  return make_tmap_raw(tmap, base, row_bytes, rows, false, box_rows);
 }
+
+int ktau_pair_tile(int obits) { return obits == 4 ? MXT : 256; }
 
 ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   if (g.nb == 0 || g.rows == 0) return KTAU_OK;
@@ -2232,10 +2410,11 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
   a.unit_lo = 0;
   a.unit_hi = g.units;
   a.tri = 1;
+  a.st = ktau_pair_tile(g.obits);
   a.bnr = BN;
-  a.afmt = g.obits == 4 ? 5 : 0;
-  ktau_status s = g.esize == 1 ? launch_contract2_map<1>(g.tmap, g.tmap, a, g.units, st)
-                               : launch_contract2_map<2>(g.tmap, g.tmap, a, g.units, st);
+  a.afmt = g.obits == 4 ? kMxFmt : 0;
+  ktau_status s = g.esize == 1 ? launch_contract2_map<1>(g.tmap_b, g.tmap, a, g.units, st)
+                               : launch_contract2_map<2>(g.tmap_b, g.tmap, a, g.units, st);
   if (s != KTAU_OK) return s;
   const int jcols = g.max_n <= 1024 ? 64 : 32;
   const size_t smem = (size_t)(JCAP + JT + 8) * 4 + (size_t)g.max_n * (jcols + 1) * sizeof(uint16_t);
@@ -2311,8 +2490,9 @@ extern "C" ktau_status ktau_permutation_exceed(const ktau_ranked* Rc, const uint
     if (e != cudaSuccess) s = ktau_cuda_fail(e, "permute_ranks_kernel");
     if (s == KTAU_OK) s = launch_sign_expand(&Rp, st);
     if (s == KTAU_OK)
-      s = R->esize == 1 ? launch_contract2_map<1>(R->tmap, Rp.tmap, a, units, st)
-                        : launch_contract2_map<2>(R->tmap, Rp.tmap, a, units, st);
+      s = R->esize == 1
+              ? launch_contract2_map<1>(pair_tmap_row(R, a), pair_tmap_col(&Rp, a), a, units, st)
+              : launch_contract2_map<2>(pair_tmap_row(R, a), pair_tmap_col(&Rp, a), a, units, st);
   }
   // The scratch goes back to the cache only once the work that uses it has finished.
   const cudaError_t e = cudaStreamSynchronize(st);

@@ -18,8 +18,13 @@
 __host__ __device__ inline int ktau_expand_rows(int64_t n) {
   return n <= 512 ? 8 : (n <= 1024 ? 4 : 2);
 }
+// Operand row length in elements: n_0 rounded up to whole stages of the contraction (128 elements
+// of FP8 / BF16; 256 packed FP4 elements, one 128-byte row of a block-scaled FP4 stage).
+__host__ __device__ inline int64_t ktau_kpad(int64_t K, int obits) {
+  return obits == 4 ? (K + 255) / 256 * 256 : (K + 127) / 128 * 128;
+}
 // Operand bits used when the caller does not choose (operand_bits = 0).
-#define KTAU_SIGNGEMM_DEFAULT_BITS 8
+#define KTAU_SIGNGEMM_DEFAULT_BITS 4
 
 bool ktau_signgemm_supported(int64_t n);
 // Operand bits of the single-matrix and query contraction: 4 (FP4 e2m1), 8 or 16.
@@ -53,10 +58,14 @@ struct ktau_sg_group {
   int64_t tie_cap;
   void* sgn;
   int64_t stride;
-  const void* tmap;            // CUtensorMap of sgn (host memory, 128 bytes)
+  const void* tmap;            // CUtensorMap of sgn (host memory, 128 bytes), 128-row boxes
+  const void* tmap_b;          // FP4: 120-row boxes for the row operand (else = tmap)
 };
+// Tensor map of a group's stacked operands, boxes of box_rows rows.
 ktau_status ktau_signgemm_make_tmap(void* tmap, void* base, int64_t row_bytes, int64_t rows,
-                                    int obits);
+                                    int obits, int box_rows);
+// Super-tile side of the pair contraction for this operand type (240 for block-scaled FP4).
+int ktau_pair_tile(int obits);
 ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st);
 // Device error word of the contraction kernels (bounded waits that gave up); 0 = none.
 ktau_status ktau_signgemm_check_error(cudaStream_t st);

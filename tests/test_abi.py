@@ -89,9 +89,14 @@ def test_workspace_size_without_gpu(lib):
     small = ktau.ktau_workspace_size([desc(10, 20)])
     big = ktau.ktau_workspace_size([desc(10, 20), desc(300, 500)])
     assert small >= 3 * 10 * 32 * 2 and big > small
-    # contraction datasets also hold their sign operands (n_0 rounded up to 128 bytes per row)
+    # contraction datasets also hold their sign operands: packed FP4 by default, n_0 rounded up to
+    # 256 elements (128 bytes) per row; FP8 takes twice that
     sg = ktau.ktau_workspace_size([desc(300, 100, 2)])
-    assert sg >= 300 * ((100 * 99 // 2 + 127) // 128 * 128)
+    assert sg >= 300 * ((100 * 99 // 2 + 255) // 256 * 128)
+    opt8 = ktau.Options()
+    opt8.operand_bits = 8
+    sg8 = ktau.ktau_workspace_size([desc(300, 100, 2)], options=opt8)
+    assert sg8 >= 300 * ((100 * 99 // 2 + 127) // 128 * 128) and sg8 > sg
     size = ctypes.c_size_t()
     assert lib.ktau_workspace_size(None, 1, None, ctypes.byref(size)) == 1
     arr = (ktau.BatchDesc * 1)(desc(1, 20))  # m < 2
