@@ -29,8 +29,10 @@
  *   - tau-b = (double)S / sqrt((double)(n_0-T_u) * (double)(n_0-T_v)) in IEEE FP64
  *     (round-to-nearest sqrt and divide); NaN when either factor is 0 (a constant variable).
  *     The FP32 output is the FP64 value rounded to nearest-even.
- *   - Limits: 2 <= n <= KTAU_MAX_N, 1 <= m <= KTAU_MAX_M (a single variable has no pairs). Values may be +-Inf; -0.0 equals +0.0;
- *     a NaN anywhere fails the call with KTAU_ENAN.
+ *   - Limits: 2 <= n <= KTAU_MAX_N, 1 <= m <= KTAU_MAX_M (a single variable has no pairs); the
+ *     batched and allocation-free forms take n <= KTAU_BATCH_MAX_N. Rows longer than 16384 samples
+ *     are ranked and counted (merge path) with library scratch in global memory. Values may be
+ *     +-Inf; -0.0 equals +0.0; a NaN anywhere fails the call with KTAU_ENAN.
  */
 #ifndef KTAU_H
 #define KTAU_H
@@ -43,7 +45,8 @@ extern "C" {
 #endif
 
 #define KTAU_ABI_VERSION 1
-#define KTAU_MAX_N 16384      /* samples per variable (ranks are stored as uint16) */
+#define KTAU_MAX_N 65535      /* samples per variable (ranks and sample indices are uint16) */
+#define KTAU_BATCH_MAX_N 16384 /* samples per variable in the batched and allocation-free forms */
 #define KTAU_MAX_M 4194304    /* variables per matrix */
 
 typedef enum {

@@ -18,7 +18,8 @@ KTAU_OK, KTAU_EINVAL, KTAU_ENAN, KTAU_ETOOLARGE, KTAU_ENOMEM, KTAU_ECUDA, KTAU_E
     KTAU_EBUSY = range(8)
 KTAU_F32, KTAU_I32 = 0, 1
 KTAU_PATH_AUTO, KTAU_PATH_MERGE, KTAU_PATH_SIGNGEMM = 0, 1, 2
-KTAU_MAX_N = 16384
+KTAU_MAX_N = 65535
+KTAU_BATCH_MAX_N = 16384
 
 STATUS_NAMES = {0: "KTAU_OK", 1: "KTAU_EINVAL", 2: "KTAU_ENAN", 3: "KTAU_ETOOLARGE",
                 4: "KTAU_ENOMEM", 5: "KTAU_ECUDA", 6: "KTAU_ETIMEOUT", 7: "KTAU_EBUSY"}

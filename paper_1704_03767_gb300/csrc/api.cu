@@ -174,12 +174,15 @@ void pin_give(ktau_stats* p) {
   g_pin_free.push_back((int)(p - g_pin));
 }
 
-// Releases the pinned slot and event of a handle whose copy has completed (or never started).
+// Releases the pinned slot and event of a handle whose copy has completed (or never started),
+// and the long-row rank scratch (the rank transform precedes the statistics copy on its stream).
 void stats_release(ktau_ranked* R) {
   if (R->stats_pin) pin_give(R->stats_pin);
   if (R->stats_ev) cudaEventDestroy(R->stats_ev);
   R->stats_pin = nullptr;
   R->stats_ev = nullptr;
+  if (R->tmp_block) ktau_dfree(R->tmp_block, R->tmp_bytes);
+  R->tmp_block = nullptr;
 }
 
 ktau_status rank_prepare_impl(const void* values, ktau_dtype dt, int64_t m, int64_t n,
@@ -248,6 +251,7 @@ ktau_status rank_prepare_impl(const void* values, ktau_dtype dt, int64_t m, int6
       s = ktau_cuda_fail(e, "cudaStreamSynchronize");
     else if (R->stats.nan_flag)
       s = ktau_fail(KTAU_ENAN, "NaN in the input matrix");
+    if (e == cudaSuccess) stats_release(R);  // the rank transform has run: its scratch is free
   }
   if (s != KTAU_OK) {
     cudaStreamSynchronize(st);

@@ -217,8 +217,9 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
       return ktau_fail(KTAU_EINVAL, "descriptor %d: bad dtype", i);
     if (d.m < 2 || d.n < 2 || d.ld < d.n)
       return ktau_fail(KTAU_EINVAL, "descriptor %d: need m >= 2, n >= 2, ld >= n", i);
-    if (d.n > KTAU_MAX_N || d.m > KTAU_MAX_M)
-      return ktau_fail(KTAU_ETOOLARGE, "descriptor %d: shape beyond the limits", i);
+    if (d.n > KTAU_BATCH_MAX_N || d.m > KTAU_MAX_M)
+      return ktau_fail(KTAU_ETOOLARGE, "descriptor %d: shape beyond the limits (n <= %d)", i,
+                       KTAU_BATCH_MAX_N);
     if ((s = ktau_check_counts(d.n, d.count_bits)) != KTAU_OK) return s;
     if (d.path < 0 || d.path > 2) return ktau_fail(KTAU_EINVAL, "descriptor %d: bad path", i);
     if (batch_path_for(d, opt) == KTAU_PATH_SIGNGEMM && d.n > KTAU_SIGNGEMM_MAX_N)

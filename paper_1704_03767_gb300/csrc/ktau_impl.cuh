@@ -28,6 +28,11 @@ struct ktau_stats {
   unsigned int pad[2];
 };
 
+// Rows longer than this are ranked in chunks of this many keys merged in global scratch, and
+// their pairs are counted with the merge buffers in global scratch (shared memory holds rows of up
+// to this length).
+#define KTAU_RANK_CHUNK 16384
+
 struct ktau_ranked {
   int64_t m, n, ld;
   int device;
@@ -47,6 +52,10 @@ struct ktau_ranked {
   // and read on first use; stats_pin is null once `stats` holds them.
   ktau_stats* stats_pin;
   cudaEvent_t stats_ev;
+  // Scratch of the long-row rank transform (n > KTAU_RANK_CHUNK), released once the statistics
+  // copy (which follows the rank transform on its stream) has completed.
+  void* tmp_block;
+  size_t tmp_bytes;
   // Sign expansion for the tensor-core path, built on first use (library-owned):
   // sgn[m][K_pad] of values in {-1, 0, +1} as FP4 e2m1 (obits 4, two per byte), FP8 e4m3
   // (obits 8) or BF16 (obits 16), K = n(n-1)/2, K_pad = K rounded up to 128; esize is the

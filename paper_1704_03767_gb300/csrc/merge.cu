@@ -182,6 +182,7 @@ struct MergeArgs {
   int tq;           // tile side
   int stage;        // rows of the tile staged in shared memory
   int cap;          // per-team buffer capacity (elements)
+  uint32_t* gbuf;   // long rows: the CTA team's two buffers in global scratch (2 * cap per CTA)
   unsigned long long* counter;  // dynamic schedule: next tile id (nullptr = static)
   ktau_out out;
 };
@@ -274,8 +275,9 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
   uint16_t* s_perm = reinterpret_cast<uint16_t*>(smem);
   uint16_t* s_srank = s_perm + (a.stage ? (int64_t)tq * ld : 0);
   uint16_t* s_rank = s_srank + (a.stage ? (int64_t)tq * ld : 0);
-  uint32_t* tbuf = reinterpret_cast<uint32_t*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
-                   (size_t)team * 2 * a.cap;
+  uint32_t* tbuf = a.gbuf ? a.gbuf + (size_t)blockIdx.x * 2 * a.cap
+                         : reinterpret_cast<uint32_t*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
+                               (size_t)team * 2 * a.cap;
   uint32_t* tbuf2 = tbuf + a.cap;
   const int n = (int)a.n;
   const int64_t n0 = a.n * (a.n - 1) / 2;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
 
 template <int TEAM, int ITEMS>
 ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas_per_sm,
-                       int64_t tiles, cudaStream_t st) {
+                       int64_t tiles, cudaStream_t st, int64_t max_grid = 0) {
   auto kern = merge_pairs_kernel<TEAM, ITEMS>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
@@ -354,6 +356,7 @@ ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas
   if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
   int64_t grid = (int64_t)occ * ktau_sm_count();
   if (grid > tiles) grid = tiles;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
   KTAU_TRACE("merge_pairs_kernel", st);
   kern<<<(unsigned)grid, threads, smem, st>>>(args);
@@ -522,6 +525,7 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
   const bool cta_team = plan.mapping == 2;
   const int items = cta_team ? (n > 2048 ? 16 : 8) : (n <= 256 ? (int)((n + 31) / 32) : 8);
   a.cap = (int)((n + (n >> 5) + 1 + 3) & ~3LL);  // pd<ITEMS>(n) + 1, rounded
+  a.gbuf = nullptr;
   const size_t team_bytes = (size_t)2 * a.cap * sizeof(uint32_t);
   // Stage the tile's rows in shared memory when they are small next to the per-pair work.
   const size_t stage_bytes = (size_t)3 * tq * R->ld * sizeof(uint16_t);
@@ -540,8 +544,22 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
                        (long long)n);
     threads = 32 * teams;
   }
-  const size_t smem = (a.stage ? stage_bytes : 0) + (size_t)teams * team_bytes;
   const int cps = plan.ctas_per_sm;
+  if (cta_team && team_bytes > budget) {
+    // Long rows: the team's two merge buffers live in global scratch, one pair per SM at a time.
+    // The scratch is released once the launch has finished, so this call returns after the work.
+    const int64_t grid = ktau_sm_count();
+    const size_t gbytes = (size_t)grid * team_bytes;
+    void* g = nullptr;
+    if (ktau_dmalloc(&g, gbytes) != KTAU_OK) return KTAU_ENOMEM;
+    a.gbuf = (uint32_t*)g;
+    ktau_status s = launch_one<256, 16>(a, threads, 0, cps, tiles, st, grid);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    ktau_dfree(g, gbytes);
+    if (s == KTAU_OK && e != cudaSuccess) s = ktau_cuda_fail(e, "cudaStreamSynchronize");
+    return s;
+  }
+  const size_t smem = (a.stage ? stage_bytes : 0) + (size_t)teams * team_bytes;
   if (cta_team)
     return items == 16 ? launch_one<256, 16>(a, threads, smem, cps, tiles, st)
                        : launch_one<256, 8>(a, threads, smem, cps, tiles, st);

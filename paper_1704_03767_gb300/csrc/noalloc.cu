@@ -50,7 +50,9 @@ extern "C" ktau_status ktau_allpairs_noalloc(const void* values, ktau_dtype dt, 
   if (dt != KTAU_F32 && dt != KTAU_I32) return ktau_fail(KTAU_EINVAL, "unknown dtype %d", (int)dt);
   if (m < 2 || n < 2) return ktau_fail(KTAU_EINVAL, "need m >= 2 and n >= 2");
   if (ld < n) return ktau_fail(KTAU_EINVAL, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
-  if (n > KTAU_MAX_N) return ktau_fail(KTAU_ETOOLARGE, "n=%lld exceeds KTAU_MAX_N", (long long)n);
+  if (n > KTAU_BATCH_MAX_N)
+    return ktau_fail(KTAU_ETOOLARGE, "n=%lld exceeds KTAU_BATCH_MAX_N=%d", (long long)n,
+                     KTAU_BATCH_MAX_N);
   ktau_status s = ktau_check_counts(n, count_bits);
   if (s != KTAU_OK) return s;
   const uint64_t P = (uint64_t)(m * (m - 1) / 2);

@@ -243,8 +243,9 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
   } else {
     ktau_merge_plan plan;
     ktau_merge_default_plan(db->n, &plan);
-    plan.mapping = 1;
-    if (db->n > 2048) plan.mapping = 1;
+    // one warp per pair; one CTA per pair (merge buffers in global scratch) for rows too long
+    // for a warp's shared-memory buffers
+    plan.mapping = db->n > KTAU_RANK_CHUNK ? 2 : 1;
     if (opt && opt->tile_q) plan.tile_q = opt->tile_q;
     s = ktau_launch_merge_rect(Q, D, db->m, out, plan, st);
   }

@@ -3,6 +3,7 @@
 // memory and emits the stable permutation pi_u, the dense ranks r_u, the ranks in sorted order,
 // and the tie statistics that Steps 2 and 4 of Sec. 3.2 would otherwise rescan for every pair
 // (n_1 and n_2 depend on one variable only).
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 
@@ -38,27 +39,11 @@ __device__ __forceinline__ unsigned long long load_key(const void* values, int64
 template <int EPL>
 __device__ __forceinline__ void cta_bitonic_hybrid(unsigned long long* sm_keys, int np2);
 
-template <int DT>
-__device__ void rank_row(const void* __restrict__ values, int64_t off, int n, int np2,
-                         int64_t ld, int64_t row, uint16_t* perm, uint16_t* rank, uint16_t* srank,
-                         int64_t* T, int32_t* ndist, int32_t* maxg, double* rs64, float2* rsff,
-                         ktau_stats* stats) {
-  extern __shared__ unsigned long long sm_keys[];                  // [np2]
-  uint16_t* sm_first = reinterpret_cast<uint16_t*>(sm_keys + np2);  // [np2] group start
-  uint16_t* sm_dense = sm_first + np2;                             // [np2] dense rank at k
-  __shared__ int warp_tot[32];
-  __shared__ unsigned long long red_T[32];
-  __shared__ int red_g[32];
-
+// Ascending sort of sm_keys[0, np2) (shared memory) by the whole CTA: bitonic network, warp
+// blocks in registers where np2 = blockDim * EPL for EPL in 2..8, all through shared memory
+// otherwise.
+__device__ void cta_sort_keys(unsigned long long* sm_keys, int np2) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  unsigned int nan_seen = 0;
-
-  for (int i = tid; i < np2; i += nt)
-    sm_keys[i] = i < n ? load_key<DT>(values, off, i, &nan_seen) : ~0ull;
-  __syncthreads();
-
-  // Bitonic sort of np2 keys, ascending: warp blocks in registers where np2 = blockDim * EPL
-  // for EPL in 2..8, the whole network through shared memory otherwise.
   const int epl = np2 / nt;
   if (epl * nt == np2 && epl >= 2 && epl <= 8) {
     switch (epl) {
@@ -84,6 +69,22 @@ __device__ void rank_row(const void* __restrict__ values, int64_t off, int n, in
     }
   }
 
+}
+
+// Outputs of one variable from its keys sorted ascending in keys[0, n) (shared or global memory):
+// group heads and dense ranks by a block-wide scan, pi_u, r_u, ranks in sorted order, T_u, the
+// number of distinct values, the largest tie group and the denominator factors. first[] and
+// dense[] are n-entry work arrays (shared or global). nan_seen: this thread's NaN flag.
+__device__ void rank_finish(const unsigned long long* keys, uint16_t* sm_first, uint16_t* sm_dense,
+                            int n, int64_t ld, int64_t row, uint16_t* perm, uint16_t* rank,
+                            uint16_t* srank, int64_t* T, int32_t* ndist, int32_t* maxg,
+                            double* rs64, float2* rsff, ktau_stats* stats,
+                            unsigned int nan_seen) {
+  __shared__ int warp_tot[32];
+  __shared__ unsigned long long red_T[32];
+  __shared__ int red_g[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const unsigned long long* sm_keys = keys;
   // Group heads and dense ranks: a block-wide inclusive scan of head flags over positions,
   // each thread owning a contiguous chunk.
   const int per = (n + nt - 1) / nt;
@@ -174,6 +175,23 @@ __device__ void rank_row(const void* __restrict__ values, int64_t off, int n, in
     atomicMax(&stats->maxg, (unsigned)g);
     if (nan_any) atomicOr(&stats->nan_flag, 1u);
   }
+}
+
+template <int DT>
+__device__ void rank_row(const void* __restrict__ values, int64_t off, int n, int np2,
+                         int64_t ld, int64_t row, uint16_t* perm, uint16_t* rank, uint16_t* srank,
+                         int64_t* T, int32_t* ndist, int32_t* maxg, double* rs64, float2* rsff,
+                         ktau_stats* stats) {
+  extern __shared__ unsigned long long sm_keys[];                  // [np2]
+  uint16_t* sm_first = reinterpret_cast<uint16_t*>(sm_keys + np2);  // [np2] group start
+  uint16_t* sm_dense = sm_first + np2;                             // [np2] dense rank at k
+  unsigned int nan_seen = 0;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x)
+    sm_keys[i] = i < n ? load_key<DT>(values, off, i, &nan_seen) : ~0ull;
+  __syncthreads();
+  cta_sort_keys(sm_keys, np2);
+  rank_finish(sm_keys, sm_first, sm_dense, n, ld, row, perm, rank, srank, T, ndist, maxg, rs64,
+              rsff, stats, nan_seen);
 }
 
 // Short rows (n <= 256): one warp per variable, EPL = np2/32 keys per lane in registers, blocked
@@ -511,6 +529,89 @@ __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ valu
                stats);
 }
 
+// Long rows (n > KTAU_RANK_CHUNK), a pass over up to kLongRows variables at a time, in four small
+// kernels over global scratch: sort keys of every element (long_keys_kernel), chunks of
+// KTAU_RANK_CHUNK keys sorted in shared memory (long_chunk_kernel), the sorted chunks merged level
+// by level (long_merge_kernel, one launch per level), and the outputs of each variable
+// (long_finish_kernel). Scratch per variable: two key arrays of np2 and two uint16 work arrays.
+constexpr int kLongRows = 256;
+constexpr int LONG_THREADS = 512;
+__host__ __device__ inline size_t long_rank_scratch(int np2) {
+  return (size_t)np2 * (2 * sizeof(unsigned long long) + 2 * sizeof(uint16_t));
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) long_keys_kernel(const void* __restrict__ values,
+                                                        int64_t ld_in, int n, int np2,
+                                                        int64_t row0, int rows,
+                                                        unsigned long long* __restrict__ keys,
+                                                        ktau_stats* stats) {
+  unsigned int nan_seen = 0;
+  const int64_t total = (int64_t)rows * np2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / np2;
+    const int k = (int)(i - r * np2);
+    keys[i] = k < n ? load_key<DT>(values, (row0 + r) * ld_in, k, &nan_seen) : ~0ull;
+  }
+  if (__any_sync(0xffffffffu, nan_seen != 0) && (threadIdx.x & 31) == 0)
+    atomicOr(&stats->nan_flag, 1u);
+}
+
+// One CTA per chunk of KTAU_RANK_CHUNK keys (chunks of a variable are consecutive).
+__global__ void __launch_bounds__(LONG_THREADS) long_chunk_kernel(unsigned long long* keys) {
+  extern __shared__ unsigned long long sm_keys[];  // [KTAU_RANK_CHUNK]
+  unsigned long long* g = keys + (size_t)blockIdx.x * KTAU_RANK_CHUNK;
+  for (int i = threadIdx.x; i < KTAU_RANK_CHUNK; i += blockDim.x) sm_keys[i] = g[i];
+  __syncthreads();
+  cta_sort_keys(sm_keys, KTAU_RANK_CHUNK);
+  for (int i = threadIdx.x; i < KTAU_RANK_CHUNK; i += blockDim.x) g[i] = sm_keys[i];
+}
+
+// One merge level: runs of s sorted keys, pairs of runs merged into `out`. Each thread writes
+// `per` consecutive outputs of one pair of runs: it finds how many come from the left run by
+// binary search along its diagonal (merge path), then merges them serially. Keys are unique
+// (the sample index is their low word) except the all-ones padding, which sorts last.
+__global__ void __launch_bounds__(256) long_merge_kernel(const unsigned long long* __restrict__ in,
+                                                         unsigned long long* __restrict__ out,
+                                                         int64_t total, int s, int per) {
+  const int64_t o = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * per;
+  if (o >= total) return;
+  const int64_t A = (o / (2 * (int64_t)s)) * (2 * (int64_t)s), B = A + s;
+  const int diag = (int)(o - A);
+  int lo = max(0, diag - s), hi = min(diag, s);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (in[A + mid] <= in[B + diag - 1 - mid])
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  int ai = lo, bi = diag - lo;
+  for (int k = 0; k < per; ++k) {
+    const unsigned long long va = ai < s ? in[A + ai] : ~0ull;
+    const unsigned long long vb = bi < s ? in[B + bi] : ~0ull;
+    if (bi < s && (ai >= s || vb < va)) {
+      out[o + k] = vb;
+      ++bi;
+    } else {
+      out[o + k] = va;
+      ++ai;
+    }
+  }
+}
+
+// Outputs of each variable of the pass from its sorted keys (one CTA per variable).
+__global__ void __launch_bounds__(LONG_THREADS) long_finish_kernel(
+    const unsigned long long* __restrict__ keys, uint16_t* work, int n, int np2, int64_t row0,
+    int64_t ld, uint16_t* perm, uint16_t* rank, uint16_t* srank, int64_t* T, int32_t* ndist,
+    int32_t* maxg, double* rs64, float2* rsff, ktau_stats* stats) {
+  const int r = blockIdx.x;
+  uint16_t* first = work + (size_t)r * 2 * np2;
+  rank_finish(keys + (size_t)r * np2, first, first + np2, n, ld, row0 + r, perm, rank, srank, T,
+              ndist, maxg, rs64, rsff, stats, 0u);
+}
+
 // Batched form: one CTA per variable of every dataset; the dataset is found from the prefix of
 // row counts (rows of a batch are numbered dataset by dataset).
 __global__ void __launch_bounds__(256) batch_rank_kernel(const ktau_bds* __restrict__ ds, int count,
@@ -585,6 +686,62 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
     }
 #undef KTAU_RANK_WARP
     KTAU_CUDA(cudaGetLastError());
+    return KTAU_OK;
+  }
+  if (np2 > KTAU_RANK_CHUNK) {
+    // Long rows: global scratch for up to kLongRows variables per pass, released by the handle
+    // once the rank transform has run (ktau_ranked_stats).
+    if (!R->block) return ktau_fail(KTAU_EINVAL, "rows longer than %d need a library handle",
+                                    KTAU_RANK_CHUNK);
+    const int64_t pass = m < kLongRows ? m : kLongRows;
+    const size_t kbytes = (size_t)pass * np2 * sizeof(unsigned long long);
+    R->tmp_bytes = (size_t)pass * long_rank_scratch(np2);
+    if (ktau_dmalloc(&R->tmp_block, R->tmp_bytes) != KTAU_OK) {
+      R->tmp_block = nullptr;
+      return KTAU_ENOMEM;
+    }
+    unsigned long long* ka = (unsigned long long*)R->tmp_block;
+    unsigned long long* kb = (unsigned long long*)((char*)R->tmp_block + kbytes);
+    uint16_t* work = (uint16_t*)((char*)R->tmp_block + 2 * kbytes);
+    const size_t smem_c = (size_t)KTAU_RANK_CHUNK * sizeof(unsigned long long);
+    KTAU_CUDA(cudaFuncSetAttribute(long_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_c));
+    auto kk = dtype == KTAU_F32 ? long_keys_kernel<KTAU_F32> : long_keys_kernel<KTAU_I32>;
+    const int per = 16;  // merge outputs per thread (divides every run length)
+    for (int64_t row0 = 0; row0 < m; row0 += pass) {
+      const int rows = (int)(m - row0 < pass ? m - row0 : pass);
+      const int64_t total = (int64_t)rows * np2;
+      {
+        KTAU_TRACE("long_keys_kernel", st);
+        kk<<<(unsigned)std::min<int64_t>((total + 255) / 256, 8LL * ktau_sm_count()), 256, 0, st>>>(
+            values, ld_in, (int)n, np2, row0, rows, ka, R->stats_dev);
+      }
+      KTAU_CUDA(cudaGetLastError());
+      {
+        KTAU_TRACE("long_chunk_kernel", st);
+        long_chunk_kernel<<<(unsigned)(total / KTAU_RANK_CHUNK), LONG_THREADS, smem_c, st>>>(ka);
+      }
+      KTAU_CUDA(cudaGetLastError());
+      unsigned long long* in = ka;
+      unsigned long long* out = kb;
+      for (int s = KTAU_RANK_CHUNK; s < np2; s <<= 1) {
+        KTAU_TRACE("long_merge_kernel", st);
+        const int64_t threads_total = total / per;
+        long_merge_kernel<<<(unsigned)((threads_total + 255) / 256), 256, 0, st>>>(in, out, total, s,
+                                                                                  per);
+        KTAU_CUDA(cudaGetLastError());
+        unsigned long long* t = in;
+        in = out;
+        out = t;
+      }
+      {
+        KTAU_TRACE("long_finish_kernel", st);
+        long_finish_kernel<<<(unsigned)rows, LONG_THREADS, 0, st>>>(
+            in, work, (int)n, np2, row0, R->ld, R->perm, R->rank, R->srank, R->T, R->ndist,
+            R->maxg, R->rs64, R->rsff, R->stats_dev);
+      }
+      KTAU_CUDA(cudaGetLastError());
+    }
     return KTAU_OK;
   }
   int threads = np2 / 2 < 32 ? 32 : (np2 / 2 > 512 ? 512 : np2 / 2);

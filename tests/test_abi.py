@@ -59,15 +59,15 @@ def test_argument_validation_without_gpu(lib):
     assert lib.ktau_rank_prepare(fake, 0, 0, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare(fake, 0, 10, 1, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare(fake, 0, 10, 10, 9, None, ctypes.byref(h)) == 1
-    # n beyond the 16-bit rank storage
-    assert lib.ktau_rank_prepare(fake, 0, 10, 16385, 16385, None, ctypes.byref(h)) == 3
+    # n beyond the 16-bit rank storage (KTAU_MAX_N = 65535)
+    assert lib.ktau_rank_prepare(fake, 0, 10, 65536, 65536, None, ctypes.byref(h)) == 3
     assert b"KTAU_MAX_N" in lib.ktau_last_error()
     assert h.value is None
     # the asynchronous form validates the same way before any device work
     assert lib.ktau_rank_prepare_async(None, 0, 10, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare_async(fake, 7, 10, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare_async(fake, 0, 10, 10, 9, None, ctypes.byref(h)) == 1
-    assert lib.ktau_rank_prepare_async(fake, 0, 10, 16385, 16385, None, ctypes.byref(h)) == 3
+    assert lib.ktau_rank_prepare_async(fake, 0, 10, 65536, 65536, None, ctypes.byref(h)) == 3
     assert h.value is None
     # trace filter: host state only
     assert lib.ktau_trace_filter(b"contract_kernel") == 0

@@ -1,6 +1,8 @@
-"""Edge cases at the limits of the ABI: the longest vectors (n = KTAU_MAX_N) on the merge path,
-a large matrix (300,000 variables) with a pair range at the end of the triangle on both paths
-(64-bit pair indices, tile walks far from the origin), and inputs just beyond the limits."""
+"""Edge cases at the limits of the ABI: the longest vectors on the merge path (rows beyond
+16384 samples are ranked in chunks merged in global scratch and counted with global merge
+buffers; n = KTAU_MAX_N = 65535 is the longest the 16-bit ranks allow), a large matrix (300,000
+variables) with a pair range at the end of the triangle on both paths (64-bit pair indices, tile
+walks far from the origin), and inputs just beyond the limits."""
 import numpy as np
 import pytest
 import torch
@@ -22,8 +24,8 @@ def ktau():
     return k
 
 
-def test_longest_vectors_merge_path(ktau):
-    n = 16384  # KTAU_MAX_N
+@pytest.mark.parametrize("n", [16384, 16385, 40000, 65535])
+def test_longest_vectors_merge_path(ktau, n):
     X = uniform_ties(5, n, tie_frac=0.3, seed=31)
     X[1] = X[0]
     X[2] = -X[0]
@@ -67,10 +69,69 @@ def test_large_matrix_tail_range(ktau, path):
     assert_tau32(tau32.cpu().numpy()[idx], rtau)
 
 
+@pytest.mark.parametrize("n", [20000, 65535])
+def test_long_rows_ranks_and_async(ktau, n):
+    """Long-row rank transform (chunks merged in global scratch) against the oracle's ranks, through
+    the synchronous and the asynchronous prepare, integer values with heavy ties."""
+    import oracle
+
+    g = np.random.default_rng(n)
+    X = g.integers(-50, 50, (3, n)).astype(np.int32)
+    X[1] = np.arange(n)[::-1]  # no ties, reversed
+    Xd = torch.from_numpy(X).cuda()
+    for fn in (ktau.ktau_rank_prepare, ktau.ktau_rank_prepare_async):
+        R = fn(Xd)
+        perm, rank = ktau.ktau_ranked_export(R)
+        T = ktau.ktau_tie_counts(R).cpu().numpy()
+        torch.cuda.synchronize()
+        for i in range(3):
+            p, r, t = oracle.rank(X[i].astype(np.float64))
+            assert np.array_equal(perm[i].cpu().numpy().astype(np.int64), p)
+            assert np.array_equal(rank[i].cpu().numpy().astype(np.int64), r)
+            assert T[i] == t
+        R.free()
+
+
+def test_long_rows_query(ktau):
+    """Query search with long profiles (n > 16384): merge path with global merge buffers."""
+    import oracle
+
+    n = 20000
+    D = uniform_ties(7, n, tie_frac=0.2, seed=41)
+    Q = uniform_ties(2, n, tie_frac=0.2, seed=42)
+    Q[1] = D[3]
+    db = ktau.ktau_rank_prepare(torch.from_numpy(D).cuda())
+    q = ktau.ktau_rank_prepare(torch.from_numpy(Q).cuda())
+    S = torch.empty((2, 7), dtype=torch.int64, device="cuda")
+    n3 = torch.empty((2, 7), dtype=torch.int64, device="cuda")
+    tau = torch.empty((2, 7), dtype=torch.float64, device="cuda")
+    idx = torch.empty((2, 3), dtype=torch.int32, device="cuda")
+    tk = torch.empty((2, 3), dtype=torch.float64, device="cuda")
+    ktau.ktau_query(db, q, tau, S, n3, 64, 3, idx, tk)
+    torch.cuda.synchronize()
+    ref = oracle.query_topk(Q, D, 3)
+    assert np.array_equal(S.cpu().numpy(), ref["S"])
+    assert np.array_equal(n3.cpu().numpy(), ref["n3"])
+    assert_tau64(tau.cpu().numpy().ravel(), ref["tau"].ravel())
+    assert np.array_equal(idx.cpu().numpy(), ref["topk_idx"])
+    db.free()
+    q.free()
+
+
 def test_beyond_limits_rejected(ktau):
-    X = torch.zeros((2, 16385), dtype=torch.float32, device="cuda")  # n > KTAU_MAX_N
-    with pytest.raises(ktau.KtauError):
+    X = torch.zeros((2, 65536), dtype=torch.float32, device="cuda")  # n > KTAU_MAX_N
+    with pytest.raises(ktau.KtauError) as ei:
         ktau.ktau_rank_prepare(X)
+    assert ei.value.status == 3
+    # the batched and allocation-free forms stop at n = 16384
+    Xb = torch.zeros((2, 16385), dtype=torch.float32, device="cuda")
+    with pytest.raises(ktau.KtauError) as ei:
+        ktau.Batch([ktau.batch_desc(Xb)])
+    assert ei.value.status == 3
+    Sb = torch.empty(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ktau.KtauError) as ei:
+        ktau.ktau_allpairs_noalloc(Xb, 0, 1, None, None, Sb, None, 32)
+    assert ei.value.status == 3
     X = torch.zeros((3, 1), dtype=torch.float32, device="cuda")  # n < 2
     with pytest.raises(ktau.KtauError):
         ktau.ktau_rank_prepare(X)
