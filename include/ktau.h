@@ -66,8 +66,12 @@ typedef enum { KTAU_F32 = 0, KTAU_I32 = 1 } ktau_dtype;
 typedef enum {
   KTAU_PATH_AUTO = 0,      /* pick by shape and measured timings (autotuner table) */
   KTAU_PATH_MERGE = 1,     /* Knight merge-sort swap counting, Sec. 3.2 Steps 1-5 */
-  KTAU_PATH_SIGNGEMM = 2   /* exact sign-matrix contraction on tensor cores, Sec. 3.1 Alg. 1 */
+  KTAU_PATH_SIGNGEMM = 2,  /* exact sign-matrix contraction on tensor cores, Sec. 3.1 Alg. 1 */
+  KTAU_PATH_BITS = 3       /* bit-parallel dominance count: the sign form of Sec. 3.1 Alg. 1 over
+                              per-sample masks of larger / smaller ranks, 32 sample pairs per
+                              AND + popcount; ktau_allpairs(_host) only, n <= KTAU_BITS_MAX_N */
 } ktau_path;
+#define KTAU_BITS_MAX_N 256
 
 /* Tuning knobs; any field left 0 means "library default / autotuned". */
 typedef struct {

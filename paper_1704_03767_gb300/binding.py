@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_PKG, "libktau.so")
 KTAU_OK, KTAU_EINVAL, KTAU_ENAN, KTAU_ETOOLARGE, KTAU_ENOMEM, KTAU_ECUDA, KTAU_ETIMEOUT, \
     KTAU_EBUSY = range(8)
 KTAU_F32, KTAU_I32 = 0, 1
-KTAU_PATH_AUTO, KTAU_PATH_MERGE, KTAU_PATH_SIGNGEMM = 0, 1, 2
+KTAU_PATH_AUTO, KTAU_PATH_MERGE, KTAU_PATH_SIGNGEMM, KTAU_PATH_BITS = 0, 1, 2, 3
+KTAU_BITS_MAX_N = 256
 KTAU_MAX_N = 65535
 KTAU_BATCH_MAX_N = 16384
 

@@ -326,6 +326,7 @@ ktau_status ktau_ranked_free(ktau_ranked* R) {
   stats_release(R);
   if (R->block) ktau_dfree(R->block, R->block_bytes);
   ktau_signgemm_release(R);
+  ktau_bits_release(R);
   free(R);
   return KTAU_OK;
 }
@@ -336,6 +337,7 @@ ktau_status ktau_ranked_free_on(ktau_ranked* R, void* stream) {
   stats_release(R);
   if (R->block) ktau_dfree(R->block, R->block_bytes);
   ktau_signgemm_release(R);
+  ktau_bits_release(R);
   free(R);
   return KTAU_OK;
 }
@@ -381,7 +383,7 @@ ktau_status ktau_check_counts(int64_t n, int count_bits) {
 
 ktau_status ktau_check_options(const ktau_options* opt) {
   if (!opt) return KTAU_OK;
-  if (opt->path < 0 || opt->path > 2) return ktau_fail(KTAU_EINVAL, "bad path %d", opt->path);
+  if (opt->path < 0 || opt->path > 3) return ktau_fail(KTAU_EINVAL, "bad path %d", opt->path);
   if (opt->tile_q < 0 || opt->tile_q > 256)
     return ktau_fail(KTAU_EINVAL, "tile_q must be in [0, 256]");
   if (opt->mapping < 0 || opt->mapping > 2) return ktau_fail(KTAU_EINVAL, "bad mapping");
@@ -426,6 +428,8 @@ extern "C" ktau_status ktau_allpairs(const ktau_ranked* R, uint64_t p_begin, uin
   ktau_out out{tau64, tau32, S, n3, count_bits, opt ? opt->statistic : 0};
   cudaStream_t st = (cudaStream_t)stream;
   const int path = ktau_choose_path(R, opt);
+  if (path == KTAU_PATH_BITS)
+    return ktau_bits_allpairs(const_cast<ktau_ranked*>(R), p_begin, p_end, out, st);
   if (path == KTAU_PATH_SIGNGEMM) {
     if (!ktau_signgemm_supported(R->n))
       return ktau_fail(KTAU_EINVAL, "sign-contraction path supports n <= %d", KTAU_SIGNGEMM_MAX_N);

@@ -210,6 +210,8 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
   ktau_status s = ktau_check_options(opt);
   if (s != KTAU_OK) return s;
   if (opt && opt->statistic != 0) return ktau_fail(KTAU_EINVAL, "the batched form computes tau-b");
+  if (opt && opt->path == KTAU_PATH_BITS)
+    return ktau_fail(KTAU_EINVAL, "the batched form runs the merge path or the contraction");
   for (int i = 0; i < count; ++i) {
     const ktau_batch_desc& d = descs[i];
     if (!d.values) return ktau_fail(KTAU_EINVAL, "descriptor %d: values is NULL", i);

@@ -85,6 +85,9 @@ struct ktau_ranked {
   unsigned long long* bkt_stat;
   size_t bkt_var_bytes;
   int ties_ready;  // tie lists and index built (on first use by an n_3 output)
+  // Bit-parallel path: per-sample dominance masks of every variable (built on first use).
+  uint32_t* bits;
+  size_t bits_bytes;
 };
 
 // The handle's rank statistics on the host: waits for the copy of an asynchronously prepared
@@ -266,6 +269,10 @@ struct ktau_merge_plan {
   int ctas_per_sm;
 };
 void ktau_merge_default_plan(int64_t n, ktau_merge_plan* plan);
+// Bit-parallel dominance count over the triangle's pairs [p_begin, p_end) (n <= KTAU_BITS_MAX_N).
+ktau_status ktau_bits_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_end,
+                               const ktau_out& out, cudaStream_t st);
+void ktau_bits_release(ktau_ranked* R);
 ktau_status ktau_launch_batch_rank(const ktau_bds* ds, int count, const int64_t* row_prefix,
                                    int64_t total_rows, int64_t max_n, ktau_stats* stats,
                                    cudaStream_t st);

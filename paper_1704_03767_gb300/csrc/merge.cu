@@ -10,6 +10,8 @@
 //   Step 2   : n_3 = joint ties = sum over runs of equal keys of t(t-1)/2 (n_1 comes from K-a).
 //   Step 3   : bottom-up merge sort of w; when an element of a right run is emitted while left
 //              elements remain, all of those are larger (ties go left): add their number to n_d.
+//   At every level of both sorts, a pair of runs already in order (last of the left run <= first
+//   of the right run) is copied without merging (predict and skip: no inversion between them).
 //   Step 4/5 : n_2 from K-a; S = n_0 - n_1 - n_2 + n_3 - 2 n_d; tau-b in FP64 (Eq. 3).
 // The merge of two sorted runs is split among the team by merge-path co-ranks (a binary search
 // along each thread's output diagonal); each thread then merges ITEMS outputs serially and counts
@@ -113,12 +115,27 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
   for (int s = ITEMS; s < n; s *= 2) {
     for (int base = 0; base < n; base += CH) {
       const int o = base + lane * ITEMS;
+      const int A = (o / (2 * s)) * (2 * s);
+      const int a_len = min(s, n - A);
+      const int B = A + a_len;
+      const int b_len = max(0, min(s, n - B));
+      const int diag = o - A;
+      // Predict and skip: when the left run's last key is not greater than the right run's
+      // first, the two runs are already in order: the outputs are the inputs in place and no
+      // pair is an inversion. Taken only when every thread of the warp can take it (a warp's
+      // threads may belong to different merges), so that no warp runs both paths.
+      const bool sorted =
+          o >= n || b_len == 0 || in[pd<ITEMS>(A + a_len - 1)] <= in[pd<ITEMS>(B)];
+      if (__all_sync(0xffffffffu, sorted)) {
+        if (o < n) {
+          const int todo = min(ITEMS, a_len + b_len - diag);
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i)
+            if (i < todo) out[pd<ITEMS>(o + i)] = in[pd<ITEMS>(o + i)];
+        }
+        continue;
+      }
       if (o < n) {
-        const int A = (o / (2 * s)) * (2 * s);
-        const int a_len = min(s, n - A);
-        const int B = A + a_len;
-        const int b_len = max(0, min(s, n - B));
-        const int diag = o - A;
         // Merge-path co-rank: number of A elements among the first `diag` outputs of a stable
         // merge (equal keys: A first).
         int lo = max(0, diag - b_len), hi = min(diag, a_len);
@@ -263,7 +280,9 @@ __device__ __forceinline__ void copy_rows(uint16_t* dst, const uint16_t* src, in
   }
 }
 
-template <int TEAM, int ITEMS>
+// GBUF: the team buffers are in global scratch (long rows); otherwise they are carved from
+// shared memory, a pointer the compiler can see is shared (shared-memory loads and stores).
+template <int TEAM, int ITEMS, bool GBUF>
 __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long red[8];
@@ -275,9 +294,9 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
   uint16_t* s_perm = reinterpret_cast<uint16_t*>(smem);
   uint16_t* s_srank = s_perm + (a.stage ? (int64_t)tq * ld : 0);
   uint16_t* s_rank = s_srank + (a.stage ? (int64_t)tq * ld : 0);
-  uint32_t* tbuf = a.gbuf ? a.gbuf + (size_t)blockIdx.x * 2 * a.cap
-                         : reinterpret_cast<uint32_t*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
-                               (size_t)team * 2 * a.cap;
+  uint32_t* tbuf = GBUF ? a.gbuf + (size_t)blockIdx.x * 2 * a.cap
+                       : reinterpret_cast<uint32_t*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
+                             (size_t)team * 2 * a.cap;
   uint32_t* tbuf2 = tbuf + a.cap;
   const int n = (int)a.n;
   const int64_t n0 = a.n * (a.n - 1) / 2;
@@ -345,10 +364,10 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
   }
 }
 
-template <int TEAM, int ITEMS>
+template <int TEAM, int ITEMS, bool GBUF = false>
 ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas_per_sm,
                        int64_t tiles, cudaStream_t st, int64_t max_grid = 0) {
-  auto kern = merge_pairs_kernel<TEAM, ITEMS>;
+  auto kern = merge_pairs_kernel<TEAM, ITEMS, GBUF>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
@@ -553,7 +572,7 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
     void* g = nullptr;
     if (ktau_dmalloc(&g, gbytes) != KTAU_OK) return KTAU_ENOMEM;
     a.gbuf = (uint32_t*)g;
-    ktau_status s = launch_one<256, 16>(a, threads, 0, cps, tiles, st, grid);
+    ktau_status s = launch_one<256, 16, true>(a, threads, 0, cps, tiles, st, grid);
     const cudaError_t e = cudaStreamSynchronize(st);
     ktau_dfree(g, gbytes);
     if (s == KTAU_OK && e != cudaSuccess) s = ktau_cuda_fail(e, "cudaStreamSynchronize");

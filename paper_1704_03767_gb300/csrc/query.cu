@@ -290,6 +290,8 @@ ktau_status ktau_query_validate(const ktau_ranked* db, const ktau_ranked* querie
   if ((s = ktau_ranked_stats(db)) != KTAU_OK || (s = ktau_ranked_stats(queries)) != KTAU_OK)
     return s;
   if (opt && opt->statistic != 0) return ktau_fail(KTAU_EINVAL, "the query form computes tau-b");
+  if (opt && opt->path == KTAU_PATH_BITS)
+    return ktau_fail(KTAU_EINVAL, "the bit-parallel path counts the triangle of one matrix only");
   if (k < 0 || k > TK_MAXK || k > db->m)
     return ktau_fail(KTAU_EINVAL, "k must be in [0, min(m_db, %d)]", TK_MAXK);
   if (k > 0 && (!topk_idx || !topk_tau)) return ktau_fail(KTAU_EINVAL, "top-k outputs are NULL");
