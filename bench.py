@@ -49,6 +49,9 @@ def _args():
                     help="skip the merge-path (Knight) measurement")
     ap.add_argument("--no-perm", action="store_true",
                     help="skip the permutation-test measurement")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: every rank takes its static share of one matrix's pair "
+                         "range (Sec. 4.4) instead of a matrix of its own")
     return ap.parse_args()
 
 
@@ -214,9 +217,11 @@ def cpu_baseline(X, seconds: float):
             "speedup_over_single_core": (sample / dt) / (one / dt1)}
 
 
-def bench_batched(ktau, steps: int, warmup: int) -> dict:
+def bench_batched(ktau, steps: int, warmup: int, fp4_tflops: float | None = None) -> dict:
     """Batched form on 1000 uneven datasets: one graph launch per step vs the plain launch
-    (rank + all-pairs per dataset, one after another)."""
+    (rank + all-pairs per dataset, one after another). The roofline of its contraction: the
+    algorithmic 2 n_0 flops of every contraction pair over the summed contraction kernel time of
+    one traced (serialised) run, against the FP4 tensor rate."""
     import torch
 
     from paper_1704_03767_gb300 import autotune
@@ -224,17 +229,18 @@ def bench_batched(ktau, steps: int, warmup: int) -> dict:
 
     mats = batched_uneven(1000, seed0=0)
     table = autotune.load()
-    paths = autotune.batch_paths(table, mats) if table else [0] * len(mats)
+    plans = autotune.batch_plans(table, mats) if table else [{"path": 0, "mapping": 0}] * len(mats)
+    paths = [pl["path"] for pl in plans]
     dev = torch.device("cuda")
     descs, keep, outs = [], [], []
-    for X, pth in zip(mats, paths):
+    for X, pl in zip(mats, plans):
         Xd = torch.from_numpy(X).to(dev)
         m = X.shape[0]
         P = m * (m - 1) // 2
         o = (torch.empty(P, dtype=torch.float32, device=dev),
              torch.empty(P, dtype=torch.int32, device=dev),
              torch.empty(P, dtype=torch.int32, device=dev))
-        descs.append(ktau.batch_desc(Xd, None, o[0], o[1], o[2], 32, pth))
+        descs.append(ktau.batch_desc(Xd, None, o[0], o[1], o[2], 32, pl["path"], pl["mapping"]))
         keep.append(Xd)
         outs.append(o)
     B = ktau.Batch(descs, keepalive=keep)
@@ -252,14 +258,39 @@ def bench_batched(ktau, steps: int, warmup: int) -> dict:
     st.synchronize()
     B.check(st)
     ms = e0.elapsed_time(e1) / steps
+    # one traced run (each launch bracketed by events, so the lanes' kernels are serialised):
+    # contraction time and its flops
+    ktau.ktau_trace_collect()
+    ktau.ktau_trace_filter(None)
+    ktau.ktau_trace_enable(True)
+    B.run(st)
+    st.synchronize()
+    ktau.ktau_trace_enable(False)
+    tr = ktau.ktau_trace_collect()
+    per_kernel = {}
+    for name, t in tr:
+        per_kernel[name] = per_kernel.get(name, 0.0) + t
+    n_sg, flops = 0, 0.0
+    for X, pth in zip(mats, paths):
+        if pth == 2 or (pth == 0 and X.shape[1] <= 2048):
+            m, n = X.shape
+            flops += 2.0 * (m * (m - 1) // 2) * (n * (n - 1) // 2)
+    c_ms = per_kernel.get("contract_kernel", 0.0)
+    roof = None
+    if c_ms > 0 and fp4_tflops:
+        ach = flops / (c_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": fp4_tflops, "unit": "TFLOP/s",
+                "frac": ach / fp4_tflops, "contraction_ms_serialised": c_ms,
+                "peak_source": "of measured: the FP4 GEMM rate of the main line's roofline"}
     # plain launch of the same work, dataset by dataset, with the same per-dataset paths
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cur = torch.cuda.current_stream()
     p0.record(cur)
-    for Xd, o, pth in zip(keep, outs, paths):
+    for Xd, o, pl in zip(keep, outs, plans):
         R = ktau.ktau_rank_prepare(Xd)
-        ktau.ktau_allpairs(R, 0, R.pairs, None, o[0], o[1], o[2], 32, {"path": pth})
+        ktau.ktau_allpairs(R, 0, R.pairs, None, o[0], o[1], o[2], 32,
+                           {"path": pl["path"], "mapping": pl["mapping"]})
         R.free_on(cur)
     p1.record(cur)
     torch.cuda.synchronize()
@@ -270,7 +301,8 @@ def bench_batched(ktau, steps: int, warmup: int) -> dict:
             "datasets": len(mats), "pairs": pairs, "paths": {"merge": n_merge, "signgemm": n_sg},
             "autotuned": bool(table), "ms_per_step": ms, "value": pairs / (ms / 1e3),
             "unit": "pairs/s", "plain_launch": {"ms": plain_ms, "value": pairs / (plain_ms / 1e3)},
-            "speedup_vs_plain": plain_ms / ms}
+            "speedup_vs_plain": plain_ms / ms, "roofline": roof,
+            "kernels_serialised_ms": per_kernel}
 
 
 def bench_merge(ktau, clocks_mhz: float | None) -> dict:
@@ -325,6 +357,37 @@ def bench_merge(ktau, clocks_mhz: float | None) -> dict:
         del Xd, S, n3, t64, t32
         torch.cuda.empty_cache()
     return out
+
+
+def bench_bits(ktau) -> dict:
+    """The bit-parallel dominance count (KTAU_PATH_BITS) on the bench matrix: its pair kernel's
+    time from the library's CUDA events (masks built by the first, untimed call)."""
+    import torch
+
+    from synthetic import gene_expression
+
+    X = gene_expression(M, N, seed=0)
+    P = M * (M - 1) // 2
+    Xd = torch.from_numpy(X).cuda()
+    R = ktau.ktau_rank_prepare(Xd)
+    S = torch.empty(P, dtype=torch.int32, device="cuda")
+    n3 = torch.empty(P, dtype=torch.int32, device="cuda")
+    t32 = torch.empty(P, dtype=torch.float32, device="cuda")
+    opts = {"path": ktau.KTAU_PATH_BITS}
+    ktau.ktau_allpairs(R, 0, P, None, t32, S, n3, 32, opts)
+    torch.cuda.synchronize()
+    ktau.ktau_trace_collect()
+    ktau.ktau_trace_filter("bits_pairs_kernel")
+    ktau.ktau_trace_enable(True)
+    for _ in range(2):
+        ktau.ktau_allpairs(R, 0, P, None, t32, S, n3, 32, opts)
+    torch.cuda.synchronize()
+    ktau.ktau_trace_enable(False)
+    ktau.ktau_trace_filter(None)
+    ms = sum(t for _, t in ktau.ktau_trace_collect()) / 2
+    R.free()
+    return {"workload": "gene-expression 16384 x 128", "kernel_ms": ms, "ns_per_pair": ms * 1e6 / P,
+            "pairs_per_s": P / (ms / 1e3)}
 
 
 def bench_permutation(ktau, Xd, P: int, B: int = 8) -> dict:
@@ -472,13 +535,18 @@ def run_ours(args):
     path = {"auto": 0, "merge": 1, "signgemm": 2}[args.path]
     opts = {"path": path}
 
-    # Weak scaling: every rank runs its own independent matrix (seed = rank); no collective.
-    X = gene_expression(M, N, seed=rank)
+    # Weak scaling (default): every rank runs its own independent matrix (seed = rank). Strong
+    # scaling (--shard): one matrix, every rank its static contiguous share of the pair range
+    # (Sec. 4.4). No collective on the data path either way.
+    from paper_1704_03767_gb300.sharding import shard_range
+
+    X = gene_expression(M, N, seed=0 if args.shard else rank)
     P = M * (M - 1) // 2
+    lo, hi = shard_range(P, world, rank) if args.shard else (0, P)
     Xd = torch.from_numpy(X).to(dev)
-    tau32 = torch.empty(P, dtype=torch.float32, device=dev)
-    S = torch.empty(P, dtype=torch.int32, device=dev)
-    n3 = torch.empty(P, dtype=torch.int32, device=dev)
+    tau32 = torch.empty(hi - lo, dtype=torch.float32, device=dev)
+    S = torch.empty(hi - lo, dtype=torch.int32, device=dev)
+    n3 = torch.empty(hi - lo, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -494,7 +562,7 @@ def run_ours(args):
         R = ktau.ktau_rank_prepare_async(Xd, stream)
         if path_id == 2:
             ktau.ktau_prepare_signs(R, stream)  # sign expansion + tie lists (part of the step)
-        ktau.ktau_allpairs(R, 0, P, None, tau32, S, n3, 32, opts, stream)
+        ktau.ktau_allpairs(R, lo, hi, None, tau32, S, n3, 32, opts, stream)
         return R
 
     for _ in range(args.warmup):
@@ -550,7 +618,8 @@ def run_ours(args):
         total_ms = max_over_ranks(total_ms, device=dev)  # whole-job time = slowest rank
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = P * world * args.steps / (total_ms / 1e3)
+    # whole-job pairs per second: every rank's own matrix (weak) or the one shared matrix (strong)
+    value = (P if args.shard else P * world) * args.steps / (total_ms / 1e3)
 
     # Roofline of the dominant kernel (the pair kernel).
     peaks = _peaks()
@@ -559,7 +628,7 @@ def run_ours(args):
         # Algorithmic work: n * ceil(log2 n) compare-and-count merge steps per pair (Step 3).
         steps_per_pair = N * 7
         kern_avg_ms = dominant_ms
-        achieved = P * steps_per_pair / (kern_avg_ms / 1e3) / 1e9
+        achieved = (hi - lo) * steps_per_pair / (kern_avg_ms / 1e3) / 1e9
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         f = (clocks.get("sm_mhz") or 1455.0) * 1e6
         peak = sms * 128 * f / 1e9  # int32 lane-ops per second at the sampled clock
@@ -573,7 +642,7 @@ def run_ours(args):
         # measured on this GPU (the FP8 rate x 3, the nominal FP4/FP8 ratio, when torch exposes
         # no FP4 GEMM). The HBM view: the
         # stored outputs (12 bytes per pair) and the operands read once.
-        flops = 2.0 * P * (N * (N - 1) // 2)
+        flops = 2.0 * (hi - lo) * (N * (N - 1) // 2)
         kern_avg_ms = dominant_ms
         achieved = flops / (kern_avg_ms / 1e3) / 1e12
         bf16 = (peaks or {}).get("bf16_tflops", 1899.7)
@@ -581,7 +650,7 @@ def run_ours(args):
             peak, src = tpeaks["fp4_tflops"], "FP4 e2m1 cuBLAS GEMM on this GPU (" + tpeaks["how"] + ")"
         else:
             peak, src = 3.0 * tpeaks["fp8_tflops"], "FP8 cuBLAS GEMM on this GPU x 3 (nominal ratio)"
-        alg_bytes = 12.0 * P + M * ((N * (N - 1) // 2 + 255) // 256 * 128)
+        alg_bytes = 12.0 * (hi - lo) + M * ((N * (N - 1) // 2 + 255) // 256 * 128)
         hbm = (peaks or {}).get("hbm_gbs", 6779.7)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _traffic("contract2_kernel"),
@@ -625,32 +694,39 @@ def run_ours(args):
         # End to end through the C ABI with host buffers: the input goes host -> device, and the
         # outputs come back in passes whose copies overlap the next pass (ktau_allpairs_host).
         Xh = torch.from_numpy(X).pin_memory()
-        out_h = [torch.empty(P, dtype=t.dtype).pin_memory() for t in (tau32, S, n3)]
+        out_h = [torch.empty(hi - lo, dtype=t.dtype).pin_memory() for t in (tau32, S, n3)]
         h2d = Xh.numel() * 4
         d2h = sum(t.numel() * t.element_size() for t in out_h)
 
         def e2e_step():
             R = ktau.ktau_rank_prepare_host(Xh, stream)  # H2D copy inside the library call
-            ktau.ktau_allpairs_host(R, 0, P, None, out_h[0], out_h[1], out_h[2], 32, opts, 0,
+            ktau.ktau_allpairs_host(R, lo, hi, None, out_h[0], out_h[1], out_h[2], 32, opts, 0,
                                     stream)
             R.free()
 
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": P * world * args.steps / e2e_s, "unit": "pairs/s",
+        if dist:
+            from paper_1704_03767_gb300.sharding import max_over_ranks
+
+            e2e_s = max_over_ranks(e2e_s, device=dev)
+        e2e = {"value": (P if args.shard else P * world) * args.steps / e2e_s, "unit": "pairs/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "ktau_rank_prepare_host (pinned host input) + ktau_allpairs_host (pinned "
                       "host outputs, passes with overlapped D2H)"}
 
     batched = None
     if not args.no_batched and world == 1:
-        batched = bench_batched(ktau, max(3, args.steps // 2), args.warmup)
+        batched = bench_batched(ktau, max(3, args.steps // 2), args.warmup,
+                                tpeaks.get("fp4_tflops", 3.0 * tpeaks["fp8_tflops"]))
     query = None
     if not args.no_query and world == 1:
         query = bench_query(ktau, args.query_batches)
@@ -660,6 +736,7 @@ def run_ours(args):
     merge = None
     if not args.no_merge and world == 1:
         merge = bench_merge(ktau, clocks.get("sm_mhz"))
+        merge["bits_path"] = bench_bits(ktau)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -670,11 +747,13 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if args.shard else "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": M, "n": N, "pairs": P, "path": path_used,
                    "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"{world} independent shards (one matrix per GPU)"},
+                   "parallelism": (f"{world} static shards of one matrix's pair range"
+                                   if args.shard else
+                                   f"{world} independent shards (one matrix per GPU)")},
         "gpu_launches": round(len(trace) / 3 * args.steps),  # library kernels per step x steps
         "kernels": kernels,
         "kernels_source": "CUDA events around every library launch in 3 steps after the timed "

@@ -297,7 +297,8 @@ typedef struct {
   void* S;
   void* n3;
   int32_t path;        /* ktau_path for this dataset; AUTO = opt->path, else by n (autotuner) */
-  int32_t reserved;
+  int32_t mapping;     /* merge path: 1 = one warp per pair, 2 = one CTA per pair, 0 = by n
+                          (a warp up to n = 1024); datasets of both kinds form separate groups */
 } ktau_batch_desc;
 
 typedef struct ktau_batch ktau_batch;

@@ -8,8 +8,10 @@ per sample count n and tie density, the fastest exact path and merge-path mappin
     autotune.batch_paths(table, matrices)                # -> per-dataset path for ktau_batch
 
 Candidates per (n, tie density): the merge path with one warp per pair (tile side 32 or 8) and
-with one CTA per pair (n > 256), and the sign contraction (n <= 2048). Times come from the
-library's own kernel trace (CUDA events around each launch), best of a few repetitions.
+with one CTA per pair (n > 256), the bit-parallel dominance count (n <= 256), and the sign
+contraction (n <= 2048) with block-scaled FP4 operands (the default) or FP8 operands. Times come
+from the library's own kernel trace (CUDA events around each launch), best of a few repetitions,
+operands and masks already built (the first call builds them).
 """
 from __future__ import annotations
 
@@ -75,8 +77,11 @@ def measure(n_grid=N_GRID, tie_grid=TIE_GRID, target_pairs=2_000_000, verbose=Tr
                      "merge_warp_q8": {"path": 1, "mapping": 1, "tile_q": 8}}
             if n > 256:
                 cands["merge_cta_q4"] = {"path": 1, "mapping": 2, "tile_q": 4}
+            if n <= kb.KTAU_BITS_MAX_N:
+                cands["bits"] = {"path": kb.KTAU_PATH_BITS}
             if n <= 2048:
                 cands["signgemm"] = {"path": 2}
+                cands["signgemm_fp8"] = {"path": 2, "operand_bits": 8}
             times = {}
             for name, o in cands.items():
                 try:
@@ -135,11 +140,39 @@ def tie_fraction(X: np.ndarray, rows: int = 32) -> float:
     return float(np.mean(reps))
 
 
+# Candidates the batched form can run (it has no bit-parallel path and one operand type per call).
+_BATCHABLE = ("merge_warp_q32", "merge_warp_q8", "merge_cta_q4", "signgemm")
+
+
+def choose_batch(table, n: int, tie_frac: float = 0.05) -> dict:
+    """Fastest batchable candidate at the nearest grid point: {"path", "mapping"}."""
+    if not table:
+        return {"path": kb.KTAU_PATH_AUTO, "mapping": 0}
+    ents = table["entries"]
+    ties = sorted({e["tie_frac"] for e in ents}, key=lambda t: abs(t - tie_frac))
+    e = min((e for e in ents if e["tie_frac"] == ties[0]),
+            key=lambda e: abs(np.log(e["n"]) - np.log(n)))
+    times = {k: v for k, v in e["ns_per_pair"].items() if k in _BATCHABLE and v is not None}
+    best = min(times, key=times.get)
+    if best == "signgemm" and n <= 2048:
+        return {"path": kb.KTAU_PATH_SIGNGEMM, "mapping": 0}
+    if best == "signgemm":
+        best = "merge_cta_q4"
+    return {"path": kb.KTAU_PATH_MERGE, "mapping": 2 if best == "merge_cta_q4" else 1}
+
+
 def batch_paths(table, matrices) -> list:
     """Per-dataset path (ktau_path) for the batched form."""
-    return [choose(table, X.shape[1], tie_fraction(X))["path"] for X in matrices]
+    return [choose_batch(table, X.shape[1], tie_fraction(X))["path"] for X in matrices]
+
+
+def batch_plans(table, matrices) -> list:
+    """Per-dataset (path, merge mapping) for the batched form's descriptors."""
+    return [choose_batch(table, X.shape[1], tie_fraction(X)) for X in matrices]
 
 
 if __name__ == "__main__":
+    import sys
+
     t = measure()
-    print(save(t))
+    print(save(t, sys.argv[1] if len(sys.argv) > 1 else None))

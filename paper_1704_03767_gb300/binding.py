@@ -49,7 +49,7 @@ class BatchDesc(ctypes.Structure):
                 ("count_bits", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("ld", ctypes.c_int64), ("tau64", ctypes.c_void_p), ("tau32", ctypes.c_void_p),
                 ("S", ctypes.c_void_p), ("n3", ctypes.c_void_p), ("path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("mapping", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -421,11 +421,11 @@ class Batch:
 
 
 def batch_desc(values: torch.Tensor, tau64=None, tau32=None, S=None, n3=None,
-               count_bits: int = 32, path: int = KTAU_PATH_AUTO) -> BatchDesc:
+               count_bits: int = 32, path: int = KTAU_PATH_AUTO, mapping: int = 0) -> BatchDesc:
     m, n = values.shape
     dt = KTAU_F32 if values.dtype == torch.float32 else KTAU_I32
     return BatchDesc(values.data_ptr(), dt, count_bits, m, n, values.stride(0), _ptr(tau64),
-                     _ptr(tau32), _ptr(S), _ptr(n3), path, 0)
+                     _ptr(tau32), _ptr(S), _ptr(n3), path, mapping)
 
 
 def ktau_workspace_size(descs, options=None) -> int:

@@ -224,6 +224,8 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
                        KTAU_BATCH_MAX_N);
     if ((s = ktau_check_counts(d.n, d.count_bits)) != KTAU_OK) return s;
     if (d.path < 0 || d.path > 2) return ktau_fail(KTAU_EINVAL, "descriptor %d: bad path", i);
+    if (d.mapping < 0 || d.mapping > 2)
+      return ktau_fail(KTAU_EINVAL, "descriptor %d: bad mapping", i);
     if (batch_path_for(d, opt) == KTAU_PATH_SIGNGEMM && d.n > KTAU_SIGNGEMM_MAX_N)
       return ktau_fail(KTAU_EINVAL, "descriptor %d: contraction path needs n <= %d", i,
                        KTAU_SIGNGEMM_MAX_N);
@@ -236,7 +238,8 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
   for (int i = 0; i < count; ++i) {
     const ktau_batch_desc& d = descs[i];
     if (batch_path_for(d, opt) == KTAU_PATH_MERGE) {
-      gkey[i] = (int64_t)1 << 40 | (d.n <= 1024 ? 0 : 1);
+      const bool cta = d.mapping == 2 || (d.mapping == 0 && d.n > 1024);
+      gkey[i] = (int64_t)1 << 40 | (cta ? 1 : 0);
     } else {
       const int ob = ktau_sign_obits(d.n, opt);
       const int64_t bytes = ktau_kpad(d.n * (d.n - 1) / 2, ob) * ob / 8;

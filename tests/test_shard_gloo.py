@@ -67,3 +67,37 @@ def test_two_rank_gather_matches_single_process():
     assert np.array_equal(S, ref["S"])
     assert np.array_equal(tau, ref["tau"], equal_nan=True)
     assert t == 2.0
+
+
+def test_merge_topk_of_row_shards_equals_whole_database():
+    """Query search with the database split by rows (Sec. 4.4 partition): each shard's exact top-k
+    (oracle order) merged on the host equals the top-k over the whole database, including rows
+    tied in |tau| across shards, a constant row (NaN, last) and a constant query."""
+    import oracle
+    from paper_1704_03767_gb300.sharding import merge_topk
+
+    g = np.random.default_rng(5)
+    n = 12
+    D = g.integers(0, 5, (23, n)).astype(float)
+    D[15] = D[2]      # equal |tau| to row 2, in another shard
+    D[20] = -D[2]
+    D[9] = 3.0        # constant row
+    Q = g.integers(0, 6, (3, n)).astype(float)
+    Q[2] = 1.0        # constant query
+    k = 7
+    ref = oracle.query_topk(Q, D, k)
+    n0 = n * (n - 1) // 2
+    parts = []
+    for lo, hi in ((0, 8), (8, 16), (16, 23)):
+        r = oracle.rect(Q, D[lo:hi])
+        Du = [n0 - int(r["n1"][i, 0]) for i in range(3)]
+        kk = min(k, hi - lo)
+        idx = [oracle.topk_order(r["S"][i], Du[i], n0 - r["n2"][i], kk) for i in range(3)]
+        parts.append({"offset": lo, "idx": idx,
+                      "tau": [r["tau"][i, idx[i]] for i in range(3)],
+                      "S": [r["S"][i, idx[i]] for i in range(3)],
+                      "T": [r["n2"][i, idx[i]] for i in range(3)]})
+    idx, tau = merge_topk(parts, k, n)
+    assert np.array_equal(idx, ref["topk_idx"])
+    assert np.array_equal(np.isnan(tau), np.isnan(ref["topk_tau"]))
+    assert np.array_equal(np.nan_to_num(tau), np.nan_to_num(ref["topk_tau"]))
