@@ -191,6 +191,15 @@ def tensor_peaks(dev) -> dict:
     return out
 
 
+def _timed_oracle(Xd, threads: int, p_end: int):
+    """Wall and process CPU seconds of one oracle run over the first p_end pairs."""
+    import oracle
+
+    c0, t0 = time.process_time(), time.perf_counter()
+    oracle.allpairs(Xd, method="knight", threads=threads, p_begin=0, p_end=p_end)
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
 def cpu_baseline(X, seconds: float):
     """The oracle as it stands (Knight per pair, Sec. 3.2; the requested pair range cut into
     equal contiguous slices, one per host core, Sec. 4.2-4.3) on the first pairs of the same
