@@ -7,6 +7,9 @@
 //              list of Step 1 already ordered by u; only samples tied in u remain unordered.
 //   Step 1   : if u has ties, sort the packed keys (group(u) << 16 | w) so that each tie group
 //              of u is ordered by v (the 15/16-bit packing of the paper's vectorised kernel).
+//              The keys arrive ordered by group, so when the largest u-tie group is short next
+//              to n the merge levels stop at runs of that length and one fix-up pass places the
+//              groups that straddle a run boundary.
 //   Step 2   : n_3 = joint ties = sum over runs of equal keys of t(t-1)/2 (n_1 comes from K-a).
 //   Step 3   : bottom-up merge sort of w; when an element of a right run is emitted while left
 //              elements remain, all of those are larger (ties go left): add their number to n_d.
@@ -50,8 +53,9 @@ __device__ __forceinline__ unsigned long long team_sum(unsigned long long v,
 // Team buffers hold element i at word pd(i) = i + i / 32 when lanes own runs of 8 or more
 // (lane l at l * ITEMS): unpadded, the accesses of one instruction would hit every
 // (32 / ITEMS)-th bank; one pad word per 32 spreads them over all banks. Shorter runs are left
-// unpadded (there the index arithmetic costs more than the conflicts). Buffers are sized for
-// the padded form: i + i / 32 + 1 words for n elements.
+// unpadded: there the index arithmetic costs more than the conflicts (measured on 16384 x 128,
+// four keys per lane: 1.75 ns per pair unpadded, 1.89 padded). Buffers are sized for the padded
+// form: i + i / 32 + 1 words for n elements.
 template <int ITEMS>
 __device__ __forceinline__ int pd(int i) { return ITEMS >= 8 ? i + (i >> 5) : i; }
 
@@ -76,12 +80,54 @@ __device__ __forceinline__ int team_excl_max(int v, unsigned long long* red) {
   return excl;
 }
 
+// Step 1 with the merge levels stopped at runs of L >= the largest u-tie group (Sec. 3.2 Step 1
+// sorts inside u-tie groups only). The keys (group << 16 | w) are ordered by group on entry and
+// every L-aligned run of `in` is sorted, so a tie group, at most L long, lies inside one run or
+// straddles one run boundary; in the second case its part left of the boundary and its part right
+// of it are each sorted. Each key of a straddling group moves to its final place: a left-part key
+// past the right-part keys below it (found by binary search in the next run: keys of later groups
+// are larger), a right-part key before the left-part keys above it (binary search in the previous
+// run: keys of earlier groups are smaller). Equal keys keep left before right. Writes `out`.
+template <int TEAM, int ITEMS>
+__device__ __forceinline__ void team_group_fixup(const uint32_t* in, uint32_t* out, int n, int L,
+                                                 int lane) {
+  for (int k = lane; k < n; k += TEAM) {
+    const uint32_t key = in[pd<ITEMS>(k)];
+    const int lo_b = k - k % L, hi_b = min(n, lo_b + L);
+    int dst = k;
+    if (hi_b < n && (in[pd<ITEMS>(hi_b)] >> 16) == (key >> 16)) {
+      int lo = hi_b, hi = min(n, hi_b + L);  // first key of the next run that is >= key
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (in[pd<ITEMS>(mid)] < key)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      dst = k + (lo - hi_b);
+    } else if (lo_b > 0 && (in[pd<ITEMS>(lo_b - 1)] >> 16) == (key >> 16)) {
+      int lo = lo_b - L, hi = lo_b;  // first key of the previous run that is > key
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (in[pd<ITEMS>(mid)] <= key)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      dst = k - L + (lo - (lo_b - L));
+    }
+    out[pd<ITEMS>(dst)] = key;
+  }
+}
+
 // Merge sort of buf[0, n) (ascending) with tmp as the second buffer. With COUNT, each thread
 // accumulates into `cnt` its share of the inversions (pairs i < j with buf[i] > buf[j]).
+// run_cap < n (Step 1 only, without COUNT): the merge levels stop once the sorted runs reach
+// run_cap, and team_group_fixup finishes the sort inside u-tie groups no longer than run_cap.
 // Returns the buffer that holds the sorted sequence. Every thread of the team must call it.
 template <int TEAM, int ITEMS, bool COUNT>
 __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int lane,
-                                     unsigned long long& cnt) {
+                                     unsigned long long& cnt, int run_cap) {
   constexpr int CH = TEAM * ITEMS;
   unsigned c = 0;
   // Runs of ITEMS sorted in registers (inversions inside a run counted directly).
@@ -112,7 +158,8 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
   team_sync<TEAM>();
   uint32_t* in = buf;
   uint32_t* out = tmp;
-  for (int s = ITEMS; s < n; s *= 2) {
+  int s = ITEMS;
+  for (; s < n && s < run_cap; s *= 2) {
     for (int base = 0; base < n; base += CH) {
       const int o = base + lane * ITEMS;
       const int A = (o / (2 * s)) * (2 * s);
@@ -146,25 +193,28 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
           else
             hi = mid;
         }
-        int ai = lo, bi = diag - lo;
+        // Serial merge of ITEMS outputs without branches: an exhausted run reads as the
+        // sentinel (above every key), so "take the right run" is vb < va; one load refills the
+        // side taken. Outputs past the merge's end are not stored.
+        int ai = A + lo, bi = B + diag - lo;
+        const int ae = A + a_len, be = B + b_len;
         const int todo = min(ITEMS, a_len + b_len - diag);
-        uint32_t va = ai < a_len ? in[pd<ITEMS>(A + ai)] : kSentinel;
-        uint32_t vb = bi < b_len ? in[pd<ITEMS>(B + bi)] : kSentinel;
+        uint32_t va = ai < ae ? in[pd<ITEMS>(ai)] : kSentinel;
+        uint32_t vb = bi < be ? in[pd<ITEMS>(bi)] : kSentinel;
+        // o is a multiple of ITEMS and, where pd pads (ITEMS 8 or 16), [o, o + ITEMS) stays
+        // within one 32-element row: the outputs are consecutive words from pd(o).
+        uint32_t* op = out + pd<ITEMS>(o);
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-          if (i < todo) {
-            const bool take_b = (ai >= a_len) || (bi < b_len && vb < va);
-            if (take_b) {
-              out[pd<ITEMS>(o + i)] = vb;
-              if (COUNT) c += (unsigned)(a_len - ai);  // remaining left elements are larger
-              ++bi;
-              vb = bi < b_len ? in[pd<ITEMS>(B + bi)] : kSentinel;
-            } else {
-              out[pd<ITEMS>(o + i)] = va;
-              ++ai;
-              va = ai < a_len ? in[pd<ITEMS>(A + ai)] : kSentinel;
-            }
-          }
+          const bool take_b = vb < va;
+          if (i < todo) op[i] = take_b ? vb : va;
+          if (COUNT) c += take_b ? (unsigned)(ae - ai) : 0u;  // remaining left keys are larger
+          ai += take_b ? 0 : 1;
+          bi += take_b ? 1 : 0;
+          const bool more = take_b ? bi < be : ai < ae;
+          const uint32_t v = more ? in[pd<ITEMS>(take_b ? bi : ai)] : kSentinel;
+          va = take_b ? va : v;
+          vb = take_b ? v : vb;
         }
       }
     }
@@ -172,6 +222,11 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
     uint32_t* t = in;
     in = out;
     out = t;
+  }
+  if (!COUNT && s < n) {
+    team_group_fixup<TEAM, ITEMS>(in, out, n, s, lane);
+    team_sync<TEAM>();
+    in = out;
   }
   cnt += c;
   return in;
@@ -182,6 +237,7 @@ struct MergeArgs {
   const uint16_t* perm;
   const uint16_t* srank;
   const int64_t* T;
+  const int32_t* maxg;   // largest tie group of each row variable
   ktau_fac fac;
   const uint16_t* rank;  // column side
   const int64_t* Tc;
@@ -208,7 +264,7 @@ struct MergeArgs {
 template <int TEAM, int ITEMS>
 __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_t* srank_u,
                                            const uint16_t* rank_v, int n, bool u_ties,
-                                           uint32_t* buf, uint32_t* tmp, int lane,
+                                           int maxg_u, uint32_t* buf, uint32_t* tmp, int lane,
                                            unsigned long long* red, long long& nd_out,
                                            long long& n3_out) {
   for (int k = lane; k < n; k += TEAM) {
@@ -219,7 +275,10 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
   unsigned long long nd = 0, n3 = 0;
   if (u_ties) {
     unsigned long long unused = 0;
-    uint32_t* sorted = team_merge_sort<TEAM, ITEMS, false>(buf, tmp, n, lane, unused);
+    // Step 1 sorts inside u-tie groups: with groups short next to n, the merge levels stop at
+    // runs as long as the largest group and a fix-up pass finishes the groups across runs.
+    const int cap = 4 * maxg_u <= n ? maxg_u : n;
+    uint32_t* sorted = team_merge_sort<TEAM, ITEMS, false>(buf, tmp, n, lane, unused, cap);
     uint32_t* other = sorted == buf ? tmp : buf;
     // Step 2: joint ties. In the sorted keys, position k has (k - first index of its run of
     // equal keys) earlier equal keys.
@@ -257,9 +316,9 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
       }
     }
     team_sync<TEAM>();
-    team_merge_sort<TEAM, ITEMS, true>(other, sorted, n, lane, nd);
+    team_merge_sort<TEAM, ITEMS, true>(other, sorted, n, lane, nd, n);
   } else {
-    team_merge_sort<TEAM, ITEMS, true>(buf, tmp, n, lane, nd);
+    team_merge_sort<TEAM, ITEMS, true>(buf, tmp, n, lane, nd, n);
   }
   nd_out = (long long)team_sum<TEAM>(nd, red);
   n3_out = (long long)team_sum<TEAM>(n3, red);
@@ -342,7 +401,7 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
       const uint16_t* rv = a.stage ? s_rank + (x - x0) * ld : a.rank + x * ld;
       const int64_t Tu = a.T[y], Tv = a.Tc[x];
       long long nd, n3;
-      count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, tbuf, tbuf2, lane, red, nd, n3);
+      count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, a.maxg[y], tbuf, tbuf2, lane, red, nd, n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
         if (a.out.tau64)
@@ -385,18 +444,18 @@ ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas
 
 // Counts of one pair with the register run length chosen from n (warp team).
 __device__ __forceinline__ void count_pair_any(int items, const uint16_t* pu, const uint16_t* su,
-                                               const uint16_t* rv, int n, bool ties, uint32_t* buf,
-                                               uint32_t* tmp, int lane, long long& nd,
-                                               long long& n3) {
+                                               const uint16_t* rv, int n, bool ties, int maxg,
+                                               uint32_t* buf, uint32_t* tmp, int lane,
+                                               long long& nd, long long& n3) {
   switch (items) {
-    case 1: count_pair<32, 1>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    case 2: count_pair<32, 2>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    case 3: count_pair<32, 3>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    case 4: count_pair<32, 4>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    case 5: count_pair<32, 5>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    case 6: count_pair<32, 6>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    case 7: count_pair<32, 7>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
-    default: count_pair<32, 8>(pu, su, rv, n, ties, buf, tmp, lane, nullptr, nd, n3); break;
+    case 1: count_pair<32, 1>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    case 2: count_pair<32, 2>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    case 3: count_pair<32, 3>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    case 4: count_pair<32, 4>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    case 5: count_pair<32, 5>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    case 6: count_pair<32, 6>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    case 7: count_pair<32, 7>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
+    default: count_pair<32, 8>(pu, su, rv, n, ties, maxg, buf, tmp, lane, nullptr, nd, n3); break;
   }
 }
 
@@ -439,10 +498,10 @@ __global__ void __launch_bounds__(256) batch_merge_kernel(const ktau_bds* __rest
       long long nd, n3;
       if (TEAM == 32)
         count_pair_any(items, D.perm + y * D.ld, D.srank + y * D.ld, D.rank + x * D.ld, n, Tu > 0,
-                       tbuf, tbuf2, lane, nd, n3);
+                       D.maxg[y], tbuf, tbuf2, lane, nd, n3);
       else
         count_pair<TEAM, 8>(D.perm + y * D.ld, D.srank + y * D.ld, D.rank + x * D.ld, n, Tu > 0,
-                            tbuf, tbuf2, lane, red, nd, n3);
+                            D.maxg[y], tbuf, tbuf2, lane, red, nd, n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
         ktau_store(D.out, ktau_pair_index(D.m, y, x), S, n3, n0, fac, y, x);
@@ -513,6 +572,7 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
   a.perm = R->perm;
   a.srank = R->srank;
   a.T = R->T;
+  a.maxg = R->maxg;
   a.fac = ktau_fac{R->rs64, R->rsff, R->T};
   a.rank = C->rank;
   a.Tc = C->T;
