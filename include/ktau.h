@@ -31,8 +31,12 @@
  *     The FP32 output is the FP64 value rounded to nearest-even.
  *   - Limits: 2 <= n <= KTAU_MAX_N, 1 <= m <= KTAU_MAX_M (a single variable has no pairs); the
  *     batched and allocation-free forms take n <= KTAU_BATCH_MAX_N. Rows longer than 16384 samples
- *     are ranked and counted (merge path) with library scratch in global memory. Values may be
- *     +-Inf; -0.0 equals +0.0; a NaN anywhere fails the call with KTAU_ENAN.
+ *     are ranked and counted (merge path) with library scratch in global memory. Rows longer than
+ *     KTAU_NARROW_MAX_N samples keep 32-bit ranks and sample indices (the 64-bit key packing the
+ *     paper's Sec. 6 anticipates): such handles serve the merge path of ktau_allpairs and
+ *     ktau_allpairs_host only, with 64-bit counts; every other form returns KTAU_EINVAL or
+ *     KTAU_ETOOLARGE for them. Values may be +-Inf; -0.0 equals +0.0; a NaN anywhere fails
+ *     the call with KTAU_ENAN.
  */
 #ifndef KTAU_H
 #define KTAU_H
@@ -44,8 +48,9 @@
 extern "C" {
 #endif
 
-#define KTAU_ABI_VERSION 1
-#define KTAU_MAX_N 65535      /* samples per variable (ranks and sample indices are uint16) */
+#define KTAU_ABI_VERSION 2
+#define KTAU_MAX_N 4194304    /* samples per variable */
+#define KTAU_NARROW_MAX_N 65535 /* longest rows kept with uint16 ranks and sample indices */
 #define KTAU_BATCH_MAX_N 16384 /* samples per variable in the batched and allocation-free forms */
 #define KTAU_MAX_M 4194304    /* variables per matrix */
 
@@ -149,8 +154,12 @@ ktau_status ktau_ranked_shape(const ktau_ranked* R, int64_t* m, int64_t* n);
 ktau_status ktau_tie_counts(const ktau_ranked* R, int64_t* T_dev, void* stream);
 
 /* Copies the permutation pi (perm[m*n]) and dense ranks r (rank[m*n]) into caller device
- * buffers, packed m x n (uint16). Either pointer may be NULL. Asynchronous on `stream`. */
+ * buffers, packed m x n (uint16). Either pointer may be NULL. Asynchronous on `stream`.
+ * EINVAL for a handle with n > KTAU_NARROW_MAX_N (use ktau_ranked_export32). */
 ktau_status ktau_ranked_export(const ktau_ranked* R, uint16_t* perm, uint16_t* rank, void* stream);
+/* The same as uint32 (any n): perm[m*n] and rank[m*n] packed m x n. Asynchronous on `stream`. */
+ktau_status ktau_ranked_export32(const ktau_ranked* R, uint32_t* perm, uint32_t* rank,
+                                 void* stream);
 
 /*
  * ktau_allpairs -- exact tau-b for every pair with packed index in [p_begin, p_end)

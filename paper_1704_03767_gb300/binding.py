@@ -19,7 +19,8 @@ KTAU_OK, KTAU_EINVAL, KTAU_ENAN, KTAU_ETOOLARGE, KTAU_ENOMEM, KTAU_ECUDA, KTAU_E
 KTAU_F32, KTAU_I32 = 0, 1
 KTAU_PATH_AUTO, KTAU_PATH_MERGE, KTAU_PATH_SIGNGEMM, KTAU_PATH_BITS = 0, 1, 2, 3
 KTAU_BITS_MAX_N = 256
-KTAU_MAX_N = 65535
+KTAU_MAX_N = 4194304
+KTAU_NARROW_MAX_N = 65535
 KTAU_BATCH_MAX_N = 16384
 
 STATUS_NAMES = {0: "KTAU_OK", 1: "KTAU_EINVAL", 2: "KTAU_ENAN", 3: "KTAU_ETOOLARGE",
@@ -69,6 +70,7 @@ _SIGS = {
     "ktau_ranked_shape": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "ktau_tie_counts": ([_vp, _vp, _vp], ctypes.c_int),
     "ktau_ranked_export": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "ktau_ranked_export32": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "ktau_allpairs": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(Options), _vp],
                       ctypes.c_int),
     "ktau_allpairs_noalloc": ([_vp, ctypes.c_int, _i64, _i64, _i64, _u64, _u64, _vp, _vp, _vp,
@@ -234,6 +236,16 @@ def ktau_ranked_export(R: Ranked, stream=None):
     perm = torch.empty((R.m, R.n), dtype=torch.uint16, device=R.device)
     rank = torch.empty((R.m, R.n), dtype=torch.uint16, device=R.device)
     _check(load().ktau_ranked_export(R.handle, perm.data_ptr(), rank.data_ptr(), _stream(stream)))
+    return perm, rank
+
+
+def ktau_ranked_export32(R: Ranked, stream=None):
+    """perm and rank as 32-bit rows (any n). Returned as int32 tensors holding the uint32 values,
+    which are below 2^31 for every n the library takes."""
+    perm = torch.empty((R.m, R.n), dtype=torch.int32, device=R.device)
+    rank = torch.empty((R.m, R.n), dtype=torch.int32, device=R.device)
+    _check(load().ktau_ranked_export32(R.handle, perm.data_ptr(), rank.data_ptr(),
+                                       _stream(stream)))
     return perm, rank
 
 

@@ -204,8 +204,10 @@ ktau_status rank_prepare_impl(const void* values, ktau_dtype dt, int64_t m, int6
   R->m = m;
   R->n = n;
   R->ld = (n + 15) & ~15LL;
+  R->wide = n > KTAU_NARROW_MAX_N;
   cudaGetDevice(&R->device);
-  const size_t arr = (size_t)m * R->ld * sizeof(uint16_t);
+  const size_t esz = R->wide ? sizeof(uint32_t) : sizeof(uint16_t);
+  const size_t arr = (size_t)m * R->ld * esz;
   const size_t arr_al = (arr + 255) & ~(size_t)255;
   const size_t t_bytes = ((size_t)m * 8 + 255) & ~(size_t)255;
   const size_t i_bytes = ((size_t)m * 4 + 255) & ~(size_t)255;
@@ -217,9 +219,15 @@ ktau_status rank_prepare_impl(const void* values, ktau_dtype dt, int64_t m, int6
   }
   cudaError_t e;
   char* b = (char*)R->block;
-  R->perm = (uint16_t*)b;
-  R->rank = (uint16_t*)(b + arr_al);
-  R->srank = (uint16_t*)(b + 2 * arr_al);
+  if (R->wide) {
+    R->perm32 = (uint32_t*)b;
+    R->rank32 = (uint32_t*)(b + arr_al);
+    R->srank32 = (uint32_t*)(b + 2 * arr_al);
+  } else {
+    R->perm = (uint16_t*)b;
+    R->rank = (uint16_t*)(b + arr_al);
+    R->srank = (uint16_t*)(b + 2 * arr_al);
+  }
   R->T = (int64_t*)(b + 3 * arr_al);
   R->ndist = (int32_t*)(b + 3 * arr_al + t_bytes);
   R->maxg = (int32_t*)(b + 3 * arr_al + t_bytes + i_bytes);
@@ -358,6 +366,9 @@ ktau_status ktau_tie_counts(const ktau_ranked* R, int64_t* T_dev, void* stream) 
 
 ktau_status ktau_ranked_export(const ktau_ranked* R, uint16_t* perm, uint16_t* rank, void* stream) {
   if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  if (R->wide)
+    return ktau_fail(KTAU_EINVAL, "n=%lld > %d has 32-bit ranks: use ktau_ranked_export32",
+                     (long long)R->n, KTAU_NARROW_MAX_N);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t pitch = (size_t)R->ld * sizeof(uint16_t), width = (size_t)R->n * sizeof(uint16_t);
   if (perm)
@@ -365,6 +376,21 @@ ktau_status ktau_ranked_export(const ktau_ranked* R, uint16_t* perm, uint16_t* r
                                 cudaMemcpyDeviceToDevice, st));
   if (rank)
     KTAU_CUDA(cudaMemcpy2DAsync(rank, width, R->rank, pitch, width, (size_t)R->m,
+                                cudaMemcpyDeviceToDevice, st));
+  return KTAU_OK;
+}
+
+ktau_status ktau_ranked_export32(const ktau_ranked* R, uint32_t* perm, uint32_t* rank,
+                                 void* stream) {
+  if (!R) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!R->wide) return ktau_launch_widen(R, perm, rank, st);
+  const size_t pitch = (size_t)R->ld * sizeof(uint32_t), width = (size_t)R->n * sizeof(uint32_t);
+  if (perm)
+    KTAU_CUDA(cudaMemcpy2DAsync(perm, width, R->perm32, pitch, width, (size_t)R->m,
+                                cudaMemcpyDeviceToDevice, st));
+  if (rank)
+    KTAU_CUDA(cudaMemcpy2DAsync(rank, width, R->rank32, pitch, width, (size_t)R->m,
                                 cudaMemcpyDeviceToDevice, st));
   return KTAU_OK;
 }

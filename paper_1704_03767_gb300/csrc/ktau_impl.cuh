@@ -19,6 +19,9 @@
 //                        NaN for a constant variable
 //   rsff [m]     float2  rs64 split into a float-float pair (hi, lo), hi + lo == rs64 to 2^-48
 // Padding entries (k >= n) hold 0xFFFF.
+// Rows longer than 65535 samples ("wide" handles) hold the same three arrays as uint32 (perm32,
+// rank32, srank32; padding 0xFFFFFFFF) and leave the uint16 pointers null: only the merge path
+// reads them.
 // ---------------------------------------------------------------------------------------------
 struct ktau_stats {
   unsigned long long T_sum;
@@ -41,6 +44,10 @@ struct ktau_ranked {
   uint16_t* perm;
   uint16_t* rank;
   uint16_t* srank;
+  int wide;  // n > KTAU_NARROW_MAX_N: 32-bit arrays below instead of the 16-bit ones above
+  uint32_t* perm32;
+  uint32_t* rank32;
+  uint32_t* srank32;
   int64_t* T;
   int32_t* ndist;
   int32_t* maxg;
@@ -179,7 +186,9 @@ __device__ __forceinline__ bool ktau_tau32_fast(int S, float2 fu, float2 fv, flo
 __device__ __forceinline__ float ktau_tau32(int64_t S, float2 fu, float2 fv, int64_t n0,
                                             int64_t Tu, int64_t Tv) {
   float f;
-  if (ktau_tau32_fast((int)S, fu, fv, f)) return f;
+  // The float-float split of S assumes |S| < 2^31 (always so for n <= 65535); longer rows whose
+  // S is larger take the FP64 formula.
+  if (S > -(1ll << 31) && S < (1ll << 31) && ktau_tau32_fast((int)S, fu, fv, f)) return f;
   return __double2float_rn(ktau_tau_b_formula(S, n0 - Tu, n0 - Tv));
 }
 
@@ -192,8 +201,10 @@ struct ktau_fac {
 // tau-a = S / n_0 (no tie correction). FP64: the IEEE quotient of two exact integers. FP32: the
 // quotient correctly rounded to FP32. With S and n_0 below 2^24 that is one IEEE division; above,
 // the FP64 quotient q is rounded to FP32, which can mislead only when q lies exactly on the
-// midpoint m of two floats; then the sign of S - m * n_0 decides (m * n_0 is exact in FP64 for
-// n_0 < 2^28, i.e. n <= 16384).
+// midpoint m of two floats; then the sign of S - m * n_0 decides. That difference is formed
+// exactly: p = RN(m * n_0) and its rounding error e = fma(m, n_0, -p) are exact doubles, S - p is
+// exact (S and p are within a factor of two of each other), and the sign of (S - p) - e is the
+// sign of the exact difference (S, n_0 < 2^53).
 __device__ __forceinline__ double ktau_taua64(int64_t S, int64_t n0) {
   return __ddiv_rn((double)S, (double)n0);
 }
@@ -206,9 +217,11 @@ __device__ __forceinline__ float ktau_taua32(int64_t S, int64_t n0) {
   const float g = nextafterf(f, q > fd ? INFINITY : -INFINITY);
   const double mid = 0.5 * (fd + (double)g);
   if (q != mid) return f;
-  const double prod = mid * (double)n0;
-  if ((double)S == prod) return f;  // exact tie: already rounded to even
-  return (double)S > prod ? fmaxf(f, g) : fminf(f, g);
+  const double prod = __dmul_rn(mid, (double)n0);
+  const double err = __fma_rn(mid, (double)n0, -prod);
+  const double diff = __dsub_rn(__dsub_rn((double)S, prod), err);
+  if (diff == 0.0) return f;  // exact tie: already rounded to even
+  return diff > 0.0 ? fmaxf(f, g) : fminf(f, g);
 }
 
 __device__ __forceinline__ void ktau_store(const ktau_out& o, uint64_t k, int64_t S, int64_t n3,
@@ -261,6 +274,9 @@ struct ktau_bds {
 // ---------------------------------------------------------------------------------------------
 ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n, int64_t ld_in,
                              ktau_ranked* R, cudaStream_t st);
+// perm / rank of a 16-bit handle widened to uint32, packed m x n (either pointer may be null).
+ktau_status ktau_launch_widen(const ktau_ranked* R, uint32_t* perm, uint32_t* rank,
+                              cudaStream_t st);
 
 struct ktau_merge_plan {
   int tile_q;     // tile side

@@ -20,12 +20,21 @@
 // along each thread's output diagonal); each thread then merges ITEMS outputs serially and counts
 // exactly as Algorithm 2 does.
 #include <algorithm>
+#include <type_traits>
 
 #include "ktau_impl.cuh"
 
 namespace {
 
-constexpr uint32_t kSentinel = 0xffffffffu;
+// Keys of the team buffers. 16-bit ranks (n <= 65535): 32-bit keys, (group << 16 | w) in Step 1.
+// 32-bit ranks (longer rows): 64-bit keys, (group << 32 | w) -- the 64-bit packing of the paper's
+// Sec. 6. The sentinel (all ones) sorts above every key.
+template <typename RT>
+using KeyOf = typename std::conditional<sizeof(RT) == 2, uint32_t, unsigned long long>::type;
+template <typename K>
+__device__ __forceinline__ constexpr K sentinel() { return (K)~(K)0; }
+template <typename K>
+constexpr int kGroupShift = (int)sizeof(K) * 4;
 
 template <int TEAM>
 __device__ __forceinline__ void team_sync() {
@@ -81,21 +90,21 @@ __device__ __forceinline__ int team_excl_max(int v, unsigned long long* red) {
 }
 
 // Step 1 with the merge levels stopped at runs of L >= the largest u-tie group (Sec. 3.2 Step 1
-// sorts inside u-tie groups only). The keys (group << 16 | w) are ordered by group on entry and
+// sorts inside u-tie groups only). The keys (group << shift | w) are ordered by group on entry and
 // every L-aligned run of `in` is sorted, so a tie group, at most L long, lies inside one run or
 // straddles one run boundary; in the second case its part left of the boundary and its part right
 // of it are each sorted. Each key of a straddling group moves to its final place: a left-part key
 // past the right-part keys below it (found by binary search in the next run: keys of later groups
 // are larger), a right-part key before the left-part keys above it (binary search in the previous
 // run: keys of earlier groups are smaller). Equal keys keep left before right. Writes `out`.
-template <int TEAM, int ITEMS>
-__device__ __forceinline__ void team_group_fixup(const uint32_t* in, uint32_t* out, int n, int L,
-                                                 int lane) {
+template <int TEAM, int ITEMS, typename K>
+__device__ __forceinline__ void team_group_fixup(const K* in, K* out, int n, int L, int lane) {
+  constexpr int sh = kGroupShift<K>;
   for (int k = lane; k < n; k += TEAM) {
-    const uint32_t key = in[pd<ITEMS>(k)];
+    const K key = in[pd<ITEMS>(k)];
     const int lo_b = k - k % L, hi_b = min(n, lo_b + L);
     int dst = k;
-    if (hi_b < n && (in[pd<ITEMS>(hi_b)] >> 16) == (key >> 16)) {
+    if (hi_b < n && (in[pd<ITEMS>(hi_b)] >> sh) == (key >> sh)) {
       int lo = hi_b, hi = min(n, hi_b + L);  // first key of the next run that is >= key
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -105,7 +114,7 @@ __device__ __forceinline__ void team_group_fixup(const uint32_t* in, uint32_t* o
           hi = mid;
       }
       dst = k + (lo - hi_b);
-    } else if (lo_b > 0 && (in[pd<ITEMS>(lo_b - 1)] >> 16) == (key >> 16)) {
+    } else if (lo_b > 0 && (in[pd<ITEMS>(lo_b - 1)] >> sh) == (key >> sh)) {
       int lo = lo_b - L, hi = lo_b;  // first key of the previous run that is > key
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -125,15 +134,19 @@ __device__ __forceinline__ void team_group_fixup(const uint32_t* in, uint32_t* o
 // run_cap < n (Step 1 only, without COUNT): the merge levels stop once the sorted runs reach
 // run_cap, and team_group_fixup finishes the sort inside u-tie groups no longer than run_cap.
 // Returns the buffer that holds the sorted sequence. Every thread of the team must call it.
-template <int TEAM, int ITEMS, bool COUNT>
-__device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int lane,
-                                     unsigned long long& cnt, int run_cap) {
+// K: key type (32-bit, or 64-bit for rows with 32-bit ranks, whose per-thread counts also need 64
+// bits).
+template <int TEAM, int ITEMS, bool COUNT, typename K>
+__device__ K* team_merge_sort(K* buf, K* tmp, int n, int lane, unsigned long long& cnt,
+                              int run_cap) {
+  using C = typename std::conditional<sizeof(K) == 4, unsigned, unsigned long long>::type;
   constexpr int CH = TEAM * ITEMS;
-  unsigned c = 0;
+  constexpr K kSentinel = sentinel<K>();
+  C c = 0;
   // Runs of ITEMS sorted in registers (inversions inside a run counted directly).
   for (int base = 0; base < n; base += CH) {
     const int s0 = base + lane * ITEMS;
-    uint32_t r[ITEMS];
+    K r[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) r[i] = (s0 + i < n) ? buf[pd<ITEMS>(s0 + i)] : kSentinel;
     if (COUNT) {
@@ -146,7 +159,7 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
     for (int p = 0; p < ITEMS; ++p) {
 #pragma unroll
       for (int i = p & 1; i + 1 < ITEMS; i += 2) {
-        uint32_t a = min(r[i], r[i + 1]), b = max(r[i], r[i + 1]);
+        const K a = min(r[i], r[i + 1]), b = max(r[i], r[i + 1]);
         r[i] = a;
         r[i + 1] = b;
       }
@@ -156,8 +169,8 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
       if (s0 + i < n) buf[pd<ITEMS>(s0 + i)] = r[i];
   }
   team_sync<TEAM>();
-  uint32_t* in = buf;
-  uint32_t* out = tmp;
+  K* in = buf;
+  K* out = tmp;
   int s = ITEMS;
   for (; s < n && s < run_cap; s *= 2) {
     for (int base = 0; base < n; base += CH) {
@@ -199,32 +212,32 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
         int ai = A + lo, bi = B + diag - lo;
         const int ae = A + a_len, be = B + b_len;
         const int todo = min(ITEMS, a_len + b_len - diag);
-        uint32_t va = ai < ae ? in[pd<ITEMS>(ai)] : kSentinel;
-        uint32_t vb = bi < be ? in[pd<ITEMS>(bi)] : kSentinel;
+        K va = ai < ae ? in[pd<ITEMS>(ai)] : kSentinel;
+        K vb = bi < be ? in[pd<ITEMS>(bi)] : kSentinel;
         // o is a multiple of ITEMS and, where pd pads (ITEMS 8 or 16), [o, o + ITEMS) stays
         // within one 32-element row: the outputs are consecutive words from pd(o).
-        uint32_t* op = out + pd<ITEMS>(o);
+        K* op = out + pd<ITEMS>(o);
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
           const bool take_b = vb < va;
           if (i < todo) op[i] = take_b ? vb : va;
-          if (COUNT) c += take_b ? (unsigned)(ae - ai) : 0u;  // remaining left keys are larger
+          if (COUNT) c += take_b ? (C)(ae - ai) : (C)0;  // remaining left keys are larger
           ai += take_b ? 0 : 1;
           bi += take_b ? 1 : 0;
           const bool more = take_b ? bi < be : ai < ae;
-          const uint32_t v = more ? in[pd<ITEMS>(take_b ? bi : ai)] : kSentinel;
+          const K v = more ? in[pd<ITEMS>(take_b ? bi : ai)] : kSentinel;
           va = take_b ? va : v;
           vb = take_b ? v : vb;
         }
       }
     }
     team_sync<TEAM>();
-    uint32_t* t = in;
+    K* t = in;
     in = out;
     out = t;
   }
   if (!COUNT && s < n) {
-    team_group_fixup<TEAM, ITEMS>(in, out, n, s, lane);
+    team_group_fixup<TEAM, ITEMS, K>(in, out, n, s, lane);
     team_sync<TEAM>();
     in = out;
   }
@@ -233,13 +246,14 @@ __device__ uint32_t* team_merge_sort(uint32_t* buf, uint32_t* tmp, int n, int la
 }
 
 struct MergeArgs {
-  // row side (u): permutation, sorted ranks, tie counts, factors; column side (v): ranks.
-  const uint16_t* perm;
-  const uint16_t* srank;
+  // row side (u): permutation, sorted ranks, tie counts, factors; column side (v): ranks. The
+  // rank arrays are uint16, or uint32 for rows longer than 65535 samples (the kernel's RT).
+  const void* perm;
+  const void* srank;
   const int64_t* T;
   const int32_t* maxg;   // largest tie group of each row variable
   ktau_fac fac;
-  const uint16_t* rank;  // column side
+  const void* rank;      // column side
   const int64_t* Tc;
   ktau_fac facc;
   int64_t m;             // row variables
@@ -255,21 +269,23 @@ struct MergeArgs {
   int tq;           // tile side
   int stage;        // rows of the tile staged in shared memory
   int cap;          // per-team buffer capacity (elements)
-  uint32_t* gbuf;   // long rows: the CTA team's two buffers in global scratch (2 * cap per CTA)
+  void* gbuf;       // long rows: the CTA team's two buffers in global scratch (2 * cap keys per CTA)
   unsigned long long* counter;  // dynamic schedule: next tile id (nullptr = static)
   ktau_out out;
 };
 
-// Counts for one pair. perm_u/srank_u/rank_v point at the three rows (shared or global).
-template <int TEAM, int ITEMS>
-__device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_t* srank_u,
-                                           const uint16_t* rank_v, int n, bool u_ties,
-                                           int maxg_u, uint32_t* buf, uint32_t* tmp, int lane,
-                                           unsigned long long* red, long long& nd_out,
+// Counts for one pair. perm_u/srank_u/rank_v point at the three rows (shared or global); RT is
+// the rank type and K = KeyOf<RT> the key type of the team buffers.
+template <int TEAM, int ITEMS, typename RT, typename K = KeyOf<RT>>
+__device__ __forceinline__ void count_pair(const RT* perm_u, const RT* srank_u, const RT* rank_v,
+                                           int n, bool u_ties, int maxg_u, K* buf, K* tmp,
+                                           int lane, unsigned long long* red, long long& nd_out,
                                            long long& n3_out) {
+  constexpr int sh = kGroupShift<K>;
+  constexpr K kLow = ((K)1 << sh) - 1;  // the w part of a packed key
   for (int k = lane; k < n; k += TEAM) {
-    const uint32_t w = rank_v[perm_u[k]];
-    buf[pd<ITEMS>(k)] = u_ties ? (((uint32_t)srank_u[k] << 16) | w) : w;
+    const K w = rank_v[perm_u[k]];
+    buf[pd<ITEMS>(k)] = u_ties ? (((K)srank_u[k] << sh) | w) : w;
   }
   team_sync<TEAM>();
   unsigned long long nd = 0, n3 = 0;
@@ -278,8 +294,8 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
     // Step 1 sorts inside u-tie groups: with groups short next to n, the merge levels stop at
     // runs as long as the largest group and a fix-up pass finishes the groups across runs.
     const int cap = 4 * maxg_u <= n ? maxg_u : n;
-    uint32_t* sorted = team_merge_sort<TEAM, ITEMS, false>(buf, tmp, n, lane, unused, cap);
-    uint32_t* other = sorted == buf ? tmp : buf;
+    K* sorted = team_merge_sort<TEAM, ITEMS, false>(buf, tmp, n, lane, unused, cap);
+    K* other = sorted == buf ? tmp : buf;
     // Step 2: joint ties. In the sorted keys, position k has (k - first index of its run of
     // equal keys) earlier equal keys.
     if (TEAM > 32) {
@@ -292,15 +308,15 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
         if (k == 0 || sorted[pd<ITEMS>(k)] != sorted[pd<ITEMS>(k - 1)]) last = k;
       int first = team_excl_max<TEAM>(last, red);
       for (int k = kb; k < ke; ++k) {
-        const uint32_t key = sorted[pd<ITEMS>(k)];
+        const K key = sorted[pd<ITEMS>(k)];
         if (k == 0 || key != sorted[pd<ITEMS>(k - 1)]) first = k;
         n3 += (unsigned long long)(k - first);
-        other[pd<ITEMS>(k)] = key & 0xffffu;
+        other[pd<ITEMS>(k)] = key & kLow;
       }
     } else {
       // Short vectors, few ties: the first index of a tied key by binary search.
       for (int k = lane; k < n; k += TEAM) {
-        const uint32_t key = sorted[pd<ITEMS>(k)];
+        const K key = sorted[pd<ITEMS>(k)];
         if (k > 0 && sorted[pd<ITEMS>(k - 1)] == key) {
           int lo = 0, hi = k;
           while (lo < hi) {
@@ -312,7 +328,7 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
           }
           n3 += (unsigned long long)(k - lo);
         }
-        other[pd<ITEMS>(k)] = key & 0xffffu;
+        other[pd<ITEMS>(k)] = key & kLow;
       }
     }
     team_sync<TEAM>();
@@ -325,10 +341,11 @@ __device__ __forceinline__ void count_pair(const uint16_t* perm_u, const uint16_
   team_sync<TEAM>();
 }
 
-__device__ __forceinline__ void copy_rows(uint16_t* dst, const uint16_t* src, int64_t first_row,
-                                          int rows, int64_t m, int64_t ld) {
-  // rows x ld uint16, ld a multiple of 16 (32-byte rows): 16-byte vector copies.
-  const int vec_per_row = (int)(ld / 8);
+template <typename RT>
+__device__ __forceinline__ void copy_rows(RT* dst, const RT* src, int64_t first_row, int rows,
+                                          int64_t m, int64_t ld) {
+  // rows x ld ranks, ld a multiple of 16 (rows of 32 or 64 bytes): 16-byte vector copies.
+  const int vec_per_row = (int)(ld * (int64_t)sizeof(RT) / 16);
   const int total = rows * vec_per_row;
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
     const int r = i / vec_per_row, c = i % vec_per_row;
@@ -341,8 +358,10 @@ __device__ __forceinline__ void copy_rows(uint16_t* dst, const uint16_t* src, in
 
 // GBUF: the team buffers are in global scratch (long rows); otherwise they are carved from
 // shared memory, a pointer the compiler can see is shared (shared-memory loads and stores).
-template <int TEAM, int ITEMS, bool GBUF>
+// RT: rank type (uint16_t, or uint32_t for rows longer than 65535 samples).
+template <int TEAM, int ITEMS, bool GBUF, typename RT>
 __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
+  using K = KeyOf<RT>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long red[8];
   __shared__ long long next_tile;
@@ -350,13 +369,16 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   const int tq = a.tq;
   const int64_t ld = a.ld;
-  uint16_t* s_perm = reinterpret_cast<uint16_t*>(smem);
-  uint16_t* s_srank = s_perm + (a.stage ? (int64_t)tq * ld : 0);
-  uint16_t* s_rank = s_srank + (a.stage ? (int64_t)tq * ld : 0);
-  uint32_t* tbuf = GBUF ? a.gbuf + (size_t)blockIdx.x * 2 * a.cap
-                       : reinterpret_cast<uint32_t*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
-                             (size_t)team * 2 * a.cap;
-  uint32_t* tbuf2 = tbuf + a.cap;
+  const RT* g_perm = static_cast<const RT*>(a.perm);
+  const RT* g_srank = static_cast<const RT*>(a.srank);
+  const RT* g_rank = static_cast<const RT*>(a.rank);
+  RT* s_perm = reinterpret_cast<RT*>(smem);
+  RT* s_srank = s_perm + (a.stage ? (int64_t)tq * ld : 0);
+  RT* s_rank = s_srank + (a.stage ? (int64_t)tq * ld : 0);
+  K* tbuf = GBUF ? static_cast<K*>(a.gbuf) + (size_t)blockIdx.x * 2 * a.cap
+                 : reinterpret_cast<K*>(s_rank + (a.stage ? (int64_t)tq * ld : 0)) +
+                       (size_t)team * 2 * a.cap;
+  K* tbuf2 = tbuf + a.cap;
   const int n = (int)a.n;
   const int64_t n0 = a.n * (a.n - 1) / 2;
 
@@ -379,9 +401,9 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
     const int64_t y0 = yq * tq, x0 = xq * tq;
     if (a.stage) {
       __syncthreads();
-      copy_rows(s_perm, a.perm, y0, tq, a.m, ld);
-      copy_rows(s_srank, a.srank, y0, tq, a.m, ld);
-      copy_rows(s_rank, a.rank, x0, tq, a.mc, ld);
+      copy_rows<RT>(s_perm, g_perm, y0, tq, a.m, ld);
+      copy_rows<RT>(s_srank, g_srank, y0, tq, a.m, ld);
+      copy_rows<RT>(s_rank, g_rank, x0, tq, a.mc, ld);
       __syncthreads();
     }
     for (int e = team; e < tq * tq; e += nteams) {
@@ -396,12 +418,13 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
         if (p < a.p_begin || p >= a.p_end) continue;
         k = p - a.p_begin;
       }
-      const uint16_t* pu = a.stage ? s_perm + (y - y0) * ld : a.perm + y * ld;
-      const uint16_t* su = a.stage ? s_srank + (y - y0) * ld : a.srank + y * ld;
-      const uint16_t* rv = a.stage ? s_rank + (x - x0) * ld : a.rank + x * ld;
+      const RT* pu = a.stage ? s_perm + (y - y0) * ld : g_perm + y * ld;
+      const RT* su = a.stage ? s_srank + (y - y0) * ld : g_srank + y * ld;
+      const RT* rv = a.stage ? s_rank + (x - x0) * ld : g_rank + x * ld;
       const int64_t Tu = a.T[y], Tv = a.Tc[x];
       long long nd, n3;
-      count_pair<TEAM, ITEMS>(pu, su, rv, n, Tu > 0, a.maxg[y], tbuf, tbuf2, lane, red, nd, n3);
+      count_pair<TEAM, ITEMS, RT>(pu, su, rv, n, Tu > 0, a.maxg[y], tbuf, tbuf2, lane, red, nd,
+                                  n3);
       if (lane == 0) {
         const int64_t S = n0 - Tu - Tv + n3 - 2 * nd;
         if (a.out.tau64)
@@ -423,10 +446,10 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
   }
 }
 
-template <int TEAM, int ITEMS, bool GBUF = false>
+template <int TEAM, int ITEMS, bool GBUF = false, typename RT = uint16_t>
 ktau_status launch_one(const MergeArgs& args, int threads, size_t smem, int ctas_per_sm,
                        int64_t tiles, cudaStream_t st, int64_t max_grid = 0) {
-  auto kern = merge_pairs_kernel<TEAM, ITEMS, GBUF>;
+  auto kern = merge_pairs_kernel<TEAM, ITEMS, GBUF, RT>;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   KTAU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
@@ -568,13 +591,14 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
   }
   const int64_t tiles = tile_hi - tile_lo;
 
+  if (R->wide != C->wide) return ktau_fail(KTAU_EINVAL, "rank widths of the two sides differ");
   MergeArgs a;
-  a.perm = R->perm;
-  a.srank = R->srank;
+  a.perm = R->wide ? (const void*)R->perm32 : (const void*)R->perm;
+  a.srank = R->wide ? (const void*)R->srank32 : (const void*)R->srank;
   a.T = R->T;
   a.maxg = R->maxg;
   a.fac = ktau_fac{R->rs64, R->rsff, R->T};
-  a.rank = C->rank;
+  a.rank = C->wide ? (const void*)C->rank32 : (const void*)C->rank;
   a.Tc = C->T;
   a.facc = ktau_fac{C->rs64, C->rsff, C->T};
   a.m = m;
@@ -602,10 +626,15 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
   }
 
   const bool cta_team = plan.mapping == 2;
+  if (R->wide && !cta_team)
+    return ktau_fail(KTAU_EINVAL, "n=%lld > %d: the merge path takes one CTA per pair (mapping 2)",
+                     (long long)n, KTAU_NARROW_MAX_N);
   const int items = cta_team ? (n > 2048 ? 16 : 8) : (n <= 256 ? (int)((n + 31) / 32) : 8);
   a.cap = (int)((n + (n >> 5) + 1 + 3) & ~3LL);  // pd<ITEMS>(n) + 1, rounded
   a.gbuf = nullptr;
-  const size_t team_bytes = (size_t)2 * a.cap * sizeof(uint32_t);
+  // keys of 4 bytes (16-bit ranks) or 8 bytes (32-bit ranks, the (group << 32 | w) packing)
+  const size_t key_bytes = R->wide ? sizeof(unsigned long long) : sizeof(uint32_t);
+  const size_t team_bytes = (size_t)2 * a.cap * key_bytes;
   // Stage the tile's rows in shared memory when they are small next to the per-pair work.
   const size_t stage_bytes = (size_t)3 * tq * R->ld * sizeof(uint16_t);
   a.stage = (!cta_team && stage_bytes <= 64 * 1024) ? 1 : 0;
@@ -631,8 +660,9 @@ static ktau_status launch_merge_impl(const ktau_ranked* R, const ktau_ranked* C,
     const size_t gbytes = (size_t)grid * team_bytes;
     void* g = nullptr;
     if (ktau_dmalloc(&g, gbytes) != KTAU_OK) return KTAU_ENOMEM;
-    a.gbuf = (uint32_t*)g;
-    ktau_status s = launch_one<256, 16, true>(a, threads, 0, cps, tiles, st, grid);
+    a.gbuf = g;
+    ktau_status s = R->wide ? launch_one<256, 16, true, uint32_t>(a, threads, 0, cps, tiles, st, grid)
+                            : launch_one<256, 16, true>(a, threads, 0, cps, tiles, st, grid);
     const cudaError_t e = cudaStreamSynchronize(st);
     ktau_dfree(g, gbytes);
     if (s == KTAU_OK && e != cudaSuccess) s = ktau_cuda_fail(e, "cudaStreamSynchronize");

@@ -281,6 +281,10 @@ ktau_status ktau_query_validate(const ktau_ranked* db, const ktau_ranked* querie
                                 int32_t k, int32_t* topk_idx, double* topk_tau,
                                 const ktau_options* opt) {
   if (!db || !queries) return ktau_fail(KTAU_EINVAL, "handle is NULL");
+  // The exact top-k compares S^2 / D_v in 64- and 128-bit integers, which holds n_0^2 for
+  // n <= 65535 only.
+  if (db->n > KTAU_NARROW_MAX_N)
+    return ktau_fail(KTAU_ETOOLARGE, "the query form takes n <= %d", KTAU_NARROW_MAX_N);
   if (db->n != queries->n)
     return ktau_fail(KTAU_EINVAL, "queries have n=%lld samples, database n=%lld",
                      (long long)queries->n, (long long)db->n);

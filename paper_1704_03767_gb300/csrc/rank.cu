@@ -74,12 +74,13 @@ __device__ void cta_sort_keys(unsigned long long* sm_keys, int np2) {
 // Outputs of one variable from its keys sorted ascending in keys[0, n) (shared or global memory):
 // group heads and dense ranks by a block-wide scan, pi_u, r_u, ranks in sorted order, T_u, the
 // number of distinct values, the largest tie group and the denominator factors. first[] and
-// dense[] are n-entry work arrays (shared or global). nan_seen: this thread's NaN flag.
-__device__ void rank_finish(const unsigned long long* keys, uint16_t* sm_first, uint16_t* sm_dense,
-                            int n, int64_t ld, int64_t row, uint16_t* perm, uint16_t* rank,
-                            uint16_t* srank, int64_t* T, int32_t* ndist, int32_t* maxg,
-                            double* rs64, float2* rsff, ktau_stats* stats,
-                            unsigned int nan_seen) {
+// dense[] are n-entry work arrays (shared or global). nan_seen: this thread's NaN flag. RT is the
+// rank type: uint16_t, or uint32_t for rows longer than 65535 samples.
+template <typename RT>
+__device__ void rank_finish(const unsigned long long* keys, RT* sm_first, RT* sm_dense, int n,
+                            int64_t ld, int64_t row, RT* perm, RT* rank, RT* srank, int64_t* T,
+                            int32_t* ndist, int32_t* maxg, double* rs64, float2* rsff,
+                            ktau_stats* stats, unsigned int nan_seen) {
   __shared__ int warp_tot[32];
   __shared__ unsigned long long red_T[32];
   __shared__ int red_g[32];
@@ -115,32 +116,33 @@ __device__ void rank_finish(const unsigned long long* keys, uint16_t* sm_first, 
   for (int k = beg; k < end; ++k) {
     bool head = (k == 0) || ((sm_keys[k] >> 32) != (sm_keys[k - 1] >> 32));
     run += head;
-    sm_dense[k] = (uint16_t)(run - 1);
-    if (head) sm_first[run - 1] = (uint16_t)k;
+    sm_dense[k] = (RT)(run - 1);
+    if (head) sm_first[run - 1] = (RT)k;
   }
   __syncthreads();
 
   // Outputs and tie statistics: position k has k - first(group) earlier equal values, so
   // the sum over k is the number of tied pairs, sum t(t-1)/2.
-  uint16_t* prow = perm + row * ld;
-  uint16_t* rrow = rank + row * ld;
-  uint16_t* srow = srank + row * ld;
+  RT* prow = perm + row * ld;
+  RT* rrow = rank + row * ld;
+  RT* srow = srank + row * ld;
+  constexpr RT kPad = (RT)~(RT)0;
   unsigned long long tsum = 0;
   int gmax = 0;
   for (int k = tid; k < (int)ld; k += nt) {
     if (k < n) {
       int idx = (int)(sm_keys[k] & 0xffffffffu);
-      int d = sm_dense[k];
-      int before = k - sm_first[d];
-      prow[k] = (uint16_t)idx;
-      srow[k] = (uint16_t)d;
-      rrow[idx] = (uint16_t)d;
+      int d = (int)sm_dense[k];
+      int before = k - (int)sm_first[d];
+      prow[k] = (RT)idx;
+      srow[k] = (RT)d;
+      rrow[idx] = (RT)d;
       tsum += (unsigned long long)before;
       gmax = max(gmax, before + 1);
     } else {
-      prow[k] = 0xffff;
-      srow[k] = 0xffff;
-      rrow[k] = 0xffff;
+      prow[k] = kPad;
+      srow[k] = kPad;
+      rrow[k] = kPad;
     }
   }
   for (int d = 16; d > 0; d >>= 1) {
@@ -168,7 +170,7 @@ __device__ void rank_finish(const unsigned long long* keys, uint16_t* sm_first, 
     const float hi = __double2float_rn(r);
     rs64[row] = r;
     rsff[row] = make_float2(hi, D > 0 ? __double2float_rn(r - (double)hi) : hi);
-    ndist[row] = sm_dense[n - 1] + 1;
+    ndist[row] = (int32_t)sm_dense[n - 1] + 1;
     maxg[row] = g;
     atomicAdd(&stats->T_sum, t);
     atomicMax(&stats->T_max, t);
@@ -190,8 +192,8 @@ __device__ void rank_row(const void* __restrict__ values, int64_t off, int n, in
     sm_keys[i] = i < n ? load_key<DT>(values, off, i, &nan_seen) : ~0ull;
   __syncthreads();
   cta_sort_keys(sm_keys, np2);
-  rank_finish(sm_keys, sm_first, sm_dense, n, ld, row, perm, rank, srank, T, ndist, maxg, rs64,
-              rsff, stats, nan_seen);
+  rank_finish<uint16_t>(sm_keys, sm_first, sm_dense, n, ld, row, perm, rank, srank, T, ndist,
+                        maxg, rs64, rsff, stats, nan_seen);
 }
 
 // Short rows (n <= 256): one warp per variable, EPL = np2/32 keys per lane in registers, blocked
@@ -533,11 +535,14 @@ __global__ void __launch_bounds__(512) rank_kernel(const void* __restrict__ valu
 // kernels over global scratch: sort keys of every element (long_keys_kernel), chunks of
 // KTAU_RANK_CHUNK keys sorted in shared memory (long_chunk_kernel), the sorted chunks merged level
 // by level (long_merge_kernel, one launch per level), and the outputs of each variable
-// (long_finish_kernel). Scratch per variable: two key arrays of np2 and two uint16 work arrays.
+// (long_finish_kernel). Scratch per variable: two key arrays of np2 and two work arrays of the
+// rank type (uint16, or uint32 above 65535 samples). A pass holds at most kLongRows variables and
+// at most kLongBudget bytes of scratch (at least one variable).
 constexpr int kLongRows = 256;
+constexpr size_t kLongBudget = (size_t)1 << 30;
 constexpr int LONG_THREADS = 512;
-__host__ __device__ inline size_t long_rank_scratch(int np2) {
-  return (size_t)np2 * (2 * sizeof(unsigned long long) + 2 * sizeof(uint16_t));
+__host__ __device__ inline size_t long_rank_scratch(int64_t np2, size_t rank_bytes) {
+  return (size_t)np2 * (2 * sizeof(unsigned long long) + 2 * rank_bytes);
 }
 
 template <int DT>
@@ -602,14 +607,26 @@ __global__ void __launch_bounds__(256) long_merge_kernel(const unsigned long lon
 }
 
 // Outputs of each variable of the pass from its sorted keys (one CTA per variable).
+template <typename RT>
 __global__ void __launch_bounds__(LONG_THREADS) long_finish_kernel(
-    const unsigned long long* __restrict__ keys, uint16_t* work, int n, int np2, int64_t row0,
-    int64_t ld, uint16_t* perm, uint16_t* rank, uint16_t* srank, int64_t* T, int32_t* ndist,
-    int32_t* maxg, double* rs64, float2* rsff, ktau_stats* stats) {
+    const unsigned long long* __restrict__ keys, RT* work, int n, int np2, int64_t row0,
+    int64_t ld, RT* perm, RT* rank, RT* srank, int64_t* T, int32_t* ndist, int32_t* maxg,
+    double* rs64, float2* rsff, ktau_stats* stats) {
   const int r = blockIdx.x;
-  uint16_t* first = work + (size_t)r * 2 * np2;
-  rank_finish(keys + (size_t)r * np2, first, first + np2, n, ld, row0 + r, perm, rank, srank, T,
-              ndist, maxg, rs64, rsff, stats, 0u);
+  RT* first = work + (size_t)r * 2 * np2;
+  rank_finish<RT>(keys + (size_t)r * np2, first, first + np2, n, ld, row0 + r, perm, rank, srank,
+                  T, ndist, maxg, rs64, rsff, stats, 0u);
+}
+
+// uint16 perm / rank rows widened to packed uint32 rows (one thread per element).
+__global__ void widen_kernel(const uint16_t* __restrict__ src, int64_t ld, int64_t m, int64_t n,
+                             uint32_t* __restrict__ dst) {
+  const int64_t total = m * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n;
+    dst[i] = src[r * ld + (i - r * n)];
+  }
 }
 
 // Batched form: one CTA per variable of every dataset; the dataset is found from the prefix of
@@ -693,16 +710,18 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
     // once the rank transform has run (ktau_ranked_stats).
     if (!R->block) return ktau_fail(KTAU_EINVAL, "rows longer than %d need a library handle",
                                     KTAU_RANK_CHUNK);
-    const int64_t pass = m < kLongRows ? m : kLongRows;
+    const size_t rb = R->wide ? sizeof(uint32_t) : sizeof(uint16_t);
+    int64_t pass = m < kLongRows ? m : kLongRows;
+    while (pass > 1 && (size_t)pass * long_rank_scratch(np2, rb) > kLongBudget) pass >>= 1;
     const size_t kbytes = (size_t)pass * np2 * sizeof(unsigned long long);
-    R->tmp_bytes = (size_t)pass * long_rank_scratch(np2);
+    R->tmp_bytes = (size_t)pass * long_rank_scratch(np2, rb);
     if (ktau_dmalloc(&R->tmp_block, R->tmp_bytes) != KTAU_OK) {
       R->tmp_block = nullptr;
       return KTAU_ENOMEM;
     }
     unsigned long long* ka = (unsigned long long*)R->tmp_block;
     unsigned long long* kb = (unsigned long long*)((char*)R->tmp_block + kbytes);
-    uint16_t* work = (uint16_t*)((char*)R->tmp_block + 2 * kbytes);
+    void* work = (char*)R->tmp_block + 2 * kbytes;
     const size_t smem_c = (size_t)KTAU_RANK_CHUNK * sizeof(unsigned long long);
     KTAU_CUDA(cudaFuncSetAttribute(long_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_c));
@@ -736,9 +755,14 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
       }
       {
         KTAU_TRACE("long_finish_kernel", st);
-        long_finish_kernel<<<(unsigned)rows, LONG_THREADS, 0, st>>>(
-            in, work, (int)n, np2, row0, R->ld, R->perm, R->rank, R->srank, R->T, R->ndist,
-            R->maxg, R->rs64, R->rsff, R->stats_dev);
+        if (R->wide)
+          long_finish_kernel<uint32_t><<<(unsigned)rows, LONG_THREADS, 0, st>>>(
+              in, (uint32_t*)work, (int)n, np2, row0, R->ld, R->perm32, R->rank32, R->srank32,
+              R->T, R->ndist, R->maxg, R->rs64, R->rsff, R->stats_dev);
+        else
+          long_finish_kernel<uint16_t><<<(unsigned)rows, LONG_THREADS, 0, st>>>(
+              in, (uint16_t*)work, (int)n, np2, row0, R->ld, R->perm, R->rank, R->srank, R->T,
+              R->ndist, R->maxg, R->rs64, R->rsff, R->stats_dev);
       }
       KTAU_CUDA(cudaGetLastError());
     }
@@ -754,5 +778,23 @@ ktau_status ktau_launch_rank(const void* values, int dtype, int64_t m, int64_t n
                                             R->srank, R->T, R->ndist, R->maxg, R->rs64, R->rsff,
                                             R->stats_dev);
   KTAU_CUDA(cudaGetLastError());
+  return KTAU_OK;
+}
+
+ktau_status ktau_launch_widen(const ktau_ranked* R, uint32_t* perm, uint32_t* rank,
+                              cudaStream_t st) {
+  const int64_t total = R->m * R->n;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8LL * ktau_sm_count());
+  if (total == 0) return KTAU_OK;
+  if (perm) {
+    KTAU_TRACE("widen_kernel", st);
+    widen_kernel<<<blocks, 256, 0, st>>>(R->perm, R->ld, R->m, R->n, perm);
+    KTAU_CUDA(cudaGetLastError());
+  }
+  if (rank) {
+    KTAU_TRACE("widen_kernel", st);
+    widen_kernel<<<blocks, 256, 0, st>>>(R->rank, R->ld, R->m, R->n, rank);
+    KTAU_CUDA(cudaGetLastError());
+  }
   return KTAU_OK;
 }

@@ -43,7 +43,7 @@ def test_every_declared_symbol_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.ktau_abi_version() == 1
+    assert lib.ktau_abi_version() == 2
     assert lib.ktau_status_string(0) == b"KTAU_OK"
     assert lib.ktau_status_string(2) == b"KTAU_ENAN"
 
@@ -59,15 +59,16 @@ def test_argument_validation_without_gpu(lib):
     assert lib.ktau_rank_prepare(fake, 0, 0, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare(fake, 0, 10, 1, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare(fake, 0, 10, 10, 9, None, ctypes.byref(h)) == 1
-    # n beyond the 16-bit rank storage (KTAU_MAX_N = 65535)
-    assert lib.ktau_rank_prepare(fake, 0, 10, 65536, 65536, None, ctypes.byref(h)) == 3
+    # n beyond KTAU_MAX_N = 4194304 (rows above 65535 samples keep 32-bit ranks)
+    big = 4194305
+    assert lib.ktau_rank_prepare(fake, 0, 10, big, big, None, ctypes.byref(h)) == 3
     assert b"KTAU_MAX_N" in lib.ktau_last_error()
     assert h.value is None
     # the asynchronous form validates the same way before any device work
     assert lib.ktau_rank_prepare_async(None, 0, 10, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare_async(fake, 7, 10, 10, 10, None, ctypes.byref(h)) == 1
     assert lib.ktau_rank_prepare_async(fake, 0, 10, 10, 9, None, ctypes.byref(h)) == 1
-    assert lib.ktau_rank_prepare_async(fake, 0, 10, 65536, 65536, None, ctypes.byref(h)) == 3
+    assert lib.ktau_rank_prepare_async(fake, 0, 10, big, big, None, ctypes.byref(h)) == 3
     assert h.value is None
     # trace filter: host state only
     assert lib.ktau_trace_filter(b"contract_kernel") == 0
