@@ -9,10 +9,13 @@
 //   (which differ by at least 1 / (D_v D_v') >= 1 / n_0^2) get distinct keys, so equal keys are
 //   exact ties (broken by the smaller row index); otherwise equal keys at the selection boundary
 //   are ordered by exact 128-bit cross-multiplication S_a^2 D_b vs S_b^2 D_a.
-//   A radix select over the 64-bit keys (8 passes of 8 bits, one CTA per query) finds the k-th
-//   largest key, the selected rows are collected in shared memory and sorted (bitonic) with the
-//   exact comparator, and tau is formed by the shared epilogue (bit-identical to the pair output).
+//   A radix select over the 64-bit keys (8 passes of 8 bits over keys cached in shared memory)
+//   finds the k-th largest key of a chunk of up to 4096 rows, one CTA per (query, chunk); each
+//   chunk's top-k rows become the candidates of the next pass, until one CTA per query selects
+//   among all of them. The selected rows are sorted (bitonic) with the exact comparator, and tau
+//   is formed by the shared epilogue (bit-identical to the pair output).
 #include <algorithm>
+#include <mutex>
 
 #include "ktau_impl.cuh"
 #include "signgemm.cuh"
@@ -72,66 +75,125 @@ __device__ __forceinline__ bool cand_before(const Cand& x, const Cand& y) {
   return x.j < y.j;
 }
 
-__global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a) {
+// One CTA selects among at most TK_CHUNK items of one query: items [c * TK_CHUNK, ...) of the
+// query's list, where item i is database row i (LIST false: the whole database) or row
+// in[q * N + i] (LIST: the candidates of an earlier pass, in increasing row order). It finds the
+// top kk = min(k, count) items under the exact order; FINAL writes them in that order with tau,
+// otherwise their rows, in increasing row order, go to out[q * nout + c * k ..]. The global top-k
+// is inside the union of every chunk's top-k, so passes of chunks reduce the candidates until one
+// CTA per query holds them all.
+constexpr int TK_CHUNK = 4096;
+
+template <bool LIST, bool FINAL>
+__global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a,
+                                                          const int32_t* __restrict__ in,
+                                                          int64_t N, int32_t* __restrict__ out,
+                                                          int64_t nout) {
+  extern __shared__ unsigned long long skey[];  // [TK_CHUNK] keys of this CTA's items
   __shared__ unsigned int hist[256];
   __shared__ unsigned long long s_prefix;
   __shared__ int s_remaining, s_cnt, s_eqcnt, s_wsum[TK_THREADS / 32];
   __shared__ Cand sel[TK_MAXK];
   __shared__ Cand eq[TK_EQCAP];
   const int64_t q = blockIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.y * TK_CHUNK;
+  const int cnt = (int)min((int64_t)TK_CHUNK, N - i0);
+  const int kk = min(a.k, cnt);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool qnan = a.Tq[q] == a.n0;  // constant query variable: every tau is NaN
+  auto row_of = [&](int i) -> int64_t {
+    return LIST ? (int64_t)in[q * N + i0 + i] : i0 + i;
+  };
+  // Keys once (the radix passes read them from shared memory).
+  for (int i = tid; i < cnt; i += blockDim.x) {
+    const int64_t j = row_of(i);
+    skey[i] = topk_key(a, load_S(a, q, j), a.n0 - a.Tdb[j], qnan);
+  }
   if (tid == 0) {
     s_prefix = 0ull;
-    s_remaining = a.k;
+    s_remaining = kk;
     s_cnt = 0;
     s_eqcnt = 0;
   }
   __syncthreads();
-  // Radix select of the k-th largest key, most significant digit first.
+  // Radix select of the kk-th largest key, most significant digit first.
   for (int pass = 7; pass >= 0; --pass) {
     for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     const unsigned long long prefix = s_prefix;
     const unsigned long long hmask = pass == 7 ? 0ull : (~0ull << (8 * (pass + 1)));
-    for (int64_t j = tid; j < a.m_db; j += blockDim.x) {
-      const unsigned long long key = topk_key(a, load_S(a, q, j), a.n0 - a.Tdb[j], qnan);
-      if ((key & hmask) == prefix) atomicAdd(&hist[(key >> (8 * pass)) & 255u], 1u);
+    if (pass == 7) {
+      // The top digit is shared by most keys: lanes with the same digit add once.
+      for (int base = 0; base < cnt; base += blockDim.x) {
+        const int i = base + tid;
+        const unsigned bin = i < cnt ? (unsigned)(skey[i] >> 56) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (i < cnt && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+      }
+    } else {
+      for (int i = tid; i < cnt; i += blockDim.x) {
+        const unsigned long long key = skey[i];
+        if ((key & hmask) == prefix) atomicAdd(&hist[(key >> (8 * pass)) & 255u], 1u);
+      }
     }
     __syncthreads();
-    if (tid == 0) {
-      int rem = s_remaining;
-      int d = 255;
-      for (; d > 0; --d) {
-        if ((int)hist[d] >= rem) break;
-        rem -= (int)hist[d];
+    if (warp == 0) {
+      // The digit d: the largest with (count of digits >= d) >= remaining. Lane l holds digits
+      // 8l .. 8l + 7; a suffix sum over the lanes finds the lane that holds d.
+      const int rem0 = s_remaining;
+      unsigned c[8];
+      unsigned tot = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        c[e] = hist[8 * lane + e];
+        tot += c[e];
       }
-      s_remaining = rem;
-      s_prefix = prefix | ((unsigned long long)d << (8 * pass));
+      unsigned suf = tot;  // digits of this lane and every higher one
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned v = __shfl_down_sync(0xffffffffu, suf, d);
+        if (lane + d < 32) suf += v;
+      }
+      const unsigned above = suf - tot;
+      if ((int)above < rem0 && ((int)suf >= rem0 || lane == 0)) {
+        int rem = rem0 - (int)above;
+        int e = 7;
+        for (; e > 0; --e) {
+          if ((int)c[e] >= rem) break;
+          rem -= (int)c[e];
+        }
+        s_remaining = rem;
+        s_prefix = prefix | ((unsigned long long)(8 * lane + e) << (8 * pass));
+      }
     }
     __syncthreads();
   }
   const unsigned long long t = s_prefix;
-  const int need_eq = s_remaining;  // how many rows with key == t are selected
-  // Rows with key > t are all selected; rows with key == t: the lowest indices when keys are
-  // exact, otherwise all of them go through the exact comparator.
+  const int need_eq = s_remaining;  // how many items with key == t are selected
+  // Items with key > t are all selected; items with key == t: the lowest rows when keys are
+  // exact (items are in increasing row order), otherwise all of them go through the exact
+  // comparator.
   int eq_before = 0;
-  for (int64_t base = 0; base < a.m_db; base += blockDim.x) {
-    const int64_t j = base + tid;
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int i = base + tid;
     long long S = 0, Dv = 0;
+    int64_t j = 0;
     unsigned long long key = 0;
-    if (j < a.m_db) {
+    if (i < cnt) {
+      key = skey[i];
+      j = row_of(i);
+    }
+    const bool gt = i < cnt && key > t;
+    const bool eqf = i < cnt && key == t;
+    if (gt || eqf) {
       S = load_S(a, q, j);
       Dv = a.n0 - a.Tdb[j];
-      key = topk_key(a, S, Dv, qnan);
     }
-    const bool gt = j < a.m_db && key > t;
-    const bool eqf = j < a.m_db && key == t;
     if (gt) {
       const int pos = atomicAdd(&s_cnt, 1);
       sel[pos] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
     }
-    // ordered rank among equal keys (block-wide exclusive scan in index order)
+    // ordered rank among equal keys (block-wide exclusive scan in item order)
     int incl = eqf ? 1 : 0;
     for (int d = 1; d < 32; d <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, d);
@@ -144,7 +206,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a) {
     const int rank_eq = before + incl - (eqf ? 1 : 0);
     if (eqf) {
       if (a.injective) {
-        if (rank_eq < need_eq) sel[a.k - need_eq + rank_eq] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
+        if (rank_eq < need_eq) sel[kk - need_eq + rank_eq] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
       } else if (rank_eq < TK_EQCAP) {
         eq[rank_eq] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
       }
@@ -162,12 +224,12 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a) {
     while (p2 < g) p2 <<= 1;
     for (int i = g + tid; i < p2 && i < TK_EQCAP; i += blockDim.x) eq[i] = Cand{0, 0, 0x7fffffff};
     __syncthreads();
-    for (int kk = 2; kk <= p2; kk <<= 1)
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+    for (int k2 = 2; k2 <= p2; k2 <<= 1)
+      for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
         for (int i = tid; i < p2; i += blockDim.x) {
           const int l = i ^ jj;
           if (l > i) {
-            const bool up = (i & kk) == 0;
+            const bool up = (i & k2) == 0;
             const bool sw = up ? cand_before(eq[l], eq[i]) : cand_before(eq[i], eq[l]);
             if (sw) {
               const Cand tmp = eq[i];
@@ -178,21 +240,22 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a) {
         }
         __syncthreads();
       }
-    for (int i = tid; i < need_eq; i += blockDim.x) sel[a.k - need_eq + i] = eq[i];
+    for (int i = tid; i < need_eq; i += blockDim.x) sel[kk - need_eq + i] = eq[i];
   }
   __syncthreads();
-  // Final exact order of the k selected rows.
+  // Order of the kk selected items: the exact order (final pass) or increasing row.
   int p2 = 1;
-  while (p2 < a.k) p2 <<= 1;
-  for (int i = a.k + tid; i < p2; i += blockDim.x) sel[i] = Cand{0, 0, 0x7fffffff};
+  while (p2 < kk) p2 <<= 1;
+  for (int i = kk + tid; i < p2; i += blockDim.x) sel[i] = Cand{0, 0, 0x7fffffff};
   __syncthreads();
-  for (int kk = 2; kk <= p2; kk <<= 1)
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+  for (int k2 = 2; k2 <= p2; k2 <<= 1)
+    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
       for (int i = tid; i < p2; i += blockDim.x) {
         const int l = i ^ jj;
         if (l > i) {
-          const bool up = (i & kk) == 0;
-          const bool sw = up ? cand_before(sel[l], sel[i]) : cand_before(sel[i], sel[l]);
+          const bool up = (i & k2) == 0;
+          const bool sw = FINAL ? (up ? cand_before(sel[l], sel[i]) : cand_before(sel[i], sel[l]))
+                                : (up ? sel[l].j < sel[i].j : sel[i].j < sel[l].j);
           if (sw) {
             const Cand tmp = sel[i];
             sel[i] = sel[l];
@@ -202,10 +265,15 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a) {
       }
       __syncthreads();
     }
-  for (int i = tid; i < a.k; i += blockDim.x) {
-    const Cand c = sel[i];
-    a.idx_out[q * a.k + i] = c.j;
-    a.tau_out[q * a.k + i] = ktau_tau64(c.S, a.rs_q[q], a.rs_db[c.j]);
+  if (FINAL) {
+    for (int i = tid; i < kk; i += blockDim.x) {
+      const Cand c = sel[i];
+      a.idx_out[q * a.k + i] = c.j;
+      a.tau_out[q * a.k + i] = ktau_tau64(c.S, a.rs_q[q], a.rs_db[c.j]);
+    }
+  } else {
+    for (int i = tid; i < kk; i += blockDim.x)
+      out[q * nout + (int64_t)blockIdx.y * a.k + i] = sel[i].j;
   }
 }
 
@@ -271,10 +339,82 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
   unsigned int* st_ptr = nullptr;
   KTAU_CUDA(cudaGetSymbolAddress((void**)&st_ptr, g_topk_status));
   a.status = st_ptr;
-  KTAU_TRACE("topk_kernel", st);
-  topk_kernel<<<(unsigned)queries->m, TK_THREADS, 0, st>>>(a);
-  KTAU_CUDA(cudaGetLastError());
-  return KTAU_OK;
+  // Passes of chunks of TK_CHUNK items, one CTA per (query, chunk), each keeping its chunk's
+  // top-k, until one chunk per query holds every candidate; then the final pass. Candidate lists
+  // live in stream-ordered allocations (no synchronisation, safe across streams).
+  const size_t dyn = (size_t)TK_CHUNK * sizeof(unsigned long long);
+  const int64_t b = queries->m;
+  if (b > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "too many queries in one call");
+  {
+    // the kernels' shared-memory limit, once per device
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    KTAU_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return ktau_fail(KTAU_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+      KTAU_CUDA(cudaFuncSetAttribute(topk_kernel<false, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      KTAU_CUDA(cudaFuncSetAttribute(topk_kernel<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      KTAU_CUDA(cudaFuncSetAttribute(topk_kernel<false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      KTAU_CUDA(cudaFuncSetAttribute(topk_kernel<true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      done[dev] = true;
+    }
+  }
+  int64_t N = db->m;
+  bool list = false;
+  const int32_t* in = nullptr;
+  int32_t* buf[2] = {nullptr, nullptr};
+  ktau_status ts = KTAU_OK;
+  for (int w = 0; N > TK_CHUNK; w ^= 1) {
+    const int64_t C = (N + TK_CHUNK - 1) / TK_CHUNK;
+    const int64_t nout = (C - 1) * k + std::min<int64_t>(k, N - (C - 1) * TK_CHUNK);
+    if (C > 65535) {
+      ts = ktau_fail(KTAU_ETOOLARGE, "database too large for the top-k passes");
+      break;
+    }
+    if (!buf[w]) {
+      const cudaError_t e = cudaMallocAsync((void**)&buf[w], (size_t)b * nout * sizeof(int32_t), st);
+      if (e != cudaSuccess) {
+        buf[w] = nullptr;
+        ts = ktau_cuda_fail(e, "cudaMallocAsync(top-k candidates)");
+        break;
+      }
+    }
+    {
+      KTAU_TRACE("topk_kernel", st);
+      const dim3 grid((unsigned)b, (unsigned)C);
+      if (list)
+        topk_kernel<true, false><<<grid, TK_THREADS, dyn, st>>>(a, in, N, buf[w], nout);
+      else
+        topk_kernel<false, false><<<grid, TK_THREADS, dyn, st>>>(a, in, N, buf[w], nout);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ts = ktau_cuda_fail(e, "topk_kernel");
+      break;
+    }
+    in = buf[w];
+    N = nout;
+    list = true;
+  }
+  if (ts == KTAU_OK) {
+    KTAU_TRACE("topk_kernel", st);
+    const dim3 grid((unsigned)b, 1u);
+    if (list)
+      topk_kernel<true, true><<<grid, TK_THREADS, dyn, st>>>(a, in, N, nullptr, 0);
+    else
+      topk_kernel<false, true><<<grid, TK_THREADS, dyn, st>>>(a, in, N, nullptr, 0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) ts = ktau_cuda_fail(e, "topk_kernel");
+  }
+  for (int w = 0; w < 2; ++w)
+    if (buf[w]) cudaFreeAsync(buf[w], st);
+  return ts;
 }
 
 ktau_status ktau_query_validate(const ktau_ranked* db, const ktau_ranked* queries, int32_t count_bits,

@@ -127,3 +127,30 @@ def test_resident_database_full_size(ktau):
         assert_tau64(taus[q], ref["tau"][0])
     Rq.free()
     Rd.free()
+
+
+@pytest.mark.parametrize("k", [1, 100, 1024])
+def test_topk_across_chunks_with_duplicate_rows(ktau, k):
+    """Top-k over a database of 20000 rows in several chunks of 4096: rows repeated every 4096
+    (exactly equal |tau| in different chunks, broken by the smaller row index), a row negated,
+    k = 1024 takes two candidate passes before the final one."""
+    D = gene_expression(20000, 64, seed=3)
+    for c in range(1, 5):
+        hi = min(20000, 4096 * (c + 1))
+        D[4096 * c:hi] = D[:hi - 4096 * c]
+    D[19999] = -D[5]
+    Q = gene_expression(3, 64, seed=4)
+    Q[2] = D[5]
+    Rd = ktau.ktau_rank_prepare(torch.from_numpy(D).cuda())
+    Rq = ktau.ktau_rank_prepare(torch.from_numpy(Q).cuda())
+    b, m = 3, 20000
+    S = torch.empty((b, m), dtype=torch.int32, device="cuda")
+    idx = torch.empty((b, k), dtype=torch.int32, device="cuda")
+    tk = torch.empty((b, k), dtype=torch.float64, device="cuda")
+    ktau.ktau_query(Rd, Rq, None, S, None, 32, k, idx, tk)
+    ktau.ktau_device_status()
+    ref = oracle.query_topk(Q, D, k)
+    assert np.array_equal(idx.cpu().numpy(), ref["topk_idx"])
+    assert_tau64(tk.cpu().numpy().ravel(), ref["topk_tau"].ravel())
+    Rq.free()
+    Rd.free()
