@@ -71,7 +71,10 @@ typedef enum { KTAU_F32 = 0, KTAU_I32 = 1 } ktau_dtype;
 typedef enum {
   KTAU_PATH_AUTO = 0,      /* pick by shape and measured timings (autotuner table) */
   KTAU_PATH_MERGE = 1,     /* Knight merge-sort swap counting, Sec. 3.2 Steps 1-5 */
-  KTAU_PATH_SIGNGEMM = 2,  /* exact sign-matrix contraction on tensor cores, Sec. 3.1 Alg. 1 */
+  KTAU_PATH_SIGNGEMM = 2,  /* exact sign-matrix contraction on tensor cores, Sec. 3.1 Alg. 1;
+                              n <= 5792 (n_0 < 2^24). n_3 from the tied sample pairs' lists, or,
+                              for tie-heavy matrices and rows above 3000 samples (FP4 operands,
+                              ktau_allpairs only), from a second contraction of the magnitudes */
   KTAU_PATH_BITS = 3       /* bit-parallel dominance count: the sign form of Sec. 3.1 Alg. 1 over
                               per-sample masks of larger / smaller ranks, 32 sample pairs per
                               AND + popcount; ktau_allpairs(_host) only, n <= KTAU_BITS_MAX_N */
@@ -87,7 +90,7 @@ typedef struct {
   int32_t ctas_per_sm;  /* persistent grid = ctas_per_sm * SM count */
   int32_t operand_bits; /* contraction operands: 4 = FP4 e2m1 (the triangle's pair kernel reads
                            them with the block-scaled FP4 MMA, scale factors 1), 8 = FP8 e4m3,
-                           16 = BF16, all exact for n <= 2048; 0 = FP4 */
+                           16 = BF16, all exact for n <= 5792 (n_0 < 2^24); 0 = FP4 */
   int32_t statistic;    /* 0 = tau-b (Eq. 3, default); 1 = tau-a = (n_c - n_d) / n_0 (Sec. 2, no
                            tie correction): tau64 = S / n_0 in IEEE FP64, tau32 = S / n_0
                            correctly rounded to FP32. ktau_allpairs, ktau_allpairs_path and
@@ -230,7 +233,7 @@ ktau_status ktau_allpairs_path(const ktau_ranked* R, const ktau_options* opt, in
  * order shared by every variable), stored as packed FP4 e2m1 (library memory, m * n_0 / 2 bytes
  * with n_0 rounded up to 256 per variable). The lists of tied
  * sample pairs that n_3 needs are built by the first ktau_allpairs call that stores n_3, beside
- * its contraction. Asynchronous on `stream` (allocates on first use). EINVAL when n > 2048
+ * its contraction. Asynchronous on `stream` (allocates on first use). EINVAL when n > 5792
  * (path unsupported). */
 ktau_status ktau_prepare_signs(ktau_ranked* R, void* stream);
 
@@ -249,7 +252,7 @@ ktau_status ktau_device_status(void* stream);
  * two-sided permutation p-value of pair p is (exceed + 1) / (B + 1).
  *   S_obs  : int32 device array, the observed S of the same range (ktau_allpairs, count_bits 32)
  *   exceed : uint32 device array of p_end - p_begin counts, accumulated (the caller zeroes it)
- * Runs on the sign contraction (EINVAL when n > 2048): per permutation one relabelled copy of
+ * Runs on the sign contraction (EINVAL when n > 5792): per permutation one relabelled copy of
  * the ranks, its sign expansion and one pass of the pair contraction. Entries of perms outside
  * 0..n-1 give meaningless counts but no out-of-range access. Allocates scratch of one rank and one
  * operand matrix and returns after the work has finished on `stream`. */

@@ -424,15 +424,17 @@ ktau_status ktau_check_options(const ktau_options* opt) {
 }
 
 // Path choice for one matrix shape, from the autotuner's measurements on GB300 (ns per pair at
-// m ~ 2000): the sign contraction wins at every n <= 1024 (e.g. 0.07 vs 3.0 at n = 128, 4.0 vs
-// 39.5 at n = 1024, with 5% or 30% duplicated values), so it is the default there unless the
-// variables are so tie-heavy that the per-pair joint-tie checks (about T_u per pair) outgrow the
-// merge path's n log2 n steps.
+// m ~ 2000): the sign contraction wins at every n it takes (e.g. 0.05 vs 2.5 at n = 128, 2.7 vs
+// 50 at n = 2000, with 5% or 30% duplicated values), so it is the default there. With FP8 or BF16
+// operands a tie-heavy matrix (more than 4n tied sample pairs per variable on average) goes to
+// the merge path instead: its n_3 would come from per-pair tie checks (about T_u per pair), which
+// outgrow the merge path's n log2 n steps; FP4 operands take n_3 from the magnitude contraction.
 int ktau_choose_path(const ktau_ranked* R, const ktau_options* opt) {
   if (opt && opt->path != KTAU_PATH_AUTO) return opt->path;
   if (ktau_signgemm_supported(R->n)) {
     const double mean_T = (double)R->stats.T_sum / (double)R->m;
-    if (mean_T <= 4.0 * (double)R->n) return KTAU_PATH_SIGNGEMM;
+    if (mean_T <= 4.0 * (double)R->n || ktau_sign_obits(R->n, opt) == 4)
+      return KTAU_PATH_SIGNGEMM;
   }
   return KTAU_PATH_MERGE;
 }

@@ -153,8 +153,10 @@ static ktau_status batch_upload(ktau_batch* B, T** dst, const std::vector<T>& v)
 static int batch_path_for(const ktau_batch_desc& d, const ktau_options* opt) {
   if (d.path != KTAU_PATH_AUTO) return d.path;
   if (opt && opt->path != KTAU_PATH_AUTO) return opt->path;
-  // Crossover measured on GB300 by the autotuner: the contraction wins up to n = 1024.
-  return d.n <= KTAU_SIGNGEMM_MAX_N ? KTAU_PATH_SIGNGEMM : KTAU_PATH_MERGE;
+  // The contraction wins wherever it applies (autotuner, GB300); its batched n_3 comes from the
+  // tie-list tile kernel, which takes n <= KTAU_SIGNGEMM_TIES_MAX_N.
+  return d.n <= (d.n3 ? KTAU_SIGNGEMM_TIES_MAX_N : KTAU_SIGNGEMM_MAX_N) ? KTAU_PATH_SIGNGEMM
+                                                                        : KTAU_PATH_MERGE;
 }
 
 ktau_status ktau_check_counts(int64_t n, int count_bits);
@@ -226,9 +228,10 @@ static ktau_status batch_build_checked(const ktau_batch_desc* descs, int32_t cou
     if (d.path < 0 || d.path > 2) return ktau_fail(KTAU_EINVAL, "descriptor %d: bad path", i);
     if (d.mapping < 0 || d.mapping > 2)
       return ktau_fail(KTAU_EINVAL, "descriptor %d: bad mapping", i);
-    if (batch_path_for(d, opt) == KTAU_PATH_SIGNGEMM && d.n > KTAU_SIGNGEMM_MAX_N)
+    if (batch_path_for(d, opt) == KTAU_PATH_SIGNGEMM &&
+        d.n > (d.n3 ? KTAU_SIGNGEMM_TIES_MAX_N : KTAU_SIGNGEMM_MAX_N))
       return ktau_fail(KTAU_EINVAL, "descriptor %d: contraction path needs n <= %d", i,
-                       KTAU_SIGNGEMM_MAX_N);
+                       d.n3 ? KTAU_SIGNGEMM_TIES_MAX_N : KTAU_SIGNGEMM_MAX_N);
   }
   B->count = count;
   cudaGetDevice(&B->device);

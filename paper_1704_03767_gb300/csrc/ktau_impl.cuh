@@ -78,6 +78,14 @@ struct ktau_ranked {
   alignas(64) unsigned char tmap_mx[128];
   alignas(64) unsigned char tmap_mxb[128];
   size_t sgn_bytes;
+  // |A| operand (FP4 only, built on first use by an n_3 output of a tie-heavy matrix): the same
+  // rows with 1 where the sample pair is not tied in the variable and 0 where it is, so that
+  // |A_u| . |A_v| = n_c + n_d = n_0 - T_u - T_v + n_3 (Table 1). Tensor maps as tmap_mx/_mxb.
+  void* sgn_abs;
+  size_t sgn_abs_bytes;
+  alignas(64) unsigned char tmap_mx_abs[128];
+  alignas(64) unsigned char tmap_mxb_abs[128];
+  int abs_ready;
   // Lists of tied sample pairs for n_3 (tie_off[m+1] = prefix of T, tie_pairs[(a << 16) | b]);
   // a variable is listed when its list ends within tie_cap entries.
   int64_t* tie_off;

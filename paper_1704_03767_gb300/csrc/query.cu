@@ -306,7 +306,9 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
   ktau_ranked* D = const_cast<ktau_ranked*>(db);
   const int path = ktau_choose_path(db, opt);
   ktau_status s;
-  if (path == KTAU_PATH_SIGNGEMM && ktau_signgemm_supported(db->n)) {
+  // n_3 of the rectangular contraction comes from the tie-list tile kernel (n <= 3000).
+  if (path == KTAU_PATH_SIGNGEMM && ktau_signgemm_supported(db->n) &&
+      (!out.n3 || db->n <= KTAU_SIGNGEMM_TIES_MAX_N)) {
     s = ktau_signgemm_rect(Q, D, out, db->m, ktau_sign_obits(db->n, opt), st);
   } else {
     ktau_merge_plan plan;

@@ -119,7 +119,8 @@ __device__ __forceinline__ uint32_t prmt_sx(uint32_t a, uint32_t b, uint32_t sel
 // Operand bytes of eight signs from the flag words: bit 15 / 31 of G[t] = (b > a) for elements
 // 2t / 2t + 1, of E[t] = (b >= a). The flags become byte masks (sign-filling byte permutes), and
 // two logic ops per word give the codes: ne = gt | !ge selects the magnitude bits, !ge the sign.
-template <int OB>
+// ABS (FP4 only): the magnitudes |sign| instead, 1.0 (0x2) where the pair is not tied, else 0.
+template <int OB, bool ABS = false>
 __device__ __forceinline__ void encode_store(const uint32_t (&G)[4], const uint32_t (&E)[4],
                                              uint8_t* __restrict__ dst) {
   if (OB == 4) {
@@ -128,7 +129,8 @@ __device__ __forceinline__ void encode_store(const uint32_t (&G)[4], const uint3
     // nibble masks: element b in the high nibble of byte b, element 4 + b in the low nibble
     const uint32_t hg = (mg0 & 0xF0F0F0F0u) | (mg1 & 0x0F0F0F0Fu);
     const uint32_t he = (me0 & 0xF0F0F0F0u) | (me1 & 0x0F0F0F0Fu);
-    *reinterpret_cast<uint32_t*>(dst) = ((hg | ~he) & 0x22222222u) | (~he & 0x88888888u);
+    *reinterpret_cast<uint32_t*>(dst) =
+        ABS ? ((hg | ~he) & 0x22222222u) : (((hg | ~he) & 0x22222222u) | (~he & 0x88888888u));
   } else if (OB == 8) {
     uint32_t w[2];
 #pragma unroll
@@ -178,7 +180,7 @@ __device__ __forceinline__ void load_rank_run(const uint16_t* __restrict__ src, 
 
 // Signs of `rows` <= RR variables (ranks rank[r * ld + x]) into out[r * row_bytes + ...],
 // positions [0, K_pad). s_r: 8 * expand_copy_len(n) uint16 per variable, 16-byte aligned.
-template <int OB, int RR>
+template <int OB, int RR, bool ABS = false>
 __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, int64_t ld,
                                              int rows, int n, int K, int K_pad,
                                              uint8_t* __restrict__ out, int64_t row_bytes,
@@ -245,7 +247,7 @@ __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, 
           G[t] = B[t] - A[t] + 0x7FFF7FFFu;
           E[t] = B[t] - A[t] + 0x80008000u;
         }
-        encode_store<OB>(G, E, dst + r * row_bytes);
+        encode_store<OB, ABS>(G, E, dst + r * row_bytes);
       }
       continue;
     }
@@ -274,7 +276,7 @@ __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, 
                                b4.z - a4.z + 0x7FFF7FFFu, b4.w - a4.w + 0x7FFF7FFFu};
         const uint32_t E[4] = {b4.x - a4.x + 0x80008000u, b4.y - a4.y + 0x80008000u,
                                b4.z - a4.z + 0x80008000u, b4.w - a4.w + 0x80008000u};
-        encode_store<OB>(G, E, dst + r * row_bytes);
+        encode_store<OB, ABS>(G, E, dst + r * row_bytes);
       }
     } else {
       const int offY = ((s + 1) & 7) * LS + ((s + 1) & ~7);
@@ -298,13 +300,13 @@ __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, 
           G[t] = B[t] - A[t] + 0x7FFF7FFFu;
           E[t] = B[t] - A[t] + 0x80008000u;
         }
-        encode_store<OB>(G, E, dst + r * row_bytes);
+        encode_store<OB, ABS>(G, E, dst + r * row_bytes);
       }
     }
   }
 }
 
-template <int OB, int RR>
+template <int OB, int RR, bool ABS = false>
 __global__ void __launch_bounds__(kExpandThreads) sign_expand_kernel(const uint16_t* __restrict__ rank,
                                                           int64_t ld, int n, int64_t m, int K,
                                                           int K_pad, uint8_t* __restrict__ out) {
@@ -312,8 +314,8 @@ __global__ void __launch_bounds__(kExpandThreads) sign_expand_kernel(const uint1
   const int64_t row0 = (int64_t)blockIdx.x * RR;
   const int rows = (int)min((int64_t)RR, m - row0);
   const int64_t row_bytes = (int64_t)K_pad * OB / 8;
-  expand_block<OB, RR>(rank + row0 * ld, ld, rows, n, K, K_pad, out + row0 * row_bytes, row_bytes,
-                   s_r);
+  expand_block<OB, RR, ABS>(rank + row0 * ld, ld, rows, n, K, K_pad, out + row0 * row_bytes,
+                            row_bytes, s_r);
 }
 
 // Batched: blocks of up to RR variables of one dataset (numbered dataset by dataset, prefix
@@ -682,6 +684,9 @@ struct ContractArgs {
   const int32_t* bids;     // datasets of this launch, in unit order
   int nb;
   const int64_t* unit_prefix;  // [nb + 1]
+  // Magnitude contraction (single matrix): the accumulator is |A_u| . |A_v| and the epilogue
+  // stores only n_3 = |A_u| . |A_v| - n_0 + T_u + T_v.
+  int absmode;
 };
 
 // The problem a unit belongs to (the whole launch, or one dataset of a batch).
@@ -694,6 +699,7 @@ struct Prob {
   ktau_out out;
   const int32_t* s_obs;
   uint32_t* exceed;
+  int absmode;
 };
 
 struct Unit {
@@ -726,6 +732,7 @@ __device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t)
     p.out = a.out;
     p.s_obs = a.s_obs;
     p.exceed = a.exceed;
+    p.absmode = a.absmode;
   } else {
     const ktau_bds& D = a.bds[t.bd];
     p.row = p.col = side_of_bds(D);
@@ -739,6 +746,7 @@ __device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t)
     p.out.n3 = nullptr;
     p.s_obs = nullptr;
     p.exceed = nullptr;
+    p.absmode = 0;
   }
   return p;
 }
@@ -1346,6 +1354,34 @@ __device__ __forceinline__ void epi_chunk(const EpiCtx& E, const RowInfo* rc, co
         const int S = __float2int_rn(__uint_as_float(r[8 * h + jj]));
         if (((valid >> jj) & 1u) && abs(S) >= abs(so[jj])) atomicAdd(P.exceed + kk[jj], 1u);
       }
+    }
+    return;
+  }
+  if (P.absmode) {
+    // n_3 from the magnitude contraction: pairs tied in neither variable number
+    // |A_u| . |A_v| = n_0 - T_u - T_v + n_3 (Table 1), an exact integer below 2^24.
+    const long long Tv = vin ? P.col.T[v] : 0;
+#pragma unroll 1
+    for (int j = 0; j < rows_here; ++j) {
+      const RowInfo R = kSmemRows ? rs(j) : rr(j);  // whole warp (shuffle form)
+      const int64_t y = ub + j;
+      const long long Tu = P.row.T[y];
+      if (!vin) continue;
+      uint64_t k;
+      if (P.tri) {
+        if (v <= y) continue;
+        const uint64_t p = (uint64_t)(R.base + v);
+        if (p < P.p_begin || p >= P.p_end) continue;
+        k = p - P.p_begin;
+      } else {
+        k = (uint64_t)(R.base + v);
+      }
+      const long long n3 =
+          (long long)__float2int_rn(__uint_as_float(reg_at(r, j))) - n0 + Tu + Tv;
+      if (E.s64)
+        __stcs((long long*)P.out.n3 + k, n3);
+      else
+        __stcs((int*)P.out.n3 + k, (int)n3);
     }
     return;
   }
@@ -2148,6 +2184,36 @@ ktau_status launch_sign_expand(const ktau_ranked* R, cudaStream_t st) {
   return KTAU_OK;
 }
 
+// |A| operand (FP4, block-scaled pair kernel only) of a handle whose FP4 signs are built:
+// expansion of the magnitudes into R->sgn_abs and its tensor maps, once per handle.
+static ktau_status signgemm_prepare_abs(ktau_ranked* R, cudaStream_t st) {
+  if (R->abs_ready) return KTAU_OK;
+  if (R->obits != 4) return ktau_fail(KTAU_EINVAL, "the magnitude operand needs FP4 signs");
+  const int64_t n = R->n;
+  R->sgn_abs_bytes = (size_t)R->m * R->K_pad / 2;
+  if (ktau_dmalloc(&R->sgn_abs, R->sgn_abs_bytes) != KTAU_OK) {
+    R->sgn_abs = nullptr;
+    return KTAU_ENOMEM;
+  }
+  const size_t smem = expand_smem(n);
+  const int rows = ktau_expand_rows(n);
+  const unsigned eblocks = (unsigned)((R->m + rows - 1) / rows);
+  auto kern = rows == 8 ? sign_expand_kernel<4, 8, true>
+                        : (rows == 4 ? sign_expand_kernel<4, 4, true> : sign_expand_kernel<4, 2, true>);
+  KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    KTAU_TRACE("sign_expand_kernel", st);
+    kern<<<eblocks, kExpandThreads, smem, st>>>(R->rank, R->ld, (int)n, R->m, (int)R->K,
+                                                (int)R->K_pad, (uint8_t*)R->sgn_abs);
+  }
+  KTAU_CUDA(cudaGetLastError());
+  ktau_status s = make_tmap_raw(R->tmap_mx_abs, R->sgn_abs, R->K_pad / 2, R->m);
+  if (s == KTAU_OK) s = make_tmap_raw(R->tmap_mxb_abs, R->sgn_abs, R->K_pad / 2, R->m, false, MXB);
+  if (s != KTAU_OK) return s;
+  R->abs_ready = 1;
+  return KTAU_OK;
+}
+
 ktau_status ktau_signgemm_prepare(ktau_ranked* R, int obits, cudaStream_t st) {
   if (obits != 4 && obits != 8 && obits != 16)
     return ktau_fail(KTAU_EINVAL, "operand bits must be 4, 8 or 16");
@@ -2242,7 +2308,7 @@ ktau_status ktau_signgemm_ties(ktau_ranked* R, cudaStream_t ss) {
 // Contraction arguments of the triangle of one matrix over the pairs [p_begin, p_end).
 ContractArgs tri_args(const ktau_ranked* R, uint64_t p_begin, uint64_t p_end, const ktau_out& out) {
   const int64_t m = R->m;
-  ContractArgs a;
+  ContractArgs a{};
   a.row = a.col = side_of(R);
   a.n = R->n;
   // FP4 operands go through the block-scaled pair kernel: 256 packed elements per stage row
@@ -2277,6 +2343,26 @@ ktau_status ktau_signgemm_allpairs(ktau_ranked* R, uint64_t p_begin, uint64_t p_
   ktau_status s = ktau_signgemm_prepare(R, obits, st);
   if (s != KTAU_OK) return s;
   const int64_t m = R->m;
+  // Tie-heavy matrices (on average more than 4n tied sample pairs per variable, where the tie
+  // lists' per-pair work outgrows a contraction) and rows too long for the tie-list tile kernel:
+  // n_3 from a second contraction over the magnitudes |A| instead of the tie lists.
+  const bool heavy = (double)R->stats.T_sum > 4.0 * (double)R->n * (double)m;
+  if (out.n3 && (heavy || R->n > KTAU_SIGNGEMM_TIES_MAX_N) && obits == 4) {
+    ktau_out oc = out;
+    oc.n3 = nullptr;
+    const ContractArgs a = tri_args(R, p_begin, p_end, oc);
+    mark_before_contraction(st);
+    s = launch_contract2<1>(R, a, a.unit_hi - a.unit_lo, st);
+    if (s == KTAU_OK) s = signgemm_prepare_abs(R, st);
+    if (s != KTAU_OK) return s;
+    ktau_out on{nullptr, nullptr, nullptr, out.n3, out.count_bits, 0};
+    ContractArgs b = tri_args(R, p_begin, p_end, on);
+    b.absmode = 1;
+    return launch_contract2_map<1>(R->tmap_mxb_abs, R->tmap_mx_abs, b, b.unit_hi - b.unit_lo, st);
+  }
+  if (out.n3 && R->n > KTAU_SIGNGEMM_TIES_MAX_N)
+    return ktau_fail(KTAU_EINVAL, "n_3 of rows longer than %d samples needs FP4 operands",
+                     KTAU_SIGNGEMM_TIES_MAX_N);
   const ContractArgs a = tri_args(R, p_begin, p_end, out);
   const int64_t units = a.unit_hi - a.unit_lo;
   // The epilogue zero-fills n_3 over the range; the joint-ties kernels then add nonzero counts.
@@ -2299,7 +2385,7 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
   ktau_status s = ktau_signgemm_prepare(Q, obits, st);
   if (s == KTAU_OK) s = ktau_signgemm_prepare(D, obits, st);
   if (s != KTAU_OK) return s;
-  ContractArgs a;
+  ContractArgs a{};
   a.row = side_of(Q);
   a.col = side_of(D);
   a.n = Q->n;
@@ -2333,6 +2419,9 @@ ktau_status ktau_signgemm_rect(ktau_ranked* Q, ktau_ranked* D, const ktau_out& o
 
 void ktau_signgemm_release(ktau_ranked* R) {
   ktau_dfree(R->sgn, R->sgn_bytes);
+  ktau_dfree(R->sgn_abs, R->sgn_abs_bytes);
+  R->sgn_abs = nullptr;
+  R->abs_ready = 0;
   ktau_dfree(R->tie_off, ((size_t)R->m + 1) * sizeof(int64_t));
   ktau_dfree(R->tie_pairs, R->tie_bytes);
   ktau_dfree(R->bkt_off, ((size_t)R->K + 1) * sizeof(int32_t));
@@ -2401,7 +2490,7 @@ ktau_status ktau_signgemm_batch(const ktau_sg_group& g, cudaStream_t st) {
         g.ds, g.bids, g.nb, g.row_prefix, g.rows, g.T, g.tie_off, g.tie_cap, g.tie_pairs);
   }
   KTAU_CUDA(cudaGetLastError());
-  ContractArgs a;
+  ContractArgs a{};
   memset(&a, 0, sizeof(a));
   a.bds = g.ds;
   a.bids = g.bids;

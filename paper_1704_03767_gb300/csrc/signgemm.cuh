@@ -3,17 +3,22 @@
 // Algorithm 1 sums sign(u_a - u_b) * sign(v_a - v_b) over all sample pairs a < b, which is
 // n_c - n_d. Writing A_u[k] = sign(r_u[a_k] - r_u[b_k]) for the k-th sample pair, the numerator of
 // every pair of variables is one dot product: S(u, v) = A_u . A_v, i.e. S = A A^T over the upper
-// triangle. The {-1, 0, +1} entries are exact in FP8 (e4m3) and BF16, every product is exact, and
-// every partial sum is an integer of magnitude at most n_0 <= 2096128 < 2^24 (n <= 2048), which
-// an FP32 accumulator holds exactly; the tcgen05 FP8 path was measured to return these sums exactly
-// at |S| = n_0 for n up to 2048 on GB300 (tests/test_gpu_signgemm.py), so FP8 is the default and
-// BF16 (twice the bytes, half the rate) stays selectable. n_3 (joint ties) comes from the tie-pair
-// lists of the variables: n_3(u, v) = number of sample pairs tied in u that are also tied in v.
+// triangle. The {-1, 0, +1} entries are exact in FP4 (e2m1), FP8 (e4m3) and BF16, every product
+// is exact, and every partial sum is an integer of magnitude at most n_0 < 2^24 for n <= 5792,
+// which an FP32 accumulator holds exactly; the tcgen05 paths were measured to return these sums
+// exactly at |S| = n_0 (tests/test_gpu_signgemm.py). n_3 (joint ties) comes from the tie-pair
+// lists of the variables (n_3(u, v) = number of sample pairs tied in u that are also tied in v),
+// or, for tie-heavy matrices, from a second contraction of the magnitudes:
+// |A_u| . |A_v| = n_c + n_d = n_0 - T_u - T_v + n_3.
 #pragma once
 #include "ktau_impl.cuh"
 
-#define KTAU_SIGNGEMM_MAX_N 2048
-#define KTAU_SIGNGEMM_FP8_MAX_N 2048
+#define KTAU_SIGNGEMM_MAX_N 5792      // n_0 = n(n-1)/2 < 2^24: exact FP32 accumulation
+#define KTAU_SIGNGEMM_FP8_MAX_N 5792
+// Longest rows whose n_3 the tie-list tile kernel can count: it stages 33 columns' ranks
+// (n x 33 uint16) beside 8192 listed tied pairs in one CTA's shared memory. Longer rows take
+// n_3 from the magnitude contraction (FP4 operands, single matrix) or from the merge path.
+#define KTAU_SIGNGEMM_TIES_MAX_N 3000
 // Variables per CTA of the sign-expansion kernels (their shared memory grows with n).
 __host__ __device__ inline int ktau_expand_rows(int64_t n) {
   return n <= 512 ? 8 : (n <= 1024 ? 4 : 2);

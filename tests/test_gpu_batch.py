@@ -50,8 +50,8 @@ def _np(o):
 def test_small_batch_matches_oracle(ktau, mode, bits):
     mats = batched_uneven(count=24, m_range=(16, 150), n_range=(20, 300), seed0=100)
     mats[3][5] = 1.0  # a constant variable
-    if mode != "signgemm":  # the contraction path is limited to n <= 1024
-        mats.append(uniform_ties(40, 2100, tie_frac=0.1, seed=5))  # long vectors: merge path
+    if mode != "signgemm":  # the batched contraction counts n_3 for n <= 3000 only
+        mats.append(uniform_ties(40, 3100, tie_frac=0.1, seed=5))  # long vectors: merge path
     paths = None if mode == "auto" else [1 if mode == "merge" else 2] * len(mats)
     B, outs = _make(ktau, mats, 64, paths, {"operand_bits": bits} if bits else None)
     nm, ns = B.paths()

@@ -244,9 +244,16 @@ def test_beyond_limits_rejected(ktau):
     X = torch.zeros((3, 1), dtype=torch.float32, device="cuda")  # n < 2
     with pytest.raises(ktau.KtauError):
         ktau.ktau_rank_prepare(X)
-    Xd = torch.from_numpy(uniform_ties(10, 3000, seed=34)).cuda()
+    Xd = torch.from_numpy(uniform_ties(10, 5793, seed=34)).cuda()
     R = ktau.ktau_rank_prepare(Xd)
     out = torch.empty(45, dtype=torch.int32, device="cuda")
-    with pytest.raises(ktau.KtauError):  # sign contraction: n <= 2048
+    with pytest.raises(ktau.KtauError):  # sign contraction: n <= 5792 (n_0 < 2^24)
         ktau.ktau_allpairs(R, 0, 45, None, None, out, None, 32, {"path": 2})
+    R.free()
+    Xd = torch.from_numpy(uniform_ties(10, 3001, seed=35)).cuda()
+    R = ktau.ktau_rank_prepare(Xd)
+    n3 = torch.empty(45, dtype=torch.int32, device="cuda")
+    with pytest.raises(ktau.KtauError) as ei:  # n_3 beyond 3000 samples: FP4 operands only
+        ktau.ktau_allpairs(R, 0, 45, None, None, out, n3, 32, {"path": 2, "operand_bits": 8})
+    assert ei.value.status == 1
     R.free()

@@ -68,12 +68,12 @@ def test_pvalues_and_errors(ktau):
     # (exceed + 1) / (B + 1): the IEEE FP64 quotient, computed by the library
     assert np.array_equal(res["pvalue"].cpu().numpy(), (ref + 1) / 10.0)
     res["ranked"].free()
-    Xl = torch.from_numpy(uniform_ties(10, 2100, seed=25)).cuda()
+    Xl = torch.from_numpy(uniform_ties(10, 5793, seed=25)).cuda()  # beyond the contraction
     R = ktau.ktau_rank_prepare(Xl)
     S = torch.zeros(45, dtype=torch.int32, device="cuda")
     exc = torch.zeros(45, dtype=torch.uint32, device="cuda")
     with pytest.raises(ktau.KtauError):
-        ktau.ktau_permutation_exceed(R, torch.from_numpy(permutations(2, 2100)).cuda(), S, exc)
+        ktau.ktau_permutation_exceed(R, torch.from_numpy(permutations(2, 5793)).cuda(), S, exc)
     with pytest.raises(ValueError):
         ktau.ktau_permutation_exceed(R, torch.zeros((2, 5), dtype=torch.int32, device="cuda"),
                                      S, exc)

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from gpu_helpers import assert_tau32, assert_tau64, oracle_full, oracle_sampled
-from synthetic import gene_expression, uniform_ties
+from synthetic import gene_expression, heavy_ties_ordinal, uniform_ties
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,8 @@ def test_ragged(ktau, n, bits):
 
 
 @pytest.mark.parametrize("n,bits", [(128, 8), (256, 8), (512, 8), (1024, 8), (2048, 8),
-                                    (256, 16), (128, 4), (300, 4), (1024, 4), (2048, 4)])
+                                    (2900, 8), (256, 16), (128, 4), (300, 4), (1024, 4),
+                                    (2048, 4), (4096, 4), (5792, 4)])
 def test_extreme_counts(ktau, n, bits):
     """Exactness of the tensor-core sums: |S| = n_0 (identical and reversed rows, the largest
     partial sums), and strongly correlated rows, whose partial sums grow large while each MMA adds
@@ -147,3 +148,18 @@ def test_joint_ties_bucket_and_tile_forms(ktau, dups):
     got = _run(ktau, X, 64, p_begin=lo, p_end=hi)
     assert np.array_equal(got["n3"].astype(np.int64), ref["n3"][lo:hi])
     assert np.array_equal(got["S"].astype(np.int64), ref["S"][lo:hi])
+
+
+@pytest.mark.parametrize("n,m", [(300, 60), (3000, 24), (5792, 8)])
+def test_heavy_ties_magnitude_contraction(ktau, n, m):
+    """Tie-heavy long profiles (64 values per variable, about n^2/128 tied sample pairs each) on
+    the default path: S from the sign contraction, n_3 from the contraction of the magnitudes
+    (|A_u| . |A_v| = n_0 - T_u - T_v + n_3), checked against the oracle element by element."""
+    X = heavy_ties_ordinal(m=m, n=n, levels=64, seed=n)
+    X[1] = X[0]
+    X[2] = 63 - X[0]
+    got = _run(ktau, X, 64, options=None)
+    _check(got, oracle_full(X))
+    R = ktau.ktau_rank_prepare(torch.from_numpy(X).cuda())
+    assert ktau.ktau_allpairs_path(R) == 2  # the contraction is the default for these rows
+    R.free()

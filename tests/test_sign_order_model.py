@@ -1,6 +1,6 @@
 """Host-side model of the sign operands' layout and arithmetic (no GPU): the circulant order of the
 sample pairs lists every unordered pair once (Algorithm 1's sum is order-free), the packed 16-bit
-compares give gt / ge for every rank difference below 2048 without borrowing across lanes, and the
+compares give gt / ge for every rank difference below 5792 without borrowing across lanes, and the
 sign-filling byte permute followed by two logic ops yields the FP8 / FP4 / BF16 codes of +1, -1
 and 0. The GPU parity tests check the kernels themselves against the oracle."""
 import itertools
@@ -30,8 +30,9 @@ def test_circulant_order_is_a_bijection_onto_pairs():
 
 
 def test_packed_compares_have_no_cross_lane_borrow():
-    # every (a, b) pair of 16-bit lanes with values below 2048, both lanes at once
-    vals = np.arange(0, 2048, 7, dtype=np.int64)
+    # (a, b) pairs of 16-bit lanes with values below 5792 (the longest contraction rows), both
+    # lanes at once, the largest differences included
+    vals = np.unique(np.concatenate([np.arange(0, 5792, 13), [1, 5790, 5791]])).astype(np.int64)
     a_lo, b_lo = np.meshgrid(vals, vals[::-1], indexing="ij")
     a_hi, b_hi = b_lo[::-1], a_lo
     A = (a_hi << 16) | a_lo
