@@ -370,6 +370,22 @@ def bench_merge(ktau, clocks_mhz: float | None) -> dict:
                      "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
                                   "unit": "G merge-steps/s vs int32 lane-ops/s", "frac": ach / peak,
                                   "steps_per_pair": steps}}
+        if bits == 64:
+            # the same outputs on the library's default path (for these rows: the sign
+            # contraction, n_3 from the contraction of the magnitudes)
+            path = ktau.ktau_allpairs_path(R)
+            ktau.ktau_allpairs(R, 0, P, t64, t32, S, n3, bits, None)  # builds the operands
+            torch.cuda.synchronize()
+            ktau.ktau_trace_collect()
+            ktau.ktau_trace_enable(True)
+            ktau.ktau_allpairs(R, 0, P, t64, t32, S, n3, bits, None)
+            torch.cuda.synchronize()
+            ktau.ktau_trace_enable(False)
+            dms = sum(t for _, t in ktau.ktau_trace_collect())
+            ktau.ktau_device_status()
+            out[name]["default_path"] = {"path": {1: "merge", 2: "signgemm"}.get(path, path),
+                                         "kernel_ms": dms, "ns_per_pair": dms * 1e6 / P,
+                                         "pairs_per_s": P / (dms / 1e3)}
         R.free()
         del Xd, S, n3, t64, t32
         torch.cuda.empty_cache()

@@ -9,7 +9,8 @@ per sample count n and tie density, the fastest exact path and merge-path mappin
 
 Candidates per (n, tie density): the merge path with one warp per pair (tile side 32 or 8) and
 with one CTA per pair (n > 256), the bit-parallel dominance count (n <= 256), and the sign
-contraction (n <= 2048) with block-scaled FP4 operands (the default) or FP8 operands. Times come
+contraction (n <= 2048 measured; it applies up to n = 5792) with block-scaled FP4 operands (the
+default) or FP8 operands. Times come
 from the library's own kernel trace (CUDA events around each launch), best of a few repetitions,
 operands and masks already built (the first call builds them).
 """
@@ -128,7 +129,7 @@ def choose(table, n: int, tie_frac: float = 0.05) -> dict:
     cand = [e for e in ents if e["tie_frac"] == ties[0]]
     e = min(cand, key=lambda e: abs(np.log(e["n"]) - np.log(n)))
     opts = dict(e["options"])
-    if opts.get("path") == kb.KTAU_PATH_SIGNGEMM and n > 2048:
+    if opts.get("path") == kb.KTAU_PATH_SIGNGEMM and n > 5792:
         opts = {"path": kb.KTAU_PATH_MERGE, "mapping": 2}
     return opts
 
@@ -154,7 +155,7 @@ def choose_batch(table, n: int, tie_frac: float = 0.05) -> dict:
             key=lambda e: abs(np.log(e["n"]) - np.log(n)))
     times = {k: v for k, v in e["ns_per_pair"].items() if k in _BATCHABLE and v is not None}
     best = min(times, key=times.get)
-    if best == "signgemm" and n <= 2048:
+    if best == "signgemm" and n <= 3000:  # the batched contraction's n_3 takes n <= 3000
         return {"path": kb.KTAU_PATH_SIGNGEMM, "mapping": 0}
     if best == "signgemm":
         best = "merge_cta_q4"
