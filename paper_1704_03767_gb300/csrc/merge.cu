@@ -341,19 +341,26 @@ __device__ __forceinline__ void count_pair(const RT* perm_u, const RT* srank_u, 
   team_sync<TEAM>();
 }
 
+// Stages rows [first_row, first_row + rows) of a rank array in shared memory with asynchronous
+// 16-byte copies (cp.async, L2 only: every row is read once per tile); rows past m are not
+// copied (no pair reads them). ld is a multiple of 16 ranks, so every row starts on 32 bytes.
+// The caller waits with cp_async_wait_all() and a CTA barrier.
 template <typename RT>
 __device__ __forceinline__ void copy_rows(RT* dst, const RT* src, int64_t first_row, int rows,
                                           int64_t m, int64_t ld) {
-  // rows x ld ranks, ld a multiple of 16 (rows of 32 or 64 bytes): 16-byte vector copies.
   const int vec_per_row = (int)(ld * (int64_t)sizeof(RT) / 16);
-  const int total = rows * vec_per_row;
+  const int valid = (int)max((int64_t)0, min((int64_t)rows, m - first_row));
+  const int total = valid * vec_per_row;
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
     const int r = i / vec_per_row, c = i % vec_per_row;
-    const int64_t g = first_row + r;
-    uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-    if (g < m) v = reinterpret_cast<const uint4*>(src + g * ld)[c];
-    reinterpret_cast<uint4*>(dst + (int64_t)r * ld)[c] = v;
+    const void* g = reinterpret_cast<const uint4*>(src + (first_row + r) * ld) + c;
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(
+        reinterpret_cast<uint4*>(dst + (int64_t)r * ld) + c);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
   }
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
 // GBUF: the team buffers are in global scratch (long rows); otherwise they are carved from
@@ -404,6 +411,7 @@ __global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
       copy_rows<RT>(s_perm, g_perm, y0, tq, a.m, ld);
       copy_rows<RT>(s_srank, g_srank, y0, tq, a.m, ld);
       copy_rows<RT>(s_rank, g_rank, x0, tq, a.mc, ld);
+      cp_async_wait_all();
       __syncthreads();
     }
     for (int e = team; e < tq * tq; e += nteams) {
