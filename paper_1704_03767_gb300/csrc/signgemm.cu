@@ -37,6 +37,9 @@ constexpr int BM = 128;            // output columns of a unit (TMEM lanes, MMA 
 constexpr int BN = 256;            // output rows of a unit, at most (TMEM columns, MMA N)
 constexpr int BKB = 128;           // bytes of K per stage row (one 128B swizzle atom row)
 constexpr int STAGES = 4;
+// Rectangular kernel with at most 128 output rows per unit (one 128-row box of the row operand):
+// 32 KB stages, so six fit where four 48 KB ones do (more operand bytes in flight).
+constexpr int STAGES_MAX = 6;
 constexpr int A_BYTES = BM * BKB;  // 16 KB
 constexpr int B_BYTES = BN * BKB;  // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -1535,17 +1538,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   RowInfo* rinfo_all = (RowInfo*)(smem + (size_t)STAGES * STAGE_BYTES);
   uint64_t* bars =
       (uint64_t*)((unsigned char*)rinfo_all + (size_t)EPI_WARPS * RI_ROWS * sizeof(RowInfo));
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]; then the TMEM base slot
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
+  // bars: full[STAGES_MAX], empty[STAGES_MAX], tfull[2], tempty[2]; then the TMEM base slot
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES_MAX + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar0 = smem_u32(bars);
   auto FULL = [&](int s) { return bar0 + 8u * s; };
-  auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES + s); };
-  auto TFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + s); };
-  auto TEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 + s); };
+  auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES_MAX + s); };
+  auto TFULL = [&](int s) { return bar0 + 8u * (2 * STAGES_MAX + s); };
+  auto TEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES_MAX + 2 + s); };
+  // ring of the stage area: 4 stages of 48 KB, or 6 of 32 KB when units have <= 128 rows
+  const bool narrow = a.bnr <= BM;
+  const int nst = narrow ? STAGES_MAX : STAGES;
+  const size_t sstride = narrow ? (size_t)(A_BYTES + BM * BKB) : (size_t)STAGE_BYTES;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(FULL(s), 1);
       mbar_init(EMPTY(s), 1);
     }
@@ -1583,7 +1590,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             ok = false;
             break;
           }
-          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * sstride);
           const uint32_t sb = sa + A_BYTES;
           // one or two 128-row boxes of rows; FP4 boxes count their packed bytes (half the
           // shared-memory footprint)
@@ -1593,7 +1600,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_load_2d(sa, &tmA, kx, t.ta, FULL(stage), pol);
           tma_load_2d(sb, &tmB, kx, t.tb, FULL(stage), pol);
           if (a.bnr > BM) tma_load_2d(sb + BM * BKB, &tmB, kx, t.tb + BM, FULL(stage), pol);
-          if (++stage == STAGES) {
+          if (++stage == nst) {
             stage = 0;
             phase ^= 1u;
           }
@@ -1623,14 +1630,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(stage_base + (size_t)stage * STAGE_BYTES);
+          const uint32_t sa = smem_u32(stage_base + (size_t)stage * sstride);
           const uint32_t sb = sa + A_BYTES;
 #pragma unroll
           for (int k = 0; k < BKB / 32; ++k)
             umma<ESIZE>(d_tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
                         (kb > 0 || k > 0) ? 1u : 0u);
           umma_commit(EMPTY(stage));  // frees the stage once these MMAs have read it
-          if (++stage == STAGES) {
+          if (++stage == nst) {
             stage = 0;
             phase ^= 1u;
           }
