@@ -702,7 +702,6 @@ struct Prob {
   ktau_out out;
   const int32_t* s_obs;
   uint32_t* exceed;
-  int absmode;
 };
 
 struct Unit {
@@ -735,7 +734,6 @@ __device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t)
     p.out = a.out;
     p.s_obs = a.s_obs;
     p.exceed = a.exceed;
-    p.absmode = a.absmode;
   } else {
     const ktau_bds& D = a.bds[t.bd];
     p.row = p.col = side_of_bds(D);
@@ -749,7 +747,6 @@ __device__ __forceinline__ Prob problem_of(const ContractArgs& a, const Unit& t)
     p.out.n3 = nullptr;
     p.s_obs = nullptr;
     p.exceed = nullptr;
-    p.absmode = 0;
   }
   return p;
 }
@@ -1320,7 +1317,7 @@ __device__ __forceinline__ EpiCtx epi_ctx(const ContractArgs& a, const Unit& t, 
 
 // Outputs of one 32-row chunk (rows ub .. ub + 31, register j = row ub + j) of one epilogue
 // warp's 32 columns, from the integer counts r.
-template <bool kSmemRows>
+template <bool kSmemRows, bool ABS = false>
 __device__ __forceinline__ void epi_chunk(const EpiCtx& E, const RowInfo* rc, const RowInfo& mine,
                                           int64_t ub, const uint32_t (&r)[32]) {
   const Prob& P = E.P;
@@ -1360,7 +1357,7 @@ __device__ __forceinline__ void epi_chunk(const EpiCtx& E, const RowInfo* rc, co
     }
     return;
   }
-  if (P.absmode) {
+  if (ABS) {
     // n_3 from the magnitude contraction: pairs tied in neither variable number
     // |A_u| . |A_v| = n_0 - T_u - T_v + n_3 (Table 1), an exact integer below 2^24.
     const long long Tv = vin ? P.col.T[v] : 0;
@@ -1488,7 +1485,7 @@ __device__ __forceinline__ void release_acc(uint32_t tempty_bar, bool remote, in
 
 // kSlot (with !kSmemRows): ri is this warp's 32-entry slot; each chunk's row data go there
 // (one entry per lane) and are read back by broadcast.
-template <bool kSmemRows, bool kSlot = false, int EW = EPI_WARPS>
+template <bool kSmemRows, bool kSlot = false, int EW = EPI_WARPS, bool ABS = false>
 __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit& t, RowInfo* ri,
                                               uint32_t tmem_base, uint32_t tfull_bar,
                                               uint32_t tfull_phase, int acc, int warp, int lane,
@@ -1518,10 +1515,10 @@ __device__ __forceinline__ bool epilogue_unit(const ContractArgs& a, const Unit&
     if (kSlot) {
       ri[lane] = mine;
       __syncwarp();
-      epi_chunk<true>(E, ri, mine, ub, r);
+      epi_chunk<true, ABS>(E, ri, mine, ub, r);
       __syncwarp();  // the slot is rewritten for the next chunk
     } else {
-      epi_chunk<kSmemRows>(E, ri + 32 * (c - half_sel * nhalf), mine, ub, r);
+      epi_chunk<kSmemRows, ABS>(E, ri + 32 * (c - half_sel * nhalf), mine, ub, r);
     }
   }
   if (kSmemRows) __syncwarp();  // ri is rewritten for the next unit
@@ -1693,7 +1690,9 @@ __device__ __forceinline__ bool pair_live(const ContractArgs& a, int64_t s2) {
 // row, every scale factor 1.0, i.e. every byte of TMEM columns kSfCol.. is 0x7F = 2^0), MMA
 // N = MXT rows: 240 x 240 super-tiles, the row operand loaded as 120 rows per CTA (tmRow's boxes
 // are 120 rows high).
-template <int ESIZE, bool MX>
+// ABS: the magnitude contraction's epilogue (n_3 only); a separate instantiation, so that the
+// sign contraction's epilogue is compiled as if the mode did not exist.
+template <int ESIZE, bool MX, bool ABS = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1)
     contract2_kernel(const __grid_constant__ CUtensorMap tmRow,
                      const __grid_constant__ CUtensorMap tmCol, const ContractArgs a) {
@@ -1860,7 +1859,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1)
       if (!pair_live(a, s2)) continue;
       const Unit t = unit_of(a, 2 * s2 + rank);
       const bool ok =
-          MX ? epilogue_unit<false, true, PAIR_EW>(a, t, rslots + 32 * (warp - 2), tmem_base,
+          MX ? epilogue_unit<false, true, PAIR_EW, ABS>(a, t, rslots + 32 * (warp - 2), tmem_base,
                                                    TFULL(acc), acc_phase, acc, warp, lane,
                                                    cluster_addr(TEMPTY(acc), 0), true)
              : epilogue_unit<false, false, PAIR_EW>(a, t, nullptr, tmem_base, TFULL(acc),
@@ -2013,11 +2012,12 @@ template <int ESIZE>
 ktau_status launch_contract2_map(const void* tmap_row, const void* tmap_col,
                                  const ContractArgs& args, int64_t units, cudaStream_t st) {
   const bool mx = ESIZE == 1 && args.afmt == kMxFmt;
-  auto kern = mx ? contract2_kernel<1, true> : contract2_kernel<ESIZE, false>;
+  auto kern = mx ? (args.absmode ? contract2_kernel<1, true, true> : contract2_kernel<1, true>)
+                 : contract2_kernel<ESIZE, false>;
   const size_t smem = mx ? SMEM2_MX_BYTES : SMEM2_BYTES;
   KTAU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  static int max_clusters_by[2][64] = {{0}};
-  int* const max_clusters = max_clusters_by[mx ? 1 : 0];
+  static int max_clusters_by[3][64] = {{0}};
+  int* const max_clusters = max_clusters_by[mx ? (args.absmode ? 2 : 1) : 0];
   int dev = 0;
   KTAU_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return ktau_fail(KTAU_EINVAL, "device index out of range");
