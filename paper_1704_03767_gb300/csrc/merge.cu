@@ -365,9 +365,12 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // GBUF: the team buffers are in global scratch (long rows); otherwise they are carved from
 // shared memory, a pointer the compiler can see is shared (shared-memory loads and stores).
-// RT: rank type (uint16_t, or uint32_t for rows longer than 65535 samples).
+// RT: rank type (uint16_t, or uint32_t for rows longer than 65535 samples). The CTA-per-pair
+// form with 16 keys per lane is held to 64 registers, four CTAs per SM (a few spilled registers;
+// 2048 x 4096 heavy ties: 105 -> 100 ns per pair against three CTAs at 79 registers).
 template <int TEAM, int ITEMS, bool GBUF, typename RT>
-__global__ void __launch_bounds__(256) merge_pairs_kernel(const MergeArgs a) {
+__global__ void __launch_bounds__(256, (TEAM == 256 && ITEMS == 16 && !GBUF) ? 4 : 1)
+    merge_pairs_kernel(const MergeArgs a) {
   using K = KeyOf<RT>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long red[8];
