@@ -365,11 +365,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // GBUF: the team buffers are in global scratch (long rows); otherwise they are carved from
 // shared memory, a pointer the compiler can see is shared (shared-memory loads and stores).
-// RT: rank type (uint16_t, or uint32_t for rows longer than 65535 samples). The CTA-per-pair
-// form with 16 keys per lane is held to 64 registers, four CTAs per SM (a few spilled registers;
-// 2048 x 4096 heavy ties: 105 -> 100 ns per pair against three CTAs at 79 registers).
+// RT: rank type (uint16_t, or uint32_t for rows longer than 65535 samples). Registers are held
+// to what a higher CTA count per SM needs where that measured faster: the CTA-per-pair form with
+// 16 keys per lane at four CTAs (64 registers, a few spilled; 2048 x 4096 heavy ties: 105 -> 100
+// ns per pair), warp-per-pair forms with up to 7 keys per lane at five CTAs (48 registers;
+// 16384 x 128: 2.26 -> 1.76 ns per pair). With 8 keys per lane five CTAs spill and were slower at
+// n = 900.
 template <int TEAM, int ITEMS, bool GBUF, typename RT>
-__global__ void __launch_bounds__(256, (TEAM == 256 && ITEMS == 16 && !GBUF) ? 4 : 1)
+__global__ void __launch_bounds__(
+    256, (TEAM == 256 && ITEMS == 16 && !GBUF) ? 4 : ((TEAM == 32 && ITEMS <= 7) ? 5 : 1))
     merge_pairs_kernel(const MergeArgs a) {
   using K = KeyOf<RT>;
   extern __shared__ __align__(16) unsigned char smem[];
