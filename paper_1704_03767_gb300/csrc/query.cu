@@ -104,29 +104,39 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a,
   auto row_of = [&](int i) -> int64_t {
     return LIST ? (int64_t)in[q * N + i0 + i] : i0 + i;
   };
-  // Keys once (the radix passes read them from shared memory).
-  for (int i = tid; i < cnt; i += blockDim.x) {
-    const int64_t j = row_of(i);
-    skey[i] = topk_key(a, load_S(a, q, j), a.n0 - a.Tdb[j], qnan);
-  }
+  __shared__ unsigned long long s_or;
   if (tid == 0) {
     s_prefix = 0ull;
     s_remaining = kk;
     s_cnt = 0;
     s_eqcnt = 0;
+    s_or = 0ull;
   }
   __syncthreads();
+  // Keys once (the radix passes read them from shared memory), and the OR of all of them: the
+  // digits above its highest set bit are 0 in every key, so the passes start below them.
+  unsigned long long any = 0ull;
+  for (int i = tid; i < cnt; i += blockDim.x) {
+    const int64_t j = row_of(i);
+    const unsigned long long key = topk_key(a, load_S(a, q, j), a.n0 - a.Tdb[j], qnan);
+    skey[i] = key;
+    any |= key;
+  }
+  for (int d = 16; d > 0; d >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, d);
+  if (lane == 0 && any) atomicOr(&s_or, any);
+  __syncthreads();
+  const int top_pass = s_or ? (63 - __clzll((long long)s_or)) / 8 : 0;
   // Radix select of the kk-th largest key, most significant digit first.
-  for (int pass = 7; pass >= 0; --pass) {
+  for (int pass = top_pass; pass >= 0; --pass) {
     for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     const unsigned long long prefix = s_prefix;
     const unsigned long long hmask = pass == 7 ? 0ull : (~0ull << (8 * (pass + 1)));
-    if (pass == 7) {
+    if (pass == top_pass) {
       // The top digit is shared by most keys: lanes with the same digit add once.
       for (int base = 0; base < cnt; base += blockDim.x) {
         const int i = base + tid;
-        const unsigned bin = i < cnt ? (unsigned)(skey[i] >> 56) : 256u + lane;
+        const unsigned bin = i < cnt ? (unsigned)((skey[i] >> (8 * pass)) & 255u) : 256u + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, bin);
         if (i < cnt && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
       }
