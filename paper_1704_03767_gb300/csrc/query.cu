@@ -183,7 +183,11 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a,
   // Items with key > t are all selected; items with key == t: the lowest rows when keys are
   // exact (items are in increasing row order), otherwise all of them go through the exact
   // comparator.
-  int eq_before = 0;
+  // An exact-key candidate pass writes its selection in item order straight from this scan (the
+  // selected items before item i: the greater keys before it, plus its rank among equal keys,
+  // up to need_eq), without collecting and sorting.
+  const bool direct = !FINAL && a.injective;
+  int eq_before = 0, gt_before = 0;
   for (int base = 0; base < cnt; base += blockDim.x) {
     const int i = base + tid;
     long long S = 0, Dv = 0;
@@ -199,22 +203,29 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a,
       S = load_S(a, q, j);
       Dv = a.n0 - a.Tdb[j];
     }
-    if (gt) {
+    if (gt && !direct) {
       const int pos = atomicAdd(&s_cnt, 1);
       sel[pos] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
     }
-    // ordered rank among equal keys (block-wide exclusive scan in item order)
-    int incl = eqf ? 1 : 0;
+    // ordered ranks among equal keys (low 16 bits) and among greater keys (high 16 bits):
+    // block-wide exclusive scan in item order
+    const int own = (eqf ? 1 : 0) + (gt ? 1 << 16 : 0);
+    int incl = own;
     for (int d = 1; d < 32; d <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, d);
       if (lane >= d) incl += v;
     }
     if (lane == 31) s_wsum[warp] = incl;
     __syncthreads();
-    int before = eq_before;
+    int before = 0;
     for (int w = 0; w < warp; ++w) before += s_wsum[w];
-    const int rank_eq = before + incl - (eqf ? 1 : 0);
-    if (eqf) {
+    const int excl = before + incl - own;
+    const int rank_eq = eq_before + (excl & 0xffff);
+    if (direct) {
+      if (gt || (eqf && rank_eq < need_eq))
+        out[q * nout + (int64_t)blockIdx.y * a.k + gt_before + (excl >> 16) + min(rank_eq, need_eq)] =
+            (int32_t)j;
+    } else if (eqf) {
       if (a.injective) {
         if (rank_eq < need_eq) sel[kk - need_eq + rank_eq] = Cand{(int)S, qnan ? 0 : (int)Dv, (int)j};
       } else if (rank_eq < TK_EQCAP) {
@@ -223,9 +234,11 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(const TopkArgs a,
     }
     int tot = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wsum[w];
-    eq_before += tot;
+    eq_before += tot & 0xffff;
+    gt_before += tot >> 16;
     __syncthreads();
   }
+  if (direct) return;
   if (!a.injective) {
     // exact order of the boundary group, keep the first need_eq
     const int g = min(eq_before, TK_EQCAP);
