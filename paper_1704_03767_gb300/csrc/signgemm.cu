@@ -214,8 +214,14 @@ __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, 
 
   constexpr int UB = OB;  // bytes of eight elements
   const int units = K_pad >> 3;
-  const float inv_n = 1.0f / (float)n;
-  for (int q = threadIdx.x; q < units; q += blockDim.x) {
+  // (d, i0) = (k0 / n, k0 % n) of this thread's first position, then advanced by the loop's
+  // stride of 8 * blockDim positions with one conditional wrap (no division per iteration).
+  const int kstep = 8 * (int)blockDim.x;
+  const int dstep = kstep / n, istep = kstep - dstep * n;
+  int dq = (8 * (int)threadIdx.x) / n;
+  int iq = 8 * (int)threadIdx.x - dq * n;
+  for (int q = threadIdx.x; q < units;
+       q += blockDim.x, dq += dstep, iq += istep, dq += iq >= n ? 1 : 0, iq -= iq >= n ? n : 0) {
     const int k0 = q << 3;
     uint8_t* dst = out + (int64_t)q * UB;
     if (k0 >= K) {  // padding
@@ -254,15 +260,7 @@ __device__ __forceinline__ void expand_block(const uint16_t* __restrict__ rank, 
       }
       continue;
     }
-    int d = (int)((float)k0 * inv_n);  // k0 / n, possibly one off
-    int i0 = k0 - d * n;
-    if (i0 < 0) {
-      --d;
-      i0 += n;
-    } else if (i0 >= n) {
-      ++d;
-      i0 -= n;
-    }
+    const int d = dq, i0 = iq;  // k0 = d * n + i0
     int s = i0 + d + 1;  // partner run r[s ..], reduced mod n
     if (s >= n) s -= n;
     const int c = n - i0;  // elements 0 .. c-1 take offset d + 1, the rest d + 2 (one sample on)
