@@ -2,9 +2,10 @@
 co-expression search, Sec. 1 of the paper).
 
 The database is ranked once and its tensor-core operands are built once; they stay on the GPU.
-Clients submit batches of query profiles (b x n) at any time. A dispatcher admits pending
-batches in arrival order whenever a stream slot is free and the batch's device memory fits the
-budget still unreserved; each slot is a thread with its own CUDA stream that runs
+Clients submit batches of query profiles (b x n) at any time. One worker thread per stream slot
+takes pending batches in arrival order whenever a slot is free and the batch's device memory fits
+the budget still unreserved (the worker that wakes first admits the head of the queue and runs
+it on the slot's own CUDA stream):
 
     host->device copy of the profiles, ktau_rank_prepare_async, ktau_query (exact tau-b against every
     database row + exact top-k by |tau|), device->host copy of the top-k
@@ -91,7 +92,7 @@ class QueryServer:
         self.k = min(k, self.m_db)
         self.options = options
         self.keep_tau = keep_tau
-        if self.n <= 1024:
+        if kb.ktau_allpairs_path(self.db) == kb.KTAU_PATH_SIGNGEMM:
             kb.ktau_prepare_signs(self.db)  # resident tensor-core operands of the database
         torch.cuda.synchronize(self.dev)
         del dbt
@@ -116,13 +117,10 @@ class QueryServer:
                 "tk_h": torch.empty((max_batch, self.k), dtype=torch.float64).pin_memory()})
         self.cv = threading.Condition()
         self.pending = collections.deque()
-        self.slot_q = [collections.deque() for _ in range(slots)]
         self.running = True
         self.next_id = 0
         self.timeline = []  # (rid, slot, admitted, finished)
-        self.threads = [threading.Thread(target=self._dispatch, daemon=True)]
-        self.threads += [threading.Thread(target=self._slot, args=(i,), daemon=True)
-                         for i in range(slots)]
+        self.threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(slots)]
         for t in self.threads:
             t.start()
 
@@ -161,64 +159,66 @@ class QueryServer:
             self.cv.notify_all()
             return True
 
-    def _dispatch(self):
-        while True:
-            with self.cv:
-                while self.running and not self.pending:
-                    self.cv.wait()
-                if not self.running and not self.pending:
-                    return
-                # The head request, plus the consecutive ones behind it that fit in one launch.
-                group = [self.pending[0]]
-                rows = group[0].queries.shape[0]
-                if self.merge and rows <= self.max_batch:
-                    for r in list(self.pending)[1:]:
-                        b = r.queries.shape[0]
-                        if rows + b > self.max_batch:
-                            break
-                        group.append(r)
-                        rows += b
-                need = self.footprint(rows)
-                if need > self.admission.budget and len(group) > 1:
-                    group, rows = group[:1], group[0].queries.shape[0]
-                    need = self.footprint(rows)
-                try:
-                    slot = self.admission.try_admit(need)
-                except ValueError as e:
-                    r = self.pending.popleft()
-                    r.error = str(e)
-                    r.finished = time.perf_counter()
-                    r.done.set()
-                    continue
-                if slot is None:
-                    self.cv.wait()
-                    continue
-                now = time.perf_counter()
-                for r in group:
-                    self.pending.popleft()
-                    r.slot, r.admitted = slot, now
-                group[0].reserved = need
-                self.slot_q[slot].append(group)
-                self.cv.notify_all()
+    def _take(self):
+        """Under the lock: the next group to run and its slot, or None to wait. The head of the
+        queue, plus the consecutive requests behind it that fit in one launch; admitted when a
+        slot is free and its memory fits (no overtaking)."""
+        group = [self.pending[0]]
+        rows = group[0].queries.shape[0]
+        if self.merge and rows <= self.max_batch:
+            for r in list(self.pending)[1:]:
+                b = r.queries.shape[0]
+                if rows + b > self.max_batch:
+                    break
+                group.append(r)
+                rows += b
+        need = self.footprint(rows)
+        if need > self.admission.budget and len(group) > 1:
+            group, rows = group[:1], group[0].queries.shape[0]
+            need = self.footprint(rows)
+        try:
+            slot = self.admission.try_admit(need)
+        except ValueError as e:  # larger than the whole budget: rejected
+            r = self.pending.popleft()
+            r.error = str(e)
+            r.finished = time.perf_counter()
+            r.done.set()
+            return "rejected"
+        if slot is None:
+            return None
+        now = time.perf_counter()
+        for r in group:
+            self.pending.popleft()
+            r.slot, r.admitted = slot, now
+        group[0].reserved = need
+        return group, slot
 
-    def _slot(self, i: int):
+    def _worker(self):
         torch.cuda.set_device(self.dev)
-        st = self.streams[i]
         while True:
             with self.cv:
-                while self.running and not self.slot_q[i]:
-                    self.cv.wait()
-                if not self.slot_q[i]:
-                    return
-                group = self.slot_q[i].popleft()
+                while True:
+                    if not self.pending:
+                        if not self.running:
+                            return
+                        self.cv.wait()
+                        continue
+                    got = self._take()
+                    if got == "rejected":
+                        continue
+                    if got is None:
+                        self.cv.wait()  # a slot or memory frees up when a batch finishes
+                        continue
+                    group, slot = got
+                    break
             try:
-                self._run(group, st, i)
+                self._run(group, self.streams[slot], slot)
             except Exception as e:  # reported on the requests; the server keeps running
                 for r in group:
                     r.error = repr(e)
             now = time.perf_counter()
             with self.cv:
-                self.admission.release(i, group[0].reserved)
+                self.admission.release(slot, group[0].reserved)
                 for r in group:
                     r.finished = now
                     self.timeline.append((r.rid, r.slot, r.admitted, r.finished))
