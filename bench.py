@@ -694,7 +694,7 @@ def run_ours(args):
                 "hbm_view": {"algorithmic_bytes": alg_bytes,
                              "achieved_gbs": alg_bytes / (kern_avg_ms / 1e3) / 1e9, "peak_gbs": hbm,
                              "frac": alg_bytes / (kern_avg_ms / 1e3) / 1e9 / hbm},
-                "kernel": "contract2_kernel<1, MX> (2-CTA tcgen05 kind::mxf4 pair)",
+                "kernel": "contract2_kernel<1, MX, 0> (2-CTA tcgen05 kind::mxf4 pair)",
                 "kernel_ms": kern_avg_ms}
 
     # tau-a (Sec. 2, no tie correction) on the same workload: the whole step without n_3.
