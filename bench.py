@@ -90,6 +90,11 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout: float):
+        t0 = time.monotonic()
+        while self.proc is not None and not self.lines and time.monotonic() - t0 < timeout:
+            time.sleep(0.01)
+
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -117,6 +122,75 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read in-process through NVML (libnvidia-ml, public C API)
+    every `period` seconds while the timed region runs: the region lasts milliseconds, shorter
+    than the interval at which nvidia-smi prints, so this gives the samples under load."""
+
+    # nvmlClocksEventReasons bits (nvml.h)
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, dev, period: float = 0.002):
+        import ctypes
+
+        self.period = period
+        self.sm, self.reasons, self.smax = [], set(), None
+        self.stop_evt = threading.Event()
+        self.t = None
+        self.lib = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            import torch
+
+            props = torch.cuda.get_device_properties(dev)
+            bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0),
+                                          getattr(props, "pci_bus_id", 0),
+                                          getattr(props, "pci_device_id", 0))
+            h, count = ctypes.c_void_p(), ctypes.c_uint()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+                # one visible GPU: NVML's index 0 is that GPU
+                if lib.nvmlDeviceGetCount_v2(ctypes.byref(count)) != 0 or count.value != 1 or \
+                        lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                    return
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                self.smax = float(mx.value)
+            self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.h, self.lib, self.ct = h, lib, ctypes
+        except (OSError, AttributeError, RuntimeError):
+            self.lib = None
+
+    def _run(self):
+        ct, lib, h = self.ct, self.lib, self.h
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_evt.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ct.byref(mhz)) == 0:
+                self.sm.append(float(mhz.value))
+            if self.reason_fn(h, ct.byref(rs)) == 0:
+                for bit, name in self.BITS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            self.stop_evt.wait(self.period)
+
+    def start(self):
+        if self.lib is not None:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+
+    def stop(self) -> dict | None:
+        if self.t is None:
+            return None
+        self.stop_evt.set()
+        self.t.join(timeout=2)
+        return {"sm_mhz": statistics.median(self.sm) if self.sm else None,
+                "sm_max_mhz": self.smax, "reasons": sorted(self.reasons),
+                "samples": len(self.sm)}
 
 
 def _traffic(kernel: str):
@@ -605,10 +679,13 @@ def run_ours(args):
     ktau.ktau_device_status(stream)
 
     sampler = ClockSampler(local)
+    nvml = NvmlSampler(dev)
+    sampler.start()
+    sampler.wait_first(5.0)  # nvidia-smi is printing before the timed region starts
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    nvml.start()
     total_ms = 0.0
     ktau.ktau_trace_collect()
     # CUDA events on the launching stream around the dominant kernel only: every traced launch
@@ -626,7 +703,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
         R.free()
+    nv = nvml.stop()
     clocks = sampler.stop()
+    if nv is not None and nv["samples"]:
+        # In-process samples inside the timed region; nvidia-smi's around it (reasons merged).
+        clocks = {"sm_mhz": nv["sm_mhz"], "sm_max_mhz": nv["sm_max_mhz"] or clocks["sm_max_mhz"],
+                  "reasons": sorted(set(nv["reasons"]) | set(clocks["reasons"])),
+                  "samples": nv["samples"], "source": "NVML every 2 ms inside the timed region",
+                  "nvidia_smi": clocks}
     ktau.ktau_trace_enable(False)
     dom = [ms for name, ms in ktau.ktau_trace_collect() if name == dominant]
     ktau.ktau_device_status(stream)
