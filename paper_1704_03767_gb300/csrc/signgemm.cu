@@ -98,8 +98,8 @@ __device__ unsigned int g_sg_error;  // set when a bounded wait gives up
 // as eight copies of the ranks repeated past n, copy c holding r[(x + c) mod n] at x, so a run that
 // starts anywhere is one aligned 16-byte load from copy (start mod 8). A thread takes eight
 // positions at a time for every variable of the CTA: b - a for the two runs in packed 16-bit lanes
-// gives the signs of eight pairs in eight adds (ranks are below 2048: bit 15 of each lane of
-// b - a + 0x7fff is b > a, of b - a + 0x8000 is b >= a), which are then packed into the operand
+// gives the signs of eight pairs in eight adds (ranks are below 2^15, so no lane borrows: bit 15
+// of each lane of b - a + 0x7fff is b > a, of b - a + 0x8000 is b >= a), then packed into the operand
 // encoding: FP8 e4m3 (+1 = 0x38, -1 = 0xB8), BF16 (0x3F80 / 0xBF80) or FP4 e2m1 (+1 = 0x2,
 // -1 = 0xA, element b of the eight in the high nibble of byte b, element 4 + b in the low nibble).
 // Positions K <= k < K_pad are zero.
@@ -2079,7 +2079,7 @@ int ktau_sign_obits(int64_t n, const ktau_options* opt) {
   if (opt && (opt->operand_bits == 4 || opt->operand_bits == 8 || opt->operand_bits == 16))
     return opt->operand_bits;
   // FP4: half the operand bytes of FP8, and the pair contraction reads them with the
-  // block-scaled FP4 MMA (measured on GB300 at 16384 x 128: 0.72 ms against 0.79 ms with FP8).
+  // block-scaled FP4 MMA (measured on GB300 at 16384 x 128: 0.69 ms against 0.79 ms with FP8).
   return n <= KTAU_SIGNGEMM_FP8_MAX_N ? KTAU_SIGNGEMM_DEFAULT_BITS : 16;
 }
 
