@@ -627,23 +627,29 @@ struct RowsReg {
 
 // Interior 32 x 32 block of the epilogue (all pairs valid, 32-bit counts, FP32 tau only): row j
 // of the block is register j; lane = column, so each store is contiguous across the warp. Rows
-// whose FP32 rounding is undecided by the float-float test are flagged in `slow`.
-template <bool WS, bool WN, int NR, class Rows>
+// whose FP32 rounding is undecided by the float-float test are flagged in `slow`. The rows go in
+// nh <= 2 passes of 16 through one loop body (the second pass selects registers 16..31), so the
+// hot code is one 16-row body per output set; TA (tau-a) is a template choice for the same
+// reason.
+template <bool WS, bool WN, bool TA, class Rows>
 __device__ __forceinline__ void epi_rows32(const uint32_t (&sv)[32], const Rows& rows,
                                            float2 c_rff, float* o32, int* oS, int* oN,
-                                           uint32_t& slow, float n0f) {
+                                           uint32_t& slow, float n0f, int nh) {
+#pragma unroll 1
+  for (int h = 0; h < nh; ++h) {
 #pragma unroll
-  for (int j = 0; j < NR; ++j) {
-    const RowInfo R = rows(j);
-    const float sh = __uint_as_float(sv[j]);  // the exact integer sum
-    float tv;
-    if (n0f != 0.f)  // tau-a: S / n_0, one IEEE division of exact FP32 integers (n_0 < 2^24)
-      tv = __fdiv_rn(sh, n0f);
-    else if (!tau32_fast_small(sh, R.rhi, R.rlo, c_rff, tv))
-      slow |= 1u << j;
-    __stcs(o32 + R.base, tv);
-    if (WS) __stcs(oS + R.base, __float2int_rn(sh));
-    if (WN) __stcs(oN + R.base, 0);
+    for (int j = 0; j < 16; ++j) {
+      const RowInfo R = rows(16 * h + j);
+      const float sh = __uint_as_float(h ? sv[16 + j] : sv[j]);  // the exact integer sum
+      float tv;
+      if (TA)  // tau-a: S / n_0, one IEEE division of exact FP32 integers (n_0 < 2^24)
+        tv = __fdiv_rn(sh, n0f);
+      else if (!tau32_fast_small(sh, R.rhi, R.rlo, c_rff, tv))
+        slow |= 1u << (16 * h + j);
+      __stcs(o32 + R.base, tv);
+      if (WS) __stcs(oS + R.base, __float2int_rn(sh));
+      if (WN) __stcs(oN + R.base, 0);
+    }
   }
 }
 
@@ -1397,28 +1403,29 @@ __device__ __forceinline__ void epi_chunk(const EpiCtx& E, const RowInfo* rc, co
     int* const oN = E.n3z ? (int*)E.n3z + (v - (int64_t)P.p_begin) : nullptr;
     uint32_t slow = 0;  // rows whose FP32 rounding the float-float test could not decide
     const float n0f = P.out.stat ? (float)n0 : 0.f;
-#define KTAU_EPI_ROWS_N(ROWS, NR)                                           \
-  if (oS && oN)                                                             \
-    epi_rows32<true, true, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);     \
-  else if (oS)                                                              \
-    epi_rows32<true, false, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);    \
-  else if (oN)                                                              \
-    epi_rows32<false, true, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);    \
-  else                                                                      \
-    epi_rows32<false, false, NR>(r, ROWS, c_rff, o32, oS, oN, slow, n0f);
+#define KTAU_EPI_ROWS_T(ROWS, TA)                                                \
+  if (oS && oN)                                                                  \
+    epi_rows32<true, true, TA>(r, ROWS, c_rff, o32, oS, oN, slow, n0f, nh);      \
+  else if (oS)                                                                   \
+    epi_rows32<true, false, TA>(r, ROWS, c_rff, o32, oS, oN, slow, n0f, nh);     \
+  else if (oN)                                                                   \
+    epi_rows32<false, true, TA>(r, ROWS, c_rff, o32, oS, oN, slow, n0f, nh);     \
+  else                                                                           \
+    epi_rows32<false, false, TA>(r, ROWS, c_rff, o32, oS, oN, slow, n0f, nh);
 #define KTAU_EPI_ROWS(ROWS)        \
-  if (rows_here == 32) {           \
-    KTAU_EPI_ROWS_N(ROWS, 32)      \
+  if (n0f != 0.f) {                \
+    KTAU_EPI_ROWS_T(ROWS, true)    \
   } else {                         \
-    KTAU_EPI_ROWS_N(ROWS, 16)      \
+    KTAU_EPI_ROWS_T(ROWS, false)   \
   }
+    const int nh = rows_here / 16;
     if (kSmemRows) {
       KTAU_EPI_ROWS(rs)
     } else {
       KTAU_EPI_ROWS(rr)
     }
 #undef KTAU_EPI_ROWS
-#undef KTAU_EPI_ROWS_N
+#undef KTAU_EPI_ROWS_T
     while (slow) {  // rare: the FP64 formula decides (same thread, stored after the fast value)
       const int j = __ffs(slow) - 1;
       slow &= slow - 1;
