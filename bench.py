@@ -537,6 +537,13 @@ def bench_query(ktau, batches_per_load: int) -> dict:
     srv = QueryServer(D, k=100, slots=4)
     for q in batches[:8]:  # warm-up
         srv.submit(q).done.wait()
+    # Like a latency-bound service after start-up: the objects made so far (this process has
+    # built the other measurements' inputs) move to the collector's permanent generation, so that
+    # no full collection pass over them stalls the server threads in the middle of a measurement.
+    import gc
+
+    gc.collect()
+    gc.freeze()
     t0 = time.perf_counter()
     reqs = [srv.submit(q) for q in batches]
     for r in reqs:
@@ -584,6 +591,7 @@ def bench_query(ktau, batches_per_load: int) -> dict:
                                  "queries_per_s": sum(r.queries.shape[0] for r in rs) / wall,
                                  "errors": sum(r.error is not None for r in rs)})
     srv.stop()
+    gc.unfreeze()
     return out
 
 

@@ -373,7 +373,8 @@ ktau_status ktau_workspace_size(const ktau_batch_desc* descs, int32_t count,
  *             tensor-core path is chosen, is built on first use and kept in the handle; with an
  *             n3 output the contraction is used for n <= 3000 only (longer rows: merge path).
  * The top-k is selected in passes over 4096-row chunks (their candidate lists in scratch from
- * the stream-ordered allocator, released on `stream`). n <= KTAU_NARROW_MAX_N (the exact
+ * a stream-ordered memory pool the library owns per device, which keeps its memory once
+ * reserved; released on `stream`). n <= KTAU_NARROW_MAX_N (the exact
  * comparison of S^2 / D_v uses 64- and 128-bit integers), else ETOOLARGE.
  * Asynchronous on `stream`. Errors: EINVAL, ETOOLARGE, ENOMEM, ECUDA.
  */

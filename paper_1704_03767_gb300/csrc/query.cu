@@ -366,18 +366,33 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
   a.status = st_ptr;
   // Passes of chunks of TK_CHUNK items, one CTA per (query, chunk), each keeping its chunk's
   // top-k, until one chunk per query holds every candidate; then the final pass. Candidate lists
-  // live in stream-ordered allocations (no synchronisation, safe across streams).
+  // live in stream-ordered allocations (no synchronisation, safe across streams) from a pool of
+  // the library's own that keeps its memory once reserved: with the default pool's release
+  // threshold of zero, every stream synchronisation would hand the memory back to the system and
+  // the next call would map it again.
   const size_t dyn = (size_t)TK_CHUNK * sizeof(unsigned long long);
   const int64_t b = queries->m;
   if (b > 0x7fffffffLL) return ktau_fail(KTAU_ETOOLARGE, "too many queries in one call");
+  cudaMemPool_t pool = nullptr;
   {
-    // the kernels' shared-memory limit, once per device
+    // the kernels' shared-memory limit and the scratch pool, once per device
     static std::mutex mu;
     static bool done[64] = {};
+    static cudaMemPool_t pools[64] = {};
     int dev = 0;
     KTAU_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return ktau_fail(KTAU_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      KTAU_CUDA(cudaMemPoolCreate(&pools[dev], &props));
+      uint64_t keep = ~0ull;
+      KTAU_CUDA(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    pool = pools[dev];
     if (!done[dev]) {
       KTAU_CUDA(cudaFuncSetAttribute(topk_kernel<false, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
@@ -403,10 +418,11 @@ ktau_status ktau_query_run(const ktau_ranked* db, const ktau_ranked* queries, co
       break;
     }
     if (!buf[w]) {
-      const cudaError_t e = cudaMallocAsync((void**)&buf[w], (size_t)b * nout * sizeof(int32_t), st);
+      const cudaError_t e = cudaMallocFromPoolAsync((void**)&buf[w],
+                                                    (size_t)b * nout * sizeof(int32_t), pool, st);
       if (e != cudaSuccess) {
         buf[w] = nullptr;
-        ts = ktau_cuda_fail(e, "cudaMallocAsync(top-k candidates)");
+        ts = ktau_cuda_fail(e, "cudaMallocFromPoolAsync(top-k candidates)");
         break;
       }
     }
