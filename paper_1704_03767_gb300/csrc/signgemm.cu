@@ -637,6 +637,7 @@ __device__ __forceinline__ void epi_rows32(const uint32_t (&sv)[32], const Rows&
                                            uint32_t& slow, float n0f, int nh) {
 #pragma unroll 1
   for (int h = 0; h < nh; ++h) {
+    uint32_t s16 = 0;  // this pass's undecided rows (bit j: row 16 h + j)
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const RowInfo R = rows(16 * h + j);
@@ -645,11 +646,12 @@ __device__ __forceinline__ void epi_rows32(const uint32_t (&sv)[32], const Rows&
       if (TA)  // tau-a: S / n_0, one IEEE division of exact FP32 integers (n_0 < 2^24)
         tv = __fdiv_rn(sh, n0f);
       else if (!tau32_fast_small(sh, R.rhi, R.rlo, c_rff, tv))
-        slow |= 1u << (16 * h + j);
+        s16 |= 1u << j;
       __stcs(o32 + R.base, tv);
       if (WS) __stcs(oS + R.base, __float2int_rn(sh));
       if (WN) __stcs(oN + R.base, 0);
     }
+    slow |= s16 << (16 * h);
   }
 }
 
